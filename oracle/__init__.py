@@ -1,0 +1,141 @@
+"""CPU oracle for recursive bilinear fast matrix multiplication (arXiv 2312.12732).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package; the library's product
+path never does.  The arithmetic lives in ``fmm_oracle.c`` (plain C, binary64,
+no FMA contraction); this module only builds and loads it and marshals numpy
+arrays.
+
+Functions (each follows the passage cited in ``fmm_oracle.c``):
+
+* ``brent_mismatches(p, U, V, W)`` -- exact Brent-equation check, Section 2.
+* ``classic(A, B)`` -- textbook triple loop, ascending k (Section 2).
+* ``bilinear(A, B, p, U, V, W, depth)`` -- recursive evaluation of equation
+  `strassen`, level by level, with the peeling rule stated in the C source.
+* ``sample_dot2(A, B, rows, cols)`` -- compensated dot products (Ogita, Rump,
+  Oishi 2005) for sampled reference entries.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fmm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, OpenMP, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+               "-std=c11", _SRC, "-o", _LIB + ".tmp", "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i64, i32, dp = ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+        ip32 = ctypes.POINTER(ctypes.c_int32)
+        ip64 = ctypes.POINTER(ctypes.c_int64)
+        lib.fmm_oracle_brent_mismatches.restype = i64
+        lib.fmm_oracle_brent_mismatches.argtypes = [i32, i32, ip32, ip32, ip32]
+        lib.fmm_oracle_classic.restype = None
+        lib.fmm_oracle_classic.argtypes = [i64, i64, i64, dp, i64, dp, i64, dp, i64]
+        lib.fmm_oracle_bilinear.restype = ctypes.c_int
+        lib.fmm_oracle_bilinear.argtypes = [i64, dp, i64, dp, i64, dp, i64, i32, i32, ip32, ip32,
+                                            ip32, i32]
+        lib.fmm_oracle_dot2.restype = ctypes.c_double
+        lib.fmm_oracle_dot2.argtypes = [i64, dp, i64, dp, i64]
+        lib.fmm_oracle_sample_dot2.restype = None
+        lib.fmm_oracle_sample_dot2.argtypes = [i64, dp, i64, dp, i64, i64, ip64, ip64, dp]
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _alg(p, U, V, W):
+    U = np.ascontiguousarray(U, dtype=np.int32)
+    V = np.ascontiguousarray(V, dtype=np.int32)
+    W = np.ascontiguousarray(W, dtype=np.int32)
+    assert U.shape == V.shape == W.shape and U.shape[0] == p * p, "U, V, W must be p^2 x R"
+    return U, V, W, int(U.shape[1])
+
+
+def _ip32(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def brent_mismatches(p: int, U, V, W) -> int:
+    """Number of Brent equations (out of p^6) that fail; 0 means (U,V,W) multiplies exactly."""
+    U, V, W, R = _alg(p, U, V, W)
+    return int(_load().fmm_oracle_brent_mismatches(p, R, _ip32(U), _ip32(V), _ip32(W)))
+
+
+def _mat(A):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    assert A.ndim == 2
+    return A
+
+
+def classic(A, B) -> np.ndarray:
+    """C = A B by the ascending-k triple loop."""
+    A, B = _mat(A), _mat(B)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    C = np.empty((M, N), dtype=np.float64)
+    _load().fmm_oracle_classic(M, N, K, _dp(A), K, _dp(B), N, _dp(C), N)
+    return C
+
+
+def bilinear(A, B, p: int, U, V, W, depth: int) -> np.ndarray:
+    """C = A B (square) by `depth` recursive levels of the bilinear algorithm (U, V, W)."""
+    A, B = _mat(A), _mat(B)
+    n = A.shape[0]
+    assert A.shape == (n, n) and B.shape == (n, n)
+    U, V, W, R = _alg(p, U, V, W)
+    C = np.empty((n, n), dtype=np.float64)
+    rc = _load().fmm_oracle_bilinear(n, _dp(A), n, _dp(B), n, _dp(C), n, p, R, _ip32(U), _ip32(V),
+                                     _ip32(W), depth)
+    if rc != 0:
+        raise MemoryError("oracle: temporary allocation failed")
+    return C
+
+
+def dot2(x, y) -> float:
+    """Compensated dot product of two vectors (Dot2)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    assert x.shape == y.shape and x.ndim == 1
+    return float(_load().fmm_oracle_dot2(x.shape[0], _dp(x), 1, _dp(y), 1))
+
+
+def sample_dot2(A, B, rows, cols) -> np.ndarray:
+    """Reference entries (A B)[rows[t], cols[t]] by compensated dot products."""
+    A, B = _mat(A), _mat(B)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    assert rows.shape == cols.shape
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    assert rows.size == 0 or (rows.min() >= 0 and rows.max() < M and cols.min() >= 0 and cols.max() < N)
+    out = np.empty(rows.shape[0], dtype=np.float64)
+    ip64 = ctypes.POINTER(ctypes.c_int64)
+    _load().fmm_oracle_sample_dot2(K, _dp(A), K, _dp(B), N, rows.shape[0], rows.ctypes.data_as(ip64),
+                                   cols.ctypes.data_as(ip64), _dp(out))
+    return out

@@ -1,0 +1,243 @@
+/*
+ * fmm_oracle.c -- plain, slow CPU oracle for recursive bilinear fast matrix
+ * multiplication (D'Alberto, "Strassen's Matrix Multiplication Algorithm Is
+ * Still Faster", arXiv 2312.12732).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library's product path may load,
+ * link or call this file; only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark do.  It shares no code, header, table or helper with the
+ * CUDA library: the algorithm (U, V, W) and the matrices arrive as inputs.
+ *
+ * Conventions (Section 2 of the paper):
+ *   - an n x n matrix split by a factor p is the row-major list of its p*p
+ *     blocks A_0 .. A_{p*p-1}; block i covers rows (i / p) * m .. and columns
+ *     (i % p) * m .. with m = n / p;
+ *   - a bilinear algorithm <p,p,p;R> is three integer p^2 x R row-major
+ *     matrices U, V, W.  Product r is P_r = S_r * T_r with
+ *     S_r = sum_i U[i][r] A_i and T_r = sum_j V[j][r] B_j, and block l of C is
+ *     C_l = sum_r W[l][r] P_r (equation `strassen`).  W indexes the blocks of C
+ *     in row-major order; the paper's printed c^t lists them as C0, C2, C1, C3,
+ *     i.e. it indexes C transposed, and the tests relabel it before use.
+ *
+ * Precision: IEEE binary64 throughout.  The file is compiled with
+ * -ffp-contract=off so that a*b+c is never fused behind the reader's back; the
+ * only fused multiply-adds are the explicit fma() calls of TwoProduct.
+ *
+ * Parity status: every function below is pinned by CPU tests against
+ * closed forms, brute force or exact rational arithmetic (no function here is
+ * "parity unpinned").
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Brent equations (Section 2, equation `strassen` read entry-wise).          */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Counts the index tuples (i, j, j2, k, i2, k2), each in [0, p), for which
+ *     sum_r U[(i,j)][r] * V[(j2,k)][r] * W[(i2,k2)][r]
+ *         != delta(j, j2) * delta(i, i2) * delta(k, k2).
+ * The algorithm computes C = A B for every A, B exactly when the count is 0.
+ * Sums are taken in int64, so the check is exact for any coefficients that
+ * fit in int32 and any R below 2^31 / max|coefficient|^3.
+ */
+int64_t fmm_oracle_brent_mismatches(int p, int R, const int32_t *U, const int32_t *V,
+                                    const int32_t *W) {
+    int64_t bad = 0;
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j)
+            for (int j2 = 0; j2 < p; ++j2)
+                for (int k = 0; k < p; ++k)
+                    for (int i2 = 0; i2 < p; ++i2)
+                        for (int k2 = 0; k2 < p; ++k2) {
+                            const int32_t *u = U + (int64_t)(i * p + j) * R;
+                            const int32_t *v = V + (int64_t)(j2 * p + k) * R;
+                            const int32_t *w = W + (int64_t)(i2 * p + k2) * R;
+                            int64_t s = 0;
+                            for (int r = 0; r < R; ++r) s += (int64_t)u[r] * v[r] * w[r];
+                            int64_t want = (j == j2 && i == i2 && k == k2) ? 1 : 0;
+                            if (s != want) ++bad;
+                        }
+    return bad;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Classic product (Section 2, definition of matrix multiplication).          */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * C[0:M, 0:N] = A[0:M, 0:K] * B[0:K, 0:N]; all row-major with leading
+ * dimensions lda, ldb, ldc.  Every C[i][j] starts at 0.0 and accumulates
+ * A[i][k] * B[k][j] in ascending k (loop order i, k, j; each product rounded,
+ * then added).  Rows are independent, so the OpenMP split over i does not
+ * change any result.
+ */
+void fmm_oracle_classic(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                        const double *B, int64_t ldb, double *C, int64_t ldc) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < M; ++i) {
+        double *c = C + i * ldc;
+        for (int64_t j = 0; j < N; ++j) c[j] = 0.0;
+        for (int64_t k = 0; k < K; ++k) {
+            const double a = A[i * lda + k];
+            const double *b = B + k * ldb;
+            for (int64_t j = 0; j < N; ++j) c[j] += a * b[j];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Recursive bilinear evaluation (Section 2, equations `strassen` and         */
+/* `eq:recursion`; recursion and composition order in the paragraphs on       */
+/* split factors).                                                             */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int p, R;
+    const int32_t *U, *V, *W;
+} oracle_alg;
+
+/* dst[0:m,0:m] (ld m) = sum_i coef[i][r] * src block i, ascending i. */
+static void combine_blocks(int64_t m, int p, int R, const int32_t *coef, int r, const double *src,
+                           int64_t ld, double *dst) {
+    for (int64_t x = 0; x < m * m; ++x) dst[x] = 0.0;
+    for (int i = 0; i < p * p; ++i) {
+        const int32_t c = coef[(int64_t)i * R + r];
+        if (c == 0) continue;
+        const double *blk = src + (int64_t)(i / p) * m * ld + (int64_t)(i % p) * m;
+        const double cd = (double)c;
+        for (int64_t y = 0; y < m; ++y)
+            for (int64_t x = 0; x < m; ++x) {
+                const double a = blk[y * ld + x];
+                if (c == 1)
+                    dst[y * m + x] += a;
+                else if (c == -1)
+                    dst[y * m + x] -= a;
+                else
+                    dst[y * m + x] += cd * a;
+            }
+    }
+}
+
+static int bilinear_rec(int64_t n, const double *A, int64_t lda, const double *B, int64_t ldb,
+                        double *C, int64_t ldc, const oracle_alg *alg, int depth) {
+    const int p = alg->p, R = alg->R;
+    if (depth <= 0 || n < p) {
+        fmm_oracle_classic(n, n, n, A, lda, B, ldb, C, ldc);
+        return 0;
+    }
+    /* Peeling rule (the paper only uses sizes that factor exactly): with
+     * q = n mod p, the leading n' = n - q rows/columns go through the fast
+     * algorithm, and the trailing q rows/columns are fixed up classically:
+     *   C[:n',:n'] = fast(A[:n',:n'], B[:n',:n']) + A[:n',n':] B[n':,:n']
+     *   C[:n',n':] = A[:n',:] B[:,n':]
+     *   C[n':,:]   = A[n':,:] B                                           */
+    const int64_t q = n % p, nc = n - q, m = nc / p;
+    double *S = (double *)malloc(sizeof(double) * m * m);
+    double *T = (double *)malloc(sizeof(double) * m * m);
+    double *Pr = (double *)malloc(sizeof(double) * m * m);
+    if (!S || !T || !Pr) {
+        free(S); free(T); free(Pr);
+        return -1;
+    }
+    for (int64_t y = 0; y < nc; ++y)
+        for (int64_t x = 0; x < nc; ++x) C[y * ldc + x] = 0.0;
+    int rc = 0;
+    for (int r = 0; r < R && rc == 0; ++r) {
+        /* S_r = sum_i U[i][r] A_i,  T_r = sum_j V[j][r] B_j */
+        combine_blocks(m, p, R, alg->U, r, A, lda, S);
+        combine_blocks(m, p, R, alg->V, r, B, ldb, T);
+        /* P_r = S_r T_r, itself by the same algorithm one level down */
+        rc = bilinear_rec(m, S, m, T, m, Pr, m, alg, depth - 1);
+        /* C_l += W[l][r] P_r for every l (so each C_l sums in ascending r) */
+        for (int l = 0; l < p * p && rc == 0; ++l) {
+            const int32_t w = alg->W[(int64_t)l * R + r];
+            if (w == 0) continue;
+            double *cb = C + (int64_t)(l / p) * m * ldc + (int64_t)(l % p) * m;
+            const double wd = (double)w;
+            for (int64_t y = 0; y < m; ++y)
+                for (int64_t x = 0; x < m; ++x) {
+                    const double v = Pr[y * m + x];
+                    if (w == 1)
+                        cb[y * ldc + x] += v;
+                    else if (w == -1)
+                        cb[y * ldc + x] -= v;
+                    else
+                        cb[y * ldc + x] += wd * v;
+                }
+        }
+    }
+    free(S); free(T); free(Pr);
+    if (rc != 0 || q == 0) return rc;
+
+    double *tmp = (double *)malloc(sizeof(double) * nc * nc);
+    if (!tmp) return -1;
+    fmm_oracle_classic(nc, nc, q, A + nc, lda, B + nc * ldb, ldb, tmp, nc);
+    for (int64_t y = 0; y < nc; ++y)
+        for (int64_t x = 0; x < nc; ++x) C[y * ldc + x] += tmp[y * nc + x];
+    free(tmp);
+    fmm_oracle_classic(nc, q, n, A, lda, B + nc, ldb, C + nc, ldc);
+    fmm_oracle_classic(q, n, n, A + nc * lda, lda, B, ldb, C + nc * ldc, ldc);
+    return 0;
+}
+
+/*
+ * C = A * B (n x n, row-major, leading dimensions lda, ldb, ldc) by `depth`
+ * levels of the bilinear algorithm (p, R, U, V, W), recursing level by level
+ * (never flattened), with classic products at the leaves and for the peeled
+ * strips.  Returns 0, or -1 if a temporary could not be allocated.
+ */
+int fmm_oracle_bilinear(int64_t n, const double *A, int64_t lda, const double *B, int64_t ldb,
+                        double *C, int64_t ldc, int p, int R, const int32_t *U, const int32_t *V,
+                        const int32_t *W, int depth) {
+    oracle_alg alg = {p, R, U, V, W};
+    return bilinear_rec(n, A, lda, B, ldb, C, ldc, &alg, depth);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Compensated dot products for sampled reference entries.                    */
+/* Ogita, Rump, Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.    */
+/* 26(6), 2005: TwoSum (Knuth), TwoProduct via FMA, and Dot2 (their Alg. 5.3). */
+/* The result is as accurate as if computed in twice the working precision and */
+/* then rounded.                                                               */
+/* ------------------------------------------------------------------------- */
+
+static inline void two_sum(double a, double b, double *s, double *e) {
+    double x = a + b;
+    double z = x - a;
+    *s = x;
+    *e = (a - (x - z)) + (b - z);
+}
+
+static inline void two_product(double a, double b, double *p, double *e) {
+    double x = a * b;
+    *p = x;
+    *e = fma(a, b, -x);
+}
+
+double fmm_oracle_dot2(int64_t K, const double *x, int64_t incx, const double *y, int64_t incy) {
+    if (K <= 0) return 0.0;
+    double p, s;
+    two_product(x[0], y[0], &p, &s);
+    for (int64_t k = 1; k < K; ++k) {
+        double h, r, q;
+        two_product(x[k * incx], y[k * incy], &h, &r);
+        two_sum(p, h, &p, &q);
+        s = s + (q + r);
+    }
+    return p + s;
+}
+
+/*
+ * out[t] = Dot2(row rows[t] of A, column cols[t] of B) for t < count, where
+ * A is M x K (ld lda) and B is K x N (ld ldb).  Indices are not checked.
+ */
+void fmm_oracle_sample_dot2(int64_t K, const double *A, int64_t lda, const double *B, int64_t ldb,
+                            int64_t count, const int64_t *rows, const int64_t *cols, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < count; ++t)
+        out[t] = fmm_oracle_dot2(K, A + rows[t] * lda, 1, B + cols[t], ldb);
+}

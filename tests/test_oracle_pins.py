@@ -1,0 +1,260 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: the checks are the paper's printed
+tables and worked examples (Section 2), the classic product it prints as a graph
+(Section 3), closed forms (products of basis matrices), exact rational arithmetic,
+brute force against an independent library product on integer-valued inputs, and
+the paper's principle that integer computations come out exact (abstract).
+"""
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from golden import algos
+from paper_2312_12732_gb300 import inputs
+
+U_DBL = 2.0 ** -53
+
+
+def all_algos():
+    return {
+        "paper_strassen": algos.paper_strassen(),
+        "strassen1969": algos.strassen1969(),
+        "winograd": algos.winograd(),
+        "laderman": algos.laderman(),
+        "classic_graph": algos.classic_from_graph(),
+    }
+
+
+# ---------------------------------------------------------------- Brent checker
+
+
+def test_paper_table_as_printed_needs_row_relabel(oracle_mod):
+    a, b, ct, labels = algos.paper_strassen_as_printed()
+    assert labels == ["C0", "C2", "C1", "C3"]
+    # Rows taken in printed order as C0, C1, C2, C3: the equations fail.
+    assert oracle_mod.brent_mismatches(2, a, b, ct) == 8
+    # Rows placed by their printed labels: exact.
+    p, U, V, W = algos.paper_strassen()
+    assert oracle_mod.brent_mismatches(p, U, V, W) == 0
+
+
+@pytest.mark.parametrize("name", list(all_algos()))
+def test_brent_accepts_published_algorithms(oracle_mod, name):
+    p, U, V, W = all_algos()[name]
+    assert oracle_mod.brent_mismatches(p, U, V, W) == 0
+
+
+def test_product_counts_match_fixture():
+    counts = {2: 7, 3: 23}
+    for factor, comp, R in algos.product_counts():
+        assert int(np.prod(comp)) == factor
+        assert int(np.prod([counts[c] for c in comp])) == R
+
+
+@pytest.mark.parametrize("name", ["paper_strassen", "laderman"])
+def test_brent_rejects_every_single_entry_change(oracle_mod, name):
+    p, U, V, W = all_algos()[name]
+    rng = np.random.default_rng(5)
+    for X in (U, V, W):
+        for idx in itertools.product(range(X.shape[0]), range(X.shape[1])):
+            if name == "laderman" and rng.random() > 0.15:
+                continue  # subsample the 3 x 207 entries of Laderman
+            old = X[idx]
+            X[idx] = old + (1 if old <= 0 else -1)
+            assert oracle_mod.brent_mismatches(p, U, V, W) > 0, idx
+            X[idx] = old
+
+
+def test_kronecker_composition_needs_row_major_reindexing(oracle_mod):
+    s = algos.paper_strassen()
+    p, U, V, W = algos.kron_compose(s, s)
+    assert (p, U.shape[1]) == (4, 49)
+    assert oracle_mod.brent_mismatches(p, U, V, W) == 0
+    p, U, V, W = algos.kron_unpermuted(s, s)
+    assert oracle_mod.brent_mismatches(p, U, V, W) == 112
+
+
+@pytest.mark.parametrize("first,second", [("paper_strassen", "laderman"), ("laderman", "winograd"),
+                                          ("laderman", "laderman")])
+def test_kronecker_compositions_of_mixed_factors(oracle_mod, first, second):
+    table = all_algos()
+    p, U, V, W = algos.kron_compose(table[first], table[second])
+    assert U.shape[1] == table[first][1].shape[1] * table[second][1].shape[1]
+    assert oracle_mod.brent_mismatches(p, U, V, W) == 0
+
+
+def test_worked_examples_match_relabelled_table():
+    p, U, V, W = algos.paper_strassen()
+    ex = algos.worked_examples()
+    for blk, prods in ex.items():
+        assert sorted(np.nonzero(W[blk])[0].tolist()) == sorted(prods)
+        for r, (aterms, bterms) in prods.items():
+            ua = {int(t.lstrip("+-")[1:]): (-1 if t[0] == "-" else 1) for t in aterms}
+            vb = {int(t.lstrip("+-")[1:]): (-1 if t[0] == "-" else 1) for t in bterms}
+            assert {i: int(U[i, r]) for i in np.nonzero(U[:, r])[0]} == ua
+            assert {j: int(V[j, r]) for j in np.nonzero(V[:, r])[0]} == vb
+            assert W[blk, r] == 1
+
+
+# ---------------------------------------------------------------- classic product
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (7, 5, 3), (33, 17, 65), (64, 64, 64)])
+def test_classic_exact_on_integers_vs_numpy(oracle_mod, M, N, K):
+    rng = np.random.default_rng(M * 100 + N)
+    A = rng.integers(-16, 17, size=(M, K)).astype(np.float64)
+    B = rng.integers(-16, 17, size=(K, N)).astype(np.float64)
+    assert np.array_equal(oracle_mod.classic(A, B), A @ B)
+
+
+def test_classic_within_dot_product_bound_vs_dot2(oracle_mod):
+    n = 200
+    A, B = inputs.operands(n, "normal", seed=11)
+    C = oracle_mod.classic(A, B)
+    rows, cols = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    ref = oracle_mod.sample_dot2(A, B, rows.ravel(), cols.ravel()).reshape(n, n)
+    gamma = n * U_DBL / (1 - n * U_DBL)
+    bound = gamma * (np.abs(A) @ np.abs(B))
+    assert np.all(np.abs(C - ref) <= bound)
+    assert np.max(np.abs(C - ref)) > 0  # the two orders do differ on real data
+
+
+# ---------------------------------------------------------------- Dot2
+
+
+def test_dot2_exact_rational_random(oracle_mod):
+    rng = np.random.default_rng(3)
+    for K in (1, 2, 17, 500):
+        x = rng.standard_normal(K) * 10.0 ** rng.uniform(-5, 5, K)
+        y = rng.standard_normal(K)
+        exact = sum(Fraction(a) * Fraction(b) for a, b in zip(x.tolist(), y.tolist()))
+        got = Fraction(oracle_mod.dot2(x, y))
+        # Ogita-Rump-Oishi: |res - exact| <= u |exact| + gamma_{K}^2 sum|x y|
+        g = K * U_DBL / (1 - K * U_DBL)
+        bound = U_DBL * abs(exact) + Fraction(g * g) * sum(Fraction(abs(a * b)) for a, b in zip(x, y))
+        assert abs(got - exact) <= bound
+
+
+def test_dot2_recovers_cancelled_sum(oracle_mod):
+    x = np.array([1e16, 1.0, -1e16])
+    y = np.array([1.0, 1.0, 1.0])
+    assert oracle_mod.dot2(x, y) == 1.0
+    x = np.array([2.0 ** 60, 3.0, -(2.0 ** 60), 2.0 ** -40])
+    assert oracle_mod.dot2(x, np.ones(4)) == 3.0 + 2.0 ** -40
+
+
+# ---------------------------------------------------------------- bilinear evaluator
+
+
+def _basis(n, i, j):
+    E = np.zeros((n, n))
+    E[i, j] = 1.0
+    return E
+
+
+@pytest.mark.parametrize("name,depth", [("paper_strassen", 1), ("paper_strassen", 2), ("winograd", 2),
+                                        ("strassen1969", 1), ("laderman", 1), ("classic_graph", 2)])
+def test_bilinear_exhaustive_basis_pairs(oracle_mod, name, depth):
+    p, U, V, W = all_algos()[name]
+    n = p ** depth
+    for i, j, k, l in itertools.product(range(n), repeat=4):
+        C = oracle_mod.bilinear(_basis(n, i, j), _basis(n, k, l), p, U, V, W, depth)
+        want = _basis(n, i, l) if j == k else np.zeros((n, n))
+        assert np.array_equal(C, want), (i, j, k, l)
+
+
+def test_bilinear_exhaustive_basis_pairs_444(oracle_mod):
+    s = algos.paper_strassen()
+    p, U, V, W = algos.kron_compose(s, s)
+    for i, j, k, l in itertools.product(range(4), repeat=4):
+        C = oracle_mod.bilinear(_basis(4, i, j), _basis(4, k, l), p, U, V, W, 1)
+        want = _basis(4, i, l) if j == k else np.zeros((4, 4))
+        assert np.array_equal(C, want)
+
+
+@pytest.mark.parametrize("name", ["paper_strassen", "winograd", "laderman"])
+def test_bilinear_brute_force_small_integers(oracle_mod, name):
+    p, U, V, W = all_algos()[name]
+    rng = np.random.default_rng(1)
+    for n in (p, p * p):
+        for _ in range(20):
+            A = rng.integers(-9, 10, (n, n)).astype(np.float64)
+            B = rng.integers(-9, 10, (n, n)).astype(np.float64)
+            depth = 1 if n == p else 2
+            assert np.array_equal(oracle_mod.bilinear(A, B, p, U, V, W, depth), A @ B)
+
+
+@pytest.mark.parametrize("name,n,depth", [
+    ("paper_strassen", 64, 1), ("paper_strassen", 64, 3), ("paper_strassen", 96, 4),
+    ("winograd", 128, 3), ("strassen1969", 48, 2), ("laderman", 81, 2), ("laderman", 54, 1),
+    # sizes that need peeling at one or more levels
+    ("paper_strassen", 37, 1), ("paper_strassen", 101, 3), ("winograd", 77, 2), ("laderman", 50, 2),
+    ("paper_strassen", 3, 2), ("laderman", 2, 1), ("paper_strassen", 1, 3)])
+def test_bilinear_bit_exact_on_integer_inputs(oracle_mod, name, n, depth):
+    p, U, V, W = all_algos()[name]
+    A, B = inputs.operands(n, "integer", seed=n + depth)
+    assert np.array_equal(oracle_mod.bilinear(A, B, p, U, V, W, depth), A @ B)
+
+
+def test_composed_algorithm_equals_two_levels(oracle_mod):
+    s = algos.paper_strassen()
+    p4, U4, V4, W4 = algos.kron_compose(s, s)
+    A, B = inputs.operands(64, "integer", seed=9)
+    C1 = oracle_mod.bilinear(A, B, p4, U4, V4, W4, 1)
+    C2 = oracle_mod.bilinear(A, B, *s, 2)
+    assert np.array_equal(C1, C2) and np.array_equal(C1, A @ B)
+
+
+def test_planted_mistakes_are_detected(oracle_mod):
+    """A sign flip in U, a transposed W (c^t without relabelling), or a swapped V column
+    each makes the evaluator disagree with the classic product on integer inputs."""
+    p, U, V, W = algos.paper_strassen()
+    A, B = inputs.operands(16, "integer", seed=4)
+    ref = A @ B
+    U2 = U.copy(); U2[2, 0] = -U2[2, 0]
+    assert U[2, 0] != 0
+    assert not np.array_equal(oracle_mod.bilinear(A, B, p, U2, V, W, 1), ref)
+    a, b, ct, _ = algos.paper_strassen_as_printed()
+    assert not np.array_equal(oracle_mod.bilinear(A, B, p, a, b, ct, 1), ref)
+    V2 = V.copy(); V2[:, [1, 2]] = V2[:, [2, 1]]
+    assert not np.array_equal(oracle_mod.bilinear(A, B, p, U, V2, W, 1), ref)
+
+
+@pytest.mark.parametrize("name,depth,tol", [("paper_strassen", 1, 1e-13), ("paper_strassen", 2, 1e-13),
+                                            ("paper_strassen", 3, 1e-12), ("winograd", 3, 1e-12),
+                                            ("laderman", 2, 1e-13)])
+def test_bilinear_real_inputs_within_normalised_tolerance(oracle_mod, name, depth, tol):
+    p, U, V, W = all_algos()[name]
+    n = 216 if p == 3 else 256
+    A, B = inputs.operands(n, "uniform", seed=21)
+    C = oracle_mod.bilinear(A, B, p, U, V, W, depth)
+    rows, cols = inputs.sample_indices(n, 2048, seed=5)
+    ref = oracle_mod.sample_dot2(A, B, rows, cols)
+    err = np.max(np.abs(C[rows, cols] - ref)) / (n * np.abs(A).max() * np.abs(B).max())
+    assert err <= tol
+    assert err > 0  # fast algorithms do round differently from the exact product
+
+
+def test_integer_workloads_stay_below_2p53():
+    """Entries in [-16, 16]: every intermediate of depth d is bounded by
+    16 * 16 * n * (max column nnz of U)^d * (max column nnz of V)^d * (max row l1 of W)^d,
+    which stays below 2^53 for the integer workloads (n <= 10007, depth <= 3)."""
+    for name in ("paper_strassen", "winograd", "laderman"):
+        p, U, V, W = all_algos()[name]
+        gu = np.abs(U).sum(0).max()
+        gv = np.abs(V).sum(0).max()
+        gw = np.abs(W).sum(1).max()
+        for depth in (1, 2, 3):
+            bound = 256.0 * 10007 * float(gu * gv * gw) ** depth
+            assert bound < 2.0 ** 53, (name, depth, bound)
+
+
+def test_sample_dot2_matches_classic_indices(oracle_mod):
+    A = inputs.matrix(30, "integer", seed=1, m=20)
+    B = inputs.matrix(20, "integer", seed=2, m=25)
+    rows, cols = inputs.sample_indices(25, 100, seed=3)
+    rows = rows % 30
+    assert np.array_equal(oracle_mod.sample_dot2(A, B, rows, cols), (A @ B)[rows, cols])
