@@ -1,0 +1,191 @@
+/*
+ * fmm.h -- C ABI of a GB300 (sm_103a) library for recursive bilinear fast
+ * matrix multiplication in FP64, after D'Alberto, "Strassen's Matrix
+ * Multiplication Algorithm Is Still Faster" (arXiv 2312.12732).
+ *
+ * The operation is C = A * B for square n x n binary64 matrices (Section 2,
+ * definition of the matrix product; Section 3 states it as C = alpha A B, and
+ * this library fixes alpha = 1 and overwrites C).  A bilinear algorithm
+ * <p,p,p;R> is given by three integer p^2 x R matrices (U, V, W): with the
+ * operands split by the factor p into row-major blocks A_0 .. A_{p^2-1}
+ * (Section 2, the single-index partition), product r is
+ *     P_r = S_r * T_r,   S_r = sum_i U[i][r] A_i,   T_r = sum_j V[j][r] B_j,
+ * and block l of C is C_l = sum_r W[l][r] P_r (Section 2, equation
+ * `strassen`; the library names the left combination S and the right one T).
+ * W indexes the blocks of C in row-major order.  `depth` levels of recursion
+ * (Section 2, recursion with the same split factor) are flattened into the
+ * Kronecker power of (U, V, W) with blocks re-indexed row-major over the
+ * p^depth x p^depth grid (Section 2, the Kronecker-product composition).
+ *
+ * Conventions for every entry point:
+ *   - matrices are row-major and contiguous (leading dimension n);
+ *   - device pointers refer to memory of the current CUDA device; host
+ *     pointers are ordinary (pageable or pinned) host memory;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default);
+ *   - calls that launch GPU work are asynchronous on `stream` unless stated;
+ *   - the library never takes ownership of caller memory;
+ *   - every function returns an fmm_status_t; on error no GPU work was
+ *     enqueued unless the error is FMM_ERR_CUDA from a launch.
+ */
+#ifndef FMM_H_
+#define FMM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_INVALID = 1,     /* bad argument: NULL pointer, n < 1, p < 2, R < 1, leaf size < 1 */
+    FMM_ERR_BRENT = 2,       /* (U, V, W) fails the Brent equations in exact integer arithmetic */
+    FMM_ERR_UNSUPPORTED = 3, /* valid request this build does not implement (dtype, limits) */
+    FMM_ERR_OOM = 4,         /* a device or host allocation failed */
+    FMM_ERR_CUDA = 5,        /* a CUDA runtime call or kernel launch failed */
+    FMM_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up (reported by fmm_sync_status) */
+    FMM_ERR_NOT_FOUND = 7    /* unknown built-in algorithm name */
+} fmm_status_t;
+
+typedef enum {
+    FMM_F64 = 0,       /* binary64 operands, FP64 tensor-core (DMMA) leaf products */
+    FMM_F64_OZAKI = 1  /* binary64 operands; leaf products emulated from low-precision slices */
+} fmm_dtype_t;
+
+/* A bilinear algorithm <p,p,p;R>.  U, V, W are row-major p^2 x R int32
+ * arrays (entry [i][r] at index i*R + r).  The library copies them. */
+typedef struct {
+    int p;
+    int R;
+    const int32_t *U;
+    const int32_t *V;
+    const int32_t *W;
+} fmm_algo_t;
+
+typedef struct fmm_plan fmm_plan_t;
+
+/* How the pre-additions S_r / T_r of the recursion levels are formed.
+ *   FMM_SCHED_AUTO   -- the planner chooses (the default);
+ *   FMM_SCHED_FUSED  -- every level is combined on the fly while staging the
+ *                       leaf operands (no S_r / T_r in device memory);
+ *   FMM_SCHED_HYBRID -- the top `materialize_levels` levels are formed level
+ *                       by level in plan workspace by an elementwise pass,
+ *                       the remaining levels are fused into staging.
+ * The post-additions C_l = sum_r W[l][r] P_r are always fused into the
+ * leaf-product epilogue. */
+typedef enum { FMM_SCHED_AUTO = 0, FMM_SCHED_FUSED = 1, FMM_SCHED_HYBRID = 2 } fmm_schedule_t;
+
+/* Optional knobs for fmm_plan_create_ex.  Zero-initialise, then set fields;
+ * a zero field means "library default". */
+typedef struct {
+    fmm_schedule_t schedule;
+    int materialize_levels;  /* FMM_SCHED_HYBRID: 0 .. depth */
+    int ozaki_slices;        /* FMM_F64_OZAKI: slices per operand (default 8) */
+    double wait_timeout_s;   /* bound on every device-side wait (default 5 s) */
+    int debug_poison_chain;  /* testing only: 1 = after the per-call reset, set one
+                                post-addition ordering counter to a value no task
+                                writes, so that its waiters time out */
+} fmm_plan_options_t;
+
+/* Read-only description of a plan (all sizes in elements). */
+typedef struct {
+    int64_t n;              /* problem size */
+    int p, depth;           /* split factor, recursion depth */
+    int64_t P;              /* blocks per side after flattening = p^depth */
+    int64_t R_total;        /* leaf products = R^depth */
+    int64_t m;              /* leaf block size = floor(n / P) */
+    int64_t n_core;         /* P * m, the part that goes through the fast algorithm */
+    int64_t tasks;          /* GPU tile tasks per multiplication */
+    int materialized_levels;
+    double flops_leaf;      /* 2 * R_total * m^3 */
+    double flops_executed;  /* leaf + additions + peel fix-ups, as scheduled */
+    size_t workspace_bytes;
+} fmm_plan_info_t;
+
+/* Status code to a static, NUL-terminated English string (never NULL). */
+const char *fmm_status_string(fmm_status_t s);
+
+/* Built-in algorithms by name (static storage, valid for the process):
+ *   "classic2"      -- <2,2,2;8> classic block product (Section 3, the printed graph)
+ *   "strassen"      -- the Strassen tables printed in Section 2, with the rows of
+ *                      c^t placed by their printed labels C0, C2, C1, C3
+ *   "strassen1969"  -- Strassen's original 18-addition form
+ *   "winograd"      -- Strassen-Winograd, flat form of the 15-addition variant
+ *   "laderman"      -- Laderman's <3,3,3;23> (1976)
+ * Returns FMM_ERR_NOT_FOUND for any other name, FMM_ERR_INVALID for NULL. */
+fmm_status_t fmm_algo_builtin(const char *name, fmm_algo_t *out);
+
+/* Number of the p^6 Brent equations that (U, V, W) violates, computed exactly
+ * in int64 (Section 2, equation `strassen` read entry-wise); 0 means the
+ * algorithm multiplies exactly.  Host-only.  Returns -1 for invalid input. */
+int64_t fmm_algo_brent_mismatches(const fmm_algo_t *algo);
+
+/* Relabel an algorithm given in the paper's printed format, where the rows of
+ * c^t index the blocks of C transposed (Section 2: printed order C0, C2, C1,
+ * C3 for p = 2), into this library's row-major W.  `ct` and `W_out` are
+ * p^2 x R int32 row-major; W_out[(i*p + k)][r] = ct[(k*p + i)][r]. */
+fmm_status_t fmm_algo_from_transposed_c(int p, int R, const int32_t *ct, int32_t *W_out);
+
+/* Two-level composition (Section 2, Kronecker products of the factor
+ * matrices): first factor outermost.  Nested block ((i1,j1),(i2,j2)) becomes
+ * block (i1*p2 + i2)*(p1*p2) + (j1*p2 + j2); product (r1, r2) becomes
+ * r1*R2 + r2.  The caller provides U_out/V_out/W_out with (p1 p2)^2 * R1 R2
+ * int32 entries each; out->U/V/W are set to them. */
+fmm_status_t fmm_algo_compose(const fmm_algo_t *first, const fmm_algo_t *second, int32_t *U_out,
+                              int32_t *V_out, int32_t *W_out, fmm_algo_t *out);
+
+/* Create a plan for C = A * B with n x n operands, `depth` levels of `algo`.
+ * depth = 0 is the classic product.  Validates arguments (FMM_ERR_INVALID),
+ * the Brent equations (FMM_ERR_BRENT), the dtype (FMM_ERR_UNSUPPORTED),
+ * flattens the recursion, lays out the tile-task schedule, uploads the
+ * coefficient tables and allocates the device workspace (FMM_ERR_OOM) on the
+ * current device.  The plan owns that workspace.  Blocking (host + a
+ * synchronous upload).  Not thread-safe with respect to the same plan. */
+fmm_status_t fmm_plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
+                             fmm_dtype_t dtype);
+fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
+                                fmm_dtype_t dtype, const fmm_plan_options_t *opts);
+
+/* C = A * B on `stream`.  A, B, C: device pointers to n x n row-major
+ * binary64; C is overwritten; A and B are read only and must not overlap C.
+ * Asynchronous.  Two calls on the same plan must not overlap in time (they
+ * share the plan's workspace); issue them on one stream.  FMM_ERR_CUDA if a
+ * launch fails.  Device-side wait timeouts surface at fmm_sync_status. */
+fmm_status_t fmm_gemm(const fmm_plan_t *plan, const double *A, const double *B, double *C,
+                      void *stream);
+
+/* Same as fmm_gemm with HOST buffers: copies A and B to plan-owned device
+ * buffers (allocated on first use, freed by fmm_plan_destroy), multiplies,
+ * copies C back and synchronizes `stream` before returning.  Blocking. */
+fmm_status_t fmm_gemm_host(fmm_plan_t *plan, const double *A_host, const double *B_host,
+                           double *C_host, void *stream);
+
+/* Batched: count independent products C[i] = A[i] * B[i], each with its own
+ * plan (sizes and algorithms may differ), as one persistent grouped launch
+ * over the union of their tile tasks.  plans/A/B/C are HOST arrays of
+ * `count` entries; A[i], B[i], C[i] are device pointers.  All plans must be
+ * FMM_F64 and not in use by another call at the same time.  Asynchronous. */
+fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double *const *A,
+                              const double *const *B, double *const *C, int count, void *stream);
+
+/* Synchronize `stream`, then read and clear the plan's device error flag:
+ * FMM_OK, FMM_ERR_TIMEOUT (a bounded wait expired; C is unspecified) or
+ * FMM_ERR_CUDA. */
+fmm_status_t fmm_sync_status(const fmm_plan_t *plan, void *stream);
+
+/* Describe a plan.  Host-only. */
+fmm_status_t fmm_plan_get_info(const fmm_plan_t *plan, fmm_plan_info_t *info);
+
+/* Device workspace owned by the plan, in bytes (0 for NULL). */
+size_t fmm_plan_workspace_bytes(const fmm_plan_t *plan);
+
+/* Release the plan and its device memory.  NULL is a no-op.  The caller must
+ * ensure no GPU work using the plan is still pending. */
+void fmm_plan_destroy(fmm_plan_t *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_H_ */

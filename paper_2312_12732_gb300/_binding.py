@@ -1,0 +1,273 @@
+"""ctypes binding of ``include/fmm.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps.  Tensors are
+``torch.Tensor`` objects (float64, contiguous, square); only their data
+pointers and the current CUDA stream cross the boundary.  All arithmetic runs
+in the library's CUDA kernels; if ``libfmm.so`` is missing the first call
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfmm.so")
+
+FMM_OK, FMM_ERR_INVALID, FMM_ERR_BRENT, FMM_ERR_UNSUPPORTED = 0, 1, 2, 3
+FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_NOT_FOUND = 4, 5, 6, 7
+FMM_F64, FMM_F64_OZAKI = 0, 1
+FMM_SCHED_AUTO, FMM_SCHED_FUSED, FMM_SCHED_HYBRID = 0, 1, 2
+
+DTYPES = {"f64": FMM_F64, "f64_ozaki": FMM_F64_OZAKI}
+SCHEDULES = {"auto": FMM_SCHED_AUTO, "fused": FMM_SCHED_FUSED, "hybrid": FMM_SCHED_HYBRID}
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+class fmm_algo_t(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("R", ctypes.c_int), ("U", _i32p), ("V", _i32p), ("W", _i32p)]
+
+
+class fmm_plan_options_t(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int), ("materialize_levels", ctypes.c_int), ("ozaki_slices", ctypes.c_int),
+                ("wait_timeout_s", ctypes.c_double), ("debug_poison_chain", ctypes.c_int)]
+
+
+class fmm_plan_info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_int), ("depth", ctypes.c_int), ("P", ctypes.c_int64),
+                ("R_total", ctypes.c_int64), ("m", ctypes.c_int64), ("n_core", ctypes.c_int64),
+                ("tasks", ctypes.c_int64), ("materialized_levels", ctypes.c_int),
+                ("flops_leaf", ctypes.c_double), ("flops_executed", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+# (name, restype, argtypes) for every symbol declared in include/fmm.h.
+SIGNATURES = [
+    ("fmm_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("fmm_algo_builtin", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(fmm_algo_t)]),
+    ("fmm_algo_brent_mismatches", ctypes.c_int64, [ctypes.POINTER(fmm_algo_t)]),
+    ("fmm_algo_from_transposed_c", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p]),
+    ("fmm_algo_compose", ctypes.c_int, [ctypes.POINTER(fmm_algo_t), ctypes.POINTER(fmm_algo_t), _i32p, _i32p, _i32p,
+                                        ctypes.POINTER(fmm_algo_t)]),
+    ("fmm_plan_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.POINTER(fmm_algo_t),
+                                       ctypes.c_int, ctypes.c_int]),
+    ("fmm_plan_create_ex", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                                          ctypes.POINTER(fmm_algo_t), ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(fmm_plan_options_t)]),
+    ("fmm_gemm", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p]),
+    ("fmm_gemm_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
+    ("fmm_gemm_batched", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.c_int, ctypes.c_void_p]),
+    ("fmm_sync_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("fmm_plan_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fmm_plan_info_t)]),
+    ("fmm_plan_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
+    ("fmm_plan_destroy", None, [ctypes.c_void_p]),
+]
+
+_lib = None
+
+
+def lib():
+    """The loaded ``libfmm.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                               "g.build()'` (the library has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class FmmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {fmm_status_string(status)} (status {status})")
+
+
+def _check(status: int, what: str):
+    if status != FMM_OK:
+        raise FmmError(status, what)
+
+
+def fmm_status_string(status: int) -> str:
+    return lib().fmm_status_string(int(status)).decode()
+
+
+class Algo:
+    """An algorithm <p,p,p;R>; keeps its int32 tables alive for the C struct."""
+
+    def __init__(self, p: int, U, V, W, name: str = "custom"):
+        self.p = int(p)
+        self.U = np.ascontiguousarray(U, dtype=np.int32)
+        self.V = np.ascontiguousarray(V, dtype=np.int32)
+        self.W = np.ascontiguousarray(W, dtype=np.int32)
+        if not (self.U.shape == self.V.shape == self.W.shape and self.U.ndim == 2
+                and self.U.shape[0] == self.p * self.p):
+            raise ValueError("U, V, W must all be p^2 x R")
+        self.R = int(self.U.shape[1])
+        self.name = name
+
+    def c_struct(self) -> fmm_algo_t:
+        return fmm_algo_t(self.p, self.R, self.U.ctypes.data_as(_i32p), self.V.ctypes.data_as(_i32p),
+                          self.W.ctypes.data_as(_i32p))
+
+    def __repr__(self):
+        return f"Algo({self.name}, <{self.p},{self.p},{self.p};{self.R}>)"
+
+
+def fmm_algo_builtin(name: str) -> Algo:
+    a = fmm_algo_t()
+    _check(lib().fmm_algo_builtin(name.encode(), ctypes.byref(a)), f"fmm_algo_builtin({name!r})")
+    p, R = a.p, a.R
+    U = np.ctypeslib.as_array(a.U, shape=(p * p * R,)).reshape(p * p, R).copy()
+    V = np.ctypeslib.as_array(a.V, shape=(p * p * R,)).reshape(p * p, R).copy()
+    W = np.ctypeslib.as_array(a.W, shape=(p * p * R,)).reshape(p * p, R).copy()
+    return Algo(p, U, V, W, name=name)
+
+
+def fmm_algo_brent_mismatches(algo: Algo) -> int:
+    a = algo.c_struct()
+    return int(lib().fmm_algo_brent_mismatches(ctypes.byref(a)))
+
+
+def fmm_algo_from_transposed_c(p: int, ct) -> np.ndarray:
+    ct = np.ascontiguousarray(ct, dtype=np.int32)
+    R = ct.shape[1]
+    W = np.empty_like(ct)
+    _check(lib().fmm_algo_from_transposed_c(p, R, ct.ctypes.data_as(_i32p), W.ctypes.data_as(_i32p)),
+           "fmm_algo_from_transposed_c")
+    return W
+
+
+def fmm_algo_compose(first: Algo, second: Algo) -> Algo:
+    p = first.p * second.p
+    R = first.R * second.R
+    U = np.empty((p * p, R), dtype=np.int32)
+    V = np.empty_like(U)
+    W = np.empty_like(U)
+    a1, a2, out = first.c_struct(), second.c_struct(), fmm_algo_t()
+    _check(lib().fmm_algo_compose(ctypes.byref(a1), ctypes.byref(a2), U.ctypes.data_as(_i32p),
+                                  V.ctypes.data_as(_i32p), W.ctypes.data_as(_i32p), ctypes.byref(out)),
+           "fmm_algo_compose")
+    return Algo(p, U, V, W, name=f"{first.name}x{second.name}")
+
+
+class Plan:
+    """Owns an ``fmm_plan_t*``; destroyed by ``fmm_plan_destroy`` or garbage collection."""
+
+    def __init__(self, handle: int, n: int, algo: Algo, depth: int, dtype: str):
+        self.handle = ctypes.c_void_p(handle)
+        self.n, self.algo, self.depth, self.dtype = n, algo, depth, dtype
+
+    def info(self) -> dict:
+        return fmm_plan_get_info(self)
+
+    def __del__(self):
+        try:
+            fmm_plan_destroy(self)
+        except Exception:
+            pass
+
+
+def fmm_plan_create(n: int, algo: Algo, depth: int, dtype: str = "f64", schedule: str = "auto",
+                    materialize_levels: int = 0, ozaki_slices: int = 0, wait_timeout_s: float = 0.0,
+                    debug_poison_chain: int = 0) -> Plan:
+    h = ctypes.c_void_p()
+    a = algo.c_struct()
+    opts = fmm_plan_options_t(SCHEDULES[schedule], int(materialize_levels), int(ozaki_slices),
+                              float(wait_timeout_s), int(debug_poison_chain))
+    _check(lib().fmm_plan_create_ex(ctypes.byref(h), int(n), ctypes.byref(a), int(depth), DTYPES[dtype],
+                                    ctypes.byref(opts)), f"fmm_plan_create(n={n}, {algo}, depth={depth})")
+    return Plan(h.value, int(n), algo, int(depth), dtype)
+
+
+def fmm_plan_destroy(plan: Plan):
+    if plan is not None and plan.handle:
+        lib().fmm_plan_destroy(plan.handle)
+        plan.handle = ctypes.c_void_p()
+
+
+def fmm_plan_get_info(plan: Plan) -> dict:
+    info = fmm_plan_info_t()
+    _check(lib().fmm_plan_get_info(plan.handle, ctypes.byref(info)), "fmm_plan_get_info")
+    return {k: getattr(info, k) for k, _ in fmm_plan_info_t._fields_}
+
+
+def fmm_plan_workspace_bytes(plan: Plan) -> int:
+    return int(lib().fmm_plan_workspace_bytes(plan.handle))
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check_operand(X, n: int, name: str, device: bool = True):
+    import torch
+
+    if not isinstance(X, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if X.dtype != torch.float64 or X.shape != (n, n) or not X.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 tensor of shape ({n}, {n})")
+    if device and not X.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device")
+    if not device and X.is_cuda:
+        raise ValueError(f"{name} must live in host memory")
+
+
+def fmm_gemm(plan: Plan, A, B, C, stream=None):
+    """C = A @ B on the GPU (asynchronous on ``stream``, default: torch's current stream)."""
+    n = plan.n
+    for X, nm in ((A, "A"), (B, "B"), (C, "C")):
+        _check_operand(X, n, nm)
+    _check(lib().fmm_gemm(plan.handle, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                          ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))), "fmm_gemm")
+    return C
+
+
+def fmm_gemm_host(plan: Plan, A, B, C, stream=None):
+    """C = A @ B with host tensors; copies in and out inside the call (blocking)."""
+    n = plan.n
+    for X, nm in ((A, "A"), (B, "B"), (C, "C")):
+        _check_operand(X, n, nm, device=False)
+    _check(lib().fmm_gemm_host(plan.handle, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                               ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+           "fmm_gemm_host")
+    return C
+
+
+def fmm_gemm_batched(plans, As, Bs, Cs, stream=None):
+    count = len(plans)
+    if not (len(As) == len(Bs) == len(Cs) == count):
+        raise ValueError("plans, A, B, C must have the same length")
+    if len({id(p) for p in plans}) != count:
+        raise ValueError("each product of a batch needs its own plan")
+    for p, A, B, C in zip(plans, As, Bs, Cs):
+        for X, nm in ((A, "A"), (B, "B"), (C, "C")):
+            _check_operand(X, p.n, nm)
+    arr = ctypes.c_void_p * max(count, 1)
+    hp = arr(*[p.handle.value for p in plans])
+    ha = arr(*[A.data_ptr() for A in As])
+    hb = arr(*[B.data_ptr() for B in Bs])
+    hc = arr(*[C.data_ptr() for C in Cs])
+    _check(lib().fmm_gemm_batched(hp, ha, hb, hc, count, ctypes.c_void_p(_stream_ptr(stream))), "fmm_gemm_batched")
+    return Cs
+
+
+def fmm_sync_status(plan: Plan, stream=None) -> int:
+    """Synchronizes the stream and returns the plan's device status code (0 = ok)."""
+    return int(lib().fmm_sync_status(plan.handle, ctypes.c_void_p(_stream_ptr(stream))))

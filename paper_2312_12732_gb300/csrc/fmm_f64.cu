@@ -1,0 +1,476 @@
+// FP64 leaf kernel of the fast-matrix-multiplication library (sm_103a).
+//
+// One persistent kernel serves the classic product (depth 0), every flattened
+// bilinear algorithm, peeled sizes and grouped batches.  CTAs fetch tile tasks
+// from a global counter in increasing order.  A core task computes one
+// kBM x kBN tile of a leaf product P_r = S_r T_r (Section 2, equation
+// `strassen`):
+//   * operand staging forms the S_r / T_r slab on the fly from the source
+//     blocks named by column r of U and V (pre-additions fused into the
+//     global -> register -> shared-memory staging; S_r and T_r never reach
+//     HBM);
+//   * the product runs on the FP64 tensor-core path, mma.sync m16n8k4 (DMMA),
+//     with accumulators in registers;
+//   * the epilogue applies C_l (+)= W[l][r] P_r for every nonzero of column r
+//     of W (post-additions fused into the epilogue).  Contributions to one
+//     (C block, tile) are applied in ascending r, ordered by a per-tile
+//     counter, so results are deterministic; the first contributor stores,
+//     the others read-modify-write.
+// Every wait points at a task with a lower index, tasks are handed out in
+// increasing order and only to running CTAs, so the lowest unfinished task can
+// always proceed: no co-residency assumption is needed.  Each wait is also
+// bounded in time; on expiry the kernel records kDevTimeout and drains.
+#include <cuda_runtime.h>
+
+#include "fmm_internal.h"
+
+namespace fmm {
+namespace {
+
+constexpr int BM = kBM, BN = kBN, BK = kBK, NT = kThreads;
+// Shared-memory row pitches (in doubles) chosen so that the m16n8k4 fragment
+// reads are free of bank conflicts: A rows 20 doubles apart (8 banks of
+// 4 bytes mod 32), B rows 132 apart (8 banks mod 32).
+constexpr int A_LD = BK + 4;
+constexpr int B_LD = BN + 4;
+
+struct Src {
+    const double *ptr;  // element (0, 0) of this source's part of the tile
+    double coef;
+};
+struct Dst {
+    double *ptr;        // element (0, 0) of the destination tile
+    unsigned *chain;    // ordering counter, or nullptr for a single writer
+    double coef;
+    int pos;            // number of contributions that must precede this one
+    int pad;
+};
+
+struct Smem {
+    double a[2][BM * A_LD];
+    double b[2][BK * B_LD];
+    Src srcA[kMaxTerms];
+    Src srcB[kMaxTerms];
+    Dst dst[kMaxTerms];
+    long long lda, ldb, ldc;
+    long long task;
+    int nA, nB, nD;
+    int rows, cols, K;
+    int ok;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
+
+// Waits until *ctr == target.  Bounded: gives up after timeout_ns or as soon
+// as another CTA has flagged an error.  Returns true on success.
+__device__ bool chain_wait(const unsigned *ctr, unsigned target, int *error, long long timeout_ns) {
+    const unsigned long long t0 = global_ns();
+    unsigned sleep = 32;
+    while (true) {
+        const unsigned v = ld_acquire(ctr);
+        if (v == target) return true;
+        if (ld_volatile(error) != kDevOk) return false;
+        if ((long long)(global_ns() - t0) > timeout_ns) {
+            atomicCAS(error, kDevOk, kDevTimeout);
+            return false;
+        }
+        __nanosleep(sleep);
+        if (sleep < 4096) sleep <<= 1;
+    }
+}
+
+// s (+)= coef * v with the fewest FP64 operations: +-1 coefficients are adds.
+__device__ __forceinline__ double combine(double s, double v, double c, bool first) {
+    if (first) return c == 1.0 ? v : (c == -1.0 ? -v : c * v);
+    return c == 1.0 ? s + v : (c == -1.0 ? s - v : fma(c, v, s));
+}
+
+__device__ __forceinline__ void dmma_16x8x4(double (&d)[4], const double (&a)[2], double b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+        : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+        : "d"(a[0]), "d"(a[1]), "d"(b));
+}
+
+// Decodes task `local` of problem `pr` into the shared source / destination
+// lists.  All threads run the index arithmetic; list entries are filled in
+// parallel.
+__device__ void setup_task(Smem &S, const F64Problem &pr, const F64Geom &g, long long local) {
+    const int tid = threadIdx.x;
+    const long long n = g.n, m = g.m, nc = g.n_core;
+    const long long q = n - nc;
+    if (local < g.tasks_core) {
+        const int tiles = g.tiles_m * g.tiles_n;
+        const long long per_sub = (long long)tiles * g.R_src;
+        const int sub = (int)(local / per_sub);
+        const long long rem = local - (long long)sub * per_sub;
+        const int t = (int)(rem / g.R_src);
+        const int r = (int)(rem - (long long)t * g.R_src);
+        const int ti = t / g.tiles_n, tj = t - ti * g.tiles_n;
+        const int rglob = sub * g.R_src + r;
+        const double *SA = pr.SA + (long long)sub * g.sub_stride_a;
+        const double *SB = pr.SB + (long long)sub * g.sub_stride_b;
+        const int ua = g.u_ptr[r], nA = g.u_ptr[r + 1] - ua;
+        const int vb = g.v_ptr[r], nB = g.v_ptr[r + 1] - vb;
+        const int wc = g.w_ptr[rglob], nD = g.w_ptr[rglob + 1] - wc;
+        for (int e = tid; e < nA; e += NT) {
+            const int2 en = g.u_ent[ua + e];
+            const long long br = en.x / g.P_src, bc = en.x % g.P_src;
+            S.srcA[e].ptr = SA + (br * m + (long long)ti * BM) * g.ld_src_a + bc * m;
+            S.srcA[e].coef = (double)en.y;
+        }
+        for (int e = tid; e < nB; e += NT) {
+            const int2 en = g.v_ent[vb + e];
+            const long long br = en.x / g.P_src, bc = en.x % g.P_src;
+            S.srcB[e].ptr = SB + (br * m) * g.ld_src_b + bc * m + (long long)tj * BN;
+            S.srcB[e].coef = (double)en.y;
+        }
+        for (int e = tid; e < nD; e += NT) {
+            const int4 en = g.w_ent[wc + e];
+            const long long br = en.x / g.P, bc = en.x % g.P;
+            S.dst[e].ptr = pr.C + (br * m + (long long)ti * BM) * n + bc * m + (long long)tj * BN;
+            S.dst[e].chain = pr.chain + (long long)en.x * tiles + t;
+            S.dst[e].coef = (double)en.y;
+            S.dst[e].pos = en.z;
+        }
+        if (tid == 0) {
+            S.nA = nA; S.nB = nB; S.nD = nD;
+            S.lda = g.ld_src_a; S.ldb = g.ld_src_b; S.ldc = n;
+            S.rows = (int)lmin(BM, m - (long long)ti * BM);
+            S.cols = (int)lmin(BN, m - (long long)tj * BN);
+            S.K = (int)m;
+        }
+        return;
+    }
+    local -= g.tasks_core;
+    if (tid != 0) return;
+    S.nA = S.nB = S.nD = 1;
+    S.lda = n; S.ldb = n; S.ldc = n;
+    S.srcA[0].coef = S.srcB[0].coef = 1.0;
+    S.dst[0].coef = 1.0;
+    if (local < g.tasks_right) {  // C[0:nc, nc:n] = A[0:nc, :] B[:, nc:n]
+        const int bi = (int)(local / g.rb_tn), bj = (int)(local % g.rb_tn);
+        S.srcA[0].ptr = pr.A + (long long)bi * BM * n;
+        S.srcB[0].ptr = pr.B + nc + (long long)bj * BN;
+        S.dst[0].ptr = pr.C + (long long)bi * BM * n + nc + (long long)bj * BN;
+        S.dst[0].chain = nullptr; S.dst[0].pos = 0;
+        S.rows = (int)lmin(BM, nc - (long long)bi * BM);
+        S.cols = (int)lmin(BN, q - (long long)bj * BN);
+        S.K = (int)n;
+        return;
+    }
+    local -= g.tasks_right;
+    if (local < g.tasks_bottom) {  // C[nc:n, :] = A[nc:n, :] B
+        const int bi = (int)(local / g.bb_tn), bj = (int)(local % g.bb_tn);
+        S.srcA[0].ptr = pr.A + (nc + (long long)bi * BM) * n;
+        S.srcB[0].ptr = pr.B + (long long)bj * BN;
+        S.dst[0].ptr = pr.C + (nc + (long long)bi * BM) * n + (long long)bj * BN;
+        S.dst[0].chain = nullptr; S.dst[0].pos = 0;
+        S.rows = (int)lmin(BM, q - (long long)bi * BM);
+        S.cols = (int)lmin(BN, n - (long long)bj * BN);
+        S.K = (int)n;
+        return;
+    }
+    local -= g.tasks_bottom;
+    {  // C[:nc, :nc] += A[:nc, nc:n] B[nc:n, :nc], tile t of block l, after every core contribution
+        const int tiles = g.tiles_m * g.tiles_n;
+        const int l = (int)(local / tiles), t = (int)(local % tiles);
+        const int ti = t / g.tiles_n, tj = t - ti * g.tiles_n;
+        const long long row0 = (long long)(l / g.P) * m + (long long)ti * BM;
+        const long long col0 = (long long)(l % g.P) * m + (long long)tj * BN;
+        S.srcA[0].ptr = pr.A + row0 * n + nc;
+        S.srcB[0].ptr = pr.B + nc * n + col0;
+        S.dst[0].ptr = pr.C + row0 * n + col0;
+        S.dst[0].chain = pr.chain + (long long)l * tiles + t;
+        S.dst[0].pos = g.w_row_nnz[l];
+        S.rows = (int)lmin(BM, m - (long long)ti * BM);
+        S.cols = (int)lmin(BN, m - (long long)tj * BN);
+        S.K = (int)q;
+    }
+}
+
+// Loads the K slab [kk, kk + BK) of both operands, combining the sources.
+__device__ __forceinline__ void load_slab(const Smem &S, int kk, double (&ra)[8], double (&rb)[8]) {
+    const int tid = threadIdx.x;
+    // A: column c of the slab, rows r0 + 16 j.
+    {
+        const int c = tid & 15, r0 = tid >> 4;
+        const bool kval = kk + c < S.K;
+        const long long lda = S.lda;
+        for (int e = 0; e < S.nA; ++e) {
+            const double *p = S.srcA[e].ptr + kk + c;
+            const double cf = S.srcA[e].coef;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int row = r0 + 16 * j;
+                const double v = (kval && row < S.rows) ? __ldg(p + row * lda) : 0.0;
+                ra[j] = combine(ra[j], v, cf, e == 0);
+            }
+        }
+        if (S.nA == 0) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) ra[j] = 0.0;
+        }
+    }
+    // B: column c of the slab, rows r0 + 2 j.
+    {
+        const int c = tid & 127, r0 = tid >> 7;
+        const bool cval = c < S.cols;
+        const long long ldb = S.ldb;
+        for (int e = 0; e < S.nB; ++e) {
+            const double *p = S.srcB[e].ptr + (long long)kk * ldb + c;
+            const double cf = S.srcB[e].coef;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int row = r0 + 2 * j;
+                const double v = (cval && kk + row < S.K) ? __ldg(p + row * ldb) : 0.0;
+                rb[j] = combine(rb[j], v, cf, e == 0);
+            }
+        }
+        if (S.nB == 0) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) rb[j] = 0.0;
+        }
+    }
+}
+
+__device__ __forceinline__ void store_slab(Smem &S, int buf, const double (&ra)[8], const double (&rb)[8]) {
+    const int tid = threadIdx.x;
+    {
+        const int c = tid & 15, r0 = tid >> 4;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) S.a[buf][(r0 + 16 * j) * A_LD + c] = ra[j];
+    }
+    {
+        const int c = tid & 127, r0 = tid >> 7;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) S.b[buf][(r0 + 2 * j) * B_LD + c] = rb[j];
+    }
+}
+
+__device__ __forceinline__ void mma_slab(const Smem &S, int buf, double (&acc)[4][4][4]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int wm = warp & 1, wn = warp >> 1;  // 2 x 4 warps, warp tile 64 x 32
+    const double *As = S.a[buf];
+    const double *Bs = S.b[buf];
+#pragma unroll
+    for (int kq = 0; kq < BK / 4; ++kq) {
+        double af[4][2], bf[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = wm * 64 + i * 16 + g;
+            af[i][0] = As[row * A_LD + kq * 4 + t];
+            af[i][1] = As[(row + 8) * A_LD + kq * 4 + t];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bf[j] = Bs[(kq * 4 + t) * B_LD + wn * 32 + j * 8 + g];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) dmma_16x8x4(acc[i][j], af[i], bf[j]);
+    }
+}
+
+template <int MAXP>
+__global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ F64Launch<MAXP> L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int wm = warp & 1, wn = warp >> 1;
+
+    while (true) {
+        if (tid == 0) {
+            long long tk = (long long)atomicAdd(L.task_counter, 1ull);
+            if (ld_volatile(L.error) != kDevOk) tk = L.total_tasks;
+            S.task = tk;
+        }
+        __syncthreads();
+        const long long task = S.task;
+        if (task >= L.total_tasks) break;
+        int pi = 0;
+        while (pi + 1 < L.nprobs && L.probs[pi + 1].task_begin <= task) ++pi;
+        const F64Problem &pr = L.probs[pi];
+        setup_task(S, pr, *pr.g, task - pr.task_begin);
+        __syncthreads();
+
+        double acc[4][4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[i][j][v] = 0.0;
+
+        const int K = S.K;
+        const int nk = (K + BK - 1) / BK;
+        double ra[8], rb[8];
+        if (nk > 0) {
+            load_slab(S, 0, ra, rb);
+            store_slab(S, 0, ra, rb);
+        }
+        __syncthreads();
+        for (int kt = 0; kt < nk; ++kt) {
+            const bool more = kt + 1 < nk;
+            if (more) load_slab(S, (kt + 1) * BK, ra, rb);
+            mma_slab(S, kt & 1, acc);
+            if (more) store_slab(S, (kt + 1) & 1, ra, rb);
+            __syncthreads();
+        }
+
+        // Epilogue: coefficient-weighted stores into every destination tile.
+        const int rows = S.rows, cols = S.cols;
+        const long long ldc = S.ldc;
+        for (int d = 0; d < S.nD; ++d) {
+            const Dst dst = S.dst[d];
+            if (tid == 0) {
+                bool ok = true;
+                if (dst.chain != nullptr && dst.pos > 0)
+                    ok = chain_wait(dst.chain, (unsigned)dst.pos, L.error, L.timeout_ns);
+                S.ok = ok ? 1 : 0;
+            }
+            __syncthreads();
+            if (!S.ok) break;
+            const bool first = dst.pos == 0;
+            const double cf = dst.coef;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int row = wm * 64 + i * 16 + g + 8 * h;
+                        if (row >= rows) continue;
+#pragma unroll
+                        for (int c2 = 0; c2 < 2; ++c2) {
+                            const int col = wn * 32 + j * 8 + 2 * t4 + c2;
+                            if (col >= cols) continue;
+                            double *p = dst.ptr + row * ldc + col;
+                            const double v = acc[i][j][2 * h + c2];
+                            double out;
+                            if (first)
+                                out = cf == 1.0 ? v : (cf == -1.0 ? -v : cf * v);
+                            else {
+                                const double old = __ldcg(p);
+                                out = cf == 1.0 ? old + v : (cf == -1.0 ? old - v : fma(cf, v, old));
+                            }
+                            *p = out;
+                        }
+                    }
+            __syncthreads();
+            if (tid == 0 && dst.chain != nullptr) {
+                __threadfence();
+                atomicAdd(dst.chain, 1u);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One materialized recursion level: one thread per (y, x) of a b x b output
+// block and input matrix blockIdx.y; all R outputs of that position.
+__global__ void materialize_level_kernel(const double *__restrict__ in, long long ld_in, long long in_stride,
+                                         long long b, int p, int R, const int *__restrict__ ptr,
+                                         const int2 *__restrict__ ent, double *__restrict__ out) {
+    const long long total = b * b;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int c = blockIdx.y;
+    const double *src = in + (long long)c * in_stride;
+    double *dst = out + (long long)c * R * total;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const long long y = e / b, x = e - y * b;
+        for (int s = 0; s < R; ++s) {
+            double acc = 0.0;
+            const int e0 = ptr[s], e1 = ptr[s + 1];
+            for (int k = e0; k < e1; ++k) {
+                const int2 en = ent[k];
+                const long long br = en.x / p, bc = en.x % p;
+                const double v = __ldg(src + (br * b + y) * ld_in + bc * b + x);
+                acc = combine(acc, v, (double)en.y, k == e0);
+            }
+            dst[(long long)s * total + e] = acc;
+        }
+    }
+}
+
+}  // namespace
+
+size_t f64_kernel_smem_bytes() { return sizeof(Smem); }
+
+static cudaError_t prepare_attr(const void *fn) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+}
+
+int f64_kernel_ctas_per_sm() {
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    if (prepare_attr((const void *)fmm_f64_kernel<1>) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fmm_f64_kernel<1>, NT, sizeof(Smem)) != cudaSuccess)
+        return 0;
+    cached = nb;
+    return nb;
+}
+
+cudaError_t launch_f64_single(const F64Launch<1> &L, int grid, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = prepare_attr((const void *)fmm_f64_kernel<1>);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    fmm_f64_kernel<1><<<grid, NT, sizeof(Smem), s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_batch(const F64Launch<kMaxBatchPerLaunch> &L, int grid, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = prepare_attr((const void *)fmm_f64_kernel<kMaxBatchPerLaunch>);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    fmm_f64_kernel<kMaxBatchPerLaunch><<<grid, NT, sizeof(Smem), s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_materialize_level(const double *in, long long ld_in, long long in_stride, int n_in,
+                                     long long b_out, int p, int R, const int *ptr, const int2 *ent, double *out,
+                                     cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long total = b_out * b_out;
+    long long bx = (total + 255) / 256;
+    long long cap = (long long)sms * 8 / (n_in > 0 ? n_in : 1);
+    if (cap < 1) cap = 1;
+    if (bx > cap) bx = cap;
+    if (bx < 1) bx = 1;
+    for (int c0 = 0; c0 < n_in; c0 += 65535) {
+        const int cnt = n_in - c0 < 65535 ? n_in - c0 : 65535;
+        dim3 grid((unsigned)bx, (unsigned)cnt);
+        materialize_level_kernel<<<grid, 256, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride, b_out, p, R,
+                                                      ptr, ent, out + (long long)c0 * R * total);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fmm

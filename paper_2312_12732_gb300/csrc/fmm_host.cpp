@@ -1,0 +1,746 @@
+// Host side of the fast-matrix-multiplication library: built-in algorithms,
+// exact Brent check, recursion flattening, tile-task planning, workspace and
+// launches.  Public entry points are declared in include/fmm.h.
+#include "fmm.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fmm_internal.h"
+
+using fmm::F64Geom;
+using fmm::F64Launch;
+using fmm::F64Problem;
+
+// ---------------------------------------------------------------------------
+// Built-in algorithms.  Each table is p^2 x R row-major over blocks; W indexes
+// the blocks of C in row-major order.
+// ---------------------------------------------------------------------------
+namespace {
+
+// <2,2,2;8>: the classic block product (Section 3, the printed graph
+// C0 = A0 B0 + A1 B2, C1 = A0 B1 + A1 B3, C2 = A2 B0 + A3 B2, C3 = A2 B1 + A3 B3).
+const int32_t kClassic2U[4 * 8] = {1, 0, 1, 0, 0, 0, 0, 0,  0, 1, 0, 1, 0, 0, 0, 0,
+                                   0, 0, 0, 0, 1, 0, 1, 0,  0, 0, 0, 0, 0, 1, 0, 1};
+const int32_t kClassic2V[4 * 8] = {1, 0, 0, 0, 1, 0, 0, 0,  0, 0, 1, 0, 0, 0, 1, 0,
+                                   0, 1, 0, 0, 0, 1, 0, 0,  0, 0, 0, 1, 0, 0, 0, 1};
+const int32_t kClassic2W[4 * 8] = {1, 1, 0, 0, 0, 0, 0, 0,  0, 0, 1, 1, 0, 0, 0, 0,
+                                   0, 0, 0, 0, 1, 1, 0, 0,  0, 0, 0, 0, 0, 0, 1, 1};
+
+// Strassen as printed in Section 2 (a, b and c^t of f['2,2,2']); the c^t rows
+// are printed with labels C0, C2, C1, C3 and are stored here under those labels.
+const int32_t kStrassenU[4 * 7] = {0, 1, 1, 0, 1, 1, 0,   0, 0, -1, 1, 0, 0, 0,
+                                   1, 1, 1, 0, 1, 0, 0,   -1, -1, -1, 0, 0, 0, 1};
+const int32_t kStrassenV[4 * 7] = {0, 0, 0, 0, 1, 1, 0,   1, 1, 0, 0, 1, 0, 1,
+                                   0, 1, 1, 1, 1, 0, 0,   0, 1, 1, 0, 1, 0, 1};
+const int32_t kStrassenW[4 * 7] = {0, 0, 0, 1, 0, 1, 0,   -1, 1, -1, -1, 0, 0, 0,
+                                   0, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 0, 1};
+
+// Strassen 1969: M1 = (A11+A22)(B11+B22), M2 = (A21+A22)B11, M3 = A11(B12-B22),
+// M4 = A22(B21-B11), M5 = (A11+A12)B22, M6 = (A21-A11)(B11+B12),
+// M7 = (A12-A22)(B21+B22); C11 = M1+M4-M5+M7, C12 = M3+M5, C21 = M2+M4,
+// C22 = M1-M2+M3+M6.
+const int32_t kS69U[4 * 7] = {1, 0, 1, 0, 1, -1, 0,  0, 0, 0, 0, 1, 0, 1,
+                              0, 1, 0, 0, 0, 1, 0,   1, 1, 0, 1, 0, 0, -1};
+const int32_t kS69V[4 * 7] = {1, 1, 0, -1, 0, 1, 0,  0, 0, 1, 0, 0, 1, 0,
+                              0, 0, 0, 1, 0, 0, 1,   1, 0, -1, 0, 1, 0, 1};
+const int32_t kS69W[4 * 7] = {1, 0, 0, 1, -1, 0, 1,  0, 0, 1, 0, 1, 0, 0,
+                              0, 1, 0, 1, 0, 0, 0,   1, -1, 1, 0, 0, 1, 0};
+
+// Strassen-Winograd (15-addition variant) in flat form:
+// M1 = A11 B11, M2 = A12 B21, M3 = (A11+A12-A21-A22) B22,
+// M4 = A22 (B11-B12-B21+B22), M5 = (A21+A22)(B12-B11),
+// M6 = (A21+A22-A11)(B11-B12+B22), M7 = (A11-A21)(B22-B12);
+// C11 = M1+M2, C12 = M1+M3+M5+M6, C21 = M1-M4+M6+M7, C22 = M1+M5+M6+M7.
+const int32_t kWinoU[4 * 7] = {1, 0, 1, 0, 0, -1, 1,  0, 1, 1, 0, 0, 0, 0,
+                               0, 0, -1, 0, 1, 1, -1, 0, 0, -1, 1, 1, 1, 0};
+const int32_t kWinoV[4 * 7] = {1, 0, 0, 1, -1, 1, 0,  0, 0, 0, -1, 1, -1, -1,
+                               0, 1, 0, -1, 0, 0, 0,  0, 0, 1, 1, 0, 1, 1};
+const int32_t kWinoW[4 * 7] = {1, 1, 0, 0, 0, 0, 0,  1, 0, 1, 0, 1, 1, 0,
+                               1, 0, 0, -1, 0, 1, 1, 1, 0, 0, 0, 1, 1, 1};
+
+// Laderman <3,3,3;23> (1976), products m1..m23 as columns; built from its
+// product list at first use.
+struct LinTerm { int sign, i, j; };
+struct LadermanProduct { LinTerm a[7]; int na; LinTerm b[7]; int nb; };
+
+std::vector<int32_t> g_lad_u, g_lad_v, g_lad_w;
+
+void build_laderman() {
+    if (!g_lad_u.empty()) return;
+    // Each product: signed a-terms (1-based row, col), signed b-terms.
+    static const LadermanProduct prods[23] = {
+        {{{1,1,1},{1,1,2},{1,1,3},{-1,2,1},{-1,2,2},{-1,3,2},{-1,3,3}}, 7, {{1,2,2}}, 1},
+        {{{1,1,1},{-1,2,1}}, 2, {{-1,1,2},{1,2,2}}, 2},
+        {{{1,2,2}}, 1, {{-1,1,1},{1,1,2},{1,2,1},{-1,2,2},{-1,2,3},{-1,3,1},{1,3,3}}, 7},
+        {{{-1,1,1},{1,2,1},{1,2,2}}, 3, {{1,1,1},{-1,1,2},{1,2,2}}, 3},
+        {{{1,2,1},{1,2,2}}, 2, {{-1,1,1},{1,1,2}}, 2},
+        {{{1,1,1}}, 1, {{1,1,1}}, 1},
+        {{{-1,1,1},{1,3,1},{1,3,2}}, 3, {{1,1,1},{-1,1,3},{1,2,3}}, 3},
+        {{{-1,1,1},{1,3,1}}, 2, {{1,1,3},{-1,2,3}}, 2},
+        {{{1,3,1},{1,3,2}}, 2, {{-1,1,1},{1,1,3}}, 2},
+        {{{1,1,1},{1,1,2},{1,1,3},{-1,2,2},{-1,2,3},{-1,3,1},{-1,3,2}}, 7, {{1,2,3}}, 1},
+        {{{1,3,2}}, 1, {{-1,1,1},{1,1,3},{1,2,1},{-1,2,2},{-1,2,3},{-1,3,1},{1,3,2}}, 7},
+        {{{-1,1,3},{1,3,2},{1,3,3}}, 3, {{1,2,2},{1,3,1},{-1,3,2}}, 3},
+        {{{1,1,3},{-1,3,3}}, 2, {{1,2,2},{-1,3,2}}, 2},
+        {{{1,1,3}}, 1, {{1,3,1}}, 1},
+        {{{1,3,2},{1,3,3}}, 2, {{-1,3,1},{1,3,2}}, 2},
+        {{{-1,1,3},{1,2,2},{1,2,3}}, 3, {{1,2,3},{1,3,1},{-1,3,3}}, 3},
+        {{{1,1,3},{-1,2,3}}, 2, {{1,2,3},{-1,3,3}}, 2},
+        {{{1,2,2},{1,2,3}}, 2, {{-1,3,1},{1,3,3}}, 2},
+        {{{1,1,2}}, 1, {{1,2,1}}, 1},
+        {{{1,2,3}}, 1, {{1,3,2}}, 1},
+        {{{1,2,1}}, 1, {{1,1,3}}, 1},
+        {{{1,3,1}}, 1, {{1,1,2}}, 1},
+        {{{1,3,3}}, 1, {{1,3,3}}, 1},
+    };
+    // c_ij as lists of 1-based product numbers, all with coefficient +1.
+    static const int cl[9][8] = {
+        {6, 14, 19},          {1, 4, 5, 6, 12, 14, 15}, {6, 7, 9, 10, 14, 16, 18},
+        {2, 3, 4, 6, 14, 16, 17}, {2, 4, 5, 6, 20},    {14, 16, 17, 18, 21},
+        {6, 7, 8, 11, 12, 13, 14}, {12, 13, 14, 15, 22}, {6, 7, 8, 9, 23}};
+    const int R = 23;
+    g_lad_u.assign(9 * R, 0);
+    g_lad_v.assign(9 * R, 0);
+    g_lad_w.assign(9 * R, 0);
+    for (int r = 0; r < R; ++r) {
+        for (int e = 0; e < prods[r].na; ++e) {
+            const LinTerm &t = prods[r].a[e];
+            g_lad_u[((t.i - 1) * 3 + (t.j - 1)) * R + r] += t.sign;
+        }
+        for (int e = 0; e < prods[r].nb; ++e) {
+            const LinTerm &t = prods[r].b[e];
+            g_lad_v[((t.i - 1) * 3 + (t.j - 1)) * R + r] += t.sign;
+        }
+    }
+    for (int l = 0; l < 9; ++l)
+        for (int e = 0; e < 8 && cl[l][e] != 0; ++e) g_lad_w[l * R + (cl[l][e] - 1)] += 1;
+}
+
+}  // namespace
+
+extern "C" const char *fmm_status_string(fmm_status_t s) {
+    switch (s) {
+        case FMM_OK: return "ok";
+        case FMM_ERR_INVALID: return "invalid argument";
+        case FMM_ERR_BRENT: return "algorithm fails the Brent equations";
+        case FMM_ERR_UNSUPPORTED: return "unsupported request";
+        case FMM_ERR_OOM: return "out of memory";
+        case FMM_ERR_CUDA: return "CUDA error";
+        case FMM_ERR_TIMEOUT: return "device-side wait timed out";
+        case FMM_ERR_NOT_FOUND: return "unknown algorithm name";
+    }
+    return "unknown status";
+}
+
+extern "C" fmm_status_t fmm_algo_builtin(const char *name, fmm_algo_t *out) {
+    if (!name || !out) return FMM_ERR_INVALID;
+    const std::string s(name);
+    if (s == "classic2") { *out = {2, 8, kClassic2U, kClassic2V, kClassic2W}; return FMM_OK; }
+    if (s == "strassen") { *out = {2, 7, kStrassenU, kStrassenV, kStrassenW}; return FMM_OK; }
+    if (s == "strassen1969") { *out = {2, 7, kS69U, kS69V, kS69W}; return FMM_OK; }
+    if (s == "winograd") { *out = {2, 7, kWinoU, kWinoV, kWinoW}; return FMM_OK; }
+    if (s == "laderman") {
+        build_laderman();
+        *out = {3, 23, g_lad_u.data(), g_lad_v.data(), g_lad_w.data()};
+        return FMM_OK;
+    }
+    return FMM_ERR_NOT_FOUND;
+}
+
+static bool algo_shape_ok(const fmm_algo_t *a) {
+    return a && a->p >= 2 && a->R >= 1 && a->U && a->V && a->W && (long long)a->p * a->p * a->R < (1LL << 28);
+}
+
+extern "C" int64_t fmm_algo_brent_mismatches(const fmm_algo_t *a) {
+    if (!algo_shape_ok(a)) return -1;
+    const int p = a->p, R = a->R;
+    int64_t bad = 0;
+    // For each (i,j) of A, (j2,k) of B, (i2,k2) of C: sum_r U V W must equal
+    // delta(j,j2) delta(i,i2) delta(k,k2).  Loop over the nonzeros of U and V
+    // per product to keep the check fast for large compositions.
+    std::vector<int64_t> acc((size_t)p * p * p * p * p * p, 0);
+    std::vector<int> unz, vnz, wnz;
+    for (int r = 0; r < R; ++r) {
+        unz.clear(); vnz.clear(); wnz.clear();
+        for (int x = 0; x < p * p; ++x) {
+            if (a->U[(int64_t)x * R + r]) unz.push_back(x);
+            if (a->V[(int64_t)x * R + r]) vnz.push_back(x);
+            if (a->W[(int64_t)x * R + r]) wnz.push_back(x);
+        }
+        for (int iu : unz)
+            for (int iv : vnz)
+                for (int iw : wnz) {
+                    const int64_t c = (int64_t)a->U[(int64_t)iu * R + r] * a->V[(int64_t)iv * R + r] *
+                                      a->W[(int64_t)iw * R + r];
+                    acc[((size_t)iu * p * p + iv) * p * p + iw] += c;
+                }
+    }
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j)
+            for (int j2 = 0; j2 < p; ++j2)
+                for (int k = 0; k < p; ++k)
+                    for (int i2 = 0; i2 < p; ++i2)
+                        for (int k2 = 0; k2 < p; ++k2) {
+                            const int64_t want = (j == j2 && i == i2 && k == k2) ? 1 : 0;
+                            const size_t idx = ((size_t)(i * p + j) * p * p + (j2 * p + k)) * p * p + (i2 * p + k2);
+                            if (acc[idx] != want) ++bad;
+                        }
+    return bad;
+}
+
+extern "C" fmm_status_t fmm_algo_from_transposed_c(int p, int R, const int32_t *ct, int32_t *W_out) {
+    if (p < 2 || R < 1 || !ct || !W_out) return FMM_ERR_INVALID;
+    for (int i = 0; i < p; ++i)
+        for (int k = 0; k < p; ++k)
+            for (int r = 0; r < R; ++r) W_out[(int64_t)(i * p + k) * R + r] = ct[(int64_t)(k * p + i) * R + r];
+    return FMM_OK;
+}
+
+extern "C" fmm_status_t fmm_algo_compose(const fmm_algo_t *f, const fmm_algo_t *s, int32_t *U_out,
+                                         int32_t *V_out, int32_t *W_out, fmm_algo_t *out) {
+    if (!algo_shape_ok(f) || !algo_shape_ok(s) || !U_out || !V_out || !W_out || !out) return FMM_ERR_INVALID;
+    const int p1 = f->p, p2 = s->p, R1 = f->R, R2 = s->R, p = p1 * p2;
+    const int64_t R = (int64_t)R1 * R2;
+    if ((int64_t)p * p * R >= (1LL << 30)) return FMM_ERR_UNSUPPORTED;
+    const int32_t *X1[3] = {f->U, f->V, f->W};
+    const int32_t *X2[3] = {s->U, s->V, s->W};
+    int32_t *XO[3] = {U_out, V_out, W_out};
+    for (int w = 0; w < 3; ++w)
+        for (int i1 = 0; i1 < p1; ++i1)
+            for (int j1 = 0; j1 < p1; ++j1)
+                for (int i2 = 0; i2 < p2; ++i2)
+                    for (int j2 = 0; j2 < p2; ++j2) {
+                        const int64_t row = (int64_t)(i1 * p2 + i2) * p + (j1 * p2 + j2);
+                        for (int r1 = 0; r1 < R1; ++r1)
+                            for (int r2 = 0; r2 < R2; ++r2)
+                                XO[w][row * R + (int64_t)r1 * R2 + r2] =
+                                    X1[w][(int64_t)(i1 * p1 + j1) * R1 + r1] * X2[w][(int64_t)(i2 * p2 + j2) * R2 + r2];
+                    }
+    *out = {p, (int)R, U_out, V_out, W_out};
+    return FMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plans
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Entry { int blk; int coef; };
+
+// Columns of the flattened coefficient matrix of `levels` recursion levels:
+// product (r_0, ..., r_{L-1}) (r_0 outermost) = sum r_l R^(L-1-l); block
+// (row, col) on the p^L grid with row = sum i_l p^(L-1-l), col likewise;
+// coefficient = prod X[(i_l, j_l)][r_l].
+std::vector<std::vector<Entry>> flatten(int p, int R, const int32_t *X, int levels) {
+    std::vector<std::vector<Entry>> cols(1, std::vector<Entry>{{0, 1}});
+    int P = 1;
+    for (int lev = 0; lev < levels; ++lev) {
+        std::vector<std::vector<Entry>> next((size_t)cols.size() * R);
+        const int Pn = P * p;
+        for (size_t c = 0; c < cols.size(); ++c)
+            for (int r = 0; r < R; ++r) {
+                auto &dst = next[c * R + r];
+                for (const Entry &e : cols[c]) {
+                    const int row = e.blk / P, col = e.blk % P;
+                    for (int x = 0; x < p * p; ++x) {
+                        const int32_t v = X[(int64_t)x * R + r];
+                        if (!v) continue;
+                        const int i = x / p, j = x % p;
+                        dst.push_back({(row * p + i) * Pn + (col * p + j), e.coef * v});
+                    }
+                }
+                std::sort(dst.begin(), dst.end(), [](const Entry &a, const Entry &b) { return a.blk < b.blk; });
+            }
+        cols.swap(next);
+        P = Pn;
+    }
+    return cols;
+}
+
+long long ipow(long long b, int e) {
+    long long r = 1;
+    while (e-- > 0) r *= b;
+    return r;
+}
+
+}  // namespace
+
+struct fmm_plan {
+    int device = 0;
+    int64_t n = 0;
+    int p = 0, R = 0, depth = 0, mat_levels = 0;
+    fmm_dtype_t dtype = FMM_F64;
+    int64_t P = 1, P_src = 1, R_total = 1, R_src = 1, nsub = 1, m = 0, n_core = 0, b_src = 0;
+    int tiles_m = 0, tiles_n = 0;
+    F64Geom geom{};  // host copy (device pointers inside)
+    long long total_tasks = 0;
+    double timeout_s = 5.0;
+    int poison = 0;
+    // device memory
+    void *d_tables = nullptr;     // geometry + CSC tables
+    size_t tables_bytes = 0;
+    void *d_ws = nullptr;         // counters (zeroed per call) + materialized operands
+    size_t counters_bytes = 0;
+    size_t ws_bytes = 0;
+    unsigned *d_chain = nullptr;
+    unsigned long long *d_task_counter = nullptr;
+    int *d_error = nullptr;
+    double *d_SA = nullptr, *d_SB = nullptr;  // materialized sources (nullptr when fused)
+    double *d_TA = nullptr, *d_TB = nullptr;  // intermediate level (materialized depth >= 2)
+    const int *d_mat_u_ptr = nullptr, *d_mat_v_ptr = nullptr;
+    const int2 *d_mat_u_ent = nullptr, *d_mat_v_ent = nullptr;
+    int64_t mat_outputs = 0;
+    // host-buffer path
+    double *d_hostA = nullptr, *d_hostB = nullptr, *d_hostC = nullptr;
+    // statistics
+    double flops_leaf = 0, flops_exec = 0;
+    int grid = 0;
+};
+
+namespace {
+
+fmm_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FMM_OK : FMM_ERR_CUDA; }
+
+void free_plan_memory(fmm_plan *pl) {
+    if (pl->d_tables) cudaFree(pl->d_tables);
+    if (pl->d_ws) cudaFree(pl->d_ws);
+    if (pl->d_hostA) cudaFree(pl->d_hostA);
+    if (pl->d_hostB) cudaFree(pl->d_hostB);
+    if (pl->d_hostC) cudaFree(pl->d_hostC);
+    pl->d_tables = pl->d_ws = nullptr;
+    pl->d_hostA = pl->d_hostB = pl->d_hostC = nullptr;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Default number of materialized levels.  On GB300 the FP64 pipe is the
+// scarce resource (about 1 TFLOP/s) while HBM bandwidth and capacity are
+// plentiful: a pre-addition fused into operand staging is recomputed once per
+// output tile column (m / kBN times), a materialized one once, and forming
+// the levels one at a time shares each level's sums across all products below
+// it.  So every level whose operands combine more than one block on average
+// is materialized; algorithms whose columns are single blocks stay fused.
+int default_materialized_levels(int p, int R, const fmm_algo_t *a, int depth) {
+    if (depth < 1) return 0;
+    long long nnz_u = 0, nnz_v = 0;
+    for (int64_t x = 0; x < (int64_t)p * p * R; ++x) {
+        nnz_u += a->U[x] != 0;
+        nnz_v += a->V[x] != 0;
+    }
+    const double avg = 0.5 * (double)(nnz_u + nnz_v) / R;  // sources per operand per level
+    return avg > 1.5 ? depth : 0;
+}
+
+}  // namespace
+
+extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
+                                           fmm_dtype_t dtype, const fmm_plan_options_t *opts) {
+    if (!out) return FMM_ERR_INVALID;
+    *out = nullptr;
+    if (n < 1 || depth < 0 || depth > 8 || !algo_shape_ok(algo)) return FMM_ERR_INVALID;
+    if (n > (1LL << 31) / 2) return FMM_ERR_UNSUPPORTED;
+    if (dtype != FMM_F64) return FMM_ERR_UNSUPPORTED;
+    if (fmm_algo_brent_mismatches(algo) != 0) return FMM_ERR_BRENT;
+    const int p = algo->p, R = algo->R;
+    const long long P = ipow(p, depth);
+    const long long Rt = ipow(R, depth);
+    if (P > n) return FMM_ERR_INVALID;  // leaf size would be < 1
+    if (Rt > (1LL << 24)) return FMM_ERR_UNSUPPORTED;
+
+    int mat = 0;
+    fmm_plan_options_t o{};
+    if (opts) o = *opts;
+    if (o.schedule == FMM_SCHED_FUSED) mat = 0;
+    else if (o.schedule == FMM_SCHED_HYBRID) mat = o.materialize_levels;
+    else mat = default_materialized_levels(p, R, algo, depth);
+    if (mat < 0 || mat > depth) return FMM_ERR_INVALID;
+
+    fmm_plan *pl = new (std::nothrow) fmm_plan();
+    if (!pl) return FMM_ERR_OOM;
+    cudaGetDevice(&pl->device);
+    pl->n = n; pl->p = p; pl->R = R; pl->depth = depth; pl->dtype = dtype; pl->mat_levels = mat;
+    pl->P = P; pl->R_total = Rt;
+    pl->m = n / P;
+    pl->n_core = P * pl->m;
+    pl->P_src = ipow(p, depth - mat);
+    pl->R_src = ipow(R, depth - mat);
+    pl->nsub = ipow(R, mat);
+    pl->b_src = pl->P_src * pl->m;
+    pl->tiles_m = (int)((pl->m + fmm::kBM - 1) / fmm::kBM);
+    pl->tiles_n = (int)((pl->m + fmm::kBN - 1) / fmm::kBN);
+    if (o.wait_timeout_s > 0) pl->timeout_s = o.wait_timeout_s;
+    pl->poison = o.debug_poison_chain;
+
+    // Coefficient tables: bottom levels for the fused operands, all levels for W.
+    auto ucols = flatten(p, R, algo->U, depth - mat);
+    auto vcols = flatten(p, R, algo->V, depth - mat);
+    auto wcols = flatten(p, R, algo->W, depth);
+    std::vector<std::vector<Entry>> mu, mv;
+    if (mat > 0) {  // one level; applied `mat` times, level by level
+        mu = flatten(p, R, algo->U, 1);
+        mv = flatten(p, R, algo->V, 1);
+    }
+    size_t maxc = 0;
+    for (auto &c : ucols) maxc = std::max(maxc, c.size());
+    for (auto &c : vcols) maxc = std::max(maxc, c.size());
+    for (auto &c : wcols) maxc = std::max(maxc, c.size());
+    if (maxc > (size_t)fmm::kMaxTerms) { delete pl; return FMM_ERR_UNSUPPORTED; }
+
+    auto csc2 = [](const std::vector<std::vector<Entry>> &cols, std::vector<int> &ptr, std::vector<int2> &ent) {
+        ptr.assign(cols.size() + 1, 0);
+        for (size_t c = 0; c < cols.size(); ++c) {
+            ptr[c + 1] = ptr[c] + (int)cols[c].size();
+            for (const Entry &e : cols[c]) ent.push_back(make_int2(e.blk, e.coef));
+        }
+    };
+    std::vector<int> u_ptr, v_ptr, w_ptr, mu_ptr, mv_ptr, w_row((size_t)P * P, 0);
+    std::vector<int2> u_ent, v_ent, mu_ent, mv_ent;
+    std::vector<int4> w_ent;
+    csc2(ucols, u_ptr, u_ent);
+    csc2(vcols, v_ptr, v_ent);
+    if (mat > 0) { csc2(mu, mu_ptr, mu_ent); csc2(mv, mv_ptr, mv_ent); }
+    w_ptr.assign(wcols.size() + 1, 0);
+    for (size_t c = 0; c < wcols.size(); ++c) {
+        w_ptr[c + 1] = w_ptr[c] + (int)wcols[c].size();
+        for (const Entry &e : wcols[c]) w_ent.push_back(make_int4(e.blk, e.coef, w_row[e.blk]++, 0));
+    }
+
+    // Task counts.
+    const long long tiles = (long long)pl->tiles_m * pl->tiles_n;
+    const long long q = n - pl->n_core;
+    F64Geom &g = pl->geom;
+    g.n = n; g.m = pl->m; g.n_core = pl->n_core;
+    g.P = (int)P; g.P_src = (int)pl->P_src; g.R_src = (int)pl->R_src; g.nsub = (int)pl->nsub;
+    g.tiles_m = pl->tiles_m; g.tiles_n = pl->tiles_n;
+    g.ld_src_a = mat > 0 ? pl->b_src : n;
+    g.ld_src_b = g.ld_src_a;
+    g.sub_stride_a = mat > 0 ? pl->b_src * pl->b_src : 0;
+    g.sub_stride_b = g.sub_stride_a;
+    g.tasks_core = tiles * Rt;
+    if (q > 0) {
+        g.rb_tm = (int)((pl->n_core + fmm::kBM - 1) / fmm::kBM);
+        g.rb_tn = (int)((q + fmm::kBN - 1) / fmm::kBN);
+        g.bb_tm = (int)((q + fmm::kBM - 1) / fmm::kBM);
+        g.bb_tn = (int)((n + fmm::kBN - 1) / fmm::kBN);
+        g.tasks_right = (long long)g.rb_tm * g.rb_tn;
+        g.tasks_bottom = (long long)g.bb_tm * g.bb_tn;
+        g.tasks_rankq = (long long)P * P * tiles;
+    }
+    pl->total_tasks = g.tasks_core + g.tasks_right + g.tasks_bottom + g.tasks_rankq;
+
+    // Flop accounting (executed, as scheduled; multiply-add = 2 flops).
+    const double md = (double)pl->m;
+    pl->flops_leaf = 2.0 * (double)Rt * md * md * md;
+    double adds = 0;
+    {
+        long long nnz_u = (long long)u_ent.size(), nnz_v = (long long)v_ent.size();
+        const double fused_factor_a = (double)pl->tiles_n;  // S slab rebuilt per tile column
+        const double fused_factor_b = (double)pl->tiles_m;
+        adds += (double)pl->nsub * ((double)(nnz_u - pl->R_src) * md * md * fused_factor_a +
+                                    (double)(nnz_v - pl->R_src) * md * md * fused_factor_b);
+        for (int lev = 1; lev <= mat; ++lev) {
+            const double bl = (double)(pl->n_core / ipow(p, lev));
+            const double cnt = (double)ipow(R, lev - 1);
+            adds += cnt * (double)((long long)mu_ent.size() - R) * bl * bl;
+            adds += cnt * (double)((long long)mv_ent.size() - R) * bl * bl;
+        }
+        adds += (double)((long long)w_ent.size() - (long long)P * P) * md * md;
+    }
+    const double qd = (double)q, ncd = (double)pl->n_core, nd = (double)n;
+    const double peel = 2.0 * (ncd * qd * nd + qd * nd * nd + ncd * ncd * qd);
+    pl->flops_exec = pl->flops_leaf + adds + peel;
+
+    // Device tables.
+    size_t off = 0;
+    auto reserve = [&](size_t bytes) { size_t o2 = align_up(off, 256); off = o2 + bytes; return o2; };
+    const size_t o_geom = reserve(sizeof(F64Geom));
+    const size_t o_uptr = reserve(u_ptr.size() * sizeof(int));
+    const size_t o_uent = reserve(std::max<size_t>(1, u_ent.size()) * sizeof(int2));
+    const size_t o_vptr = reserve(v_ptr.size() * sizeof(int));
+    const size_t o_vent = reserve(std::max<size_t>(1, v_ent.size()) * sizeof(int2));
+    const size_t o_wptr = reserve(w_ptr.size() * sizeof(int));
+    const size_t o_went = reserve(std::max<size_t>(1, w_ent.size()) * sizeof(int4));
+    const size_t o_wrow = reserve(w_row.size() * sizeof(int));
+    size_t o_muptr = 0, o_muent = 0, o_mvptr = 0, o_mvent = 0;
+    if (mat > 0) {
+        o_muptr = reserve(mu_ptr.size() * sizeof(int));
+        o_muent = reserve(mu_ent.size() * sizeof(int2));
+        o_mvptr = reserve(mv_ptr.size() * sizeof(int));
+        o_mvent = reserve(mv_ent.size() * sizeof(int2));
+    }
+    pl->tables_bytes = off;
+    if (cudaMalloc(&pl->d_tables, pl->tables_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete pl;
+        return FMM_ERR_OOM;
+    }
+    char *base = (char *)pl->d_tables;
+    g.u_ptr = (const int *)(base + o_uptr);
+    g.u_ent = (const int2 *)(base + o_uent);
+    g.v_ptr = (const int *)(base + o_vptr);
+    g.v_ent = (const int2 *)(base + o_vent);
+    g.w_ptr = (const int *)(base + o_wptr);
+    g.w_ent = (const int4 *)(base + o_went);
+    g.w_row_nnz = (const int *)(base + o_wrow);
+    std::vector<char> host(pl->tables_bytes, 0);
+    auto put = [&](size_t o2, const void *src, size_t bytes) { if (bytes) std::memcpy(host.data() + o2, src, bytes); };
+    put(o_uptr, u_ptr.data(), u_ptr.size() * sizeof(int));
+    put(o_uent, u_ent.data(), u_ent.size() * sizeof(int2));
+    put(o_vptr, v_ptr.data(), v_ptr.size() * sizeof(int));
+    put(o_vent, v_ent.data(), v_ent.size() * sizeof(int2));
+    put(o_wptr, w_ptr.data(), w_ptr.size() * sizeof(int));
+    put(o_went, w_ent.data(), w_ent.size() * sizeof(int4));
+    put(o_wrow, w_row.data(), w_row.size() * sizeof(int));
+    if (mat > 0) {
+        put(o_muptr, mu_ptr.data(), mu_ptr.size() * sizeof(int));
+        put(o_muent, mu_ent.data(), mu_ent.size() * sizeof(int2));
+        put(o_mvptr, mv_ptr.data(), mv_ptr.size() * sizeof(int));
+        put(o_mvent, mv_ent.data(), mv_ent.size() * sizeof(int2));
+        pl->d_mat_u_ptr = (const int *)(base + o_muptr);
+        pl->d_mat_u_ent = (const int2 *)(base + o_muent);
+        pl->d_mat_v_ptr = (const int *)(base + o_mvptr);
+        pl->d_mat_v_ent = (const int2 *)(base + o_mvent);
+        pl->mat_outputs = (int64_t)mu.size();
+    }
+    put(o_geom, &g, sizeof(F64Geom));
+    if (cudaMemcpy(pl->d_tables, host.data(), pl->tables_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan_memory(pl);
+        delete pl;
+        return FMM_ERR_CUDA;
+    }
+
+    // Workspace: [error int][pad][task counter u64][chain counters] then the
+    // materialized operands.
+    const size_t chain_count = (size_t)P * P * (size_t)tiles;
+    pl->counters_bytes = align_up(16 + chain_count * sizeof(unsigned), 256);
+    size_t ws = pl->counters_bytes;
+    size_t o_sa = 0, o_sb = 0, o_ta = 0, o_tb = 0;
+    if (mat > 0) {
+        const size_t bytes = (size_t)pl->nsub * (size_t)pl->b_src * (size_t)pl->b_src * sizeof(double);
+        o_sa = ws; ws = align_up(ws + bytes, 256);
+        o_sb = ws; ws = align_up(ws + bytes, 256);
+        if (mat >= 2) {  // level mat-1 output; levels alternate between it and the final buffer
+            const size_t b1 = (size_t)(pl->n_core / ipow(p, mat - 1));
+            const size_t tbytes = (size_t)ipow(R, mat - 1) * b1 * b1 * sizeof(double);
+            o_ta = ws; ws = align_up(ws + tbytes, 256);
+            o_tb = ws; ws = align_up(ws + tbytes, 256);
+        }
+    }
+    pl->ws_bytes = ws;
+    if (cudaMalloc(&pl->d_ws, ws) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan_memory(pl);
+        delete pl;
+        return FMM_ERR_OOM;
+    }
+    char *wsb = (char *)pl->d_ws;
+    pl->d_error = (int *)wsb;
+    pl->d_task_counter = (unsigned long long *)(wsb + 8);
+    pl->d_chain = (unsigned *)(wsb + 16);
+    if (mat > 0) {
+        pl->d_SA = (double *)(wsb + o_sa);
+        pl->d_SB = (double *)(wsb + o_sb);
+        if (mat >= 2) {
+            pl->d_TA = (double *)(wsb + o_ta);
+            pl->d_TB = (double *)(wsb + o_tb);
+        }
+    }
+    if (cudaMemset(pl->d_ws, 0, pl->counters_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan_memory(pl);
+        delete pl;
+        return FMM_ERR_CUDA;
+    }
+
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
+    const int per_sm = fmm::f64_kernel_ctas_per_sm();
+    if (per_sm <= 0) {
+        cudaGetLastError();
+        free_plan_memory(pl);
+        delete pl;
+        return FMM_ERR_CUDA;
+    }
+    pl->grid = (int)std::min<long long>(pl->total_tasks, (long long)sms * per_sm);
+    if (pl->grid < 1) pl->grid = 1;
+    *out = pl;
+    return FMM_OK;
+}
+
+extern "C" fmm_status_t fmm_plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
+                                        fmm_dtype_t dtype) {
+    return fmm_plan_create_ex(out, n, algo, depth, dtype, nullptr);
+}
+
+namespace {
+
+const F64Geom *dev_geom(const fmm_plan *pl) { return (const F64Geom *)pl->d_tables; }
+
+// Enqueues the counter reset and the materialization pass of one plan.
+fmm_status_t prepare(const fmm_plan *pl, const double *A, const double *B, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(pl->d_ws, 0, pl->counters_bytes, st);
+    if (e != cudaSuccess) return FMM_ERR_CUDA;
+    if (pl->poison) {
+        e = cudaMemsetAsync(pl->d_chain, 0xFF, sizeof(unsigned), st);
+        if (e != cudaSuccess) return FMM_ERR_CUDA;
+    }
+    // Level lev reads level lev-1 (level 0 = the n_core x n_core corner of the
+    // operand, ld n) and writes R^lev matrices of size n_core / p^lev; the last
+    // level lands in d_SA / d_SB, earlier ones alternate with d_TA / d_TB.
+    for (int side = 0; side < 2; ++side) {
+        const double *src = side == 0 ? A : B;
+        double *fin = side == 0 ? pl->d_SA : pl->d_SB;
+        double *tmp = side == 0 ? pl->d_TA : pl->d_TB;
+        const int *ptr = side == 0 ? pl->d_mat_u_ptr : pl->d_mat_v_ptr;
+        const int2 *ent = side == 0 ? pl->d_mat_u_ent : pl->d_mat_v_ent;
+        long long ld_in = pl->n, b_in = pl->n_core;
+        for (int lev = 1; lev <= pl->mat_levels; ++lev) {
+            double *dst = ((pl->mat_levels - lev) % 2 == 0) ? fin : tmp;
+            const long long b_out = b_in / pl->p;
+            e = fmm::launch_materialize_level(src, ld_in, lev == 1 ? 0 : b_in * b_in, (int)ipow(pl->R, lev - 1), b_out,
+                                              pl->p, pl->R, ptr, ent, dst, st);
+            if (e != cudaSuccess) return FMM_ERR_CUDA;
+            src = dst;
+            ld_in = b_out;
+            b_in = b_out;
+        }
+    }
+    return FMM_OK;
+}
+
+F64Problem problem_of(const fmm_plan *pl, const double *A, const double *B, double *C, long long begin) {
+    F64Problem pr{};
+    pr.g = dev_geom(pl);
+    pr.A = A; pr.B = B; pr.C = C;
+    pr.SA = pl->mat_levels > 0 ? pl->d_SA : A;
+    pr.SB = pl->mat_levels > 0 ? pl->d_SB : B;
+    pr.chain = pl->d_chain;
+    pr.task_begin = begin;
+    return pr;
+}
+
+}  // namespace
+
+extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const double *B, double *C, void *stream) {
+    if (!pl || !A || !B || !C) return FMM_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    fmm_status_t s = prepare(pl, A, B, st);
+    if (s != FMM_OK) return s;
+    F64Launch<1> L{};
+    L.nprobs = 1;
+    L.total_tasks = pl->total_tasks;
+    L.task_counter = pl->d_task_counter;
+    L.error = pl->d_error;
+    L.timeout_ns = (long long)(pl->timeout_s * 1e9);
+    L.probs[0] = problem_of(pl, A, B, C, 0);
+    return cuda_status(fmm::launch_f64_single(L, pl->grid, st));
+}
+
+extern "C" fmm_status_t fmm_gemm_host(fmm_plan_t *pl, const double *hA, const double *hB, double *hC, void *stream) {
+    if (!pl || !hA || !hB || !hC) return FMM_ERR_INVALID;
+    const size_t bytes = (size_t)pl->n * (size_t)pl->n * sizeof(double);
+    if (!pl->d_hostA) {
+        if (cudaMalloc(&pl->d_hostA, bytes) != cudaSuccess || cudaMalloc(&pl->d_hostB, bytes) != cudaSuccess ||
+            cudaMalloc(&pl->d_hostC, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            if (pl->d_hostA) cudaFree(pl->d_hostA);
+            if (pl->d_hostB) cudaFree(pl->d_hostB);
+            if (pl->d_hostC) cudaFree(pl->d_hostC);
+            pl->d_hostA = pl->d_hostB = pl->d_hostC = nullptr;
+            return FMM_ERR_OOM;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(pl->d_hostA, hA, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (cudaMemcpyAsync(pl->d_hostB, hB, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FMM_ERR_CUDA;
+    fmm_status_t s = fmm_gemm(pl, pl->d_hostA, pl->d_hostB, pl->d_hostC, stream);
+    if (s != FMM_OK) return s;
+    if (cudaMemcpyAsync(hC, pl->d_hostC, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return FMM_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+extern "C" fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double *const *A, const double *const *B,
+                                         double *const *C, int count, void *stream) {
+    if (count < 0 || (count > 0 && (!plans || !A || !B || !C))) return FMM_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i)
+        if (!plans[i] || !A[i] || !B[i] || !C[i] || plans[i]->dtype != FMM_F64) return FMM_ERR_INVALID;
+    for (int i0 = 0; i0 < count; i0 += fmm::kMaxBatchPerLaunch) {
+        const int cnt = std::min(count - i0, fmm::kMaxBatchPerLaunch);
+        // The first plan of each chunk owns the shared task counter / error word.
+        F64Launch<fmm::kMaxBatchPerLaunch> *L = new (std::nothrow) F64Launch<fmm::kMaxBatchPerLaunch>();
+        if (!L) return FMM_ERR_OOM;
+        long long begin = 0;
+        int grid = 0;
+        for (int k = 0; k < cnt; ++k) {
+            const fmm_plan *pl = plans[i0 + k];
+            fmm_status_t s = prepare(pl, A[i0 + k], B[i0 + k], st);
+            if (s != FMM_OK) { delete L; return s; }
+            L->probs[k] = problem_of(pl, A[i0 + k], B[i0 + k], C[i0 + k], begin);
+            begin += pl->total_tasks;
+            grid = std::max(grid, pl->grid);
+        }
+        const fmm_plan *lead = plans[i0];
+        L->nprobs = cnt;
+        L->total_tasks = begin;
+        L->task_counter = lead->d_task_counter;
+        L->error = lead->d_error;
+        L->timeout_ns = (long long)(lead->timeout_s * 1e9);
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lead->device);
+        grid = (int)std::min<long long>(begin, (long long)sms * fmm::f64_kernel_ctas_per_sm());
+        if (grid < 1) grid = 1;
+        cudaError_t e = fmm::launch_f64_batch(*L, grid, st);
+        delete L;
+        if (e != cudaSuccess) return FMM_ERR_CUDA;
+    }
+    return FMM_OK;
+}
+
+extern "C" fmm_status_t fmm_sync_status(const fmm_plan_t *pl, void *stream) {
+    if (!pl) return FMM_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, pl->d_error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FMM_ERR_CUDA;
+    if (err != fmm::kDevOk) {
+        const int zero = 0;
+        cudaMemcpy(pl->d_error, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return FMM_ERR_TIMEOUT;
+    }
+    return FMM_OK;
+}
+
+extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t *info) {
+    if (!pl || !info) return FMM_ERR_INVALID;
+    info->n = pl->n;
+    info->p = pl->p;
+    info->depth = pl->depth;
+    info->P = pl->P;
+    info->R_total = pl->R_total;
+    info->m = pl->m;
+    info->n_core = pl->n_core;
+    info->tasks = pl->total_tasks;
+    info->materialized_levels = pl->mat_levels;
+    info->flops_leaf = pl->flops_leaf;
+    info->flops_executed = pl->flops_exec;
+    info->workspace_bytes = pl->ws_bytes;
+    return FMM_OK;
+}
+
+extern "C" size_t fmm_plan_workspace_bytes(const fmm_plan_t *pl) { return pl ? pl->ws_bytes : 0; }
+
+extern "C" void fmm_plan_destroy(fmm_plan_t *pl) {
+    if (!pl) return;
+    free_plan_memory(pl);
+    delete pl;
+}

@@ -1,0 +1,92 @@
+// Internal declarations shared by the host planner and the CUDA kernels of the
+// fast-matrix-multiplication library.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fmm {
+
+// CTA tile of the FP64 leaf kernel (rows x cols of a product tile, K slab).
+constexpr int kBM = 128;
+constexpr int kBN = 128;
+constexpr int kBK = 16;
+constexpr int kThreads = 256;
+// Upper bound on the number of blocks combined into one operand (nonzeros of a
+// flattened U or V column) and on the destinations of one product (nonzeros
+// of a flattened W column).
+constexpr int kMaxTerms = 256;
+
+// Device error codes written to the plan's error word.
+enum : int { kDevOk = 0, kDevTimeout = 1 };
+
+// Geometry and coefficient tables of one plan, resident in device memory.
+// "Core" tasks compute one kBM x kBN tile of one leaf product; peel tasks fix
+// up the trailing n - n_core rows/columns.
+struct F64Geom {
+    long long n;           // full problem size
+    long long m;           // leaf block size
+    long long n_core;      // P * m
+    long long ld_src_a;    // leading dimension of the core-task operand sources
+    long long ld_src_b;
+    long long sub_stride_a;  // elements between consecutive materialized sub-problems
+    long long sub_stride_b;
+    int P;                 // blocks per side of C (p^depth)
+    int P_src;             // blocks per side of a core-task source (p^(depth - materialized))
+    int R_src;             // products per sub-problem (R^(depth - materialized))
+    int nsub;              // sub-problems (R^materialized)
+    int tiles_m, tiles_n;  // tiles per leaf block
+    // CSC over products: U/V columns are indexed by the sub-problem-local
+    // product, W columns by the global product s * R_src + r.
+    const int *u_ptr;
+    const int2 *u_ent;  // {source block, coefficient}
+    const int *v_ptr;
+    const int2 *v_ent;
+    const int *w_ptr;
+    const int4 *w_ent;  // {C block, coefficient, position among the row's nonzeros, 0}
+    const int *w_row_nnz;
+    long long tasks_core, tasks_right, tasks_bottom, tasks_rankq;
+    int rb_tm, rb_tn;  // right-border tiling (n_core x q)
+    int bb_tm, bb_tn;  // bottom-border tiling (q x n)
+};
+
+struct F64Problem {
+    const F64Geom *g;    // device pointer
+    const double *A;     // original operands (ld = n)
+    const double *B;
+    const double *SA;    // sources of core tasks (A itself, or materialized S)
+    const double *SB;
+    double *C;           // output (ld = n)
+    unsigned *chain;     // [P*P][tiles] post-add ordering counters
+    long long task_begin;
+};
+
+template <int MAXP>
+struct F64Launch {
+    int nprobs;
+    long long total_tasks;
+    unsigned long long *task_counter;
+    int *error;
+    long long timeout_ns;
+    F64Problem probs[MAXP];
+};
+
+constexpr int kMaxBatchPerLaunch = 128;
+
+// Kernel launchers (fmm_f64.cu).  Return cudaSuccess or the launch error.
+cudaError_t launch_f64_single(const F64Launch<1> &L, int grid, cudaStream_t s);
+cudaError_t launch_f64_batch(const F64Launch<kMaxBatchPerLaunch> &L, int grid, cudaStream_t s);
+int f64_kernel_ctas_per_sm();  // resident CTAs per SM of the leaf kernel (0 on error)
+size_t f64_kernel_smem_bytes();
+
+// Pre-addition pass for one materialized recursion level (fmm_f64.cu).
+// Input matrix c (c < n_in) starts at in + c * in_stride with leading
+// dimension ld_in and is split into p x p blocks of size b_out; output
+// c * R + s is the b_out x b_out matrix sum_e coef_e * block(blk_e) over the
+// CSC column s (s < R) of the one-level coefficient matrix, stored densely at
+// out + (c * R + s) * b_out^2.
+cudaError_t launch_materialize_level(const double *in, long long ld_in, long long in_stride, int n_in,
+                                     long long b_out, int p, int R, const int *ptr, const int2 *ent, double *out,
+                                     cudaStream_t s);
+
+}  // namespace fmm

@@ -1,0 +1,121 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+declared symbol, carries the paper's tables, and validates algorithms exactly."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from golden import algos
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fmm():
+    from paper_2312_12732_gb300 import _build
+
+    _build.build()
+    import paper_2312_12732_gb300 as m
+
+    return m
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(fmm_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(fmm):
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2312_12732_gb300", "libfmm.so"))
+    names = declared_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    bound = {s[0] for s in fmm._binding.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def test_status_strings(fmm):
+    for s in range(8):
+        assert fmm.fmm_status_string(s)
+    assert fmm.fmm_status_string(2) == "algorithm fails the Brent equations"
+
+
+@pytest.mark.parametrize("name,golden", [("strassen", algos.paper_strassen), ("winograd", algos.winograd),
+                                         ("strassen1969", algos.strassen1969), ("laderman", algos.laderman),
+                                         ("classic2", algos.classic_from_graph)])
+def test_builtin_tables_equal_golden(fmm, name, golden):
+    a = fmm.fmm_algo_builtin(name)
+    p, U, V, W = golden()
+    assert a.p == p
+    assert np.array_equal(a.U, U) and np.array_equal(a.V, V) and np.array_equal(a.W, W)
+    assert fmm.fmm_algo_brent_mismatches(a) == 0
+
+
+def test_unknown_builtin(fmm):
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_algo_builtin("bini")
+    assert e.value.status == 7
+
+
+def test_brent_rejects_paper_ct_without_relabel(fmm):
+    a, b, ct, _ = algos.paper_strassen_as_printed()
+    assert fmm.fmm_algo_brent_mismatches(fmm.Algo(2, a, b, ct)) == 8
+    W = fmm.fmm_algo_from_transposed_c(2, ct)
+    # the printed rows C0, C2, C1, C3 are exactly C transposed, row-major
+    assert fmm.fmm_algo_brent_mismatches(fmm.Algo(2, a, b, W)) == 0
+    assert np.array_equal(W, algos.paper_strassen()[3])
+
+
+def test_brent_rejects_single_changes(fmm):
+    s = fmm.fmm_algo_builtin("strassen")
+    for X in ("U", "V", "W"):
+        T = getattr(s, X)
+        for idx in np.ndindex(*T.shape):
+            M = {k: getattr(s, k).copy() for k in "UVW"}
+            M[X][idx] += 1
+            assert fmm.fmm_algo_brent_mismatches(fmm.Algo(2, M["U"], M["V"], M["W"])) > 0
+
+
+def test_compose_matches_reindexed_kronecker(fmm):
+    s = fmm.fmm_algo_builtin("strassen")
+    lad = fmm.fmm_algo_builtin("laderman")
+    for a1, a2, g1, g2 in ((s, s, algos.paper_strassen(), algos.paper_strassen()),
+                           (s, lad, algos.paper_strassen(), algos.laderman())):
+        c = fmm.fmm_algo_compose(a1, a2)
+        p, U, V, W = algos.kron_compose(g1, g2)
+        assert c.p == p and np.array_equal(c.U, U) and np.array_equal(c.V, V) and np.array_equal(c.W, W)
+        assert fmm.fmm_algo_brent_mismatches(c) == 0
+    assert fmm.algorithm("strassen", 2).R == 49
+
+
+def test_plan_create_rejects_bad_requests_before_touching_the_gpu(fmm):
+    s = fmm.fmm_algo_builtin("strassen")
+    bad = fmm.Algo(2, s.U, s.V, s.W[[0, 2, 1, 3]])
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_plan_create(64, bad, 1)
+    assert e.value.status == 2
+    for n, depth in ((0, 1), (64, -1), (3, 2)):
+        with pytest.raises(fmm.FmmError) as e:
+            fmm.fmm_plan_create(n, s, depth)
+        assert e.value.status == 1
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_plan_create(64, s, 1, schedule="hybrid", materialize_levels=2)
+    assert e.value.status == 1
+
+
+def test_binding_requires_built_library(monkeypatch, tmp_path):
+    from paper_2312_12732_gb300 import _binding
+
+    monkeypatch.setattr(_binding, "_lib", None)
+    monkeypatch.setattr(_binding, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _binding.lib()
