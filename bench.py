@@ -1,0 +1,458 @@
+#!/usr/bin/env python
+"""Benchmark: effective FP64 TFLOP/s (2 n^3 / t) of a fast bilinear algorithm
+against the classic product, on one GB300.
+
+Default workload: C = A B with n = 8192 FP64 operands, entries uniform[-1, 1]
+(SplitMix64 seeds 1 and 2), Strassen's algorithm as printed in the paper
+(Section 2) at the default depth, the planner's default schedule.  One step is
+one fmm_gemm call: pre-additions, leaf products and post-additions, i.e. the
+whole hot path.  Inputs (3 x 512 MiB) are larger than L2 (129 MB), so no
+flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W]       # one JSON line
+    python bench.py --impl reference ...                      # CPU oracle arm
+    python bench.py --sweep                                   # per-algorithm table
+
+With N > 1 (launched by torchrun) every rank runs an independent replica of
+the workload on its own GPU (the product does not shard across GPUs): the
+value is the multiplications of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "effective FP64 TFLOP/s (2n³/t), fast algorithm vs classic GEMM, same GB300"
+NOMINAL_FP64_TFLOPS = 1.25     # GB300 nominal FP64 (= FP64 tensor) rate
+NOMINAL_BF16_TFLOPS = 2250.0   # GB300 nominal dense bf16 rate
+FALLBACK_BF16_TFLOPS = 1900.0  # recipe fallback when no measured peaks exist
+L2_BYTES = 129e6
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--algo", default="strassen", help="built-in name; suffix ^2 for its Kronecker square")
+    ap.add_argument("--depth", type=int, default=3)
+    ap.add_argument("--schedule", default="auto", choices=["auto", "fused", "hybrid"])
+    ap.add_argument("--materialize-levels", type=int, default=0)
+    ap.add_argument("--kind", default="uniform", choices=["uniform", "normal", "integer"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-classic", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=4096, help="size of the CPU-oracle sample")
+    ap.add_argument("--sweep", action="store_true", help="print one JSON line per algorithm/depth/schedule")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- helpers
+
+
+def workload_name(a) -> str:
+    return f"{a.algo.replace('^2', 'x2')}_d{a.depth}_n{a.n}_{a.kind}_fp64"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def fp64_peak_tflops():
+    """FP64 tensor peak: the measured bf16 burst peak times the nominal FP64:bf16 ratio."""
+    pk = measured_peaks()
+    if pk and pk.get("bf16_tflops"):
+        return pk["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS, \
+            "of measured (MEASURED_PEAKS.json bf16 burst x nominal FP64/bf16 ratio 1.25/2250)"
+    return FALLBACK_BF16_TFLOPS * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS, \
+        "of fallback (1.9 PFLOP/s bf16 x nominal FP64/bf16 ratio 1.25/2250)"
+
+
+def profile_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch recorded by an ncu capture in profiles/, if it was
+    taken on the current kernel source and this workload; else None."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2312_12732_gb300", "csrc", "fmm_f64.cu")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith(".md"):
+            continue
+        kv = {}
+        for line in open(os.path.join(pdir, fn)):
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source_sha256_16") == digest:
+            try:
+                return float(kv["dram_bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable: nvidia-smi gave no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle arm
+
+
+def cpu_oracle_run(a, n_sample: int, reps: int):
+    """Times the oracle's recursive evaluation of the same algorithm and depth on
+    an n_sample x n_sample sample of the workload distribution (all host cores)."""
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    import oracle
+    import paper_2312_12732_gb300 as fmm
+    from paper_2312_12732_gb300 import inputs
+
+    oracle.build()
+    algo = make_algo(fmm, a.algo)
+    A, B = inputs.operands(n_sample, a.kind, seed=1)
+    depth = a.depth
+    while depth > 0 and algo.p ** depth > n_sample:
+        depth -= 1
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.bilinear(A, B, algo.p, algo.U, algo.V, algo.W, depth)
+        times.append(time.perf_counter() - t0)
+    cores = int(os.environ["OMP_NUM_THREADS"])
+    return times, cores, depth
+
+
+def run_reference(a):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    times, cores, depth = cpu_oracle_run(a, a.cpu_n, a.warmup + a.steps)
+    timed = times[a.warmup:] if len(times) > a.warmup else times
+    t = statistics.mean(timed)
+    value = 2.0 * a.cpu_n ** 3 / t / 1e12
+    sample = (f"oracle bilinear evaluation ({a.algo}, depth {depth}) of one {a.cpu_n}x{a.cpu_n} product "
+              f"per step, {a.kind} entries, {cores} OpenMP threads; the GPU arm's n={a.n} product is "
+              f"sampled at this size to bound CPU time")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "sample_n": a.cpu_n},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def make_algo(fmm, name):
+    if name.endswith("^2"):
+        return fmm.algorithm(name[:-2], 2)
+    return fmm.fmm_algo_builtin(name)
+
+
+def time_plan(torch, fmm, plan, dA, dB, dC, warmup, steps, dist=None, stream=None):
+    """(ms per step over the timed region, mean leaf-kernel ms per launch)."""
+    stream = stream or torch.cuda.current_stream()
+    for _ in range(warmup):
+        fmm.fmm_gemm(plan, dA, dB, dC, stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    leaf = []
+    e0.record(stream)
+    for _ in range(steps):
+        fmm.fmm_gemm(plan, dA, dB, dC, stream)
+        leaf.append(fmm.fmm_plan_last_kernel_ms(plan)[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    st = fmm.fmm_sync_status(plan, stream)
+    if st != 0:
+        raise RuntimeError("device status after timed region: " + fmm.fmm_status_string(st))
+    return e0.elapsed_time(e1) / steps, statistics.mean(leaf)
+
+
+def run_sweep(a):
+    import torch
+
+    import paper_2312_12732_gb300 as fmm
+    from paper_2312_12732_gb300 import _build, inputs
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    configs = [("strassen", 0, "auto", 0)]
+    for algo in ("strassen", "winograd"):
+        for d in (1, 2, 3):
+            configs += [(algo, d, "fused", 0), (algo, d, "auto", 0)]
+    configs += [("strassen^2", 1, "fused", 0), ("strassen^2", 1, "auto", 0), ("strassen^2", 2, "auto", 0)]
+    n = a.n
+    A, B = inputs.operands(n, a.kind, seed=1)
+    dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    dC = torch.empty_like(dA)
+    rows = [(n, c) for c in configs]
+    if a.n == 8192:
+        rows += [(6912, ("laderman", d, s, 0)) for d in (1, 2) for s in ("fused", "auto")]
+        rows += [(6912, ("strassen", 0, "auto", 0))]
+    cache = {n: (dA, dB, dC)}
+    for nn, (algo_name, depth, sched, ml) in rows:
+        if nn not in cache:
+            A2, B2 = inputs.operands(nn, a.kind, seed=1)
+            xA2 = torch.from_numpy(A2).to(dev)
+            cache = {nn: (xA2, torch.from_numpy(B2).to(dev), torch.empty_like(xA2))}
+        xA, xB, xC = cache[nn]
+        algo = make_algo(fmm, algo_name)
+        plan = fmm.fmm_plan_create(nn, algo, depth, schedule=sched, materialize_levels=ml, record_kernel_time=True)
+        ms, leaf = time_plan(torch, fmm, plan, xA, xB, xC, 1, 2)
+        info = plan.info()
+        print(json.dumps({"n": nn, "algo": algo_name, "depth": depth, "schedule": sched,
+                          "materialized": info["materialized_levels"], "ms": round(ms, 3),
+                          "leaf_ms": round(leaf, 3), "eff_tflops": round(2.0 * nn ** 3 / ms / 1e9, 4),
+                          "exec_tflops_leaf_kernel": round(info["flops_leaf"] / leaf / 1e9, 4)}), flush=True)
+        fmm.fmm_plan_destroy(plan)
+    return 0
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import paper_2312_12732_gb300 as fmm
+    from paper_2312_12732_gb300 import _build, inputs
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist_mod
+
+        torch.cuda.set_device(local)
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+
+    n = a.n
+    algo = make_algo(fmm, a.algo)
+    A, B = inputs.operands(n, a.kind, seed=1)
+    dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    dC = torch.empty_like(dA)
+    plan = fmm.fmm_plan_create(n, algo, a.depth, schedule=a.schedule, materialize_levels=a.materialize_levels,
+                               record_kernel_time=True)
+    info = plan.info()
+
+    dmma_peak, dfma_peak = fmm.fmm_measure_fp64_peak()
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    with sampler:
+        ms, leaf_ms = time_plan(torch, fmm, plan, dA, dB, dC, max(a.warmup, 3), a.steps, dist)
+    clocks = sampler.summary()
+
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops_eff = 2.0 * n ** 3
+    value = flops_eff * ws / (ms * 1e-3) / 1e12
+
+    # sanity: a few sampled entries against a float64 torch dot product on the GPU
+    rows = torch.arange(0, n, max(1, n // 16), device=dev)
+    ref = dA[rows] @ dB[:, :64]
+    err = (dC[rows, :64] - ref).abs().max().item() / (n * dA.abs().max().item() * dB.abs().max().item())
+
+    classic = None
+    if not a.no_classic and a.depth > 0:
+        p0 = fmm.fmm_plan_create(n, algo, 0, record_kernel_time=True)
+        ms0, leaf0 = time_plan(torch, fmm, p0, dA, dB, dC, 1, max(2, a.steps // 2), dist)
+        classic = {"value": flops_eff / (ms0 * 1e-3) / 1e12, "ms_per_step": ms0, "leaf_kernel_ms": leaf0}
+        fmm.fmm_plan_destroy(p0)
+        fmm.fmm_gemm(plan, dA, dB, dC)  # leave the fast result in C
+        torch.cuda.synchronize()
+
+    e2e = None
+    if not a.no_e2e:
+        hA = torch.from_numpy(A).pin_memory()
+        hB = torch.from_numpy(B).pin_memory()
+        hC = torch.empty_like(hA).pin_memory()
+        fmm.fmm_gemm_host(plan, hA, hB, hC)  # allocates the plan's host-path buffers
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        k_e2e = max(2, a.steps // 2)
+        for _ in range(k_e2e):
+            fmm.fmm_gemm_host(plan, hA, hB, hC)
+        t1 = time.perf_counter()
+        te = (t1 - t0) / k_e2e
+        if dist is not None:
+            tt = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": flops_eff * ws / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * n * n * 8,
+               "d2h_bytes_per_step": n * n * 8, "ms_per_step": te * 1e3, "steps": k_e2e,
+               "path": "fmm_gemm_host (pinned host buffers, copies inside the timed region)"}
+
+    peak, peak_note = fp64_peak_tflops()
+    nc = info["n_core"]
+    q = n - nc
+    contraction_flops = info["flops_leaf"] + 2.0 * (nc * q * n + q * n * n + nc * nc * q)
+    achieved = contraction_flops / (leaf_ms * 1e-3) / 1e12
+    kernel_name = "fmm_f64_kernel"
+    traffic = profile_traffic(kernel_name, workload_name(a))
+    roofline = {"bound": "tensor", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_note": peak_note,
+                "algorithmic_flops_per_launch": contraction_flops, "avg_launch_ms": leaf_ms,
+                "kernel_share_of_step": leaf_ms / ms if ms > 0 else None,
+                "dmma_peak_measured_here": dmma_peak, "dfma_peak_measured_here": dfma_peak,
+                "frac_of_dmma_measured_here": achieved / dmma_peak if dmma_peak else None}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        times, cores, cdepth = cpu_oracle_run(a, a.cpu_n, 1)
+        t = times[0]
+        cpu = {"value": 2.0 * a.cpu_n ** 3 / t / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle bilinear ({a.algo}, depth {cdepth}) on one {a.cpu_n}x{a.cpu_n} {a.kind} "
+                         f"product, {t:.1f} s on {cores} threads"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": a.steps,
+        "warmup": max(a.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "n": n, "algorithm": a.algo, "depth": a.depth,
+                   "schedule": a.schedule, "materialized_levels": info["materialized_levels"],
+                   "leaf_m": info["m"], "products": info["R_total"], "entries": a.kind,
+                   "l2": "inputs 3 x %.0f MiB > L2 (129 MB), no flush" % (n * n * 8 / 2 ** 20),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "classic_depth0": classic,
+        "speedup_vs_classic": (value / ws) / classic["value"] if classic else None,
+        "normalised_error_sampled": err,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": a.steps * (1 + 2 * info["materialized_levels"]),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "flops_executed_per_step": info["flops_executed"],
+        "executed_tflops": info["flops_executed"] / (ms * 1e-3) / 1e12,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    fmm.fmm_plan_destroy(plan)
+    if dist is not None:
+        dist.destroy_process_group()
+    _ = np
+    return 0
+
+
+def main(argv=None):
+    a = parse_args(argv)
+    if a.impl == "reference":
+        return run_reference(a)
+    if a.sweep:
+        return run_sweep(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

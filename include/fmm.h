@@ -86,6 +86,8 @@ typedef struct {
     int debug_poison_chain;  /* testing only: 1 = after the per-call reset, set one
                                 post-addition ordering counter to a value no task
                                 writes, so that its waiters time out */
+    int record_kernel_time;  /* 1 = record CUDA events around each call's work on
+                                its stream (see fmm_plan_last_kernel_ms) */
 } fmm_plan_options_t;
 
 /* Read-only description of a plan (all sizes in elements). */
@@ -173,6 +175,20 @@ fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double *const *A,
  * FMM_OK, FMM_ERR_TIMEOUT (a bounded wait expired; C is unspecified) or
  * FMM_ERR_CUDA. */
 fmm_status_t fmm_sync_status(const fmm_plan_t *plan, void *stream);
+
+/* Timing of the most recent fmm_gemm on a plan created with
+ * record_kernel_time = 1: `leaf_ms` is the leaf-product kernel alone,
+ * `total_ms` the whole call (counter reset, materialization, leaf kernel),
+ * both measured with CUDA events on the call's stream.  Waits for the call's
+ * end event.  FMM_ERR_INVALID if timing was not enabled or no call was made. */
+fmm_status_t fmm_plan_last_kernel_ms(const fmm_plan_t *plan, float *leaf_ms, float *total_ms);
+
+/* Calibration, with no counterpart in the paper: measures the FP64
+ * throughput the current device delivers on the leaf kernel's instruction
+ * (mma.sync m16n8k4 f64, "DMMA") and on scalar DFMA, in TFLOP/s, with CUDA
+ * events on `stream` (about 0.1 s of GPU time; allocates and frees a small
+ * scratch buffer).  Blocking.  Either output pointer may be NULL. */
+fmm_status_t fmm_measure_fp64_peak(void *stream, double *dmma_tflops, double *dfma_tflops);
 
 /* Describe a plan.  Host-only. */
 fmm_status_t fmm_plan_get_info(const fmm_plan_t *plan, fmm_plan_info_t *info);

@@ -28,6 +28,8 @@ from ._binding import (  # noqa: F401
     fmm_plan_create,
     fmm_plan_destroy,
     fmm_plan_get_info,
+    fmm_plan_last_kernel_ms,
+    fmm_measure_fp64_peak,
     fmm_plan_workspace_bytes,
     fmm_status_string,
     fmm_sync_status,

@@ -33,7 +33,8 @@ class fmm_algo_t(ctypes.Structure):
 
 class fmm_plan_options_t(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int), ("materialize_levels", ctypes.c_int), ("ozaki_slices", ctypes.c_int),
-                ("wait_timeout_s", ctypes.c_double), ("debug_poison_chain", ctypes.c_int)]
+                ("wait_timeout_s", ctypes.c_double), ("debug_poison_chain", ctypes.c_int),
+                ("record_kernel_time", ctypes.c_int)]
 
 
 class fmm_plan_info_t(ctypes.Structure):
@@ -65,6 +66,10 @@ SIGNATURES = [
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.c_int, ctypes.c_void_p]),
     ("fmm_sync_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("fmm_plan_last_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                                               ctypes.POINTER(ctypes.c_float)]),
+    ("fmm_measure_fp64_peak", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double)]),
     ("fmm_plan_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fmm_plan_info_t)]),
     ("fmm_plan_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
     ("fmm_plan_destroy", None, [ctypes.c_void_p]),
@@ -182,11 +187,11 @@ class Plan:
 
 def fmm_plan_create(n: int, algo: Algo, depth: int, dtype: str = "f64", schedule: str = "auto",
                     materialize_levels: int = 0, ozaki_slices: int = 0, wait_timeout_s: float = 0.0,
-                    debug_poison_chain: int = 0) -> Plan:
+                    debug_poison_chain: int = 0, record_kernel_time: bool = False) -> Plan:
     h = ctypes.c_void_p()
     a = algo.c_struct()
     opts = fmm_plan_options_t(SCHEDULES[schedule], int(materialize_levels), int(ozaki_slices),
-                              float(wait_timeout_s), int(debug_poison_chain))
+                              float(wait_timeout_s), int(debug_poison_chain), int(bool(record_kernel_time)))
     _check(lib().fmm_plan_create_ex(ctypes.byref(h), int(n), ctypes.byref(a), int(depth), DTYPES[dtype],
                                     ctypes.byref(opts)), f"fmm_plan_create(n={n}, {algo}, depth={depth})")
     return Plan(h.value, int(n), algo, int(depth), dtype)
@@ -202,6 +207,21 @@ def fmm_plan_get_info(plan: Plan) -> dict:
     info = fmm_plan_info_t()
     _check(lib().fmm_plan_get_info(plan.handle, ctypes.byref(info)), "fmm_plan_get_info")
     return {k: getattr(info, k) for k, _ in fmm_plan_info_t._fields_}
+
+
+def fmm_plan_last_kernel_ms(plan: Plan):
+    """(leaf-kernel ms, whole-call ms) of the plan's most recent fmm_gemm (needs record_kernel_time)."""
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(lib().fmm_plan_last_kernel_ms(plan.handle, ctypes.byref(a), ctypes.byref(b)), "fmm_plan_last_kernel_ms")
+    return float(a.value), float(b.value)
+
+
+def fmm_measure_fp64_peak(stream=None):
+    """(DMMA TFLOP/s, DFMA TFLOP/s) measured on the current device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().fmm_measure_fp64_peak(ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(a), ctypes.byref(b)),
+           "fmm_measure_fp64_peak")
+    return float(a.value), float(b.value)
 
 
 def fmm_plan_workspace_bytes(plan: Plan) -> int:

@@ -34,16 +34,18 @@ constexpr int BM = kBM, BN = kBN, BK = kBK, NT = kThreads;
 constexpr int A_LD = BK + 4;
 constexpr int B_LD = BN + 4;
 
+// Coefficients stay integers on the device: tests on them run on the integer
+// pipe, and only coefficients other than +-1 are ever converted to FP64.
 struct Src {
     const double *ptr;  // element (0, 0) of this source's part of the tile
-    double coef;
+    int coef;
+    int pad;
 };
 struct Dst {
     double *ptr;        // element (0, 0) of the destination tile
     unsigned *chain;    // ordering counter, or nullptr for a single writer
-    double coef;
+    int coef;
     int pos;            // number of contributions that must precede this one
-    int pad;
 };
 
 struct Smem {
@@ -93,10 +95,15 @@ __device__ bool chain_wait(const unsigned *ctr, unsigned target, int *error, lon
     }
 }
 
-// s (+)= coef * v with the fewest FP64 operations: +-1 coefficients are adds.
-__device__ __forceinline__ double combine(double s, double v, double c, bool first) {
-    if (first) return c == 1.0 ? v : (c == -1.0 ? -v : c * v);
-    return c == 1.0 ? s + v : (c == -1.0 ? s - v : fma(c, v, s));
+// Sign flip on the integer pipe (FP64 units are the scarce resource).
+__device__ __forceinline__ double neg(double v) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL);
+}
+
+// s (+)= c * v with the fewest FP64 operations: +-1 coefficients are adds.
+__device__ __forceinline__ double combine(double s, double v, int c, bool first) {
+    if (first) return c == 1 ? v : (c == -1 ? neg(v) : (double)c * v);
+    return c == 1 ? s + v : (c == -1 ? s - v : fma((double)c, v, s));
 }
 
 __device__ __forceinline__ void dmma_16x8x4(double (&d)[4], const double (&a)[2], double b) {
@@ -131,20 +138,20 @@ __device__ void setup_task(Smem &S, const F64Problem &pr, const F64Geom &g, long
             const int2 en = g.u_ent[ua + e];
             const long long br = en.x / g.P_src, bc = en.x % g.P_src;
             S.srcA[e].ptr = SA + (br * m + (long long)ti * BM) * g.ld_src_a + bc * m;
-            S.srcA[e].coef = (double)en.y;
+            S.srcA[e].coef = en.y;
         }
         for (int e = tid; e < nB; e += NT) {
             const int2 en = g.v_ent[vb + e];
             const long long br = en.x / g.P_src, bc = en.x % g.P_src;
             S.srcB[e].ptr = SB + (br * m) * g.ld_src_b + bc * m + (long long)tj * BN;
-            S.srcB[e].coef = (double)en.y;
+            S.srcB[e].coef = en.y;
         }
         for (int e = tid; e < nD; e += NT) {
             const int4 en = g.w_ent[wc + e];
             const long long br = en.x / g.P, bc = en.x % g.P;
             S.dst[e].ptr = pr.C + (br * m + (long long)ti * BM) * n + bc * m + (long long)tj * BN;
             S.dst[e].chain = pr.chain + (long long)en.x * tiles + t;
-            S.dst[e].coef = (double)en.y;
+            S.dst[e].coef = en.y;
             S.dst[e].pos = en.z;
         }
         if (tid == 0) {
@@ -160,8 +167,8 @@ __device__ void setup_task(Smem &S, const F64Problem &pr, const F64Geom &g, long
     if (tid != 0) return;
     S.nA = S.nB = S.nD = 1;
     S.lda = n; S.ldb = n; S.ldc = n;
-    S.srcA[0].coef = S.srcB[0].coef = 1.0;
-    S.dst[0].coef = 1.0;
+    S.srcA[0].coef = S.srcB[0].coef = 1;
+    S.dst[0].coef = 1;
     if (local < g.tasks_right) {  // C[0:nc, nc:n] = A[0:nc, :] B[:, nc:n]
         const int bi = (int)(local / g.rb_tn), bj = (int)(local % g.rb_tn);
         S.srcA[0].ptr = pr.A + (long long)bi * BM * n;
@@ -203,6 +210,36 @@ __device__ void setup_task(Smem &S, const F64Problem &pr, const F64Geom &g, long
     }
 }
 
+// Accumulates one source's 8 values into r[] with the coefficient's sign
+// resolved once per source (uniform across the CTA, so no divergence).
+__device__ __forceinline__ void accumulate8(double (&r)[8], const double (&v)[8], int c, bool first) {
+    if (first) {
+        if (c == 1) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) r[j] = v[j];
+        } else if (c == -1) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) r[j] = neg(v[j]);
+        } else {
+            const double cd = (double)c;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) r[j] = cd * v[j];
+        }
+    } else {
+        if (c == 1) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) r[j] += v[j];
+        } else if (c == -1) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) r[j] -= v[j];
+        } else {
+            const double cd = (double)c;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) r[j] = fma(cd, v[j], r[j]);
+        }
+    }
+}
+
 // Loads the K slab [kk, kk + BK) of both operands, combining the sources.
 __device__ __forceinline__ void load_slab(const Smem &S, int kk, double (&ra)[8], double (&rb)[8]) {
     const int tid = threadIdx.x;
@@ -213,13 +250,13 @@ __device__ __forceinline__ void load_slab(const Smem &S, int kk, double (&ra)[8]
         const long long lda = S.lda;
         for (int e = 0; e < S.nA; ++e) {
             const double *p = S.srcA[e].ptr + kk + c;
-            const double cf = S.srcA[e].coef;
+            double v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int row = r0 + 16 * j;
-                const double v = (kval && row < S.rows) ? __ldg(p + row * lda) : 0.0;
-                ra[j] = combine(ra[j], v, cf, e == 0);
+                v[j] = (kval && row < S.rows) ? __ldg(p + row * lda) : 0.0;
             }
+            accumulate8(ra, v, S.srcA[e].coef, e == 0);
         }
         if (S.nA == 0) {
 #pragma unroll
@@ -233,13 +270,13 @@ __device__ __forceinline__ void load_slab(const Smem &S, int kk, double (&ra)[8]
         const long long ldb = S.ldb;
         for (int e = 0; e < S.nB; ++e) {
             const double *p = S.srcB[e].ptr + (long long)kk * ldb + c;
-            const double cf = S.srcB[e].coef;
+            double v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int row = r0 + 2 * j;
-                const double v = (cval && kk + row < S.K) ? __ldg(p + row * ldb) : 0.0;
-                rb[j] = combine(rb[j], v, cf, e == 0);
+                v[j] = (cval && kk + row < S.K) ? __ldg(p + row * ldb) : 0.0;
             }
+            accumulate8(rb, v, S.srcB[e].coef, e == 0);
         }
         if (S.nB == 0) {
 #pragma unroll
@@ -348,7 +385,10 @@ __global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ 
             __syncthreads();
             if (!S.ok) break;
             const bool first = dst.pos == 0;
-            const double cf = dst.coef;
+            const int cf = dst.coef;
+            const double cfd = (double)cf;  // used only when |cf| != 1
+            // mode: 0 store v, 1 store -v, 2 store cf*v, 3 add, 4 subtract, 5 fma
+            const int mode = first ? (cf == 1 ? 0 : (cf == -1 ? 1 : 2)) : (cf == 1 ? 3 : (cf == -1 ? 4 : 5));
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -364,11 +404,13 @@ __global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ 
                             double *p = dst.ptr + row * ldc + col;
                             const double v = acc[i][j][2 * h + c2];
                             double out;
-                            if (first)
-                                out = cf == 1.0 ? v : (cf == -1.0 ? -v : cf * v);
-                            else {
-                                const double old = __ldcg(p);
-                                out = cf == 1.0 ? old + v : (cf == -1.0 ? old - v : fma(cf, v, old));
+                            switch (mode) {
+                                case 0: out = v; break;
+                                case 1: out = neg(v); break;
+                                case 2: out = cfd * v; break;
+                                case 3: out = __ldcg(p) + v; break;
+                                case 4: out = __ldcg(p) - v; break;
+                                default: out = fma(cfd, v, __ldcg(p)); break;
                             }
                             *p = out;
                         }
@@ -383,28 +425,30 @@ __global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ 
     }
 }
 
-// One materialized recursion level: one thread per (y, x) of a b x b output
-// block and input matrix blockIdx.y; all R outputs of that position.
+// One materialized recursion level.  blockIdx.y selects the input matrix;
+// CTAs stride over rows y of the b x b output blocks and threads over
+// columns x, so every load and store is coalesced and no index needs a
+// division.  All R outputs of a position are formed from the p^2 inputs.
 __global__ void materialize_level_kernel(const double *__restrict__ in, long long ld_in, long long in_stride,
                                          long long b, int p, int R, const int *__restrict__ ptr,
-                                         const int2 *__restrict__ ent, double *__restrict__ out) {
+                                         const int4 *__restrict__ ent, double *__restrict__ out) {
     const long long total = b * b;
-    const long long stride = (long long)gridDim.x * blockDim.x;
     const int c = blockIdx.y;
     const double *src = in + (long long)c * in_stride;
     double *dst = out + (long long)c * R * total;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-        const long long y = e / b, x = e - y * b;
-        for (int s = 0; s < R; ++s) {
-            double acc = 0.0;
-            const int e0 = ptr[s], e1 = ptr[s + 1];
-            for (int k = e0; k < e1; ++k) {
-                const int2 en = ent[k];
-                const long long br = en.x / p, bc = en.x % p;
-                const double v = __ldg(src + (br * b + y) * ld_in + bc * b + x);
-                acc = combine(acc, v, (double)en.y, k == e0);
+    for (long long y = blockIdx.x; y < b; y += gridDim.x) {
+        for (long long x = threadIdx.x; x < b; x += blockDim.x) {
+            const double *pos = src + y * ld_in + x;
+            for (int s = 0; s < R; ++s) {
+                double acc = 0.0;
+                const int e0 = ptr[s], e1 = ptr[s + 1];
+                for (int k = e0; k < e1; ++k) {
+                    const int4 en = ent[k];  // {block row, block col, coefficient, 0}
+                    const double v = __ldg(pos + (long long)en.x * b * ld_in + (long long)en.y * b);
+                    acc = combine(acc, v, en.z, k == e0);
+                }
+                dst[(long long)s * total + y * b + x] = acc;
             }
-            dst[(long long)s * total + e] = acc;
         }
     }
 }
@@ -451,22 +495,20 @@ cudaError_t launch_f64_batch(const F64Launch<kMaxBatchPerLaunch> &L, int grid, c
 }
 
 cudaError_t launch_materialize_level(const double *in, long long ld_in, long long in_stride, int n_in,
-                                     long long b_out, int p, int R, const int *ptr, const int2 *ent, double *out,
+                                     long long b_out, int p, int R, const int *ptr, const int4 *ent, double *out,
                                      cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long total = b_out * b_out;
-    long long bx = (total + 255) / 256;
-    long long cap = (long long)sms * 8 / (n_in > 0 ? n_in : 1);
-    if (cap < 1) cap = 1;
-    if (bx > cap) bx = cap;
+    long long bx = (long long)sms * 8 / (n_in > 0 ? n_in : 1);
+    if (bx > b_out) bx = b_out;
     if (bx < 1) bx = 1;
+    const int threads = b_out >= 256 ? 256 : (int)((b_out + 31) / 32 * 32);
     for (int c0 = 0; c0 < n_in; c0 += 65535) {
         const int cnt = n_in - c0 < 65535 ? n_in - c0 : 65535;
         dim3 grid((unsigned)bx, (unsigned)cnt);
-        materialize_level_kernel<<<grid, 256, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride, b_out, p, R,
-                                                      ptr, ent, out + (long long)c0 * R * total);
+        materialize_level_kernel<<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride, b_out, p,
+                                                          R, ptr, ent, out + (long long)c0 * R * b_out * b_out);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -296,10 +296,13 @@ struct fmm_plan {
     double *d_SA = nullptr, *d_SB = nullptr;  // materialized sources (nullptr when fused)
     double *d_TA = nullptr, *d_TB = nullptr;  // intermediate level (materialized depth >= 2)
     const int *d_mat_u_ptr = nullptr, *d_mat_v_ptr = nullptr;
-    const int2 *d_mat_u_ent = nullptr, *d_mat_v_ent = nullptr;
+    const int4 *d_mat_u_ent = nullptr, *d_mat_v_ent = nullptr;
     int64_t mat_outputs = 0;
     // host-buffer path
     double *d_hostA = nullptr, *d_hostB = nullptr, *d_hostC = nullptr;
+    // optional timing events: [0] call start, [1] leaf start, [2] leaf end
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool timed_once = false;
     // statistics
     double flops_leaf = 0, flops_exec = 0;
     int grid = 0;
@@ -310,6 +313,8 @@ namespace {
 fmm_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FMM_OK : FMM_ERR_CUDA; }
 
 void free_plan_memory(fmm_plan *pl) {
+    for (auto &e : pl->ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
     if (pl->d_tables) cudaFree(pl->d_tables);
     if (pl->d_ws) cudaFree(pl->d_ws);
     if (pl->d_hostA) cudaFree(pl->d_hostA);
@@ -402,11 +407,17 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         }
     };
     std::vector<int> u_ptr, v_ptr, w_ptr, mu_ptr, mv_ptr, w_row((size_t)P * P, 0);
-    std::vector<int2> u_ent, v_ent, mu_ent, mv_ent;
+    std::vector<int2> u_ent, v_ent, mu_ent2, mv_ent2;
+    std::vector<int4> mu_ent, mv_ent;
     std::vector<int4> w_ent;
     csc2(ucols, u_ptr, u_ent);
     csc2(vcols, v_ptr, v_ent);
-    if (mat > 0) { csc2(mu, mu_ptr, mu_ent); csc2(mv, mv_ptr, mv_ent); }
+    if (mat > 0) {
+        csc2(mu, mu_ptr, mu_ent2);
+        csc2(mv, mv_ptr, mv_ent2);
+        for (const int2 &e : mu_ent2) mu_ent.push_back(make_int4(e.x / p, e.x % p, e.y, 0));
+        for (const int2 &e : mv_ent2) mv_ent.push_back(make_int4(e.x / p, e.x % p, e.y, 0));
+    }
     w_ptr.assign(wcols.size() + 1, 0);
     for (size_t c = 0; c < wcols.size(); ++c) {
         w_ptr[c + 1] = w_ptr[c] + (int)wcols[c].size();
@@ -472,9 +483,9 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     size_t o_muptr = 0, o_muent = 0, o_mvptr = 0, o_mvent = 0;
     if (mat > 0) {
         o_muptr = reserve(mu_ptr.size() * sizeof(int));
-        o_muent = reserve(mu_ent.size() * sizeof(int2));
+        o_muent = reserve(mu_ent.size() * sizeof(int4));
         o_mvptr = reserve(mv_ptr.size() * sizeof(int));
-        o_mvent = reserve(mv_ent.size() * sizeof(int2));
+        o_mvent = reserve(mv_ent.size() * sizeof(int4));
     }
     pl->tables_bytes = off;
     if (cudaMalloc(&pl->d_tables, pl->tables_bytes) != cudaSuccess) {
@@ -501,13 +512,13 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     put(o_wrow, w_row.data(), w_row.size() * sizeof(int));
     if (mat > 0) {
         put(o_muptr, mu_ptr.data(), mu_ptr.size() * sizeof(int));
-        put(o_muent, mu_ent.data(), mu_ent.size() * sizeof(int2));
+        put(o_muent, mu_ent.data(), mu_ent.size() * sizeof(int4));
         put(o_mvptr, mv_ptr.data(), mv_ptr.size() * sizeof(int));
-        put(o_mvent, mv_ent.data(), mv_ent.size() * sizeof(int2));
+        put(o_mvent, mv_ent.data(), mv_ent.size() * sizeof(int4));
         pl->d_mat_u_ptr = (const int *)(base + o_muptr);
-        pl->d_mat_u_ent = (const int2 *)(base + o_muent);
+        pl->d_mat_u_ent = (const int4 *)(base + o_muent);
         pl->d_mat_v_ptr = (const int *)(base + o_mvptr);
-        pl->d_mat_v_ent = (const int2 *)(base + o_mvent);
+        pl->d_mat_v_ent = (const int4 *)(base + o_mvent);
         pl->mat_outputs = (int64_t)mu.size();
     }
     put(o_geom, &g, sizeof(F64Geom));
@@ -572,6 +583,15 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     }
     pl->grid = (int)std::min<long long>(pl->total_tasks, (long long)sms * per_sm);
     if (pl->grid < 1) pl->grid = 1;
+    if (o.record_kernel_time) {
+        for (auto &e : pl->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                free_plan_memory(pl);
+                delete pl;
+                return FMM_ERR_CUDA;
+            }
+    }
     *out = pl;
     return FMM_OK;
 }
@@ -601,7 +621,7 @@ fmm_status_t prepare(const fmm_plan *pl, const double *A, const double *B, cudaS
         double *fin = side == 0 ? pl->d_SA : pl->d_SB;
         double *tmp = side == 0 ? pl->d_TA : pl->d_TB;
         const int *ptr = side == 0 ? pl->d_mat_u_ptr : pl->d_mat_v_ptr;
-        const int2 *ent = side == 0 ? pl->d_mat_u_ent : pl->d_mat_v_ent;
+        const int4 *ent = side == 0 ? pl->d_mat_u_ent : pl->d_mat_v_ent;
         long long ld_in = pl->n, b_in = pl->n_core;
         for (int lev = 1; lev <= pl->mat_levels; ++lev) {
             double *dst = ((pl->mat_levels - lev) % 2 == 0) ? fin : tmp;
@@ -633,8 +653,10 @@ F64Problem problem_of(const fmm_plan *pl, const double *A, const double *B, doub
 extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const double *B, double *C, void *stream) {
     if (!pl || !A || !B || !C) return FMM_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
+    if (pl->ev[0] && cudaEventRecord(pl->ev[0], st) != cudaSuccess) return FMM_ERR_CUDA;
     fmm_status_t s = prepare(pl, A, B, st);
     if (s != FMM_OK) return s;
+    if (pl->ev[1] && cudaEventRecord(pl->ev[1], st) != cudaSuccess) return FMM_ERR_CUDA;
     F64Launch<1> L{};
     L.nprobs = 1;
     L.total_tasks = pl->total_tasks;
@@ -642,7 +664,24 @@ extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const do
     L.error = pl->d_error;
     L.timeout_ns = (long long)(pl->timeout_s * 1e9);
     L.probs[0] = problem_of(pl, A, B, C, 0);
-    return cuda_status(fmm::launch_f64_single(L, pl->grid, st));
+    fmm_status_t ls = cuda_status(fmm::launch_f64_single(L, pl->grid, st));
+    if (ls != FMM_OK) return ls;
+    if (pl->ev[2]) {
+        if (cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
+        const_cast<fmm_plan *>(pl)->timed_once = true;
+    }
+    return FMM_OK;
+}
+
+extern "C" fmm_status_t fmm_plan_last_kernel_ms(const fmm_plan_t *pl, float *leaf_ms, float *total_ms) {
+    if (!pl || !pl->ev[0] || !pl->timed_once) return FMM_ERR_INVALID;
+    if (cudaEventSynchronize(pl->ev[2]) != cudaSuccess) return FMM_ERR_CUDA;
+    float a = 0, b = 0;
+    if (cudaEventElapsedTime(&a, pl->ev[1], pl->ev[2]) != cudaSuccess) return FMM_ERR_CUDA;
+    if (cudaEventElapsedTime(&b, pl->ev[0], pl->ev[2]) != cudaSuccess) return FMM_ERR_CUDA;
+    if (leaf_ms) *leaf_ms = a;
+    if (total_ms) *total_ms = b;
+    return FMM_OK;
 }
 
 extern "C" fmm_status_t fmm_gemm_host(fmm_plan_t *pl, const double *hA, const double *hB, double *hC, void *stream) {
@@ -735,6 +774,10 @@ extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t 
     info->flops_executed = pl->flops_exec;
     info->workspace_bytes = pl->ws_bytes;
     return FMM_OK;
+}
+
+extern "C" fmm_status_t fmm_measure_fp64_peak(void *stream, double *dmma, double *dfma) {
+    return cuda_status(fmm::measure_fp64_peaks((cudaStream_t)stream, dmma, dfma));
 }
 
 extern "C" size_t fmm_plan_workspace_bytes(const fmm_plan_t *pl) { return pl ? pl->ws_bytes : 0; }

@@ -82,11 +82,16 @@ size_t f64_kernel_smem_bytes();
 // Pre-addition pass for one materialized recursion level (fmm_f64.cu).
 // Input matrix c (c < n_in) starts at in + c * in_stride with leading
 // dimension ld_in and is split into p x p blocks of size b_out; output
-// c * R + s is the b_out x b_out matrix sum_e coef_e * block(blk_e) over the
-// CSC column s (s < R) of the one-level coefficient matrix, stored densely at
+// c * R + s is the b_out x b_out matrix sum_e coef_e * block(row_e, col_e)
+// over the CSC column s (s < R) of the one-level coefficient matrix, entries
+// {block row, block col, coefficient, 0}, stored densely at
 // out + (c * R + s) * b_out^2.
 cudaError_t launch_materialize_level(const double *in, long long ld_in, long long in_stride, int n_in,
-                                     long long b_out, int p, int R, const int *ptr, const int2 *ent, double *out,
+                                     long long b_out, int p, int R, const int *ptr, const int4 *ent, double *out,
                                      cudaStream_t s);
+
+// Calibration (fmm_calib.cu): FP64 throughput of DMMA (mma.sync m16n8k4) and
+// DFMA on the current device, in TFLOP/s, timed with CUDA events on `s`.
+cudaError_t measure_fp64_peaks(cudaStream_t s, double *dmma_tflops, double *dfma_tflops);
 
 }  // namespace fmm
