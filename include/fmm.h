@@ -45,7 +45,8 @@ typedef enum {
     FMM_ERR_OOM = 4,         /* a device or host allocation failed */
     FMM_ERR_CUDA = 5,        /* a CUDA runtime call or kernel launch failed */
     FMM_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up (reported by fmm_sync_status) */
-    FMM_ERR_NOT_FOUND = 7    /* unknown built-in algorithm name */
+    FMM_ERR_NOT_FOUND = 7,   /* unknown built-in algorithm name */
+    FMM_ERR_SCRATCH_LIMIT = 8 /* fmm_gemm_noalloc: request needs more than its static scratch */
 } fmm_status_t;
 
 typedef enum {
@@ -189,6 +190,42 @@ fmm_status_t fmm_plan_last_kernel_ms(const fmm_plan_t *plan, float *leaf_ms, flo
  * events on `stream` (about 0.1 s of GPU time; allocates and frees a small
  * scratch buffer).  Blocking.  Either output pointer may be NULL. */
 fmm_status_t fmm_measure_fp64_peak(void *stream, double *dmma_tflops, double *dfma_tflops);
+
+/* Size of the static device scratch array used by fmm_gemm_noalloc. */
+#define FMM_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/* C = A * B without allocating any memory; there is no counterpart in the
+ * paper.  For callers that cannot allocate device memory at all -- code
+ * running inside an allocator or memory-pool callback, frameworks that
+ * reserve all device memory up front, real-time paths where cudaMalloc and
+ * its implicit synchronization are not allowed.
+ *
+ * Runs the fused schedule (every recursion level combined while staging the
+ * leaf operands) of `depth` levels of `algo` on n x n row-major binary64
+ * device matrices A, B, C (C overwritten, A and B not overlapping C), on
+ * `stream`.  All scratch state (ordering counters, task counter, error word,
+ * flattened coefficient tables) lives in one file-scope __device__ array of
+ * FMM_NOALLOC_SCRATCH_BYTES (4 MiB) that every GPU loading the library holds
+ * until the process exits; host-side planning uses fixed static buffers.  The
+ * call makes no cudaMalloc, cudaFree or other allocating call.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Each call copies its tables into the array and clears the counters on
+ * `stream` before launching; the copy from host memory first waits for work
+ * already queued on `stream`.  Every call shares the one array, which keeps
+ * the last call's contents: calls that overlap on the GPU (for example on
+ * different streams) race and give wrong results.  Host calls are serialized
+ * by a mutex.  Device-side wait timeouts end the kernel but are not reported
+ * by this entry point.
+ *
+ * Errors: FMM_ERR_INVALID (NULL pointer, n < 1, p < 2, R < 1, depth < 0,
+ * leaf size < 1), FMM_ERR_BRENT, FMM_ERR_SCRATCH_LIMIT (p > 4, depth > 4, or
+ * tables plus counters larger than FMM_NOALLOC_SCRATCH_BYTES),
+ * FMM_ERR_UNSUPPORTED (a flattened column with more than 256 terms, or
+ * n > 2^30), FMM_ERR_CUDA. */
+fmm_status_t fmm_gemm_noalloc(int64_t n, const fmm_algo_t *algo, int depth, const double *A, const double *B,
+                              double *C, void *stream);
 
 /* Describe a plan.  Host-only. */
 fmm_status_t fmm_plan_get_info(const fmm_plan_t *plan, fmm_plan_info_t *info);

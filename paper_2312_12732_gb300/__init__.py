@@ -25,6 +25,7 @@ from ._binding import (  # noqa: F401
     fmm_gemm,
     fmm_gemm_batched,
     fmm_gemm_host,
+    fmm_gemm_noalloc,
     fmm_plan_create,
     fmm_plan_destroy,
     fmm_plan_get_info,

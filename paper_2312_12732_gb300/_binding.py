@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libfmm.so")
 
 FMM_OK, FMM_ERR_INVALID, FMM_ERR_BRENT, FMM_ERR_UNSUPPORTED = 0, 1, 2, 3
 FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_NOT_FOUND = 4, 5, 6, 7
+FMM_ERR_SCRATCH_LIMIT = 8
 FMM_F64, FMM_F64_OZAKI = 0, 1
 FMM_SCHED_AUTO, FMM_SCHED_FUSED, FMM_SCHED_HYBRID = 0, 1, 2
 
@@ -70,6 +71,8 @@ SIGNATURES = [
                                                ctypes.POINTER(ctypes.c_float)]),
     ("fmm_measure_fp64_peak", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double)]),
+    ("fmm_gemm_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(fmm_algo_t), ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fmm_plan_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fmm_plan_info_t)]),
     ("fmm_plan_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
     ("fmm_plan_destroy", None, [ctypes.c_void_p]),
@@ -267,6 +270,18 @@ def fmm_gemm_host(plan: Plan, A, B, C, stream=None):
     _check(lib().fmm_gemm_host(plan.handle, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                                ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
            "fmm_gemm_host")
+    return C
+
+
+def fmm_gemm_noalloc(algo: Algo, depth: int, A, B, C, stream=None):
+    """C = A @ B through the allocation-free entry point (fused schedule, static scratch)."""
+    n = A.shape[0]
+    for X, nm in ((A, "A"), (B, "B"), (C, "C")):
+        _check_operand(X, n, nm)
+    a = algo.c_struct()
+    _check(lib().fmm_gemm_noalloc(int(n), ctypes.byref(a), int(depth), ctypes.c_void_p(A.data_ptr()),
+                                  ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+                                  ctypes.c_void_p(_stream_ptr(stream))), "fmm_gemm_noalloc")
     return C
 
 

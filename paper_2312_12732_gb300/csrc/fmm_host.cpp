@@ -136,6 +136,7 @@ extern "C" const char *fmm_status_string(fmm_status_t s) {
         case FMM_ERR_CUDA: return "CUDA error";
         case FMM_ERR_TIMEOUT: return "device-side wait timed out";
         case FMM_ERR_NOT_FOUND: return "unknown algorithm name";
+        case FMM_ERR_SCRATCH_LIMIT: return "request exceeds the static scratch of fmm_gemm_noalloc";
     }
     return "unknown status";
 }
