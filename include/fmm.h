@@ -51,7 +51,8 @@ typedef enum {
 
 typedef enum {
     FMM_F64 = 0,       /* binary64 operands, FP64 tensor-core (DMMA) leaf products */
-    FMM_F64_OZAKI = 1  /* binary64 operands; leaf products emulated from low-precision slices */
+    FMM_F64_OZAKI = 1  /* binary64 operands; S_r/T_r formed in FP64, leaf products emulated from
+                          e4m3 slices (Ozaki scheme) on the tensor cores, post-additions in FP64 */
 } fmm_dtype_t;
 
 /* A bilinear algorithm <p,p,p;R>.  U, V, W are row-major p^2 x R int32
@@ -82,7 +83,7 @@ typedef enum { FMM_SCHED_AUTO = 0, FMM_SCHED_FUSED = 1, FMM_SCHED_HYBRID = 2 } f
 typedef struct {
     fmm_schedule_t schedule;
     int materialize_levels;  /* FMM_SCHED_HYBRID: 0 .. depth */
-    int ozaki_slices;        /* FMM_F64_OZAKI: slices per operand (default 8) */
+    int ozaki_slices;        /* FMM_F64_OZAKI: slices per operand, 2..12 (default 11) */
     double wait_timeout_s;   /* bound on every device-side wait (default 5 s) */
     int debug_poison_chain;  /* testing only: 1 = after the per-call reset, set one
                                 post-addition ordering counter to a value no task
@@ -102,8 +103,10 @@ typedef struct {
     int64_t tasks;          /* GPU tile tasks per multiplication */
     int materialized_levels;
     double flops_leaf;      /* 2 * R_total * m^3 */
-    double flops_executed;  /* leaf + additions + peel fix-ups, as scheduled */
+    double flops_executed;  /* FP64 work: leaf (FMM_F64) + additions + peel fix-ups, as scheduled */
     size_t workspace_bytes;
+    int ozaki_slices;       /* FMM_F64_OZAKI: slices per operand (0 otherwise) */
+    double flops_lowp;      /* FMM_F64_OZAKI: e4m3 tensor-core flops of the slice products */
 } fmm_plan_info_t;
 
 /* Status code to a static, NUL-terminated English string (never NULL). */

@@ -43,7 +43,7 @@ class fmm_plan_info_t(ctypes.Structure):
                 ("R_total", ctypes.c_int64), ("m", ctypes.c_int64), ("n_core", ctypes.c_int64),
                 ("tasks", ctypes.c_int64), ("materialized_levels", ctypes.c_int),
                 ("flops_leaf", ctypes.c_double), ("flops_executed", ctypes.c_double),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("ozaki_slices", ctypes.c_int), ("flops_lowp", ctypes.c_double)]
 
 
 # (name, restype, argtypes) for every symbol declared in include/fmm.h.

@@ -293,12 +293,20 @@ struct fmm_plan {
     size_t ws_bytes = 0;
     unsigned *d_chain = nullptr;
     unsigned long long *d_task_counter = nullptr;
+    unsigned long long *d_task_counter2 = nullptr;  // second launch of a call (peel after emulated leaf)
     int *d_error = nullptr;
     double *d_SA = nullptr, *d_SB = nullptr;  // materialized sources (nullptr when fused)
     double *d_TA = nullptr, *d_TB = nullptr;  // intermediate level (materialized depth >= 2)
     const int *d_mat_u_ptr = nullptr, *d_mat_v_ptr = nullptr;
     const int4 *d_mat_u_ent = nullptr, *d_mat_v_ent = nullptr;
     int64_t mat_outputs = 0;
+    // emulated leaf (FMM_F64_OZAKI)
+    int oz_s = 0, oz_L = 0;
+    int64_t oz_Mp = 0;
+    unsigned char *d_sla = nullptr, *d_slb = nullptr;  // slices
+    int *d_mxa = nullptr, *d_mxb = nullptr;            // exponents (zeroed per call with the counters)
+    const F64Geom *d_geom_peel = nullptr;              // FP64 peel-only geometry
+    double flops_lowp = 0;
     // host-buffer path
     double *d_hostA = nullptr, *d_hostB = nullptr, *d_hostC = nullptr;
     // optional timing events: [0] call start, [1] leaf start, [2] leaf end
@@ -307,6 +315,7 @@ struct fmm_plan {
     // statistics
     double flops_leaf = 0, flops_exec = 0;
     int grid = 0;
+    int sms = 0;
 };
 
 namespace {
@@ -353,7 +362,7 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     *out = nullptr;
     if (n < 1 || depth < 0 || depth > 8 || !algo_shape_ok(algo)) return FMM_ERR_INVALID;
     if (n > (1LL << 31) / 2) return FMM_ERR_UNSUPPORTED;
-    if (dtype != FMM_F64) return FMM_ERR_UNSUPPORTED;
+    if (dtype != FMM_F64 && dtype != FMM_F64_OZAKI) return FMM_ERR_UNSUPPORTED;
     if (fmm_algo_brent_mismatches(algo) != 0) return FMM_ERR_BRENT;
     const int p = algo->p, R = algo->R;
     const long long P = ipow(p, depth);
@@ -368,6 +377,15 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     else if (o.schedule == FMM_SCHED_HYBRID) mat = o.materialize_levels;
     else mat = default_materialized_levels(p, R, algo, depth);
     if (mat < 0 || mat > depth) return FMM_ERR_INVALID;
+    int oz_s = 0;
+    if (dtype == FMM_F64_OZAKI) {
+        // S_r and T_r must exist in FP64 before they are sliced: materialize all levels.
+        if (o.schedule != FMM_SCHED_AUTO && mat != depth) return FMM_ERR_UNSUPPORTED;
+        mat = depth;
+        oz_s = o.ozaki_slices ? o.ozaki_slices : 11;
+        if (oz_s < 2 || oz_s > fmm::kOzMaxSlices) return FMM_ERR_INVALID;
+        if (n / P > (1LL << 30) / 128) return FMM_ERR_UNSUPPORTED;
+    }
 
     fmm_plan *pl = new (std::nothrow) fmm_plan();
     if (!pl) return FMM_ERR_OOM;
@@ -468,12 +486,13 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     }
     const double qd = (double)q, ncd = (double)pl->n_core, nd = (double)n;
     const double peel = 2.0 * (ncd * qd * nd + qd * nd * nd + ncd * ncd * qd);
-    pl->flops_exec = pl->flops_leaf + adds + peel;
+    pl->flops_exec = (dtype == FMM_F64_OZAKI ? 0.0 : pl->flops_leaf) + adds + peel;
 
     // Device tables.
     size_t off = 0;
     auto reserve = [&](size_t bytes) { size_t o2 = align_up(off, 256); off = o2 + bytes; return o2; };
     const size_t o_geom = reserve(sizeof(F64Geom));
+    const size_t o_geom_peel = reserve(sizeof(F64Geom));
     const size_t o_uptr = reserve(u_ptr.size() * sizeof(int));
     const size_t o_uent = reserve(std::max<size_t>(1, u_ent.size()) * sizeof(int2));
     const size_t o_vptr = reserve(v_ptr.size() * sizeof(int));
@@ -523,6 +542,12 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         pl->mat_outputs = (int64_t)mu.size();
     }
     put(o_geom, &g, sizeof(F64Geom));
+    {
+        F64Geom gp = g;  // the peel tasks alone, run after the emulated leaf products
+        gp.tasks_core = 0;
+        put(o_geom_peel, &gp, sizeof(F64Geom));
+        pl->d_geom_peel = (const F64Geom *)(base + o_geom_peel);
+    }
     if (cudaMemcpy(pl->d_tables, host.data(), pl->tables_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         free_plan_memory(pl);
@@ -530,10 +555,22 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         return FMM_ERR_CUDA;
     }
 
-    // Workspace: [error int][pad][task counter u64][chain counters] then the
-    // materialized operands.
+    // Workspace: [error int][pad][task counter u64][second task counter u64]
+    // [pad][chain counters] then the materialized operands.
     const size_t chain_count = (size_t)P * P * (size_t)tiles;
-    pl->counters_bytes = align_up(16 + chain_count * sizeof(unsigned), 256);
+    pl->counters_bytes = align_up(32 + chain_count * sizeof(unsigned), 256);
+    size_t o_mx = 0;
+    if (dtype == FMM_F64_OZAKI) {
+        pl->oz_s = oz_s;
+        pl->oz_Mp = (pl->m + 127) / 128 * 128;
+        o_mx = pl->counters_bytes;
+        pl->counters_bytes = align_up(o_mx + 2 * (size_t)Rt * (size_t)pl->oz_Mp * sizeof(int), 256);
+        // int64 recombination stays below 2^62: L >= log2(1.1 Kp 256) + 5 (s - 1) - 62
+        const double lg = std::log2(1.1 * (double)pl->oz_Mp * 256.0) + fmm::kOzDigitBits * (oz_s - 1) - 62.0;
+        pl->oz_L = lg > 0 ? (int)std::ceil(lg) : 0;
+        const double mp = (double)pl->oz_Mp;
+        pl->flops_lowp = 2.0 * (double)Rt * (oz_s * (oz_s + 1) / 2) * mp * mp * mp;
+    }
     size_t ws = pl->counters_bytes;
     size_t o_sa = 0, o_sb = 0, o_ta = 0, o_tb = 0;
     if (mat > 0) {
@@ -547,6 +584,12 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
             o_tb = ws; ws = align_up(ws + tbytes, 256);
         }
     }
+    size_t o_sla = 0, o_slb = 0, slice_bytes = 0;
+    if (dtype == FMM_F64_OZAKI) {
+        slice_bytes = (size_t)Rt * (size_t)oz_s * (size_t)pl->oz_Mp * (size_t)pl->oz_Mp;
+        o_sla = ws; ws = align_up(ws + slice_bytes, 256);
+        o_slb = ws; ws = align_up(ws + slice_bytes, 256);
+    }
     pl->ws_bytes = ws;
     if (cudaMalloc(&pl->d_ws, ws) != cudaSuccess) {
         cudaGetLastError();
@@ -557,13 +600,27 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     char *wsb = (char *)pl->d_ws;
     pl->d_error = (int *)wsb;
     pl->d_task_counter = (unsigned long long *)(wsb + 8);
-    pl->d_chain = (unsigned *)(wsb + 16);
+    pl->d_task_counter2 = (unsigned long long *)(wsb + 16);
+    pl->d_chain = (unsigned *)(wsb + 32);
     if (mat > 0) {
         pl->d_SA = (double *)(wsb + o_sa);
         pl->d_SB = (double *)(wsb + o_sb);
         if (mat >= 2) {
             pl->d_TA = (double *)(wsb + o_ta);
             pl->d_TB = (double *)(wsb + o_tb);
+        }
+    }
+    if (dtype == FMM_F64_OZAKI) {
+        pl->d_mxa = (int *)(wsb + o_mx);
+        pl->d_mxb = pl->d_mxa + (size_t)Rt * pl->oz_Mp;
+        pl->d_sla = (unsigned char *)(wsb + o_sla);
+        pl->d_slb = (unsigned char *)(wsb + o_slb);
+        // padding rows/columns of the slices are never written by the kernels
+        if (cudaMemset(pl->d_sla, 0, slice_bytes) != cudaSuccess || cudaMemset(pl->d_slb, 0, slice_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_plan_memory(pl);
+            delete pl;
+            return FMM_ERR_CUDA;
         }
     }
     if (cudaMemset(pl->d_ws, 0, pl->counters_bytes) != cudaSuccess) {
@@ -575,8 +632,8 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
-    const int per_sm = fmm::f64_kernel_ctas_per_sm();
-    if (per_sm <= 0) {
+    const int per_sm = dtype == FMM_F64_OZAKI ? fmm::ozaki_ctas_per_sm() : fmm::f64_kernel_ctas_per_sm();
+    if (per_sm <= 0 || fmm::f64_kernel_ctas_per_sm() <= 0) {
         cudaGetLastError();
         free_plan_memory(pl);
         delete pl;
@@ -584,6 +641,7 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     }
     pl->grid = (int)std::min<long long>(pl->total_tasks, (long long)sms * per_sm);
     if (pl->grid < 1) pl->grid = 1;
+    pl->sms = sms;
     if (o.record_kernel_time) {
         for (auto &e : pl->ev)
             if (cudaEventCreate(&e) != cudaSuccess) {
@@ -651,12 +709,87 @@ F64Problem problem_of(const fmm_plan *pl, const double *A, const double *B, doub
 
 }  // namespace
 
+namespace {
+
+// Emulated leaf: FP64 pre-additions, exponents and slices of every S_r / T_r,
+// the slice GEMM with fused post-additions, then the FP64 peel tasks.
+fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, double *C, cudaStream_t st) {
+    const long long m = pl->m;
+    const int nmat = (int)pl->R_total;
+    const double *S = pl->depth > 0 ? pl->d_SA : A;
+    const double *T = pl->depth > 0 ? pl->d_SB : B;
+    const long long ld = pl->depth > 0 ? m : pl->n;
+    const long long stride = pl->depth > 0 ? m * m : 0;
+    const int Mp = (int)pl->oz_Mp;
+    if (fmm::launch_ozaki_exponents(S, ld, stride, nmat, (int)m, (int)m, true, pl->d_mxa, Mp, st) != cudaSuccess ||
+        fmm::launch_ozaki_exponents(T, ld, stride, nmat, (int)m, (int)m, false, pl->d_mxb, Mp, st) != cudaSuccess ||
+        fmm::launch_ozaki_slices(S, ld, stride, nmat, (int)m, (int)m, true, pl->d_mxa, Mp, pl->oz_s, Mp, Mp,
+                                 pl->d_sla, st) != cudaSuccess ||
+        fmm::launch_ozaki_slices(T, ld, stride, nmat, (int)m, (int)m, false, pl->d_mxb, Mp, pl->oz_s, Mp, Mp,
+                                 pl->d_slb, st) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    if (pl->ev[1] && cudaEventRecord(pl->ev[1], st) != cudaSuccess) return FMM_ERR_CUDA;
+    fmm::OzParams P{};
+    P.sa = pl->d_sla;
+    P.sb = pl->d_slb;
+    P.mxa = pl->d_mxa;
+    P.mxb = pl->d_mxb;
+    P.C = C;
+    P.ldc = pl->n;
+    P.m = m;
+    P.Mp = Mp;
+    P.Kp = Mp;
+    P.s = pl->oz_s;
+    P.L = pl->oz_L;
+    P.tiles_m = pl->tiles_m;
+    P.tiles_n = pl->tiles_n;
+    P.R = nmat;
+    P.P = (int)pl->P;
+    P.w_ptr = pl->geom.w_ptr;
+    P.w_ent = pl->geom.w_ent;
+    P.chain = pl->d_chain;
+    P.tasks = (long long)nmat * pl->tiles_m * pl->tiles_n;
+    P.task_counter = pl->d_task_counter;
+    P.error = pl->d_error;
+    P.timeout_ns = (long long)(pl->timeout_s * 1e9);
+    const int grid = (int)std::min<long long>(P.tasks, (long long)pl->sms * fmm::ozaki_ctas_per_sm());
+    if (fmm::launch_ozaki_gemm(P, grid < 1 ? 1 : grid, st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (pl->ev[2] && cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
+    const long long peel = pl->geom.tasks_right + pl->geom.tasks_bottom + pl->geom.tasks_rankq;
+    if (peel > 0) {
+        F64Launch<1> L{};
+        L.nprobs = 1;
+        L.total_tasks = peel;
+        L.task_counter = pl->d_task_counter2;
+        L.error = pl->d_error;
+        L.timeout_ns = (long long)(pl->timeout_s * 1e9);
+        L.probs[0].g = pl->d_geom_peel;
+        L.probs[0].A = A;
+        L.probs[0].B = B;
+        L.probs[0].SA = A;
+        L.probs[0].SB = B;
+        L.probs[0].C = C;
+        L.probs[0].chain = pl->d_chain;
+        L.probs[0].task_begin = 0;
+        const int g2 = (int)std::min<long long>(peel, (long long)pl->sms * fmm::f64_kernel_ctas_per_sm());
+        if (fmm::launch_f64_single(L, g2 < 1 ? 1 : g2, st) != cudaSuccess) return FMM_ERR_CUDA;
+    }
+    return FMM_OK;
+}
+
+}  // namespace
+
 extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const double *B, double *C, void *stream) {
     if (!pl || !A || !B || !C) return FMM_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     if (pl->ev[0] && cudaEventRecord(pl->ev[0], st) != cudaSuccess) return FMM_ERR_CUDA;
     fmm_status_t s = prepare(pl, A, B, st);
     if (s != FMM_OK) return s;
+    if (pl->dtype == FMM_F64_OZAKI) {
+        s = gemm_ozaki(pl, A, B, C, st);
+        if (s == FMM_OK && pl->ev[2]) const_cast<fmm_plan *>(pl)->timed_once = true;
+        return s;
+    }
     if (pl->ev[1] && cudaEventRecord(pl->ev[1], st) != cudaSuccess) return FMM_ERR_CUDA;
     F64Launch<1> L{};
     L.nprobs = 1;
@@ -774,6 +907,8 @@ extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t 
     info->flops_leaf = pl->flops_leaf;
     info->flops_executed = pl->flops_exec;
     info->workspace_bytes = pl->ws_bytes;
+    info->ozaki_slices = pl->oz_s;
+    info->flops_lowp = pl->flops_lowp;
     return FMM_OK;
 }
 

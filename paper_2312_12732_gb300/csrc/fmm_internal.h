@@ -73,6 +73,43 @@ struct F64Launch {
 
 constexpr int kMaxBatchPerLaunch = 128;
 
+// Emulated-FP64 leaf (fmm_ozaki.cu): balanced digits of kOzDigitBits bits
+// stored as e4m3, up to kOzMaxSlices slices per operand.
+constexpr int kOzDigitBits = 5;
+constexpr int kOzMaxSlices = 12;
+
+struct OzParams {
+    const unsigned char *sa;  // left slices  [R][s][Mp][Kp] (row r of S_r, K contiguous)
+    const unsigned char *sb;  // right slices [R][s][Mp][Kp] (column j of T_r, K contiguous)
+    const int *mxa;           // [R][Mp] largest biased exponent of each row of S_r
+    const int *mxb;           // [R][Mp] ... of each column of T_r
+    double *C;
+    long long ldc;
+    long long m;              // leaf size
+    int Mp, Kp;               // padded to multiples of 128
+    int s;                    // slices per operand
+    int L;                    // right shift keeping the int64 recombination in range
+    int tiles_m, tiles_n;
+    int R;                    // leaf products
+    int P;                    // C blocks per side
+    const int *w_ptr;
+    const int4 *w_ent;
+    unsigned *chain;
+    long long tasks;
+    unsigned long long *task_counter;
+    int *error;
+    long long timeout_ns;
+};
+
+cudaError_t launch_ozaki_exponents(const double *X, long long ld, long long mat_stride, int nmat, int rows, int cols,
+                                   bool by_rows, int *mx, int pitch, cudaStream_t s);
+cudaError_t launch_ozaki_slices(const double *X, long long ld, long long mat_stride, int nmat, int rows, int cols,
+                                bool by_rows, const int *mx, int pitch, int s, int Mp, int Kp, unsigned char *out,
+                                cudaStream_t st);
+cudaError_t launch_ozaki_gemm(const OzParams &P, int grid, cudaStream_t s);
+int ozaki_ctas_per_sm();
+size_t ozaki_smem_bytes();
+
 // Kernel launchers (fmm_f64.cu).  Return cudaSuccess or the launch error.
 cudaError_t launch_f64_single(const F64Launch<1> &L, int grid, cudaStream_t s);
 cudaError_t launch_f64_batch(const F64Launch<kMaxBatchPerLaunch> &L, int grid, cudaStream_t s);

@@ -1,0 +1,105 @@
+"""GPU parity of the emulated-FP64 leaf (FMM_F64_OZAKI) against the oracle.
+
+Bar: integer-valued inputs (entries in [-16, 16]) come out bit-exact -- their
+slices are exact, each diagonal group is an exact integer in FP32, the int64
+recombination keeps every bit and the FP64 post-additions stay below 2^53.
+Real inputs: the normalised error against Dot2 reference entries stays within
+the FP64 tolerance of its depth and within 2x the error of the plain FP64
+path (FMM_F64) on the same inputs (plus an absolute floor of 2^-53 for cases
+where both are at the rounding level).
+"""
+import numpy as np
+import pytest
+
+from paper_2312_12732_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def fmm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_12732_gb300 import _build
+
+    _build.build()
+    import paper_2312_12732_gb300 as m
+
+    return m
+
+
+def run(fmm, plan, A, B):
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    dC = torch.full_like(dA, float("nan"))
+    fmm.fmm_gemm(plan, dA, dB, dC)
+    st = fmm.fmm_sync_status(plan)
+    assert st == 0, fmm.fmm_status_string(st)
+    return dC.cpu().numpy()
+
+
+def nerr(C, ref, A, B):
+    n = A.shape[0]
+    return float(np.max(np.abs(C - ref)) / (n * np.abs(A).max() * np.abs(B).max()))
+
+
+def ref_entries(oracle_mod, A, B, count=4096, seed=3):
+    n = A.shape[0]
+    if n * n <= count:
+        rows, cols = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        rows, cols = rows.ravel(), cols.ravel()
+    else:
+        rows, cols = inputs.sample_indices(n, count, seed=seed)
+    return rows, cols, oracle_mod.sample_dot2(A, B, rows, cols)
+
+
+@pytest.mark.parametrize("name,depth,n", [("strassen", 0, 128), ("strassen", 0, 300), ("strassen", 1, 512),
+                                          ("strassen", 2, 1000), ("winograd", 2, 1024), ("laderman", 1, 384),
+                                          ("strassen", 1, 7)])
+def test_ozaki_bit_exact_on_integers(fmm, oracle_mod, name, depth, n):
+    algo = fmm.fmm_algo_builtin(name)
+    plan = fmm.fmm_plan_create(n, algo, depth, dtype="f64_ozaki")
+    A, B = inputs.operands(n, "integer", seed=n + depth)
+    assert np.array_equal(run(fmm, plan, A, B), oracle_mod.classic(A, B))
+
+
+@pytest.mark.parametrize("name,depth,n,kind,phi", [
+    ("strassen", 0, 256, "uniform", 0), ("strassen", 1, 512, "uniform", 0), ("strassen", 2, 1024, "uniform", 0),
+    ("strassen", 2, 1000, "normal", 0), ("strassen", 2, 1024, "wide", 4), ("strassen", 2, 1024, "wide", 8),
+    ("winograd", 1, 640, "uniform", 0), ("laderman", 1, 576, "uniform", 0)])
+def test_ozaki_accuracy_vs_fp64_path(fmm, oracle_mod, name, depth, n, kind, phi):
+    algo = fmm.fmm_algo_builtin(name)
+    A, B = inputs.operands(n, kind, seed=7, phi=phi)
+    rows, cols, ref = ref_entries(oracle_mod, A, B)
+    C_oz = run(fmm, fmm.fmm_plan_create(n, algo, depth, dtype="f64_ozaki"), A, B)
+    C_64 = run(fmm, fmm.fmm_plan_create(n, algo, depth), A, B)
+    e_oz = nerr(C_oz[rows, cols], ref, A, B)
+    e_64 = nerr(C_64[rows, cols], ref, A, B)
+    assert e_oz <= (1e-13 if depth <= 2 else 1e-12)
+    assert e_oz <= 2.0 * e_64 + U, (e_oz, e_64)
+
+
+def test_fewer_slices_lose_accuracy(fmm, oracle_mod):
+    """The slice count is the precision knob: 4 slices (20 bits) must be visibly
+    worse than the default, and still bounded by 2^-20 relative to the row/column scale."""
+    n = 256
+    algo = fmm.fmm_algo_builtin("strassen")
+    A, B = inputs.operands(n, "uniform", seed=9)
+    rows, cols, ref = ref_entries(oracle_mod, A, B)
+    e4 = nerr(run(fmm, fmm.fmm_plan_create(n, algo, 1, dtype="f64_ozaki", ozaki_slices=4), A, B)[rows, cols],
+              ref, A, B)
+    e11 = nerr(run(fmm, fmm.fmm_plan_create(n, algo, 1, dtype="f64_ozaki"), A, B)[rows, cols], ref, A, B)
+    assert e4 > 100 * e11
+    assert e4 < 2.0 ** -18
+
+
+def test_ozaki_plan_info(fmm):
+    plan = fmm.fmm_plan_create(1000, fmm.fmm_algo_builtin("strassen"), 2, dtype="f64_ozaki", ozaki_slices=9)
+    info = plan.info()
+    assert info["ozaki_slices"] == 9 and info["materialized_levels"] == 2
+    assert info["flops_lowp"] == 2.0 * 49 * 45 * 256 ** 3
+    with pytest.raises(fmm.FmmError):
+        fmm.fmm_plan_create(64, fmm.fmm_algo_builtin("strassen"), 1, dtype="f64_ozaki", ozaki_slices=13)
