@@ -50,7 +50,10 @@ def parse_args(argv=None):
     ap.add_argument("--depth", type=int, default=3)
     ap.add_argument("--schedule", default="auto", choices=["auto", "fused", "hybrid"])
     ap.add_argument("--materialize-levels", type=int, default=0)
-    ap.add_argument("--kind", default="uniform", choices=["uniform", "normal", "integer"])
+    ap.add_argument("--kind", default="uniform", choices=["uniform", "normal", "integer", "wide"])
+    ap.add_argument("--phi", type=float, default=0.0, help="decades of spread for --kind wide")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f64_ozaki"])
+    ap.add_argument("--slices", type=int, default=0, help="emulated leaf: slices per operand (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-classic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -63,7 +66,9 @@ def parse_args(argv=None):
 
 
 def workload_name(a) -> str:
-    return f"{a.algo.replace('^2', 'x2')}_d{a.depth}_n{a.n}_{a.kind}_fp64"
+    kind = a.kind if a.kind != "wide" else f"wide{a.phi:g}"
+    leaf = "fp64" if a.dtype == "f64" else f"ozaki{a.slices or 11}"
+    return f"{a.algo.replace('^2', 'x2')}_d{a.depth}_n{a.n}_{kind}_{leaf}"
 
 
 def measured_peaks():
@@ -83,6 +88,15 @@ def fp64_peak_tflops():
             "of measured (MEASURED_PEAKS.json bf16 burst x nominal FP64/bf16 ratio 1.25/2250)"
     return FALLBACK_BF16_TFLOPS * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS, \
         "of fallback (1.9 PFLOP/s bf16 x nominal FP64/bf16 ratio 1.25/2250)"
+
+
+def fp8_peak_tflops():
+    """e4m3 tensor peak: the measured bf16 burst peak times the nominal fp8/bf16 ratio (4.5/2.25)."""
+    pk = measured_peaks()
+    if pk and pk.get("bf16_tflops"):
+        return pk["bf16_tflops"] * 4.5 / 2.25, \
+            "of measured (MEASURED_PEAKS.json bf16 burst x nominal fp8/bf16 ratio 4.5/2.25)"
+    return FALLBACK_BF16_TFLOPS * 2.0, "of fallback (1.9 PFLOP/s bf16 x nominal fp8/bf16 ratio 2)"
 
 
 def profile_traffic(kernel: str, workload: str):
@@ -287,26 +301,32 @@ def run_sweep(a):
         for d in (1, 2, 3):
             configs += [(algo, d, "fused", 0), (algo, d, "auto", 0)]
     configs += [("strassen^2", 1, "fused", 0), ("strassen^2", 1, "auto", 0), ("strassen^2", 2, "auto", 0)]
+    configs = [c + ("f64",) for c in configs]
+    configs += [("strassen", d, "auto", 0, "f64_ozaki") for d in (0, 1, 2, 3)]
     n = a.n
     A, B = inputs.operands(n, a.kind, seed=1)
     dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
     dC = torch.empty_like(dA)
     rows = [(n, c) for c in configs]
     if a.n == 8192:
-        rows += [(6912, ("laderman", d, s, 0)) for d in (1, 2) for s in ("fused", "auto")]
-        rows += [(6912, ("strassen", 0, "auto", 0))]
+        rows += [(6912, ("laderman", d, s, 0, "f64")) for d in (1, 2) for s in ("fused", "auto")]
+        rows += [(6912, ("strassen", 0, "auto", 0, "f64"))]
+        rows += [(16384, ("strassen", d, "auto", 0, "f64_ozaki")) for d in (0, 2)]
     cache = {n: (dA, dB, dC)}
-    for nn, (algo_name, depth, sched, ml) in rows:
+    for nn, (algo_name, depth, sched, ml, dt) in rows:
         if nn not in cache:
             A2, B2 = inputs.operands(nn, a.kind, seed=1)
             xA2 = torch.from_numpy(A2).to(dev)
             cache = {nn: (xA2, torch.from_numpy(B2).to(dev), torch.empty_like(xA2))}
         xA, xB, xC = cache[nn]
         algo = make_algo(fmm, algo_name)
-        plan = fmm.fmm_plan_create(nn, algo, depth, schedule=sched, materialize_levels=ml, record_kernel_time=True)
+        plan = fmm.fmm_plan_create(nn, algo, depth, dtype=dt, schedule=sched, materialize_levels=ml,
+                                   record_kernel_time=True)
         ms, leaf = time_plan(torch, fmm, plan, xA, xB, xC, 1, 2)
         info = plan.info()
-        print(json.dumps({"n": nn, "algo": algo_name, "depth": depth, "schedule": sched,
+        lowp = info["flops_lowp"] / leaf / 1e9 if dt == "f64_ozaki" else None
+        print(json.dumps({"n": nn, "algo": algo_name, "depth": depth, "schedule": sched, "dtype": dt,
+                          "lowp_tflops_leaf_kernel": round(lowp, 1) if lowp else None,
                           "materialized": info["materialized_levels"], "ms": round(ms, 3),
                           "leaf_ms": round(leaf, 3), "eff_tflops": round(2.0 * nn ** 3 / ms / 1e9, 4),
                           "exec_tflops_leaf_kernel": round(info["flops_leaf"] / leaf / 1e9, 4)}), flush=True)
@@ -338,14 +358,16 @@ def run_ours(a):
 
     n = a.n
     algo = make_algo(fmm, a.algo)
-    A, B = inputs.operands(n, a.kind, seed=1)
+    A, B = inputs.operands(n, a.kind, seed=1, phi=a.phi)
     dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
     dC = torch.empty_like(dA)
-    plan = fmm.fmm_plan_create(n, algo, a.depth, schedule=a.schedule, materialize_levels=a.materialize_levels,
+    plan = fmm.fmm_plan_create(n, algo, a.depth, dtype=a.dtype, schedule=a.schedule,
+                               materialize_levels=a.materialize_levels, ozaki_slices=a.slices,
                                record_kernel_time=True)
     info = plan.info()
 
     dmma_peak, dfma_peak = fmm.fmm_measure_fp64_peak()
+    e4m3_peak = fmm.fmm_measure_e4m3_peak() if a.dtype == "f64_ozaki" else None
     sampler = ClockSampler(gpu_uuid(torch, dev))
     with sampler:
         ms, leaf_ms = time_plan(torch, fmm, plan, dA, dB, dC, max(a.warmup, 3), a.steps, dist)
@@ -394,19 +416,28 @@ def run_ours(a):
                "d2h_bytes_per_step": n * n * 8, "ms_per_step": te * 1e3, "steps": k_e2e,
                "path": "fmm_gemm_host (pinned host buffers, copies inside the timed region)"}
 
-    peak, peak_note = fp64_peak_tflops()
     nc = info["n_core"]
     q = n - nc
-    contraction_flops = info["flops_leaf"] + 2.0 * (nc * q * n + q * n * n + nc * nc * q)
+    if a.dtype == "f64":
+        peak, peak_note = fp64_peak_tflops()
+        contraction_flops = info["flops_leaf"] + 2.0 * (nc * q * n + q * n * n + nc * nc * q)
+        kernel_name = "fmm_f64_kernel"
+        extra = {"dmma_peak_measured_here": dmma_peak, "dfma_peak_measured_here": dfma_peak}
+        ref_rate = dmma_peak
+    else:
+        peak, peak_note = fp8_peak_tflops()
+        contraction_flops = info["flops_lowp"]
+        kernel_name = "ozaki_tc_kernel"
+        extra = {"e4m3_mma_sync_peak_measured_here": e4m3_peak, "dmma_peak_measured_here": dmma_peak,
+                 "ozaki_slices": info["ozaki_slices"]}
+        ref_rate = e4m3_peak
     achieved = contraction_flops / (leaf_ms * 1e-3) / 1e12
-    kernel_name = "fmm_f64_kernel"
     traffic = profile_traffic(kernel_name, workload_name(a))
     roofline = {"bound": "tensor", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_note": peak_note,
                 "algorithmic_flops_per_launch": contraction_flops, "avg_launch_ms": leaf_ms,
                 "kernel_share_of_step": leaf_ms / ms if ms > 0 else None,
-                "dmma_peak_measured_here": dmma_peak, "dfma_peak_measured_here": dfma_peak,
-                "frac_of_dmma_measured_here": achieved / dmma_peak if dmma_peak else None}
+                "frac_of_instruction_rate_measured_here": achieved / ref_rate if ref_rate else None, **extra}
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
@@ -421,6 +452,7 @@ def run_ours(a):
         "warmup": max(a.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "n": n, "algorithm": a.algo, "depth": a.depth,
+                   "leaf": "fp64 DMMA" if a.dtype == "f64" else f"emulated FP64, {info['ozaki_slices']} e4m3 slices",
                    "schedule": a.schedule, "materialized_levels": info["materialized_levels"],
                    "leaf_m": info["m"], "products": info["R_total"], "entries": a.kind,
                    "l2": "inputs 3 x %.0f MiB > L2 (129 MB), no flush" % (n * n * 8 / 2 ** 20),
@@ -430,7 +462,8 @@ def run_ours(a):
         "normalised_error_sampled": err,
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": a.steps * (1 + 2 * info["materialized_levels"]),
+        "gpu_launches": a.steps * ((1 + 2 * info["materialized_levels"]) if a.dtype == "f64" else
+                                   (2 * info["materialized_levels"] + 5 + (1 if q > 0 else 0))),
         "roofline": roofline,
         "cpu_baseline": cpu,
         "flops_executed_per_step": info["flops_executed"],

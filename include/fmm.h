@@ -194,6 +194,11 @@ fmm_status_t fmm_plan_last_kernel_ms(const fmm_plan_t *plan, float *leaf_ms, flo
  * scratch buffer).  Blocking.  Either output pointer may be NULL. */
 fmm_status_t fmm_measure_fp64_peak(void *stream, double *dmma_tflops, double *dfma_tflops);
 
+/* Calibration, with no counterpart in the paper: throughput of the emulated
+ * leaf's instruction (mma.sync m16n8k32 e4m3 with FP32 accumulation) on the
+ * current device, in TFLOP/s, timed like fmm_measure_fp64_peak.  Blocking. */
+fmm_status_t fmm_measure_e4m3_peak(void *stream, double *tflops);
+
 /* Size of the static device scratch array used by fmm_gemm_noalloc. */
 #define FMM_NOALLOC_SCRATCH_BYTES (4u << 20)
 

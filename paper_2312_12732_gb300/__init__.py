@@ -30,6 +30,7 @@ from ._binding import (  # noqa: F401
     fmm_plan_destroy,
     fmm_plan_get_info,
     fmm_plan_last_kernel_ms,
+    fmm_measure_e4m3_peak,
     fmm_measure_fp64_peak,
     fmm_plan_workspace_bytes,
     fmm_status_string,

@@ -73,6 +73,7 @@ SIGNATURES = [
                                              ctypes.POINTER(ctypes.c_double)]),
     ("fmm_gemm_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(fmm_algo_t), ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fmm_measure_e4m3_peak", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("fmm_plan_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fmm_plan_info_t)]),
     ("fmm_plan_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
     ("fmm_plan_destroy", None, [ctypes.c_void_p]),
@@ -225,6 +226,13 @@ def fmm_measure_fp64_peak(stream=None):
     _check(lib().fmm_measure_fp64_peak(ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(a), ctypes.byref(b)),
            "fmm_measure_fp64_peak")
     return float(a.value), float(b.value)
+
+
+def fmm_measure_e4m3_peak(stream=None) -> float:
+    """TFLOP/s of mma.sync m16n8k32 e4m3 (FP32 accumulation) measured on the current device."""
+    a = ctypes.c_double()
+    _check(lib().fmm_measure_e4m3_peak(ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(a)), "fmm_measure_e4m3_peak")
+    return float(a.value)
 
 
 def fmm_plan_workspace_bytes(plan: Plan) -> int:

@@ -15,6 +15,8 @@
 
 #include "fmm_internal.h"
 
+#include <cudaTypedefs.h>
+
 using fmm::F64Geom;
 using fmm::F64Launch;
 using fmm::F64Problem;
@@ -306,6 +308,8 @@ struct fmm_plan {
     unsigned char *d_sla = nullptr, *d_slb = nullptr;  // slices
     int *d_mxa = nullptr, *d_mxb = nullptr;            // exponents (zeroed per call with the counters)
     const F64Geom *d_geom_peel = nullptr;              // FP64 peel-only geometry
+    int oz_engine = 1;                                  // 1 = tcgen05, 0 = mma.sync
+    CUtensorMap oz_map_a{}, oz_map_b{};                 // TMA maps over the slices
     double flops_lowp = 0;
     // host-buffer path
     double *d_hostA = nullptr, *d_hostB = nullptr, *d_hostC = nullptr;
@@ -321,6 +325,37 @@ struct fmm_plan {
 namespace {
 
 fmm_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FMM_OK : FMM_ERR_CUDA; }
+
+// cuTensorMapEncodeTiled from the driver, without linking libcuda.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D uint8 map over `rows` x `kp` bytes (row pitch kp), 128 x 128 boxes, 128B swizzle.
+bool make_slice_map(CUtensorMap *map, void *base, unsigned long long rows, unsigned long long kp) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {kp, rows};
+    const cuuint64_t strides[1] = {kp};
+    const cuuint32_t box[2] = {128, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 void free_plan_memory(fmm_plan *pl) {
     for (auto &e : pl->ev)
@@ -615,6 +650,15 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         pl->d_mxb = pl->d_mxa + (size_t)Rt * pl->oz_Mp;
         pl->d_sla = (unsigned char *)(wsb + o_sla);
         pl->d_slb = (unsigned char *)(wsb + o_slb);
+        const char *eng = std::getenv("FMM_OZAKI_ENGINE");
+        pl->oz_engine = (eng && std::string(eng) == "mma_sync") ? 0 : 1;
+        const unsigned long long srows = (unsigned long long)Rt * oz_s * pl->oz_Mp;
+        if (pl->oz_engine == 1 && (!make_slice_map(&pl->oz_map_a, pl->d_sla, srows, pl->oz_Mp) ||
+                                   !make_slice_map(&pl->oz_map_b, pl->d_slb, srows, pl->oz_Mp))) {
+            free_plan_memory(pl);
+            delete pl;
+            return FMM_ERR_CUDA;
+        }
         // padding rows/columns of the slices are never written by the kernels
         if (cudaMemset(pl->d_sla, 0, slice_bytes) != cudaSuccess || cudaMemset(pl->d_slb, 0, slice_bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -752,8 +796,14 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     P.task_counter = pl->d_task_counter;
     P.error = pl->d_error;
     P.timeout_ns = (long long)(pl->timeout_s * 1e9);
-    const int grid = (int)std::min<long long>(P.tasks, (long long)pl->sms * fmm::ozaki_ctas_per_sm());
-    if (fmm::launch_ozaki_gemm(P, grid < 1 ? 1 : grid, st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (pl->oz_engine == 1) {
+        const int grid = (int)std::min<long long>(P.tasks, (long long)pl->sms);
+        if (fmm::launch_ozaki_tc(pl->oz_map_a, pl->oz_map_b, P, grid < 1 ? 1 : grid, st) != cudaSuccess)
+            return FMM_ERR_CUDA;
+    } else {
+        const int grid = (int)std::min<long long>(P.tasks, (long long)pl->sms * fmm::ozaki_ctas_per_sm());
+        if (fmm::launch_ozaki_gemm(P, grid < 1 ? 1 : grid, st) != cudaSuccess) return FMM_ERR_CUDA;
+    }
     if (pl->ev[2] && cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
     const long long peel = pl->geom.tasks_right + pl->geom.tasks_bottom + pl->geom.tasks_rankq;
     if (peel > 0) {
@@ -914,6 +964,10 @@ extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t 
 
 extern "C" fmm_status_t fmm_measure_fp64_peak(void *stream, double *dmma, double *dfma) {
     return cuda_status(fmm::measure_fp64_peaks((cudaStream_t)stream, dmma, dfma));
+}
+
+extern "C" fmm_status_t fmm_measure_e4m3_peak(void *stream, double *tflops) {
+    return cuda_status(fmm::measure_e4m3_peak((cudaStream_t)stream, tflops));
 }
 
 extern "C" size_t fmm_plan_workspace_bytes(const fmm_plan_t *pl) { return pl ? pl->ws_bytes : 0; }

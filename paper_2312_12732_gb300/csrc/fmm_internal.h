@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace fmm {
@@ -109,6 +110,10 @@ cudaError_t launch_ozaki_slices(const double *X, long long ld, long long mat_str
 cudaError_t launch_ozaki_gemm(const OzParams &P, int grid, cudaStream_t s);
 int ozaki_ctas_per_sm();
 size_t ozaki_smem_bytes();
+// tcgen05 slice GEMM (fmm_ozaki_tc.cu): map_a / map_b are 2-D uint8 tensor
+// maps over the slice buffers ([rows][Kp], 128 x 128 boxes, 128B swizzle).
+cudaError_t launch_ozaki_tc(const CUtensorMap &map_a, const CUtensorMap &map_b, const OzParams &P, int grid,
+                            cudaStream_t s);
 
 // Kernel launchers (fmm_f64.cu).  Return cudaSuccess or the launch error.
 cudaError_t launch_f64_single(const F64Launch<1> &L, int grid, cudaStream_t s);
@@ -130,5 +135,7 @@ cudaError_t launch_materialize_level(const double *in, long long ld_in, long lon
 // Calibration (fmm_calib.cu): FP64 throughput of DMMA (mma.sync m16n8k4) and
 // DFMA on the current device, in TFLOP/s, timed with CUDA events on `s`.
 cudaError_t measure_fp64_peaks(cudaStream_t s, double *dmma_tflops, double *dfma_tflops);
+// ... and of mma.sync m16n8k32 e4m3 with FP32 accumulation (the emulated leaf's instruction).
+cudaError_t measure_e4m3_peak(cudaStream_t s, double *tflops);
 
 }  // namespace fmm

@@ -1,0 +1,467 @@
+// Emulated-FP64 slice GEMM on the 5th-generation tensor cores (tcgen05),
+// sm_103a.  Same arithmetic as the mma.sync kernel in fmm_ozaki.cu (Ozaki
+// scheme: diagonal groups D_g = sum_{t+u=g} Shat_t That_u of e4m3 slices,
+// exact in FP32, folded into int64, one FP64 conversion per element, FP64
+// post-additions in ascending product order), organised the Blackwell way:
+//
+//   warp 0     TMA producer: fetches tile tasks in increasing order, streams
+//              128 x 128-byte slabs of both slice operands into a 5-stage
+//              shared-memory ring (128B swizzle) with cp.async.bulk.tensor;
+//   warp 1     MMA issuer: one thread issues tcgen05.mma kind::f8f6f4
+//              (M = 128, N = 128, K = 32) from the ring into one of two TMEM
+//              accumulators (one per diagonal group in flight) and releases
+//              ring slots / hands finished groups over with tcgen05.commit;
+//   warps 2-9  epilogue: each thread owns one tile row and 64 columns, reads
+//              D_g with tcgen05.ld, folds it into 64 int64 registers while the
+//              next group accumulates in the other TMEM buffer, then scales to
+//              FP64 and applies the post-additions.
+//
+// Every mbarrier wait is bounded by %globaltimer; on expiry the CTA records a
+// timeout, stops issuing, waits (bounded) for its own copies and MMAs in
+// flight, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "fmm_device.cuh"
+#include "fmm_internal.h"
+
+namespace fmm {
+namespace {
+
+using dev::chain_wait;
+using dev::global_ns;
+using dev::ld_volatile;
+using dev::neg;
+
+constexpr int OB = kOzDigitBits;
+constexpr int TM = 128, TN = 128, SLAB = 128;  // tile rows, tile cols, K bytes per stage
+constexpr int STAGES = 5;
+constexpr int NTHREADS = 320;                  // 10 warps
+constexpr int EPI_WARP0 = 2, NEPI = 8;
+constexpr int TMEM_COLS = 256;                 // two 128-column FP32 accumulators
+constexpr int TASK_RING = 2;
+constexpr uint32_t STAGE_BYTES = 2u * TM * SLAB;
+
+struct __align__(8) Bars {
+    unsigned long long full[STAGES], empty[STAGES];
+    unsigned long long accfull[2], accempty[2];
+    unsigned long long tfull[TASK_RING], tempty[TASK_RING];
+    unsigned long long drain;
+    unsigned long long epi_go, epi_done;  // epilogue hand-offs around each post-addition
+    long long task[TASK_RING];
+    unsigned tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity, volatile int *abort,
+                                          int *gerror, long long timeout_ns) {
+    if (mbar_test(b, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_test(b, parity)) return true;
+        if (*abort) return false;
+        if ((long long)(global_ns() - t0) > timeout_ns) {
+            *abort = 1;
+            atomicCAS(gerror, kDevOk, kDevTimeout);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            su32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor: kind::f8f6f4, A = B = e4m3, D = f32, both K-major.
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+__device__ __forceinline__ double scale2(double v, int sc) {
+    while (sc > 1023) {
+        v *= pow2(1023);
+        sc -= 1023;
+    }
+    while (sc < -1022) {
+        v *= pow2(-1022);
+        sc += 1022;
+    }
+    return v * pow2(sc);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    ozaki_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                    const __grid_constant__ OzParams P) {
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte alignment for the 128B-swizzled stages
+    unsigned char *base =
+        (unsigned char *)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
+    unsigned char *stage_mem = base;  // STAGES x (A slab 16 KB, B slab 16 KB)
+    Bars &B = *reinterpret_cast<Bars *>(base + STAGES * STAGE_BYTES);
+    volatile int *abort = &B.abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles = P.tiles_m * P.tiles_n;
+    const int nkb = P.Kp / SLAB;
+    const int s = P.s;
+
+    if (tid == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&B.full[i], 1);
+            mbar_init(&B.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&B.accfull[i], 1);
+            mbar_init(&B.accempty[i], NEPI);
+        }
+        for (int i = 0; i < TASK_RING; ++i) {
+            mbar_init(&B.tfull[i], 1);
+            mbar_init(&B.tempty[i], 1 + NEPI);
+        }
+        mbar_init(&B.drain, 1);
+        mbar_init(&B.epi_go, 1);
+        mbar_init(&B.epi_done, NEPI * 32);
+        B.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&B.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = B.tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&map_a) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&map_b) : "memory");
+            uint32_t stage = 0, sphase = 0;  // ring position and its wrap parity
+            long long issued_tx = 0;          // stages issued (for draining)
+            int tslot = 0;
+            uint32_t tphase = 0;
+            while (!*abort) {
+                long long task = (long long)atomicAdd(P.task_counter, 1ull);
+                if (ld_volatile(P.error) != kDevOk) task = P.tasks;
+                if (!mbar_wait(&B.tempty[tslot], tphase ^ 1u, abort, P.error, P.timeout_ns)) break;
+                B.task[tslot] = task;
+                mbar_arrive(&B.tfull[tslot]);
+                if (++tslot == TASK_RING) {
+                    tslot = 0;
+                    tphase ^= 1u;
+                }
+                if (task >= P.tasks) break;
+                const int r = (int)(task / tiles);
+                const int t = (int)(task - (long long)r * tiles);
+                const int ti = t / P.tiles_n, tj = t - ti * P.tiles_n;
+                bool ok = true;
+                for (int g = 2; g <= s + 1 && ok; ++g)
+                    for (int ta = max(1, g - s); ta <= min(s, g - 1) && ok; ++ta)
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            if (!mbar_wait(&B.empty[stage], sphase ^ 1u, abort, P.error, P.timeout_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            unsigned char *sa = stage_mem + stage * STAGE_BYTES;
+                            unsigned char *sb = sa + TM * SLAB;
+                            mbar_expect_tx(&B.full[stage], STAGE_BYTES);
+                            const int ya = (r * s + (ta - 1)) * P.Mp + ti * TM;
+                            const int yb = (r * s + (g - ta - 1)) * P.Mp + tj * TN;
+                            tma_load_2d(sa, &map_a, kb * SLAB, ya, &B.full[stage]);
+                            tma_load_2d(sb, &map_b, kb * SLAB, yb, &B.full[stage]);
+                            ++issued_tx;
+                            if (++stage == STAGES) {
+                                stage = 0;
+                                sphase ^= 1u;
+                            }
+                        }
+                if (!ok) break;
+            }
+            if (*abort) {
+                // wait (bounded) for the copies this thread issued into the ring
+                uint32_t st2 = stage, ph2 = sphase;
+                for (int k = 0; k < STAGES && issued_tx > 0; ++k, --issued_tx) {
+                    if (st2 == 0) {
+                        st2 = STAGES - 1;
+                        ph2 ^= 1u;
+                    } else {
+                        --st2;
+                    }
+                    const unsigned long long t0 = global_ns();
+                    while (!mbar_test(&B.full[st2], ph2) && (long long)(global_ns() - t0) < P.timeout_ns) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t stage = 0, sphase = 0;
+            uint32_t buf = 0, bphase = 0;  // accumulator buffer and its wrap parity
+            int tslot = 0;
+            uint32_t tphase = 0;
+            const uint32_t sbase = su32(stage_mem);
+            bool any = false;
+            while (!*abort) {
+                if (!mbar_wait(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
+                const long long task = B.task[tslot];
+                mbar_arrive(&B.tempty[tslot]);
+                if (++tslot == TASK_RING) {
+                    tslot = 0;
+                    tphase ^= 1u;
+                }
+                if (task >= P.tasks) break;
+                bool ok = true;
+                for (int g = 2; g <= s + 1 && ok; ++g) {
+                    if (!mbar_wait(&B.accempty[buf], bphase ^ 1u, abort, P.error, P.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dtm = tmem + buf * TN;
+                    bool first = true;
+                    for (int ta = max(1, g - s); ta <= min(s, g - 1) && ok; ++ta)
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            if (!mbar_wait(&B.full[stage], sphase, abort, P.error, P.timeout_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t sa = sbase + stage * STAGE_BYTES;
+                            const uint64_t da = desc_sw128(sa), db = desc_sw128(sa + TM * SLAB);
+#pragma unroll
+                            for (int k = 0; k < SLAB / 32; ++k) {
+                                const uint64_t adv = (uint64_t)((k * 32) >> 4);
+                                mma_e4m3(dtm, da + adv, db + adv, first ? 0u : 1u);
+                                first = false;
+                            }
+                            mma_commit(&B.empty[stage]);
+                            any = true;
+                            if (++stage == STAGES) {
+                                stage = 0;
+                                sphase ^= 1u;
+                            }
+                        }
+                    if (!ok) break;
+                    mma_commit(&B.accfull[buf]);
+                    if (++buf == 2) {
+                        buf = 0;
+                        bphase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+            }
+            if (any) {
+                // all MMAs issued by this thread complete before TMEM is released
+                mma_commit(&B.drain);
+                const unsigned long long t0 = global_ns();
+                while (!mbar_test(&B.drain, 0) && (long long)(global_ns() - t0) < P.timeout_ns) {
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int e = warp - EPI_WARP0;      // 0..7
+        const int quad = warp & 3;           // TMEM lane quadrant of this warp
+        const int half = e >> 2;             // column half
+        const int row = quad * 32 + lane;    // tile row owned by this thread
+        const int col0 = half * 64;
+        uint32_t buf = 0, bphase = 0;
+        int tslot = 0;
+        uint32_t tphase = 0;
+        uint32_t dphase = 0;  // parity of the post-addition hand-offs
+        const bool leader = tid == EPI_WARP0 * 32;
+        while (!*abort) {
+            if (!mbar_wait(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
+            const long long task = B.task[tslot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&B.tempty[tslot]);
+            if (++tslot == TASK_RING) {
+                tslot = 0;
+                tphase ^= 1u;
+            }
+            if (task >= P.tasks) break;
+            const int r = (int)(task / tiles);
+            const int t = (int)(task - (long long)r * tiles);
+            const int ti = t / P.tiles_n, tj = t - ti * P.tiles_n;
+
+            long long acc[64];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) acc[j] = 0;
+            bool ok = true;
+            for (int g = 2; g <= s + 1; ++g) {
+                if (!mbar_wait(&B.accfull[buf], bphase, abort, P.error, P.timeout_ns)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int sh = OB * (s + 1 - g) - P.L;
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + buf * TN + col0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t v[16];
+                    tmem_ld16(taddr + c * 16, v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const long long vi = (long long)__float2int_rn(__uint_as_float(v[j]));
+                        acc[c * 16 + j] += sh >= 0 ? vi * (1LL << sh) : ((vi + (1LL << (-sh - 1))) >> (-sh));
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&B.accempty[buf]);
+                if (++buf == 2) {
+                    buf = 0;
+                    bphase ^= 1u;
+                }
+            }
+            if (!ok) break;
+
+            // FP64 values of this thread's 64 elements of P_r
+            const int rows = (int)min((long long)TM, P.m - (long long)ti * TM);
+            const int cols = (int)min((long long)TN, P.m - (long long)tj * TN);
+            const int ea = row < rows ? max(P.mxa[(long long)r * P.Mp + (long long)ti * TM + row], 1) - 1021 : 0;
+            double pv[64];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const int col = col0 + j;
+                const int eb = col < cols ? max(P.mxb[(long long)r * P.Mp + (long long)tj * TN + col], 1) - 1021 : 0;
+                pv[j] = acc[j] == 0 ? 0.0 : scale2(__ll2double_rn(acc[j]), ea + eb - OB * (s + 1) + P.L);
+            }
+
+            // post-additions C_l (+)= W[l][r] P_r in ascending r (per-tile counters)
+            const int wc = P.w_ptr[r], nD = P.w_ptr[r + 1] - wc;
+            for (int d = 0; d < nD && ok; ++d) {
+                const int4 en = P.w_ent[wc + d];
+                const long long br = en.x / P.P, bc = en.x % P.P;
+                double *dst = P.C + (br * P.m + (long long)ti * TM) * P.ldc + bc * P.m + (long long)tj * TN;
+                unsigned *chain = P.chain + (long long)en.x * tiles + t;
+                if (leader) {
+                    if (en.z > 0 && !chain_wait(chain, (unsigned)en.z, P.error, P.timeout_ns)) *abort = 1;
+                    mbar_arrive(&B.epi_go);
+                }
+                if (!mbar_wait(&B.epi_go, dphase, abort, P.error, P.timeout_ns) || *abort) {
+                    ok = false;
+                    break;
+                }
+                const int cf = en.y;
+                const double cfd = (double)cf;
+                const int mode = en.z == 0 ? (cf == 1 ? 0 : (cf == -1 ? 1 : 2)) : (cf == 1 ? 3 : (cf == -1 ? 4 : 5));
+                if (row < rows) {
+                    double *prow = dst + (long long)row * P.ldc + col0;
+#pragma unroll
+                    for (int j = 0; j < 64; ++j) {
+                        if (col0 + j >= cols) break;
+                        const double v = pv[j];
+                        double out;
+                        switch (mode) {
+                            case 0: out = v; break;
+                            case 1: out = neg(v); break;
+                            case 2: out = cfd * v; break;
+                            case 3: out = __ldcg(prow + j) + v; break;
+                            case 4: out = __ldcg(prow + j) - v; break;
+                            default: out = fma(cfd, v, __ldcg(prow + j)); break;
+                        }
+                        prow[j] = out;
+                    }
+                }
+                __threadfence();
+                mbar_arrive(&B.epi_done);
+                if (leader) {
+                    if (!mbar_wait(&B.epi_done, dphase, abort, P.error, P.timeout_ns)) {
+                        ok = false;
+                    } else {
+                        __threadfence();
+                        atomicAdd(chain, 1u);
+                    }
+                }
+                dphase ^= 1u;
+            }
+            if (!ok) break;
+        }
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+constexpr size_t kSmemBytes = 1024 + STAGES * STAGE_BYTES + sizeof(Bars);
+
+}  // namespace
+
+cudaError_t launch_ozaki_tc(const CUtensorMap &map_a, const CUtensorMap &map_b, const OzParams &P, int grid,
+                            cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    ozaki_tc_kernel<<<grid, NTHREADS, kSmemBytes, s>>>(map_a, map_b, P);
+    return cudaGetLastError();
+}
+
+}  // namespace fmm
