@@ -46,8 +46,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=8192)
-    ap.add_argument("--algo", default="strassen", help="built-in name; suffix ^2 for its Kronecker square")
-    ap.add_argument("--depth", type=int, default=3)
+    ap.add_argument("--algo", default="strassen^2", help="built-in name; suffix ^2 for its Kronecker square")
+    ap.add_argument("--depth", type=int, default=2)
     ap.add_argument("--schedule", default="auto", choices=["auto", "fused", "hybrid"])
     ap.add_argument("--materialize-levels", type=int, default=0)
     ap.add_argument("--kind", default="uniform", choices=["uniform", "normal", "integer", "wide"])
@@ -59,6 +59,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=4096, help="size of the CPU-oracle sample")
     ap.add_argument("--sweep", action="store_true", help="print one JSON line per algorithm/depth/schedule")
+    ap.add_argument("--batched", action="store_true",
+                    help="batched workload: 256 products, n log-uniform in [128, 4096], one captured graph")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--no-emulated", action="store_true",
+                    help="skip the emulated-FP64 (Ozaki, Strassen depth 2) measurement added to the JSON line")
     return ap.parse_args(argv)
 
 
@@ -334,6 +339,77 @@ def run_sweep(a):
     return 0
 
 
+def run_batched(a):
+    import collections
+
+    import torch
+
+    import paper_2312_12732_gb300 as fmm
+    from paper_2312_12732_gb300 import _build, autotune, inputs
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sizes = inputs.batch_sizes(a.batch_count, 128, 4096, seed=3)
+    t0 = time.perf_counter()
+    plans, picks = autotune.plan_batch(sizes, candidates=("strassen", "winograd"), max_depth=3, min_leaf=128)
+    tune_s = time.perf_counter() - t0
+    As, Bs, Cs = [], [], []
+    for i, n in enumerate(sizes):
+        A, B = inputs.operands(n, "uniform", seed=1000 + 2 * i)
+        As.append(torch.from_numpy(A).to(dev))
+        Bs.append(torch.from_numpy(B).to(dev))
+        Cs.append(torch.empty_like(As[-1]))
+    flops = sum(2.0 * n ** 3 for n in sizes)
+    flops_exec = sum(p.info()["flops_executed"] for p in plans)
+
+    def time_graph(g, steps, warm):
+        stream = torch.cuda.current_stream()
+        for _ in range(warm):
+            fmm.fmm_batch_graph_launch(g, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fmm.fmm_batch_graph_launch(g, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    g = fmm.fmm_batch_graph_create(plans, As, Bs, Cs)
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    with sampler:
+        ms = time_graph(g, a.steps, max(a.warmup, 3))
+    st = fmm.fmm_sync_status(plans[0])
+    if st != 0:
+        raise RuntimeError("device status: " + fmm.fmm_status_string(st))
+    # spot check: a few products against a float64 GPU product
+    errs = []
+    for i in range(0, len(sizes), max(1, len(sizes) // 8)):
+        ref = As[i] @ Bs[i]
+        errs.append(((Cs[i] - ref).abs().max() / (sizes[i] * As[i].abs().max() * Bs[i].abs().max())).item())
+    plans0 = [fmm.fmm_plan_create(n, fmm.fmm_algo_builtin("strassen"), 0) for n in sizes]
+    g0 = fmm.fmm_batch_graph_create(plans0, As, Bs, Cs)
+    ms0 = time_graph(g0, max(2, a.steps // 2), 1)
+    hist = collections.Counter(f"{nm}:d{d}" for nm, d in picks)
+    line = {
+        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps,
+        "warmup": max(a.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batched_{len(sizes)}_loguniform_128_4096_uniform_fp64", "products": len(sizes),
+                   "sizes_min_max": [min(sizes), max(sizes)], "picks": dict(hist), "autotune_s": tune_s,
+                   "launch": "one CUDA graph: per-plan counter resets and materialization passes, then one "
+                             "grouped persistent leaf launch"},
+        "classic_depth0_graph": {"value": flops / (ms0 * 1e-3) / 1e12, "ms_per_step": ms0},
+        "flops_executed_per_step": flops_exec, "executed_tflops": flops_exec / (ms * 1e-3) / 1e12,
+        "speedup_vs_classic": ms0 / ms,
+        "normalised_error_sampled_max": max(errs),
+        "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -439,6 +515,37 @@ def run_ours(a):
                 "kernel_share_of_step": leaf_ms / ms if ms > 0 else None,
                 "frac_of_instruction_rate_measured_here": achieved / ref_rate if ref_rate else None, **extra}
 
+    emulated = None
+    if a.dtype == "f64" and not a.no_emulated:
+        e_algo = fmm.fmm_algo_builtin("strassen")
+        e_plan = fmm.fmm_plan_create(n, e_algo, 2, dtype="f64_ozaki", record_kernel_time=True)
+        e_ms, e_leaf = time_plan(torch, fmm, e_plan, dA, dB, dC, max(a.warmup, 3), a.steps, dist)
+        if dist is not None:
+            tt = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e_info = e_plan.info()
+        e_ref = dA[rows] @ dB[:, :64]
+        e_err = (dC[rows, :64] - e_ref).abs().max().item() / (n * dA.abs().max().item() * dB.abs().max().item())
+        fp8_peak, fp8_note = fp8_peak_tflops()
+        e4m3_rate = fmm.fmm_measure_e4m3_peak()
+        e_achieved = e_info["flops_lowp"] / (e_leaf * 1e-3) / 1e12
+        emulated = {
+            "workload": f"strassen_d2_n{n}_{a.kind}_ozaki{e_info['ozaki_slices']}",
+            "value": flops_eff * ws / (e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
+            "speedup_vs_classic": (flops_eff / (e_ms * 1e-3) / 1e12) / classic["value"] if classic else None,
+            "normalised_error_sampled": e_err, "ozaki_slices": e_info["ozaki_slices"],
+            "gpu_launches": a.steps * (2 * e_info["materialized_levels"] + 5 + (1 if n % 4 else 0)),
+            "roofline": {"bound": "tensor", "kernel": "ozaki_tc_kernel", "achieved": e_achieved, "peak": fp8_peak,
+                         "unit": "TFLOP/s", "frac": e_achieved / fp8_peak, "peak_note": fp8_note,
+                         "traffic": profile_traffic("ozaki_tc_kernel", f"strassen_d2_n{n}_{a.kind}_ozaki11"),
+                         "algorithmic_flops_per_launch": e_info["flops_lowp"], "avg_launch_ms": e_leaf,
+                         "kernel_share_of_step": e_leaf / e_ms,
+                         "e4m3_mma_sync_rate_measured_here": e4m3_rate},
+            "note": "same FP64 operands; S_r/T_r and post-additions in FP64, leaf products from 11 e4m3 "
+                    "slices with exact FP32/int64 sums (precision configuration)"}
+        fmm.fmm_plan_destroy(e_plan)
+
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         times, cores, cdepth = cpu_oracle_run(a, a.cpu_n, 1)
@@ -465,6 +572,7 @@ def run_ours(a):
         "gpu_launches": a.steps * ((1 + 2 * info["materialized_levels"]) if a.dtype == "f64" else
                                    (2 * info["materialized_levels"] + 5 + (1 if q > 0 else 0))),
         "roofline": roofline,
+        "emulated_fp64": emulated,
         "cpu_baseline": cpu,
         "flops_executed_per_step": info["flops_executed"],
         "executed_tflops": info["flops_executed"] / (ms * 1e-3) / 1e12,
@@ -484,6 +592,8 @@ def main(argv=None):
         return run_reference(a)
     if a.sweep:
         return run_sweep(a)
+    if a.batched:
+        return run_batched(a)
     return run_ours(a)
 
 

@@ -175,6 +175,36 @@ fmm_status_t fmm_gemm_host(fmm_plan_t *plan, const double *A_host, const double 
 fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double *const *A,
                               const double *const *B, double *const *C, int count, void *stream);
 
+/* A batched multiplication captured once into a CUDA graph (the counter
+ * resets, materialization passes and the one grouped leaf launch of
+ * fmm_gemm_batched), replayed with fmm_batch_graph_launch.  The plans and the
+ * A/B/C pointers are baked into the graph: they must stay valid and unchanged
+ * until fmm_batch_graph_destroy.  Creation captures on a private stream and
+ * does not run the work. */
+typedef struct fmm_batch_graph fmm_batch_graph_t;
+fmm_status_t fmm_batch_graph_create(fmm_batch_graph_t **out, fmm_plan_t *const *plans, const double *const *A,
+                                    const double *const *B, double *const *C, int count);
+/* Enqueue one replay of the captured batch on `stream` (asynchronous). */
+fmm_status_t fmm_batch_graph_launch(const fmm_batch_graph_t *g, void *stream);
+/* Free the graph (NULL-safe).  No replay may be pending. */
+void fmm_batch_graph_destroy(fmm_batch_graph_t *g);
+
+/* Autotuner, with no counterpart in the paper beyond its observation that the
+ * best algorithm depends on the problem size (Section 3): times one
+ * multiplication of size n on scratch operands for every candidate algorithm
+ * (index into `algos`) at every depth 0..max_depth whose leaf is at least
+ * min_leaf, with the default schedule and FMM_F64, and returns the fastest
+ * choice.  Depth 0 (the classic product) is always a candidate.  Blocking;
+ * allocates and frees 3 n^2 doubles and the candidate plans on the current
+ * device. */
+typedef struct {
+    int algo_index;   /* index into the candidate list */
+    int depth;
+    double ms;        /* measured time of the best candidate */
+} fmm_tune_result_t;
+fmm_status_t fmm_autotune(int64_t n, const fmm_algo_t *const *algos, int nalgos, int max_depth, int64_t min_leaf,
+                          void *stream, fmm_tune_result_t *best);
+
 /* Synchronize `stream`, then read and clear the plan's device error flag:
  * FMM_OK, FMM_ERR_TIMEOUT (a bounded wait expired; C is unspecified) or
  * FMM_ERR_CUDA. */

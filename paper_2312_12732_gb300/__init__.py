@@ -16,6 +16,11 @@ Typical use::
 """
 from ._binding import (  # noqa: F401
     Algo,
+    BatchGraph,
+    fmm_autotune,
+    fmm_batch_graph_create,
+    fmm_batch_graph_destroy,
+    fmm_batch_graph_launch,
     FmmError,
     Plan,
     fmm_algo_brent_mismatches,

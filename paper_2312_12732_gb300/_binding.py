@@ -67,6 +67,13 @@ SIGNATURES = [
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.c_int, ctypes.c_void_p]),
     ("fmm_sync_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("fmm_batch_graph_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                              ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                              ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
+    ("fmm_batch_graph_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("fmm_batch_graph_destroy", None, [ctypes.c_void_p]),
+    ("fmm_autotune", ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.POINTER(fmm_algo_t)), ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     ("fmm_plan_last_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
                                                ctypes.POINTER(ctypes.c_float)]),
     ("fmm_measure_fp64_peak", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -309,6 +316,59 @@ def fmm_gemm_batched(plans, As, Bs, Cs, stream=None):
     hc = arr(*[C.data_ptr() for C in Cs])
     _check(lib().fmm_gemm_batched(hp, ha, hb, hc, count, ctypes.c_void_p(_stream_ptr(stream))), "fmm_gemm_batched")
     return Cs
+
+
+class BatchGraph:
+    """A captured fmm_gemm_batched; keeps its plans and tensors alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keep
+
+    def __del__(self):
+        try:
+            fmm_batch_graph_destroy(self)
+        except Exception:
+            pass
+
+
+def fmm_batch_graph_create(plans, As, Bs, Cs) -> BatchGraph:
+    count = len(plans)
+    if not (len(As) == len(Bs) == len(Cs) == count) or count < 1:
+        raise ValueError("plans, A, B, C must have the same nonzero length")
+    for p, A, B, C in zip(plans, As, Bs, Cs):
+        for X, nm in ((A, "A"), (B, "B"), (C, "C")):
+            _check_operand(X, p.n, nm)
+    arr = ctypes.c_void_p * count
+    h = ctypes.c_void_p()
+    _check(lib().fmm_batch_graph_create(ctypes.byref(h), arr(*[p.handle.value for p in plans]),
+                                        arr(*[A.data_ptr() for A in As]), arr(*[B.data_ptr() for B in Bs]),
+                                        arr(*[C.data_ptr() for C in Cs]), count), "fmm_batch_graph_create")
+    return BatchGraph(h.value, (list(plans), list(As), list(Bs), list(Cs)))
+
+
+def fmm_batch_graph_launch(graph: BatchGraph, stream=None):
+    _check(lib().fmm_batch_graph_launch(graph.handle, ctypes.c_void_p(_stream_ptr(stream))), "fmm_batch_graph_launch")
+
+
+def fmm_batch_graph_destroy(graph: BatchGraph):
+    if graph is not None and graph.handle:
+        lib().fmm_batch_graph_destroy(graph.handle)
+        graph.handle = ctypes.c_void_p()
+
+
+class fmm_tune_result_t(ctypes.Structure):
+    _fields_ = [("algo_index", ctypes.c_int), ("depth", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
+def fmm_autotune(n: int, algos, max_depth: int = 3, min_leaf: int = 64, stream=None):
+    """(best algorithm, depth, ms) for size n among the candidates (the first also gives depth 0)."""
+    structs = [a.c_struct() for a in algos]
+    ptrs = (ctypes.POINTER(fmm_algo_t) * len(algos))(*[ctypes.pointer(x) for x in structs])
+    res = fmm_tune_result_t()
+    _check(lib().fmm_autotune(int(n), ptrs, len(algos), int(max_depth), int(min_leaf),
+                              ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(res)), f"fmm_autotune(n={n})")
+    return algos[res.algo_index], res.depth, res.ms
 
 
 def fmm_sync_status(plan: Plan, stream=None) -> int:

@@ -37,7 +37,7 @@ __device__ __forceinline__ bool chain_wait(const unsigned *ctr, unsigned target,
             return false;
         }
         __nanosleep(sleep);
-        if (sleep < 4096) sleep <<= 1;
+        if (sleep < 256) sleep <<= 1;
     }
 }
 

@@ -60,6 +60,8 @@ struct Smem {
     int nA, nB, nD;
     int rows, cols, K;
     int ok;
+    int pick;
+    unsigned char done[kMaxTerms];  // destinations of the current task already applied
 };
 
 using dev::chain_wait;
@@ -122,6 +124,7 @@ __device__ void setup_task(Smem &S, const F64Problem &pr, const F64Geom &g, long
             S.dst[e].chain = pr.chain + (long long)en.x * tiles + t;
             S.dst[e].coef = en.y;
             S.dst[e].pos = en.z;
+            S.done[e] = 0;
         }
         if (tid == 0) {
             S.nA = nA; S.nB = nB; S.nD = nD;
@@ -138,6 +141,7 @@ __device__ void setup_task(Smem &S, const F64Problem &pr, const F64Geom &g, long
     S.lda = n; S.ldb = n; S.ldc = n;
     S.srcA[0].coef = S.srcB[0].coef = 1;
     S.dst[0].coef = 1;
+    S.done[0] = 0;
     if (local < g.tasks_right) {  // C[0:nc, nc:n] = A[0:nc, :] B[:, nc:n]
         const int bi = (int)(local / g.rb_tn), bj = (int)(local % g.rb_tn);
         S.srcA[0].ptr = pr.A + (long long)bi * BM * n;
@@ -268,7 +272,12 @@ __device__ __forceinline__ void store_slab(Smem &S, int buf, const double (&ra)[
     }
 }
 
-__device__ __forceinline__ void mma_slab(const Smem &S, int buf, double (&acc)[4][4][4]) {
+// One K slab of MMAs.  m16 x n8 sub-tiles that lie entirely outside the
+// valid rows / columns of a ragged tile are skipped (row_ok / col_ok are
+// uniform across the warp): the FP64 pipe is shared by the SM's warps, so the
+// skipped work shortens the task instead of being computed on zeros.
+__device__ __forceinline__ void mma_slab(const Smem &S, int buf, double (&acc)[4][4][4], unsigned row_ok,
+                                         unsigned col_ok) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int wm = warp & 1, wn = warp >> 1;  // 2 x 4 warps, warp tile 64 x 32
@@ -288,7 +297,32 @@ __device__ __forceinline__ void mma_slab(const Smem &S, int buf, double (&acc)[4
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) dmma_16x8x4(acc[i][j], af[i], bf[j]);
+            for (int j = 0; j < 4; ++j)
+                if (((row_ok >> i) & (col_ok >> j)) & 1u) dmma_16x8x4(acc[i][j], af[i], bf[j]);
+    }
+}
+
+// Index of a destination of the current task that is not applied yet and
+// whose ordering counter has reached its position (or -1 after a timeout or
+// another CTA's error).  Destinations are applied in whatever order they
+// become ready; each (C block, tile) still sees its contributions in
+// ascending product order.  Called by one thread.
+__device__ int pick_ready(const Smem &S, int *error, long long timeout_ns) {
+    const unsigned long long t0 = global_ns();
+    unsigned sleep = 32;
+    while (true) {
+        for (int d = 0; d < S.nD; ++d) {
+            if (S.done[d]) continue;
+            const Dst &dst = S.dst[d];
+            if (dst.chain == nullptr || dst.pos == 0 || dev::ld_acquire(dst.chain) == (unsigned)dst.pos) return d;
+        }
+        if (ld_volatile(error) != kDevOk) return -1;
+        if ((long long)(global_ns() - t0) > timeout_ns) {
+            atomicCAS(error, kDevOk, kDevTimeout);
+            return -1;
+        }
+        __nanosleep(sleep);
+        if (sleep < 256) sleep <<= 1;
     }
 }
 
@@ -311,9 +345,26 @@ __global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ 
         const long long task = S.task;
         if (task >= L.total_tasks) break;
         int pi = 0;
-        while (pi + 1 < L.nprobs && L.probs[pi + 1].task_begin <= task) ++pi;
+        long long local = 0;
+        if (L.interleave) {
+            // seg_start[q - 1] (the first global index of the rounds with q
+            // active problems) never increases with q; the segment holding
+            // `task` is the smallest q with seg_start[q - 1] <= task.
+            int lo = 1, hi = L.nprobs;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (L.seg_start[mid - 1] <= task) hi = mid; else lo = mid + 1;
+            }
+            const int q = lo;
+            const long long o = task - L.seg_start[q - 1];
+            local = L.seg_round[q - 1] + o / q;
+            pi = L.order[(int)(o % q)];
+        } else {
+            while (pi + 1 < L.nprobs && L.probs[pi + 1].task_begin <= task) ++pi;
+            local = task - L.probs[pi].task_begin;
+        }
         const F64Problem &pr = L.probs[pi];
-        setup_task(S, pr, *pr.g, task - pr.task_begin);
+        setup_task(S, pr, *pr.g, local);
         __syncthreads();
 
         double acc[4][4][4];
@@ -326,6 +377,12 @@ __global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ 
 
         const int K = S.K;
         const int nk = (K + BK - 1) / BK;
+        unsigned row_ok = 0, col_ok = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            row_ok |= (unsigned)(wm * 64 + i * 16 < S.rows) << i;
+            col_ok |= (unsigned)(wn * 32 + i * 8 < S.cols) << i;
+        }
         double ra[8], rb[8];
         if (nk > 0) {
             load_slab(S, 0, ra, rb);
@@ -335,7 +392,7 @@ __global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ 
         for (int kt = 0; kt < nk; ++kt) {
             const bool more = kt + 1 < nk;
             if (more) load_slab(S, (kt + 1) * BK, ra, rb);
-            mma_slab(S, kt & 1, acc);
+            mma_slab(S, kt & 1, acc, row_ok, col_ok);
             if (more) store_slab(S, (kt + 1) & 1, ra, rb);
             __syncthreads();
         }
@@ -343,16 +400,12 @@ __global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ 
         // Epilogue: coefficient-weighted stores into every destination tile.
         const int rows = S.rows, cols = S.cols;
         const long long ldc = S.ldc;
-        for (int d = 0; d < S.nD; ++d) {
-            const Dst dst = S.dst[d];
-            if (tid == 0) {
-                bool ok = true;
-                if (dst.chain != nullptr && dst.pos > 0)
-                    ok = chain_wait(dst.chain, (unsigned)dst.pos, L.error, L.timeout_ns);
-                S.ok = ok ? 1 : 0;
-            }
+        for (int remaining = S.nD; remaining > 0; --remaining) {
+            if (tid == 0) S.pick = pick_ready(S, L.error, L.timeout_ns);
             __syncthreads();
-            if (!S.ok) break;
+            const int d = S.pick;
+            if (d < 0) break;
+            const Dst dst = S.dst[d];
             const bool first = dst.pos == 0;
             const int cf = dst.coef;
             const double cfd = (double)cf;  // used only when |cf| != 1
@@ -385,9 +438,12 @@ __global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ 
                         }
                     }
             __syncthreads();
-            if (tid == 0 && dst.chain != nullptr) {
-                __threadfence();
-                atomicAdd(dst.chain, 1u);
+            if (tid == 0) {
+                if (dst.chain != nullptr) {
+                    __threadfence();
+                    atomicAdd(dst.chain, 1u);
+                }
+                S.done[d] = 1;
             }
         }
         __syncthreads();

@@ -895,8 +895,11 @@ extern "C" fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double 
                                          double *const *C, int count, void *stream) {
     if (count < 0 || (count > 0 && (!plans || !A || !B || !C))) return FMM_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
         if (!plans[i] || !A[i] || !B[i] || !C[i] || plans[i]->dtype != FMM_F64) return FMM_ERR_INVALID;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return FMM_ERR_INVALID;  // a plan's counters serve one product
+    }
     for (int i0 = 0; i0 < count; i0 += fmm::kMaxBatchPerLaunch) {
         const int cnt = std::min(count - i0, fmm::kMaxBatchPerLaunch);
         // The first plan of each chunk owns the shared task counter / error word.
@@ -918,6 +921,26 @@ extern "C" fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double 
         L->task_counter = lead->d_task_counter;
         L->error = lead->d_error;
         L->timeout_ns = (long long)(lead->timeout_s * 1e9);
+        if (cnt > 1) {
+            // interleaved order: problems by task count, descending, round-robin
+            std::vector<int> idx(cnt);
+            for (int k = 0; k < cnt; ++k) idx[k] = k;
+            std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+                return plans[i0 + x]->total_tasks > plans[i0 + y]->total_tasks;
+            });
+            std::vector<long long> c(cnt + 1, 0);
+            for (int j = 0; j < cnt; ++j) {
+                c[j] = plans[i0 + idx[j]]->total_tasks;
+                L->order[j] = (short)idx[j];
+            }
+            long long G = 0;
+            for (int q = cnt; q >= 1; --q) {  // segment with q active problems
+                L->seg_start[q - 1] = G;
+                L->seg_round[q - 1] = (int)c[q];
+                G += (long long)q * (c[q - 1] - c[q]);
+            }
+            L->interleave = 1;
+        }
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lead->device);
         grid = (int)std::min<long long>(begin, (long long)sms * fmm::f64_kernel_ctas_per_sm());
@@ -927,6 +950,133 @@ extern "C" fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double 
         if (e != cudaSuccess) return FMM_ERR_CUDA;
     }
     return FMM_OK;
+}
+
+struct fmm_batch_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" fmm_status_t fmm_batch_graph_create(fmm_batch_graph_t **out, fmm_plan_t *const *plans,
+                                               const double *const *A, const double *const *B, double *const *C,
+                                               int count) {
+    if (!out || count < 1) return FMM_ERR_INVALID;
+    *out = nullptr;
+    // kernel attributes are set outside the capture
+    if (fmm::f64_kernel_ctas_per_sm() <= 0) return FMM_ERR_CUDA;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return FMM_ERR_CUDA;
+    fmm_batch_graph *g = new (std::nothrow) fmm_batch_graph();
+    if (!g) {
+        cudaStreamDestroy(cs);
+        return FMM_ERR_OOM;
+    }
+    fmm_status_t st = FMM_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        st = FMM_ERR_CUDA;
+    } else {
+        st = fmm_gemm_batched(plans, A, B, C, count, (void *)cs);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (st == FMM_OK && e != cudaSuccess) st = FMM_ERR_CUDA;
+        g->graph = graph;
+        if (st == FMM_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) st = FMM_ERR_CUDA;
+    }
+    cudaStreamDestroy(cs);
+    if (st != FMM_OK) {
+        cudaGetLastError();
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return FMM_OK;
+}
+
+extern "C" fmm_status_t fmm_batch_graph_launch(const fmm_batch_graph_t *g, void *stream) {
+    if (!g || !g->exec) return FMM_ERR_INVALID;
+    return cuda_status(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+}
+
+extern "C" void fmm_batch_graph_destroy(fmm_batch_graph_t *g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+namespace {
+
+__global__ void fill_kernel(double *x, long long count, unsigned long long seed) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ULL;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        x[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    }
+}
+
+}  // namespace
+
+extern "C" fmm_status_t fmm_autotune(int64_t n, const fmm_algo_t *const *algos, int nalgos, int max_depth,
+                                     int64_t min_leaf, void *stream, fmm_tune_result_t *best) {
+    if (n < 1 || !algos || nalgos < 1 || max_depth < 0 || !best || min_leaf < 1) return FMM_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
+    double *A = nullptr, *B = nullptr, *C = nullptr;
+    if (cudaMalloc(&A, bytes) != cudaSuccess || cudaMalloc(&B, bytes) != cudaSuccess ||
+        cudaMalloc(&C, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(A);
+        cudaFree(B);
+        cudaFree(C);
+        return FMM_ERR_OOM;
+    }
+    fill_kernel<<<256, 256, 0, st>>>(A, (long long)n * n, 11);
+    fill_kernel<<<256, 256, 0, st>>>(B, (long long)n * n, 12);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fmm_status_t result = FMM_ERR_INVALID;
+    best->ms = 1e30;
+    for (int ai = 0; ai < nalgos; ++ai) {
+        if (!algos[ai]) continue;
+        for (int d = (ai == 0 ? 0 : 1); d <= max_depth; ++d) {
+            long long P = 1;
+            for (int k = 0; k < d; ++k) P *= algos[ai]->p;
+            if (d > 0 && n / P < min_leaf) break;
+            fmm_plan_t *pl = nullptr;
+            if (fmm_plan_create(&pl, n, algos[ai], d, FMM_F64) != FMM_OK) continue;
+            float ms = 0.f, best_run = 1e30f;
+            bool ok = fmm_gemm(pl, A, B, C, st) == FMM_OK;  // warm-up
+            for (int rep = 0; rep < 2 && ok; ++rep) {
+                cudaEventRecord(e0, st);
+                ok = fmm_gemm(pl, A, B, C, st) == FMM_OK;
+                cudaEventRecord(e1, st);
+                if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                    best_run = ms < best_run ? ms : best_run;
+                else
+                    ok = false;
+            }
+            if (ok && fmm_sync_status(pl, stream) == FMM_OK && best_run < best->ms) {
+                best->ms = best_run;
+                best->algo_index = ai;
+                best->depth = d;
+                result = FMM_OK;
+            }
+            fmm_plan_destroy(pl);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(A);
+    cudaFree(B);
+    cudaFree(C);
+    if (cudaGetLastError() != cudaSuccess) return FMM_ERR_CUDA;
+    return result;
 }
 
 extern "C" fmm_status_t fmm_sync_status(const fmm_plan_t *pl, void *stream) {

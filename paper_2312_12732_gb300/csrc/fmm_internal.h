@@ -69,10 +69,21 @@ struct F64Launch {
     unsigned long long *task_counter;
     int *error;
     long long timeout_ns;
+    // Interleaved order (grouped launches, interleave = 1): problems sorted by
+    // task count, descending, are visited round-robin by local task index, so
+    // that concurrently running tasks mostly belong to different problems.
+    // Segment q (q = nprobs .. 1 active problems) starts at global index
+    // seg_start[q - 1] and covers rounds [seg_round[q - 1], ...); order[j] is
+    // the problem at sorted position j.  Each problem's own order is kept, so
+    // every post-addition wait still points at a lower global index.
+    int interleave;
+    long long seg_start[MAXP];
+    int seg_round[MAXP];
+    short order[MAXP];
     F64Problem probs[MAXP];
 };
 
-constexpr int kMaxBatchPerLaunch = 128;
+constexpr int kMaxBatchPerLaunch = 256;
 
 // Emulated-FP64 leaf (fmm_ozaki.cu): balanced digits of kOzDigitBits bits
 // stored as e4m3, up to kOzMaxSlices slices per operand.
