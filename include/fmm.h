@@ -90,6 +90,8 @@ typedef struct {
                                 writes, so that its waiters time out */
     int record_kernel_time;  /* 1 = record CUDA events around each call's work on
                                 its stream (see fmm_plan_last_kernel_ms) */
+    int tile_n;              /* FMM_F64 leaf tile width: 128 (one 8-warp CTA per SM)
+                                or 64 (two 4-warp CTAs per SM); 0 = planner's choice */
 } fmm_plan_options_t;
 
 /* Read-only description of a plan (all sizes in elements). */
@@ -107,6 +109,7 @@ typedef struct {
     size_t workspace_bytes;
     int ozaki_slices;       /* FMM_F64_OZAKI: slices per operand (0 otherwise) */
     double flops_lowp;      /* FMM_F64_OZAKI: e4m3 tensor-core flops of the slice products */
+    int tile_n;             /* leaf tile width of the FP64 kernel (128 or 64) */
 } fmm_plan_info_t;
 
 /* Status code to a static, NUL-terminated English string (never NULL). */

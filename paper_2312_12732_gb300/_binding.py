@@ -35,7 +35,7 @@ class fmm_algo_t(ctypes.Structure):
 class fmm_plan_options_t(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int), ("materialize_levels", ctypes.c_int), ("ozaki_slices", ctypes.c_int),
                 ("wait_timeout_s", ctypes.c_double), ("debug_poison_chain", ctypes.c_int),
-                ("record_kernel_time", ctypes.c_int)]
+                ("record_kernel_time", ctypes.c_int), ("tile_n", ctypes.c_int)]
 
 
 class fmm_plan_info_t(ctypes.Structure):
@@ -43,7 +43,8 @@ class fmm_plan_info_t(ctypes.Structure):
                 ("R_total", ctypes.c_int64), ("m", ctypes.c_int64), ("n_core", ctypes.c_int64),
                 ("tasks", ctypes.c_int64), ("materialized_levels", ctypes.c_int),
                 ("flops_leaf", ctypes.c_double), ("flops_executed", ctypes.c_double),
-                ("workspace_bytes", ctypes.c_size_t), ("ozaki_slices", ctypes.c_int), ("flops_lowp", ctypes.c_double)]
+                ("workspace_bytes", ctypes.c_size_t), ("ozaki_slices", ctypes.c_int), ("flops_lowp", ctypes.c_double),
+                ("tile_n", ctypes.c_int)]
 
 
 # (name, restype, argtypes) for every symbol declared in include/fmm.h.
@@ -198,11 +199,12 @@ class Plan:
 
 def fmm_plan_create(n: int, algo: Algo, depth: int, dtype: str = "f64", schedule: str = "auto",
                     materialize_levels: int = 0, ozaki_slices: int = 0, wait_timeout_s: float = 0.0,
-                    debug_poison_chain: int = 0, record_kernel_time: bool = False) -> Plan:
+                    debug_poison_chain: int = 0, record_kernel_time: bool = False, tile_n: int = 0) -> Plan:
     h = ctypes.c_void_p()
     a = algo.c_struct()
     opts = fmm_plan_options_t(SCHEDULES[schedule], int(materialize_levels), int(ozaki_slices),
-                              float(wait_timeout_s), int(debug_poison_chain), int(bool(record_kernel_time)))
+                              float(wait_timeout_s), int(debug_poison_chain), int(bool(record_kernel_time)),
+                              int(tile_n))
     _check(lib().fmm_plan_create_ex(ctypes.byref(h), int(n), ctypes.byref(a), int(depth), DTYPES[dtype],
                                     ctypes.byref(opts)), f"fmm_plan_create(n={n}, {algo}, depth={depth})")
     return Plan(h.value, int(n), algo, int(depth), dtype)

@@ -3,7 +3,7 @@
 // One persistent kernel serves the classic product (depth 0), every flattened
 // bilinear algorithm, peeled sizes and grouped batches.  CTAs fetch tile tasks
 // from a global counter in increasing order.  A core task computes one
-// kBM x kBN tile of a leaf product P_r = S_r T_r (Section 2, equation
+// 128 x 128 (or 128 x 64) tile of a leaf product P_r = S_r T_r (Section 2, equation
 // `strassen`):
 //   * operand staging forms the S_r / T_r slab on the fly from the source
 //     blocks named by column r of U and V (pre-additions fused into the
@@ -28,12 +28,15 @@
 namespace fmm {
 namespace {
 
-constexpr int BM = kBM, BN = kBN, BK = kBK, NT = kThreads;
+// Tile configurations (template parameter BNT): BM = 128 rows by BNT = 128
+// or 64 columns, NT = 2 * BNT threads (2 x BNT/32 warps, warp tile 64 x 32).
+// The 128-column tile runs one CTA per SM; the 64-column tile fits two, so
+// one CTA's prologue and epilogue overlap the other's MMAs.
+constexpr int BM = kBM, BK = kBK;
 // Shared-memory row pitches (in doubles) chosen so that the m16n8k4 fragment
 // reads are free of bank conflicts: A rows 20 doubles apart (8 banks of
-// 4 bytes mod 32), B rows 132 apart (8 banks mod 32).
+// 4 bytes mod 32), B rows BNT + 4 apart (8 banks mod 32 for BNT = 64, 128).
 constexpr int A_LD = BK + 4;
-constexpr int B_LD = BN + 4;
 
 // Coefficients stay integers on the device: tests on them run on the integer
 // pipe, and only coefficients other than +-1 are ever converted to FP64.
@@ -49,9 +52,10 @@ struct Dst {
     int pos;            // number of contributions that must precede this one
 };
 
+template <int BNT>
 struct Smem {
     double a[2][BM * A_LD];
-    double b[2][BK * B_LD];
+    double b[2][BK * (BNT + 4)];
     Src srcA[kMaxTerms];
     Src srcB[kMaxTerms];
     Dst dst[kMaxTerms];
@@ -87,7 +91,9 @@ __device__ __forceinline__ void dmma_16x8x4(double (&d)[4], const double (&a)[2]
 // Decodes task `local` of problem `pr` into the shared source / destination
 // lists.  All threads run the index arithmetic; list entries are filled in
 // parallel.
-__device__ void setup_task(Smem &S, const F64Problem &pr, const F64Geom &g, long long local) {
+template <int BNT>
+__device__ void setup_task(Smem<BNT> &S, const F64Problem &pr, const F64Geom &g, long long local) {
+    constexpr int BN = BNT, NT = 2 * BNT;
     const int tid = threadIdx.x;
     const long long n = g.n, m = g.m, nc = g.n_core;
     const long long q = n - nc;
@@ -185,60 +191,64 @@ __device__ void setup_task(Smem &S, const F64Problem &pr, const F64Geom &g, long
 
 // Accumulates one source's 8 values into r[] with the coefficient's sign
 // resolved once per source (uniform across the CTA, so no divergence).
-__device__ __forceinline__ void accumulate8(double (&r)[8], const double (&v)[8], int c, bool first) {
+template <int N>
+__device__ __forceinline__ void accumulate(double (&r)[N], const double (&v)[N], int c, bool first) {
     if (first) {
         if (c == 1) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) r[j] = v[j];
+            for (int j = 0; j < N; ++j) r[j] = v[j];
         } else if (c == -1) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) r[j] = neg(v[j]);
+            for (int j = 0; j < N; ++j) r[j] = neg(v[j]);
         } else {
             const double cd = (double)c;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) r[j] = cd * v[j];
+            for (int j = 0; j < N; ++j) r[j] = cd * v[j];
         }
     } else {
         if (c == 1) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) r[j] += v[j];
+            for (int j = 0; j < N; ++j) r[j] += v[j];
         } else if (c == -1) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) r[j] -= v[j];
+            for (int j = 0; j < N; ++j) r[j] -= v[j];
         } else {
             const double cd = (double)c;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) r[j] = fma(cd, v[j], r[j]);
+            for (int j = 0; j < N; ++j) r[j] = fma(cd, v[j], r[j]);
         }
     }
 }
 
 // Loads the K slab [kk, kk + BK) of both operands, combining the sources.
-__device__ __forceinline__ void load_slab(const Smem &S, int kk, double (&ra)[8], double (&rb)[8]) {
+// A: thread column c = tid % 16, rows r0 + (NT/16) j; B: column tid % BNT,
+// rows r0 + 2 j.
+template <int BNT>
+__device__ __forceinline__ void load_slab(const Smem<BNT> &S, int kk, double (&ra)[1024 / BNT],
+                                          double (&rb)[8]) {
+    constexpr int NT = 2 * BNT, AP = 2048 / NT, RS = NT / 16;
     const int tid = threadIdx.x;
-    // A: column c of the slab, rows r0 + 16 j.
     {
         const int c = tid & 15, r0 = tid >> 4;
         const bool kval = kk + c < S.K;
         const long long lda = S.lda;
         for (int e = 0; e < S.nA; ++e) {
             const double *p = S.srcA[e].ptr + kk + c;
-            double v[8];
+            double v[AP];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int row = r0 + 16 * j;
+            for (int j = 0; j < AP; ++j) {
+                const int row = r0 + RS * j;
                 v[j] = (kval && row < S.rows) ? __ldg(p + row * lda) : 0.0;
             }
-            accumulate8(ra, v, S.srcA[e].coef, e == 0);
+            accumulate<AP>(ra, v, S.srcA[e].coef, e == 0);
         }
         if (S.nA == 0) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) ra[j] = 0.0;
+            for (int j = 0; j < AP; ++j) ra[j] = 0.0;
         }
     }
-    // B: column c of the slab, rows r0 + 2 j.
     {
-        const int c = tid & 127, r0 = tid >> 7;
+        const int c = tid & (BNT - 1), r0 = tid / BNT;
         const bool cval = c < S.cols;
         const long long ldb = S.ldb;
         for (int e = 0; e < S.nB; ++e) {
@@ -249,7 +259,7 @@ __device__ __forceinline__ void load_slab(const Smem &S, int kk, double (&ra)[8]
                 const int row = r0 + 2 * j;
                 v[j] = (cval && kk + row < S.K) ? __ldg(p + row * ldb) : 0.0;
             }
-            accumulate8(rb, v, S.srcB[e].coef, e == 0);
+            accumulate<8>(rb, v, S.srcB[e].coef, e == 0);
         }
         if (S.nB == 0) {
 #pragma unroll
@@ -258,17 +268,20 @@ __device__ __forceinline__ void load_slab(const Smem &S, int kk, double (&ra)[8]
     }
 }
 
-__device__ __forceinline__ void store_slab(Smem &S, int buf, const double (&ra)[8], const double (&rb)[8]) {
+template <int BNT>
+__device__ __forceinline__ void store_slab(Smem<BNT> &S, int buf, const double (&ra)[1024 / BNT],
+                                           const double (&rb)[8]) {
+    constexpr int NT = 2 * BNT, AP = 2048 / NT, RS = NT / 16;
     const int tid = threadIdx.x;
     {
         const int c = tid & 15, r0 = tid >> 4;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) S.a[buf][(r0 + 16 * j) * A_LD + c] = ra[j];
+        for (int j = 0; j < AP; ++j) S.a[buf][(r0 + RS * j) * A_LD + c] = ra[j];
     }
     {
-        const int c = tid & 127, r0 = tid >> 7;
+        const int c = tid & (BNT - 1), r0 = tid / BNT;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) S.b[buf][(r0 + 2 * j) * B_LD + c] = rb[j];
+        for (int j = 0; j < 8; ++j) S.b[buf][(r0 + 2 * j) * (BNT + 4) + c] = rb[j];
     }
 }
 
@@ -276,11 +289,13 @@ __device__ __forceinline__ void store_slab(Smem &S, int buf, const double (&ra)[
 // valid rows / columns of a ragged tile are skipped (row_ok / col_ok are
 // uniform across the warp): the FP64 pipe is shared by the SM's warps, so the
 // skipped work shortens the task instead of being computed on zeros.
-__device__ __forceinline__ void mma_slab(const Smem &S, int buf, double (&acc)[4][4][4], unsigned row_ok,
+template <int BNT>
+__device__ __forceinline__ void mma_slab(const Smem<BNT> &S, int buf, double (&acc)[4][4][4], unsigned row_ok,
                                          unsigned col_ok) {
+    constexpr int B_LD = BNT + 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int wm = warp & 1, wn = warp >> 1;  // 2 x 4 warps, warp tile 64 x 32
+    const int wm = warp & 1, wn = warp >> 1;  // 2 x BNT/32 warps, warp tile 64 x 32
     const double *As = S.a[buf];
     const double *Bs = S.b[buf];
 #pragma unroll
@@ -307,7 +322,8 @@ __device__ __forceinline__ void mma_slab(const Smem &S, int buf, double (&acc)[4
 // another CTA's error).  Destinations are applied in whatever order they
 // become ready; each (C block, tile) still sees its contributions in
 // ascending product order.  Called by one thread.
-__device__ int pick_ready(const Smem &S, int *error, long long timeout_ns) {
+template <int BNT>
+__device__ int pick_ready(const Smem<BNT> &S, int *error, long long timeout_ns) {
     const unsigned long long t0 = global_ns();
     unsigned sleep = 32;
     while (true) {
@@ -326,10 +342,10 @@ __device__ int pick_ready(const Smem &S, int *error, long long timeout_ns) {
     }
 }
 
-template <int MAXP>
-__global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ F64Launch<MAXP> L) {
+template <int MAXP, int BNT>
+__global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __grid_constant__ F64Launch<MAXP> L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    Smem<BNT> &S = *reinterpret_cast<Smem<BNT> *>(smem_raw);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t4 = lane & 3;
@@ -383,7 +399,7 @@ __global__ void __launch_bounds__(NT, 1) fmm_f64_kernel(const __grid_constant__ 
             row_ok |= (unsigned)(wm * 64 + i * 16 < S.rows) << i;
             col_ok |= (unsigned)(wn * 32 + i * 8 < S.cols) << i;
         }
-        double ra[8], rb[8];
+        double ra[1024 / BNT], rb[8];
         if (nk > 0) {
             load_slab(S, 0, ra, rb);
             store_slab(S, 0, ra, rb);
@@ -480,43 +496,44 @@ __global__ void materialize_level_kernel(const double *__restrict__ in, long lon
 
 }  // namespace
 
-size_t f64_kernel_smem_bytes() { return sizeof(Smem); }
+size_t f64_kernel_smem_bytes(int bn) { return bn == 64 ? sizeof(Smem<64>) : sizeof(Smem<128>); }
 
-static cudaError_t prepare_attr(const void *fn) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+template <int MAXP, int BNT>
+static cudaError_t launch_cfg(const F64Launch<MAXP> &L, int grid, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(fmm_f64_kernel<MAXP, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(Smem<BNT>));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    fmm_f64_kernel<MAXP, BNT><<<grid, 2 * BNT, sizeof(Smem<BNT>), s>>>(L);
+    return cudaGetLastError();
 }
 
-int f64_kernel_ctas_per_sm() {
+template <int BNT>
+static int ctas_per_sm_cfg() {
     static int cached = -1;
     if (cached >= 0) return cached;
-    if (prepare_attr((const void *)fmm_f64_kernel<1>) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(fmm_f64_kernel<1, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(Smem<BNT>)) != cudaSuccess)
+        return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fmm_f64_kernel<1>, NT, sizeof(Smem)) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fmm_f64_kernel<1, BNT>, 2 * BNT, sizeof(Smem<BNT>)) !=
+        cudaSuccess)
         return 0;
     cached = nb;
     return nb;
 }
 
-cudaError_t launch_f64_single(const F64Launch<1> &L, int grid, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = prepare_attr((const void *)fmm_f64_kernel<1>);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    fmm_f64_kernel<1><<<grid, NT, sizeof(Smem), s>>>(L);
-    return cudaGetLastError();
+int f64_kernel_ctas_per_sm(int bn) { return bn == 64 ? ctas_per_sm_cfg<64>() : ctas_per_sm_cfg<128>(); }
+
+cudaError_t launch_f64_single(const F64Launch<1> &L, int grid, cudaStream_t s, int bn) {
+    return bn == 64 ? launch_cfg<1, 64>(L, grid, s) : launch_cfg<1, 128>(L, grid, s);
 }
 
-cudaError_t launch_f64_batch(const F64Launch<kMaxBatchPerLaunch> &L, int grid, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = prepare_attr((const void *)fmm_f64_kernel<kMaxBatchPerLaunch>);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    fmm_f64_kernel<kMaxBatchPerLaunch><<<grid, NT, sizeof(Smem), s>>>(L);
-    return cudaGetLastError();
+cudaError_t launch_f64_batch(const F64Launch<kMaxBatchPerLaunch> &L, int grid, cudaStream_t s, int bn) {
+    return bn == 64 ? launch_cfg<kMaxBatchPerLaunch, 64>(L, grid, s) : launch_cfg<kMaxBatchPerLaunch, 128>(L, grid, s);
 }
 
 cudaError_t launch_materialize_level(const double *in, long long ld_in, long long in_stride, int n_in,

@@ -283,6 +283,7 @@ struct fmm_plan {
     fmm_dtype_t dtype = FMM_F64;
     int64_t P = 1, P_src = 1, R_total = 1, R_src = 1, nsub = 1, m = 0, n_core = 0, b_src = 0;
     int tiles_m = 0, tiles_n = 0;
+    int bn = fmm::kBN;  // leaf tile width of the FP64 kernel
     F64Geom geom{};  // host copy (device pointers inside)
     long long total_tasks = 0;
     double timeout_s = 5.0;
@@ -318,6 +319,7 @@ struct fmm_plan {
     bool timed_once = false;
     // statistics
     double flops_leaf = 0, flops_exec = 0;
+    long long total_products_hint = 0;
     int grid = 0;
     int sms = 0;
 };
@@ -389,6 +391,18 @@ int default_materialized_levels(int p, int R, const fmm_algo_t *a, int depth) {
     return avg > 1.5 ? depth : 0;
 }
 
+// Leaf tile width.  Both widths run the same 64 x 32 warp tiles; the 64-column
+// tile fits two CTAs per SM so that one CTA's prologue and epilogue overlap
+// the other's MMAs, and it halves the ragged-tile waste for small leaves.
+int default_tile_n(long long m, long long products) {
+    (void)products;
+    (void)m;
+    const char *env = std::getenv("FMM_TILE_N");
+    if (env && std::string(env) == "128") return 128;
+    if (env && std::string(env) == "64") return 64;
+    return 64;
+}
+
 }  // namespace
 
 extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
@@ -434,7 +448,15 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     pl->nsub = ipow(R, mat);
     pl->b_src = pl->P_src * pl->m;
     pl->tiles_m = (int)((pl->m + fmm::kBM - 1) / fmm::kBM);
-    pl->tiles_n = (int)((pl->m + fmm::kBN - 1) / fmm::kBN);
+    if (dtype == FMM_F64_OZAKI) {
+        pl->bn = fmm::kBN;  // the slice GEMM and its counters use 128 x 128 tiles
+    } else if (o.tile_n) {
+        if (o.tile_n != 64 && o.tile_n != 128) { delete pl; return FMM_ERR_INVALID; }
+        pl->bn = o.tile_n;
+    } else {
+        pl->bn = default_tile_n(pl->m, pl->total_products_hint = Rt);
+    }
+    pl->tiles_n = (int)((pl->m + pl->bn - 1) / pl->bn);
     if (o.wait_timeout_s > 0) pl->timeout_s = o.wait_timeout_s;
     pl->poison = o.debug_poison_chain;
 
@@ -485,6 +507,7 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     g.n = n; g.m = pl->m; g.n_core = pl->n_core;
     g.P = (int)P; g.P_src = (int)pl->P_src; g.R_src = (int)pl->R_src; g.nsub = (int)pl->nsub;
     g.tiles_m = pl->tiles_m; g.tiles_n = pl->tiles_n;
+    g.bn = pl->bn;
     g.ld_src_a = mat > 0 ? pl->b_src : n;
     g.ld_src_b = g.ld_src_a;
     g.sub_stride_a = mat > 0 ? pl->b_src * pl->b_src : 0;
@@ -492,9 +515,9 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     g.tasks_core = tiles * Rt;
     if (q > 0) {
         g.rb_tm = (int)((pl->n_core + fmm::kBM - 1) / fmm::kBM);
-        g.rb_tn = (int)((q + fmm::kBN - 1) / fmm::kBN);
+        g.rb_tn = (int)((q + pl->bn - 1) / pl->bn);
         g.bb_tm = (int)((q + fmm::kBM - 1) / fmm::kBM);
-        g.bb_tn = (int)((n + fmm::kBN - 1) / fmm::kBN);
+        g.bb_tn = (int)((n + pl->bn - 1) / pl->bn);
         g.tasks_right = (long long)g.rb_tm * g.rb_tn;
         g.tasks_bottom = (long long)g.bb_tm * g.bb_tn;
         g.tasks_rankq = (long long)P * P * tiles;
@@ -676,8 +699,8 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
-    const int per_sm = dtype == FMM_F64_OZAKI ? fmm::ozaki_ctas_per_sm() : fmm::f64_kernel_ctas_per_sm();
-    if (per_sm <= 0 || fmm::f64_kernel_ctas_per_sm() <= 0) {
+    const int per_sm = dtype == FMM_F64_OZAKI ? fmm::ozaki_ctas_per_sm() : fmm::f64_kernel_ctas_per_sm(pl->bn);
+    if (per_sm <= 0 || fmm::f64_kernel_ctas_per_sm(pl->bn) <= 0) {
         cudaGetLastError();
         free_plan_memory(pl);
         delete pl;
@@ -821,8 +844,8 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
         L.probs[0].C = C;
         L.probs[0].chain = pl->d_chain;
         L.probs[0].task_begin = 0;
-        const int g2 = (int)std::min<long long>(peel, (long long)pl->sms * fmm::f64_kernel_ctas_per_sm());
-        if (fmm::launch_f64_single(L, g2 < 1 ? 1 : g2, st) != cudaSuccess) return FMM_ERR_CUDA;
+        const int g2 = (int)std::min<long long>(peel, (long long)pl->sms * fmm::f64_kernel_ctas_per_sm(pl->bn));
+        if (fmm::launch_f64_single(L, g2 < 1 ? 1 : g2, st, pl->bn) != cudaSuccess) return FMM_ERR_CUDA;
     }
     return FMM_OK;
 }
@@ -848,7 +871,7 @@ extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const do
     L.error = pl->d_error;
     L.timeout_ns = (long long)(pl->timeout_s * 1e9);
     L.probs[0] = problem_of(pl, A, B, C, 0);
-    fmm_status_t ls = cuda_status(fmm::launch_f64_single(L, pl->grid, st));
+    fmm_status_t ls = cuda_status(fmm::launch_f64_single(L, pl->grid, st, pl->bn));
     if (ls != FMM_OK) return ls;
     if (pl->ev[2]) {
         if (cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
@@ -900,54 +923,58 @@ extern "C" fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double 
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return FMM_ERR_INVALID;  // a plan's counters serve one product
     }
-    for (int i0 = 0; i0 < count; i0 += fmm::kMaxBatchPerLaunch) {
-        const int cnt = std::min(count - i0, fmm::kMaxBatchPerLaunch);
-        // The first plan of each chunk owns the shared task counter / error word.
-        F64Launch<fmm::kMaxBatchPerLaunch> *L = new (std::nothrow) F64Launch<fmm::kMaxBatchPerLaunch>();
-        if (!L) return FMM_ERR_OOM;
-        long long begin = 0;
-        int grid = 0;
-        for (int k = 0; k < cnt; ++k) {
-            const fmm_plan *pl = plans[i0 + k];
-            fmm_status_t s = prepare(pl, A[i0 + k], B[i0 + k], st);
-            if (s != FMM_OK) { delete L; return s; }
-            L->probs[k] = problem_of(pl, A[i0 + k], B[i0 + k], C[i0 + k], begin);
-            begin += pl->total_tasks;
-            grid = std::max(grid, pl->grid);
-        }
-        const fmm_plan *lead = plans[i0];
-        L->nprobs = cnt;
-        L->total_tasks = begin;
-        L->task_counter = lead->d_task_counter;
-        L->error = lead->d_error;
-        L->timeout_ns = (long long)(lead->timeout_s * 1e9);
-        if (cnt > 1) {
-            // interleaved order: problems by task count, descending, round-robin
-            std::vector<int> idx(cnt);
-            for (int k = 0; k < cnt; ++k) idx[k] = k;
-            std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
-                return plans[i0 + x]->total_tasks > plans[i0 + y]->total_tasks;
-            });
-            std::vector<long long> c(cnt + 1, 0);
-            for (int j = 0; j < cnt; ++j) {
-                c[j] = plans[i0 + idx[j]]->total_tasks;
-                L->order[j] = (short)idx[j];
+    // one grouped launch per tile width present in the batch
+    for (int bn : {128, 64}) {
+        std::vector<int> sel;
+        for (int i = 0; i < count; ++i)
+            if (plans[i]->bn == bn) sel.push_back(i);
+        for (size_t c0 = 0; c0 < sel.size(); c0 += fmm::kMaxBatchPerLaunch) {
+            const int cnt = (int)std::min<size_t>(sel.size() - c0, fmm::kMaxBatchPerLaunch);
+            F64Launch<fmm::kMaxBatchPerLaunch> *L = new (std::nothrow) F64Launch<fmm::kMaxBatchPerLaunch>();
+            if (!L) return FMM_ERR_OOM;
+            long long begin = 0;
+            for (int k = 0; k < cnt; ++k) {
+                const int i = sel[c0 + k];
+                const fmm_plan *pl = plans[i];
+                fmm_status_t s = prepare(pl, A[i], B[i], st);
+                if (s != FMM_OK) { delete L; return s; }
+                L->probs[k] = problem_of(pl, A[i], B[i], C[i], begin);
+                begin += pl->total_tasks;
             }
-            long long G = 0;
-            for (int q = cnt; q >= 1; --q) {  // segment with q active problems
-                L->seg_start[q - 1] = G;
-                L->seg_round[q - 1] = (int)c[q];
-                G += (long long)q * (c[q - 1] - c[q]);
+            const fmm_plan *lead = plans[sel[c0]];
+            L->nprobs = cnt;
+            L->total_tasks = begin;
+            L->task_counter = lead->d_task_counter;
+            L->error = lead->d_error;
+            L->timeout_ns = (long long)(lead->timeout_s * 1e9);
+            if (cnt > 1) {
+                // interleaved order: problems by task count, descending, round-robin
+                std::vector<int> idx(cnt);
+                for (int k = 0; k < cnt; ++k) idx[k] = k;
+                std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+                    return plans[sel[c0 + x]]->total_tasks > plans[sel[c0 + y]]->total_tasks;
+                });
+                std::vector<long long> c(cnt + 1, 0);
+                for (int j = 0; j < cnt; ++j) {
+                    c[j] = plans[sel[c0 + idx[j]]]->total_tasks;
+                    L->order[j] = (short)idx[j];
+                }
+                long long G = 0;
+                for (int q = cnt; q >= 1; --q) {  // segment with q active problems
+                    L->seg_start[q - 1] = G;
+                    L->seg_round[q - 1] = (int)c[q];
+                    G += (long long)q * (c[q - 1] - c[q]);
+                }
+                L->interleave = 1;
             }
-            L->interleave = 1;
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lead->device);
+            int grid = (int)std::min<long long>(begin, (long long)sms * fmm::f64_kernel_ctas_per_sm(bn));
+            if (grid < 1) grid = 1;
+            cudaError_t e = fmm::launch_f64_batch(*L, grid, st, bn);
+            delete L;
+            if (e != cudaSuccess) return FMM_ERR_CUDA;
         }
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lead->device);
-        grid = (int)std::min<long long>(begin, (long long)sms * fmm::f64_kernel_ctas_per_sm());
-        if (grid < 1) grid = 1;
-        cudaError_t e = fmm::launch_f64_batch(*L, grid, st);
-        delete L;
-        if (e != cudaSuccess) return FMM_ERR_CUDA;
     }
     return FMM_OK;
 }
@@ -963,7 +990,7 @@ extern "C" fmm_status_t fmm_batch_graph_create(fmm_batch_graph_t **out, fmm_plan
     if (!out || count < 1) return FMM_ERR_INVALID;
     *out = nullptr;
     // kernel attributes are set outside the capture
-    if (fmm::f64_kernel_ctas_per_sm() <= 0) return FMM_ERR_CUDA;
+    if (fmm::f64_kernel_ctas_per_sm(128) <= 0 || fmm::f64_kernel_ctas_per_sm(64) <= 0) return FMM_ERR_CUDA;
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return FMM_ERR_CUDA;
     fmm_batch_graph *g = new (std::nothrow) fmm_batch_graph();
@@ -1108,6 +1135,7 @@ extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t 
     info->flops_executed = pl->flops_exec;
     info->workspace_bytes = pl->ws_bytes;
     info->ozaki_slices = pl->oz_s;
+    info->tile_n = pl->bn;
     info->flops_lowp = pl->flops_lowp;
     return FMM_OK;
 }

@@ -8,11 +8,11 @@
 
 namespace fmm {
 
-// CTA tile of the FP64 leaf kernel (rows x cols of a product tile, K slab).
+// CTA tile of the FP64 leaf kernel: kBM rows x kBN (or 64) columns of a
+// product tile, K slab kBK.
 constexpr int kBM = 128;
 constexpr int kBN = 128;
 constexpr int kBK = 16;
-constexpr int kThreads = 256;
 // Upper bound on the number of blocks combined into one operand (nonzeros of a
 // flattened U or V column) and on the destinations of one product (nonzeros
 // of a flattened W column).
@@ -37,6 +37,7 @@ struct F64Geom {
     int R_src;             // products per sub-problem (R^(depth - materialized))
     int nsub;              // sub-problems (R^materialized)
     int tiles_m, tiles_n;  // tiles per leaf block
+    int bn;                // tile columns: 128 or 64 (0 means 128)
     // CSC over products: U/V columns are indexed by the sub-problem-local
     // product, W columns by the global product s * R_src + r.
     const int *u_ptr;
@@ -127,10 +128,11 @@ cudaError_t launch_ozaki_tc(const CUtensorMap &map_a, const CUtensorMap &map_b, 
                             cudaStream_t s);
 
 // Kernel launchers (fmm_f64.cu).  Return cudaSuccess or the launch error.
-cudaError_t launch_f64_single(const F64Launch<1> &L, int grid, cudaStream_t s);
-cudaError_t launch_f64_batch(const F64Launch<kMaxBatchPerLaunch> &L, int grid, cudaStream_t s);
-int f64_kernel_ctas_per_sm();  // resident CTAs per SM of the leaf kernel (0 on error)
-size_t f64_kernel_smem_bytes();
+// bn selects the tile configuration (128 or 64 columns).
+cudaError_t launch_f64_single(const F64Launch<1> &L, int grid, cudaStream_t s, int bn = kBN);
+cudaError_t launch_f64_batch(const F64Launch<kMaxBatchPerLaunch> &L, int grid, cudaStream_t s, int bn = kBN);
+int f64_kernel_ctas_per_sm(int bn = kBN);  // resident CTAs per SM of the leaf kernel (0 on error)
+size_t f64_kernel_smem_bytes(int bn = kBN);
 
 // Pre-addition pass for one materialized recursion level (fmm_f64.cu).
 // Input matrix c (c < n_in) starts at in + c * in_stride with leading
