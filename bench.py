@@ -104,15 +104,24 @@ def fp8_peak_tflops():
     return FALLBACK_BF16_TFLOPS * 2.0, "of fallback (1.9 PFLOP/s bf16 x nominal fp8/bf16 ratio 2)"
 
 
+KERNEL_SOURCES = {"fmm_f64_kernel": "fmm_f64.cu", "ozaki_tc_kernel": "fmm_ozaki_tc.cu"}
+
+
+def source_digest(kernel: str):
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2312_12732_gb300", "csrc", KERNEL_SOURCES.get(kernel, "fmm_f64.cu"))
+    try:
+        return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
 def profile_traffic(kernel: str, workload: str):
     """DRAM bytes per launch recorded by an ncu capture in profiles/, if it was
     taken on the current kernel source and this workload; else None."""
-    import hashlib
-
-    src = os.path.join(ROOT, "paper_2312_12732_gb300", "csrc", "fmm_f64.cu")
-    try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
+    digest = source_digest(kernel)
+    if digest is None:
         return None
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
@@ -199,6 +208,22 @@ def gpu_uuid(torch, dev):
         return u if u.startswith("GPU-") else "GPU-" + u
     except Exception:
         return None
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest value across ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job rate: the units of all ranks over the slowest rank's time."""
+    return units_per_rank * world / max_seconds
 
 
 def dist_env():
@@ -449,12 +474,9 @@ def run_ours(a):
         ms, leaf_ms = time_plan(torch, fmm, plan, dA, dB, dC, max(a.warmup, 3), a.steps, dist)
     clocks = sampler.summary()
 
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     flops_eff = 2.0 * n ** 3
-    value = flops_eff * ws / (ms * 1e-3) / 1e12
+    value = job_throughput(flops_eff, ws, ms * 1e-3) / 1e12
 
     # sanity: a few sampled entries against a float64 torch dot product on the GPU
     rows = torch.arange(0, n, max(1, n // 16), device=dev)
@@ -483,12 +505,8 @@ def run_ours(a):
         for _ in range(k_e2e):
             fmm.fmm_gemm_host(plan, hA, hB, hC)
         t1 = time.perf_counter()
-        te = (t1 - t0) / k_e2e
-        if dist is not None:
-            tt = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": flops_eff * ws / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * n * n * 8,
+        te = max_over_ranks((t1 - t0) / k_e2e, dist, dev)
+        e2e = {"value": job_throughput(flops_eff, ws, te) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * n * n * 8,
                "d2h_bytes_per_step": n * n * 8, "ms_per_step": te * 1e3, "steps": k_e2e,
                "path": "fmm_gemm_host (pinned host buffers, copies inside the timed region)"}
 
@@ -520,10 +538,7 @@ def run_ours(a):
         e_algo = fmm.fmm_algo_builtin("strassen")
         e_plan = fmm.fmm_plan_create(n, e_algo, 2, dtype="f64_ozaki", record_kernel_time=True)
         e_ms, e_leaf = time_plan(torch, fmm, e_plan, dA, dB, dC, max(a.warmup, 3), a.steps, dist)
-        if dist is not None:
-            tt = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
+        e_ms = max_over_ranks(e_ms, dist, dev)
         e_info = e_plan.info()
         e_ref = dA[rows] @ dB[:, :64]
         e_err = (dC[rows, :64] - e_ref).abs().max().item() / (n * dA.abs().max().item() * dB.abs().max().item())
@@ -532,7 +547,7 @@ def run_ours(a):
         e_achieved = e_info["flops_lowp"] / (e_leaf * 1e-3) / 1e12
         emulated = {
             "workload": f"strassen_d2_n{n}_{a.kind}_ozaki{e_info['ozaki_slices']}",
-            "value": flops_eff * ws / (e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
+            "value": job_throughput(flops_eff, ws, e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
             "speedup_vs_classic": (flops_eff / (e_ms * 1e-3) / 1e12) / classic["value"] if classic else None,
             "normalised_error_sampled": e_err, "ozaki_slices": e_info["ozaki_slices"],
             "gpu_launches": a.steps * (2 * e_info["materialized_levels"] + 5 + (1 if n % 4 else 0)),
