@@ -72,7 +72,7 @@ def parse_args(argv=None):
 
 def workload_name(a) -> str:
     kind = a.kind if a.kind != "wide" else f"wide{a.phi:g}"
-    leaf = "fp64" if a.dtype == "f64" else f"ozaki{a.slices or 11}"
+    leaf = "fp64" if a.dtype == "f64" else f"ozaki{a.slices or 12}"
     return f"{a.algo.replace('^2', 'x2')}_d{a.depth}_n{a.n}_{kind}_{leaf}"
 
 
@@ -303,10 +303,12 @@ def time_plan(torch, fmm, plan, dA, dB, dC, warmup, steps, dist=None, stream=Non
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     leaf = []
+    phases = []
     e0.record(stream)
     for _ in range(steps):
         fmm.fmm_gemm(plan, dA, dB, dC, stream)
         leaf.append(fmm.fmm_plan_last_kernel_ms(plan)[0])
+        phases.append(fmm.fmm_plan_last_phase_ms(plan))
     e1.record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -314,6 +316,7 @@ def time_plan(torch, fmm, plan, dA, dB, dC, warmup, steps, dist=None, stream=Non
     st = fmm.fmm_sync_status(plan, stream)
     if st != 0:
         raise RuntimeError("device status after timed region: " + fmm.fmm_status_string(st))
+    time_plan.last_phases = {k: statistics.mean(p[k] for p in phases) for k in phases[0]} if phases else None
     return e0.elapsed_time(e1) / steps, statistics.mean(leaf)
 
 
@@ -531,6 +534,7 @@ def run_ours(a):
                 "frac": achieved / peak, "traffic": traffic, "peak_note": peak_note,
                 "algorithmic_flops_per_launch": contraction_flops, "avg_launch_ms": leaf_ms,
                 "kernel_share_of_step": leaf_ms / ms if ms > 0 else None,
+                "phase_ms": time_plan.last_phases,
                 "frac_of_instruction_rate_measured_here": achieved / ref_rate if ref_rate else None, **extra}
 
     emulated = None
@@ -553,12 +557,13 @@ def run_ours(a):
             "gpu_launches": a.steps * (2 * e_info["materialized_levels"] + 5 + (1 if n % 4 else 0)),
             "roofline": {"bound": "tensor", "kernel": "ozaki_tc_kernel", "achieved": e_achieved, "peak": fp8_peak,
                          "unit": "TFLOP/s", "frac": e_achieved / fp8_peak, "peak_note": fp8_note,
-                         "traffic": profile_traffic("ozaki_tc_kernel", f"strassen_d2_n{n}_{a.kind}_ozaki11"),
+                         "traffic": profile_traffic("ozaki_tc_kernel",
+                                                    f"strassen_d2_n{n}_{a.kind}_ozaki{e_info['ozaki_slices']}"),
                          "algorithmic_flops_per_launch": e_info["flops_lowp"], "avg_launch_ms": e_leaf,
-                         "kernel_share_of_step": e_leaf / e_ms,
+                         "kernel_share_of_step": e_leaf / e_ms, "phase_ms": time_plan.last_phases,
                          "e4m3_mma_sync_rate_measured_here": e4m3_rate},
-            "note": "same FP64 operands; S_r/T_r and post-additions in FP64, leaf products from 11 e4m3 "
-                    "slices with exact FP32/int64 sums (precision configuration)"}
+            "note": f"same FP64 operands; S_r/T_r and post-additions in FP64, leaf products from "
+                    f"{e_info['ozaki_slices']} e4m3 slices with exact FP32/int64 sums (precision configuration)"}
         fmm.fmm_plan_destroy(e_plan)
 
     cpu = None

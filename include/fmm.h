@@ -83,7 +83,9 @@ typedef enum { FMM_SCHED_AUTO = 0, FMM_SCHED_FUSED = 1, FMM_SCHED_HYBRID = 2 } f
 typedef struct {
     fmm_schedule_t schedule;
     int materialize_levels;  /* FMM_SCHED_HYBRID: 0 .. depth */
-    int ozaki_slices;        /* FMM_F64_OZAKI: slices per operand, 2..12 (default 11) */
+    int ozaki_slices;        /* FMM_F64_OZAKI: slices per operand, 2..12 (default 12:
+                                60 bits, within 2x of the FP64 path's error on uniform,
+                                normal and wide-exponent inputs) */
     double wait_timeout_s;   /* bound on every device-side wait (default 5 s) */
     int debug_poison_chain;  /* testing only: 1 = after the per-call reset, set one
                                 post-addition ordering counter to a value no task
@@ -219,6 +221,14 @@ fmm_status_t fmm_sync_status(const fmm_plan_t *plan, void *stream);
  * both measured with CUDA events on the call's stream.  Waits for the call's
  * end event.  FMM_ERR_INVALID if timing was not enabled or no call was made. */
 fmm_status_t fmm_plan_last_kernel_ms(const fmm_plan_t *plan, float *leaf_ms, float *total_ms);
+
+/* Phase times of the most recent fmm_gemm on a plan created with
+ * record_kernel_time = 1, in milliseconds, measured with CUDA events on the
+ * call's stream: phases[0] counter reset and materialized pre-additions,
+ * phases[1] exponents and slicing (FMM_F64_OZAKI; 0 otherwise), phases[2]
+ * the leaf-product kernel, phases[3] the peel tasks run after an emulated
+ * leaf (0 otherwise).  Fills min(count, 4) entries; waits for the call. */
+fmm_status_t fmm_plan_last_phase_ms(const fmm_plan_t *plan, float *phases, int count);
 
 /* Calibration, with no counterpart in the paper: measures the FP64
  * throughput the current device delivers on the leaf kernel's instruction

@@ -35,6 +35,7 @@ from ._binding import (  # noqa: F401
     fmm_plan_destroy,
     fmm_plan_get_info,
     fmm_plan_last_kernel_ms,
+    fmm_plan_last_phase_ms,
     fmm_measure_e4m3_peak,
     fmm_measure_fp64_peak,
     fmm_plan_workspace_bytes,

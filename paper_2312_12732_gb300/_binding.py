@@ -82,6 +82,7 @@ SIGNATURES = [
     ("fmm_gemm_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(fmm_algo_t), ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fmm_measure_e4m3_peak", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    ("fmm_plan_last_phase_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     ("fmm_plan_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fmm_plan_info_t)]),
     ("fmm_plan_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
     ("fmm_plan_destroy", None, [ctypes.c_void_p]),
@@ -242,6 +243,13 @@ def fmm_measure_e4m3_peak(stream=None) -> float:
     a = ctypes.c_double()
     _check(lib().fmm_measure_e4m3_peak(ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(a)), "fmm_measure_e4m3_peak")
     return float(a.value)
+
+
+def fmm_plan_last_phase_ms(plan: Plan) -> dict:
+    """{materialize, slice, leaf, peel} milliseconds of the plan's most recent fmm_gemm."""
+    arr = (ctypes.c_float * 4)()
+    _check(lib().fmm_plan_last_phase_ms(plan.handle, arr, 4), "fmm_plan_last_phase_ms")
+    return dict(zip(("materialize", "slice", "leaf", "peel"), (float(x) for x in arr)))
 
 
 def fmm_plan_workspace_bytes(plan: Plan) -> int:

@@ -314,8 +314,9 @@ struct fmm_plan {
     double flops_lowp = 0;
     // host-buffer path
     double *d_hostA = nullptr, *d_hostB = nullptr, *d_hostC = nullptr;
-    // optional timing events: [0] call start, [1] leaf start, [2] leaf end
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // optional timing events: [0] call start, [1] leaf start, [2] leaf end,
+    // [3] after counter reset + materialization, [4] call end
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool timed_once = false;
     // statistics
     double flops_leaf = 0, flops_exec = 0;
@@ -431,7 +432,7 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         // S_r and T_r must exist in FP64 before they are sliced: materialize all levels.
         if (o.schedule != FMM_SCHED_AUTO && mat != depth) return FMM_ERR_UNSUPPORTED;
         mat = depth;
-        oz_s = o.ozaki_slices ? o.ozaki_slices : 11;
+        oz_s = o.ozaki_slices ? o.ozaki_slices : 12;
         if (oz_s < 2 || oz_s > fmm::kOzMaxSlices) return FMM_ERR_INVALID;
         if (n / P > (1LL << 30) / 128) return FMM_ERR_UNSUPPORTED;
     }
@@ -788,9 +789,7 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     const long long ld = pl->depth > 0 ? m : pl->n;
     const long long stride = pl->depth > 0 ? m * m : 0;
     const int Mp = (int)pl->oz_Mp;
-    if (fmm::launch_ozaki_exponents(S, ld, stride, nmat, (int)m, (int)m, true, pl->d_mxa, Mp, st) != cudaSuccess ||
-        fmm::launch_ozaki_exponents(T, ld, stride, nmat, (int)m, (int)m, false, pl->d_mxb, Mp, st) != cudaSuccess ||
-        fmm::launch_ozaki_slices(S, ld, stride, nmat, (int)m, (int)m, true, pl->d_mxa, Mp, pl->oz_s, Mp, Mp,
+    if (fmm::launch_ozaki_slices(S, ld, stride, nmat, (int)m, (int)m, true, pl->d_mxa, Mp, pl->oz_s, Mp, Mp,
                                  pl->d_sla, st) != cudaSuccess ||
         fmm::launch_ozaki_slices(T, ld, stride, nmat, (int)m, (int)m, false, pl->d_mxb, Mp, pl->oz_s, Mp, Mp,
                                  pl->d_slb, st) != cudaSuccess)
@@ -858,8 +857,10 @@ extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const do
     if (pl->ev[0] && cudaEventRecord(pl->ev[0], st) != cudaSuccess) return FMM_ERR_CUDA;
     fmm_status_t s = prepare(pl, A, B, st);
     if (s != FMM_OK) return s;
+    if (pl->ev[3] && cudaEventRecord(pl->ev[3], st) != cudaSuccess) return FMM_ERR_CUDA;
     if (pl->dtype == FMM_F64_OZAKI) {
         s = gemm_ozaki(pl, A, B, C, st);
+        if (s == FMM_OK && pl->ev[4] && cudaEventRecord(pl->ev[4], st) != cudaSuccess) return FMM_ERR_CUDA;
         if (s == FMM_OK && pl->ev[2]) const_cast<fmm_plan *>(pl)->timed_once = true;
         return s;
     }
@@ -875,7 +876,21 @@ extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const do
     if (ls != FMM_OK) return ls;
     if (pl->ev[2]) {
         if (cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
+        if (cudaEventRecord(pl->ev[4], st) != cudaSuccess) return FMM_ERR_CUDA;
         const_cast<fmm_plan *>(pl)->timed_once = true;
+    }
+    return FMM_OK;
+}
+
+extern "C" fmm_status_t fmm_plan_last_phase_ms(const fmm_plan_t *pl, float *phases, int count) {
+    if (!pl || !phases || count < 1 || !pl->ev[0] || !pl->timed_once) return FMM_ERR_INVALID;
+    if (cudaEventSynchronize(pl->ev[4]) != cudaSuccess) return FMM_ERR_CUDA;
+    // [0] counter reset + materialization, [1] slicing (emulated leaf), [2] leaf kernel, [3] peel tasks
+    const cudaEvent_t marks[5] = {pl->ev[0], pl->ev[3], pl->ev[1], pl->ev[2], pl->ev[4]};
+    for (int i = 0; i < count && i < 4; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, marks[i], marks[i + 1]) != cudaSuccess) return FMM_ERR_CUDA;
+        phases[i] = ms;
     }
     return FMM_OK;
 }

@@ -114,10 +114,11 @@ struct OzParams {
     long long timeout_ns;
 };
 
-cudaError_t launch_ozaki_exponents(const double *X, long long ld, long long mat_stride, int nmat, int rows, int cols,
-                                   bool by_rows, int *mx, int pitch, cudaStream_t s);
+// Exponents and slices of every row (by_rows) or column of the nmat matrices
+// X + i * mat_stride (rows x cols, leading dimension ld); mx receives the
+// largest biased exponent of each line ([mat][pitch]).
 cudaError_t launch_ozaki_slices(const double *X, long long ld, long long mat_stride, int nmat, int rows, int cols,
-                                bool by_rows, const int *mx, int pitch, int s, int Mp, int Kp, unsigned char *out,
+                                bool by_rows, int *mx, int pitch, int s, int Mp, int Kp, unsigned char *out,
                                 cudaStream_t st);
 cudaError_t launch_ozaki_gemm(const OzParams &P, int grid, cudaStream_t s);
 int ozaki_ctas_per_sm();

@@ -10,8 +10,9 @@
 //
 //  * every row i of S_r is scaled by a power of two 2^(E_i - 1) at least its
 //    largest magnitude and rounded to a fixed-point integer Y with s*5 bits,
-//    which is split exactly into s balanced base-32 digits d_1..d_s in
-//    [-16, 16] (most significant first); every column j of T_r likewise;
+//    which is split exactly into s balanced base-32 digits d_1..d_s
+//    (most significant first; d_1 in [-16, 16], the others in [-16, 15]) read
+//    as bit fields of Y + 16 (32^s - 1) / 31; every column j of T_r likewise;
 //    digits are stored as e4m3 bytes, which hold these integers exactly;
 //  * for each diagonal g = t + u (2 <= g <= s + 1, the triangular truncation
 //    of the slice expansion) the kernel accumulates
@@ -82,134 +83,143 @@ __device__ __forceinline__ long long to_fixed(double x, int E, int bs) {
     return (b >> 63) ? -Y : Y;
 }
 
-// Balanced base-2^OB digits of Y, most significant first, each in [-16, 16].
-__device__ __forceinline__ void digits(long long Y, int s, int (&d)[kOzMaxSlices]) {
-    int w = OB * (s - 1);
-#pragma unroll
-    for (int t = 0; t < kOzMaxSlices; ++t) {
-        if (t < s - 1) {
-            const long long q = (Y + (1LL << (w - 1))) >> w;
-            Y -= q * (1LL << w);
-            d[t] = (int)q;
-            w -= OB;
-        } else if (t == s - 1) {
-            d[t] = (int)Y;
-        } else {
-            d[t] = 0;
-        }
-    }
-}
-
 __device__ __forceinline__ unsigned char e4m3(int v) {
     return (unsigned char)__nv_cvt_float_to_fp8((float)v, __NV_SATFINITE, __NV_E4M3);
 }
 
+// Digits by bit fields: with O = 16 (32^s - 1) / 31, Z = Y + O has plain
+// base-32 digits z_t in [0, 31] (the top one in [0, 32]) and Y's balanced
+// digits are z_t - 16, so each digit is a shift and a mask; the e4m3 byte of
+// z - 16 comes from a 33-entry table.  Writes byte t of the element into
+// bits [8q, 8q + 8) of packed[t].
+__device__ __forceinline__ long long digit_offset(int s) { return ((1LL << (OB * s)) - 1) / 31 * 16; }
+
+__device__ __forceinline__ void pack_digits(long long Z, int s, const unsigned char *lut,
+                                            unsigned (&packed)[kOzMaxSlices], int q) {
+#pragma unroll
+    for (int t = 0; t < kOzMaxSlices; ++t) {
+        if (t < s) {
+            const int sh = OB * (s - 1 - t);
+            const int z = t == 0 ? (int)(Z >> sh) : (int)((Z >> sh) & 31);
+            packed[t] |= (unsigned)lut[z] << (8 * q);
+        }
+    }
+}
+
+__device__ __forceinline__ void fill_lut(unsigned char *lut) {
+    for (int i = threadIdx.x; i < 33; i += blockDim.x) lut[i] = e4m3(i - 16);
+}
+
 // ---------------------------------------------------------------------------
-// Exponents.  mx[] receives the largest biased exponent (0 for an all-zero
-// line); E = max(mx, 1) - 1021 then bounds the line by 2^(E - 1).
+// Exponents and slices, fused.  For every row (left operand) or column (right
+// operand) the kernels first take the largest biased exponent (mx, 0 for an
+// all-zero line; E = max(mx, 1) - 1021 bounds the line by 2^(E - 1)), then
+// split each element into s digits.  Output layout [mat][t][Mp][Kp] bytes
+// (K contiguous); padding rows/columns stay zero from the plan's first clear.
+// All per-slice arrays are indexed with compile-time indices (registers).
 // ---------------------------------------------------------------------------
-__global__ void row_exp_kernel(const double *__restrict__ X, long long ld, long long mat_stride, int rows, int cols,
-                               int *__restrict__ mx, int pitch) {
+
+// Left operand: one warp per row r of X (rows x cols, ld); lane j handles
+// elements 4(j + 32 i) .. +3, so each slice row is written with coalesced
+// 4-byte stores.
+__global__ void slice_rows_kernel(const double *__restrict__ X, long long ld, long long mat_stride, int rows,
+                                  int cols, int *__restrict__ mx, int pitch, int s, int Mp, int Kp,
+                                  unsigned char *__restrict__ out) {
+    __shared__ unsigned char lut[33];
+    fill_lut(lut);
+    __syncthreads();
     const int mat = blockIdx.y;
     const double *Xm = X + (long long)mat * mat_stride;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int bs = OB * s;
+    const long long O = digit_offset(s);
     for (int r = warp; r < rows; r += nwarps) {
+        const double *row = Xm + (long long)r * ld;
         int m = 0;
-        for (int c = lane; c < cols; c += 32) m = max(m, biased_exponent(__ldg(Xm + (long long)r * ld + c)));
+        for (int c = lane; c < cols; c += 32) m = max(m, biased_exponent(__ldg(row + c)));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) mx[(long long)mat * pitch + r] = m;
-    }
-}
-
-// Column maxima: thread per column, CTAs over row chunks (blockIdx.z),
-// combined with atomicMax into a zeroed mx[].
-__global__ void col_exp_kernel(const double *__restrict__ X, long long ld, long long mat_stride, int rows, int cols,
-                               int rows_per_chunk, int *__restrict__ mx, int pitch) {
-    const int mat = blockIdx.y;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    const double *Xm = X + (long long)mat * mat_stride;
-    const int r0 = blockIdx.z * rows_per_chunk;
-    const int r1 = min(rows, r0 + rows_per_chunk);
-    int m = 0;
-    for (int r = r0; r < r1; ++r) m = max(m, biased_exponent(__ldg(Xm + (long long)r * ld + c)));
-    atomicMax(mx + (long long)mat * pitch + c, m);
-}
-
-// ---------------------------------------------------------------------------
-// Slicing.  Output layout [mat][t][Mp][Kp] bytes (row-major, K contiguous);
-// padding rows/columns are left at zero from the plan's initial clear.
-// ---------------------------------------------------------------------------
-
-// Rows of X (the left operand S_r): element (r, k) -> slice t at [t][r][k].
-__global__ void slice_rows_kernel(const double *__restrict__ X, long long ld, long long mat_stride, int rows,
-                                  int cols, const int *__restrict__ mx, int pitch, int s, int Mp, int Kp,
-                                  unsigned char *__restrict__ out) {
-    const int mat = blockIdx.y;
-    const double *Xm = X + (long long)mat * mat_stride;
-    const int cols4 = (cols + 3) >> 2;
-    const int bs = OB * s;
-    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-        const int E = max(mx[(long long)mat * pitch + r], 1) - 1021;
-        for (int c4 = threadIdx.x; c4 < cols4; c4 += blockDim.x) {
+        const int E = max(m, 1) - 1021;
+        unsigned char *orow = out + ((long long)mat * s * Mp + r) * Kp;
+        const long long slice_stride = (long long)Mp * Kp;
+        for (int c4 = lane; c4 * 4 < cols; c4 += 32) {
             unsigned packed[kOzMaxSlices];
 #pragma unroll
             for (int t = 0; t < kOzMaxSlices; ++t) packed[t] = 0u;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = c4 * 4 + q;
-                if (c >= cols) break;
-                int d[kOzMaxSlices];
-                digits(to_fixed(__ldg(Xm + (long long)r * ld + c), E, bs), s, d);
-#pragma unroll
-                for (int t = 0; t < kOzMaxSlices; ++t) packed[t] |= (unsigned)e4m3(d[t]) << (8 * q);
+                if (c < cols) pack_digits(to_fixed(__ldg(row + c), E, bs) + O, s, lut, packed, q);
             }
-            for (int t = 0; t < s; ++t)
-                *reinterpret_cast<unsigned *>(out + (((long long)mat * s + t) * Mp + r) * Kp + c4 * 4) = packed[t];
+#pragma unroll
+            for (int t = 0; t < kOzMaxSlices; ++t)
+                if (t < s) *reinterpret_cast<unsigned *>(orow + t * slice_stride + c4 * 4) = packed[t];
         }
     }
 }
 
-// Columns of X (the right operand T_r, row-major K x cols): element (k, c) ->
-// slice t at [t][c][k], transposed through a 32 x 32 shared-memory tile.
+// Right operand: one CTA (32 x 8 threads) per strip of 32 columns of X
+// (rows = K): the column maxima first, then 32 x 32 tiles whose digits are
+// transposed through shared memory so that slice row c (K contiguous) is
+// written with coalesced stores.
 __global__ void slice_cols_kernel(const double *__restrict__ X, long long ld, long long mat_stride, int rows,
-                                  int cols, const int *__restrict__ mx, int pitch, int s, int Mp, int Kp,
-                                  int tiles_c, unsigned char *__restrict__ out) {
+                                  int cols, int *__restrict__ mx, int pitch, int s, int Mp, int Kp,
+                                  unsigned char *__restrict__ out) {
     __shared__ unsigned char tile[kOzMaxSlices][32][36];
+    __shared__ int colmax[8][32];
+    __shared__ unsigned char lut[33];
+    fill_lut(lut);
+    const long long O = digit_offset(s);
     const int mat = blockIdx.y;
     const double *Xm = X + (long long)mat * mat_stride;
-    const int tc = blockIdx.x % tiles_c, tk = blockIdx.x / tiles_c;
-    const int c0 = tc * 32, k0 = tk * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-    const int bs = OB * s;
+    const int c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int c = c0 + tx;
-    const int E = c < cols ? max(mx[(long long)mat * pitch + c], 1) - 1021 : 0;
+    const int bs = OB * s;
+    int m = 0;
+    if (c < cols)
+        for (int k = ty; k < rows; k += 8) m = max(m, biased_exponent(__ldg(Xm + (long long)k * ld + c)));
+    colmax[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int kk = ty + 8 * q;
-        const int k = k0 + kk;
-        int d[kOzMaxSlices];
-        if (c < cols && k < rows)
-            digits(to_fixed(__ldg(Xm + (long long)k * ld + c), E, bs), s, d);
-        else
-#pragma unroll
-            for (int t = 0; t < kOzMaxSlices; ++t) d[t] = 0;
-#pragma unroll
-        for (int t = 0; t < kOzMaxSlices; ++t)
-            if (t < s) tile[t][tx][kk] = e4m3(d[t]);
+        for (int j = 1; j < 8; ++j) m = max(m, colmax[j][tx]);
+        colmax[0][tx] = m;
+        if (c < cols) mx[(long long)mat * pitch + c] = m;
     }
     __syncthreads();
-    // 256 threads: row cc = threadIdx.x >> 3 (0..31), 4-byte chunk ch = threadIdx.x & 7.
+    const int E = max(colmax[0][tx], 1) - 1021;
     const int cc = threadIdx.x >> 3, ch = threadIdx.x & 7;
-    if (c0 + cc < Mp && k0 + ch * 4 < Kp) {
-        for (int t = 0; t < s; ++t) {
-            const unsigned v = (unsigned)tile[t][cc][ch * 4] | ((unsigned)tile[t][cc][ch * 4 + 1] << 8) |
-                               ((unsigned)tile[t][cc][ch * 4 + 2] << 16) | ((unsigned)tile[t][cc][ch * 4 + 3] << 24);
-            *reinterpret_cast<unsigned *>(out + (((long long)mat * s + t) * Mp + c0 + cc) * Kp + k0 + ch * 4) = v;
+    const long long slice_stride = (long long)Mp * Kp;
+    unsigned char *obase = out + ((long long)mat * s * Mp + c0 + cc) * Kp;
+    for (int k0 = 0; k0 < rows; k0 += 32) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int kk = ty + 8 * q;
+            const int k = k0 + kk;
+            unsigned packed[kOzMaxSlices];
+#pragma unroll
+            for (int t = 0; t < kOzMaxSlices; ++t) packed[t] = 0u;
+            if (c < cols && k < rows) pack_digits(to_fixed(__ldg(Xm + (long long)k * ld + c), E, bs) + O, s, lut, packed, 0);
+#pragma unroll
+            for (int t = 0; t < kOzMaxSlices; ++t)
+                if (t < s) tile[t][tx][kk] = (unsigned char)packed[t];
         }
+        __syncthreads();
+        if (c0 + cc < Mp && k0 + ch * 4 < Kp) {
+#pragma unroll
+            for (int t = 0; t < kOzMaxSlices; ++t)
+                if (t < s) {
+                    const unsigned v = (unsigned)tile[t][cc][ch * 4] | ((unsigned)tile[t][cc][ch * 4 + 1] << 8) |
+                                       ((unsigned)tile[t][cc][ch * 4 + 2] << 16) |
+                                       ((unsigned)tile[t][cc][ch * 4 + 3] << 24);
+                    *reinterpret_cast<unsigned *>(obase + t * slice_stride + k0 + ch * 4) = v;
+                }
+        }
+        __syncthreads();
     }
 }
 
@@ -493,39 +503,8 @@ __global__ void __launch_bounds__(NT, 1) ozaki_gemm_kernel(const __grid_constant
 
 size_t ozaki_smem_bytes() { return sizeof(Smem); }
 
-cudaError_t launch_ozaki_exponents(const double *X, long long ld, long long mat_stride, int nmat, int rows, int cols,
-                                   bool by_rows, int *mx, int pitch, cudaStream_t s) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int m0 = 0; m0 < nmat; m0 += 65535) {
-        const int cnt = nmat - m0 < 65535 ? nmat - m0 : 65535;
-        if (by_rows) {
-            int bx = (rows * 32 + 255) / 256;
-            const int cap = (sms * 16 + cnt - 1) / cnt;
-            if (bx > cap) bx = cap;
-            if (bx < 1) bx = 1;
-            row_exp_kernel<<<dim3(bx, cnt), 256, 0, s>>>(X + (long long)m0 * mat_stride, ld, mat_stride, rows, cols,
-                                                         mx + (long long)m0 * pitch, pitch);
-        } else {
-            const int bx = (cols + 255) / 256;
-            // enough row chunks for about 8 CTAs per SM in total
-            long long want = (long long)sms * 8 / ((long long)bx * cnt);
-            if (want < 1) want = 1;
-            if (want > rows) want = rows;
-            const int chunk = (int)((rows + want - 1) / want);
-            const int bz = (rows + chunk - 1) / chunk;
-            col_exp_kernel<<<dim3(bx, cnt, bz), 256, 0, s>>>(X + (long long)m0 * mat_stride, ld, mat_stride, rows,
-                                                             cols, chunk, mx + (long long)m0 * pitch, pitch);
-        }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 cudaError_t launch_ozaki_slices(const double *X, long long ld, long long mat_stride, int nmat, int rows, int cols,
-                                bool by_rows, const int *mx, int pitch, int s, int Mp, int Kp, unsigned char *out,
+                                bool by_rows, int *mx, int pitch, int s, int Mp, int Kp, unsigned char *out,
                                 cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -534,18 +513,16 @@ cudaError_t launch_ozaki_slices(const double *X, long long ld, long long mat_str
         const int cnt = nmat - m0 < 65535 ? nmat - m0 : 65535;
         const double *Xm = X + (long long)m0 * mat_stride;
         unsigned char *om = out + (long long)m0 * s * Mp * Kp;
-        const int *mxm = mx + (long long)m0 * pitch;
+        int *mxm = mx + (long long)m0 * pitch;
         if (by_rows) {
-            int bx = rows;
+            int bx = (rows * 32 + 255) / 256;  // one warp per row
             const int cap = (sms * 16 + cnt - 1) / cnt;
             if (bx > cap) bx = cap;
             if (bx < 1) bx = 1;
             slice_rows_kernel<<<dim3(bx, cnt), 256, 0, st>>>(Xm, ld, mat_stride, rows, cols, mxm, pitch, s, Mp, Kp, om);
         } else {
-            // columns of X become rows of the output: tiles over (cols, rows of X)
-            const int tiles_c = (cols + 31) / 32, tiles_k = (rows + 31) / 32;
-            slice_cols_kernel<<<dim3(tiles_c * tiles_k, cnt), 256, 0, st>>>(Xm, ld, mat_stride, rows, cols, mxm,
-                                                                            pitch, s, Mp, Kp, tiles_c, om);
+            slice_cols_kernel<<<dim3((cols + 31) / 32, cnt), 256, 0, st>>>(Xm, ld, mat_stride, rows, cols, mxm,
+                                                                           pitch, s, Mp, Kp, om);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
