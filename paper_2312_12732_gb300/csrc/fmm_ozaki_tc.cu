@@ -144,6 +144,8 @@ __device__ __forceinline__ double scale2(double v, int sc) {
     return v * pow2(sc);
 }
 
+// Ten warps put three warps on some of the SM's four register-file partitions
+// (16K registers each), which caps the kernel at 168 registers per thread.
 __global__ void __launch_bounds__(NTHREADS, 1)
     ozaki_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                     const __grid_constant__ OzParams P) {
@@ -409,8 +411,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int mode = en.z == 0 ? (cf == 1 ? 0 : (cf == -1 ? 1 : 2)) : (cf == 1 ? 3 : (cf == -1 ? 4 : 5));
                 if (row < rows) {
                     double *prow = dst + (long long)row * P.ldc + col0;
+                    // whole 32-byte sectors per access when the row is aligned
+                    const bool vec = (((unsigned long long)prow) & 31ull) == 0;
+                    const int nv = vec ? max(0, min(64, cols - col0)) / 4 : 0;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        if (u >= nv) break;
+                        double v0 = pv[4 * u], v1 = pv[4 * u + 1], v2 = pv[4 * u + 2], v3 = pv[4 * u + 3];
+                        if (mode >= 3) {
+                            double o0, o1, o2, o3;
+                            asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];"
+                                         : "=d"(o0), "=d"(o1), "=d"(o2), "=d"(o3)
+                                         : "l"(prow + 4 * u));
+                            if (mode == 3) {
+                                v0 = o0 + v0; v1 = o1 + v1; v2 = o2 + v2; v3 = o3 + v3;
+                            } else if (mode == 4) {
+                                v0 = o0 - v0; v1 = o1 - v1; v2 = o2 - v2; v3 = o3 - v3;
+                            } else {
+                                v0 = fma(cfd, v0, o0); v1 = fma(cfd, v1, o1); v2 = fma(cfd, v2, o2); v3 = fma(cfd, v3, o3);
+                            }
+                        } else if (mode == 1) {
+                            v0 = neg(v0); v1 = neg(v1); v2 = neg(v2); v3 = neg(v3);
+                        } else if (mode == 2) {
+                            v0 *= cfd; v1 *= cfd; v2 *= cfd; v3 *= cfd;
+                        }
+                        asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(prow + 4 * u), "d"(v0), "d"(v1),
+                                     "d"(v2), "d"(v3)
+                                     : "memory");
+                    }
 #pragma unroll
                     for (int j = 0; j < 64; ++j) {
+                        if (j < 4 * nv) continue;
                         if (col0 + j >= cols) break;
                         const double v = pv[j];
                         double out;
