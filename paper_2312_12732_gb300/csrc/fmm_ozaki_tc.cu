@@ -5,8 +5,9 @@
 // post-additions in ascending product order), organised the Blackwell way:
 //
 //   warp 0     TMA producer: fetches tile tasks in increasing order, streams
-//              128 x 128-byte slabs of both slice operands into a 5-stage
-//              shared-memory ring (128B swizzle) with cp.async.bulk.tensor;
+//              128 x 256-byte slabs of both slice operands (two 128B-swizzled
+//              boxes each) into a 3-stage shared-memory ring with
+//              cp.async.bulk.tensor;
 //   warp 1     MMA issuer: one thread issues tcgen05.mma kind::f8f6f4
 //              (M = 128, N = 128, K = 32) from the ring into one of two TMEM
 //              accumulators (one per diagonal group in flight) and releases
@@ -34,8 +35,13 @@ using dev::ld_volatile;
 using dev::neg;
 
 constexpr int OB = kOzDigitBits;
-constexpr int TM = 128, TN = 128, SLAB = 128;  // tile rows, tile cols, K bytes per stage
-constexpr int STAGES = 5;
+constexpr int TM = 128, TN = 128, BOX = 128;  // tile rows, tile cols, K bytes per TMA box
+// Two 128-byte K boxes per operand and stage: the MMA thread waits once per
+// eight MMAs.  An mbarrier wait costs the issuing thread about as long as two
+// MMAs of this shape take on the tensor pipe, so one wait per four MMAs left
+// the pipe idle a third of the time.
+constexpr int KBOX = 2, SLAB = BOX * KBOX;     // K bytes per stage
+constexpr int STAGES = 3;
 constexpr int NTHREADS = 320;                  // 10 warps
 constexpr int EPI_WARP0 = 2, NEPI = 8;
 constexpr int TMEM_COLS = 256;                 // two 128-column FP32 accumulators
@@ -159,7 +165,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles = P.tiles_m * P.tiles_n;
-    const int nkb = P.Kp / SLAB;
+    const int nbox = P.Kp / BOX;                 // 128-byte K boxes per slice row
+    const int nkb = (nbox + KBOX - 1) / KBOX;    // stages per slice pair (the last may hold one box)
     const int s = P.s;
 
     if (tid == 0) {
@@ -225,11 +232,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             }
                             unsigned char *sa = stage_mem + stage * STAGE_BYTES;
                             unsigned char *sb = sa + TM * SLAB;
-                            mbar_expect_tx(&B.full[stage], STAGE_BYTES);
+                            const int boxes = min(KBOX, nbox - kb * KBOX);
+                            mbar_expect_tx(&B.full[stage], (uint32_t)boxes * (TM + TN) * BOX);
                             const int ya = (r * s + (ta - 1)) * P.Mp + ti * TM;
                             const int yb = (r * s + (g - ta - 1)) * P.Mp + tj * TN;
-                            tma_load_2d(sa, &map_a, kb * SLAB, ya, &B.full[stage]);
-                            tma_load_2d(sb, &map_b, kb * SLAB, yb, &B.full[stage]);
+                            for (int bx = 0; bx < boxes; ++bx) {
+                                const int x = (kb * KBOX + bx) * BOX;
+                                tma_load_2d(sa + bx * TM * BOX, &map_a, x, ya, &B.full[stage]);
+                                tma_load_2d(sb + bx * TN * BOX, &map_b, x, yb, &B.full[stage]);
+                            }
                             ++issued_tx;
                             if (++stage == STAGES) {
                                 stage = 0;
@@ -290,10 +301,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                             const uint32_t sa = sbase + stage * STAGE_BYTES;
                             const uint64_t da = desc_sw128(sa), db = desc_sw128(sa + TM * SLAB);
+                            const int kmma = min(KBOX, nbox - kb * KBOX) * (BOX / 32);
 #pragma unroll
                             for (int k = 0; k < SLAB / 32; ++k) {
-                                const uint64_t adv = (uint64_t)((k * 32) >> 4);
-                                mma_e4m3(dtm, da + adv, db + adv, first ? 0u : 1u);
+                                if (k >= kmma) break;
+                                // 32-byte K step inside a box, 16 KB box stride (descriptor units of 16 B)
+                                const uint64_t adv = (uint64_t)(((k % (BOX / 32)) * 32) >> 4);
+                                const uint64_t boxa = (uint64_t)(((k / (BOX / 32)) * TM * BOX) >> 4);
+                                const uint64_t boxb = (uint64_t)(((k / (BOX / 32)) * TN * BOX) >> 4);
+                                mma_e4m3(dtm, da + boxa + adv, db + boxb + adv, first ? 0u : 1u);
                                 first = false;
                             }
                             mma_commit(&B.empty[stage]);
