@@ -57,6 +57,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-classic", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cublas", action="store_true", help="skip the cuBLAS DGEMM context timing")
     ap.add_argument("--cpu-n", type=int, default=4096, help="size of the CPU-oracle sample")
     ap.add_argument("--sweep", action="store_true", help="print one JSON line per algorithm/depth/schedule")
     ap.add_argument("--batched", action="store_true",
@@ -291,6 +292,19 @@ def make_algo(fmm, name):
     return fmm.fmm_algo_builtin(name)
 
 
+def materialized_bytes(n_core: int, p: int, R_total: int, depth: int, levels: int) -> float:
+    """Algorithmic HBM bytes of the materialized pre-additions of both operands: level l reads the
+    R^(l-1) blocks of side n_core/p^(l-1) once and writes R^l blocks of side n_core/p^l."""
+    if depth <= 0 or levels <= 0:
+        return 0.0
+    R = round(R_total ** (1.0 / depth))
+    total, b = 0.0, float(n_core)
+    for lev in range(1, levels + 1):
+        total += R ** (lev - 1) * b * b + R ** lev * (b / p) ** 2
+        b /= p
+    return 2 * 8 * total
+
+
 def time_plan(torch, fmm, plan, dA, dB, dC, warmup, steps, dist=None, stream=None):
     """(ms per step over the timed region, mean leaf-kernel ms per launch)."""
     stream = stream or torch.cuda.current_stream()
@@ -476,6 +490,7 @@ def run_ours(a):
     with sampler:
         ms, leaf_ms = time_plan(torch, fmm, plan, dA, dB, dC, max(a.warmup, 3), a.steps, dist)
     clocks = sampler.summary()
+    main_phases = time_plan.last_phases
 
     ms = max_over_ranks(ms, dist, dev)
     flops_eff = 2.0 * n ** 3
@@ -534,7 +549,7 @@ def run_ours(a):
                 "frac": achieved / peak, "traffic": traffic, "peak_note": peak_note,
                 "algorithmic_flops_per_launch": contraction_flops, "avg_launch_ms": leaf_ms,
                 "kernel_share_of_step": leaf_ms / ms if ms > 0 else None,
-                "phase_ms": time_plan.last_phases,
+                "phase_ms": main_phases,
                 "frac_of_instruction_rate_measured_here": achieved / ref_rate if ref_rate else None, **extra}
 
     emulated = None
@@ -566,6 +581,39 @@ def run_ours(a):
                     f"{e_info['ozaki_slices']} e4m3 slices with exact FP32/int64 sums (precision configuration)"}
         fmm.fmm_plan_destroy(e_plan)
 
+    # context only, not on the product path: the vendor FP64 GEMM (cuBLAS DGEMM through torch.matmul)
+    dgemm = None
+    if not a.no_cublas:
+        torch.matmul(dA, dB, out=dC)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record()
+        for _ in range(3):
+            torch.matmul(dA, dB, out=dC)
+        c1.record()
+        torch.cuda.synchronize()
+        ms_blas = c0.elapsed_time(c1) / 3
+        dgemm = {"value": flops_eff / (ms_blas * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms_blas,
+                 "path": "torch.matmul float64 (cuBLAS DGEMM), context only"}
+        fmm.fmm_gemm(plan, dA, dB, dC)  # leave the fast result in C
+        torch.cuda.synchronize()
+
+    # HBM side: measured DRAM bytes of the dominant kernel (single-pass ncu capture) per launch over its
+    # live duration, and the algorithmic bytes of the materialized pre-additions over their phase time
+    hbm_gbs = (measured_peaks() or {}).get("hbm_gbs") or 6800.0
+    phases = main_phases or {}
+    hbm = {"peak_gbs": hbm_gbs, "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)" if measured_peaks() else
+           "of fallback (6.8 TB/s)"}
+    if traffic:
+        hbm["leaf_kernel_gbs"] = traffic / (leaf_ms * 1e-3) / 1e9
+        hbm["leaf_kernel_frac"] = hbm["leaf_kernel_gbs"] / hbm_gbs
+    mat_bytes = materialized_bytes(nc, info["p"], info["R_total"], info["depth"], info["materialized_levels"])
+    if mat_bytes and phases.get("materialize"):
+        hbm["pre_additions_bytes"] = mat_bytes
+        hbm["pre_additions_gbs"] = mat_bytes / (phases["materialize"] * 1e-3) / 1e9
+        hbm["pre_additions_frac"] = hbm["pre_additions_gbs"] / hbm_gbs
+
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         times, cores, cdepth = cpu_oracle_run(a, a.cpu_n, 1)
@@ -586,6 +634,8 @@ def run_ours(a):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "classic_depth0": classic,
         "speedup_vs_classic": (value / ws) / classic["value"] if classic else None,
+        "context_cublas_dgemm": dgemm,
+        "hbm": hbm,
         "normalised_error_sampled": err,
         "clocks": clocks,
         "e2e": e2e,

@@ -84,3 +84,15 @@ def test_single_process_aggregation_is_identity():
 
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_throughput(10.0, 1, 2.0) == 5.0
+
+
+def test_materialized_bytes_counts_each_level_once():
+    import bench
+
+    n = 1024
+    # one Strassen level: read A (n^2), write 7 blocks of (n/2)^2; both operands, 8 bytes each
+    assert bench.materialized_bytes(n, 2, 7, 1, 1) == 2 * 8 * (n * n + 7 * (n // 2) ** 2)
+    # two levels: the second reads the 7 first-level blocks and writes 49 of side n/4
+    two = 2 * 8 * (n * n + 7 * (n // 2) ** 2 + 7 * (n // 2) ** 2 + 49 * (n // 4) ** 2)
+    assert bench.materialized_bytes(n, 2, 49, 2, 2) == two
+    assert bench.materialized_bytes(n, 2, 49, 2, 0) == 0.0
