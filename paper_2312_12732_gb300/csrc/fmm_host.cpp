@@ -309,8 +309,8 @@ struct fmm_plan {
     unsigned char *d_sla = nullptr, *d_slb = nullptr;  // slices
     int *d_mxa = nullptr, *d_mxb = nullptr;            // exponents (zeroed per call with the counters)
     const F64Geom *d_geom_peel = nullptr;              // FP64 peel-only geometry
-    int oz_engine = 1;                                  // 1 = tcgen05, 0 = mma.sync
-    CUtensorMap oz_map_a{}, oz_map_b{};                 // TMA maps over the slices
+    int oz_engine = 2;                                  // 2 = tcgen05 CTA pairs, 1 = tcgen05, 0 = mma.sync
+    CUtensorMap oz_map_a{}, oz_map_b{}, oz_map_bh{};    // TMA maps over the slices (bh: 64-row boxes)
     double flops_lowp = 0;
     // host-buffer path
     double *d_hostA = nullptr, *d_hostB = nullptr, *d_hostC = nullptr;
@@ -348,12 +348,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // 2-D uint8 map over `rows` x `kp` bytes (row pitch kp), 128 x 128 boxes, 128B swizzle.
-bool make_slice_map(CUtensorMap *map, void *base, unsigned long long rows, unsigned long long kp) {
+// TMA map over slices stored as rows x kp bytes; boxes of 128 K-bytes by box_rows rows.
+bool make_slice_map(CUtensorMap *map, void *base, unsigned long long rows, unsigned long long kp,
+                    unsigned box_rows = 128) {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[2] = {kp, rows};
     const cuuint64_t strides[1] = {kp};
-    const cuuint32_t box[2] = {128, 128};
+    const cuuint32_t box[2] = {128, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -674,11 +676,15 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         pl->d_mxb = pl->d_mxa + (size_t)Rt * pl->oz_Mp;
         pl->d_sla = (unsigned char *)(wsb + o_sla);
         pl->d_slb = (unsigned char *)(wsb + o_slb);
+        // engine: CTA pairs by default; FMM_OZAKI_ENGINE=tc1 (one CTA per tile) or mma_sync
         const char *eng = std::getenv("FMM_OZAKI_ENGINE");
-        pl->oz_engine = (eng && std::string(eng) == "mma_sync") ? 0 : 1;
+        const std::string es = eng ? eng : "";
+        pl->oz_engine = es == "mma_sync" ? 0 : (es == "tc1" ? 1 : 2);
+        if (pl->oz_engine == 2 && fmm::ozaki_tc_max_pairs() < 1) pl->oz_engine = 1;
         const unsigned long long srows = (unsigned long long)Rt * oz_s * pl->oz_Mp;
-        if (pl->oz_engine == 1 && (!make_slice_map(&pl->oz_map_a, pl->d_sla, srows, pl->oz_Mp) ||
-                                   !make_slice_map(&pl->oz_map_b, pl->d_slb, srows, pl->oz_Mp))) {
+        if (pl->oz_engine >= 1 && (!make_slice_map(&pl->oz_map_a, pl->d_sla, srows, pl->oz_Mp) ||
+                                   !make_slice_map(&pl->oz_map_b, pl->d_slb, srows, pl->oz_Mp) ||
+                                   !make_slice_map(&pl->oz_map_bh, pl->d_slb, srows, pl->oz_Mp, 64))) {
             free_plan_memory(pl);
             delete pl;
             return FMM_ERR_CUDA;
@@ -818,7 +824,13 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     P.task_counter = pl->d_task_counter;
     P.error = pl->d_error;
     P.timeout_ns = (long long)(pl->timeout_s * 1e9);
-    if (pl->oz_engine == 1) {
+    if (pl->oz_engine == 2) {
+        // a task covers a pair of tile rows; the second row of the last pair may be padding
+        P.tasks = (long long)nmat * ((pl->tiles_m + 1) / 2) * pl->tiles_n;
+        const int pairs = (int)std::min<long long>(P.tasks, (long long)fmm::ozaki_tc_max_pairs());
+        if (fmm::launch_ozaki_tc_pair(pl->oz_map_a, pl->oz_map_bh, P, pairs < 1 ? 1 : pairs, st) != cudaSuccess)
+            return FMM_ERR_CUDA;
+    } else if (pl->oz_engine == 1) {
         const int grid = (int)std::min<long long>(P.tasks, (long long)pl->sms);
         if (fmm::launch_ozaki_tc(pl->oz_map_a, pl->oz_map_b, P, grid < 1 ? 1 : grid, st) != cudaSuccess)
             return FMM_ERR_CUDA;

@@ -127,6 +127,12 @@ size_t ozaki_smem_bytes();
 // maps over the slice buffers ([rows][Kp], 128 x 128 boxes, 128B swizzle).
 cudaError_t launch_ozaki_tc(const CUtensorMap &map_a, const CUtensorMap &map_b, const OzParams &P, int grid,
                             cudaStream_t s);
+// The same slice GEMM on CTA pairs (clusters of two, tcgen05 cta_group::2);
+// map_bh has 128 x 64-row boxes over the right slices.  `pairs` clusters.
+cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_bh, const OzParams &P,
+                                 int pairs, cudaStream_t s);
+// Largest number of co-resident pairs of the pair kernel (0 if it cannot run).
+int ozaki_tc_max_pairs();
 
 // Kernel launchers (fmm_f64.cu).  Return cudaSuccess or the launch error.
 // bn selects the tile configuration (128 or 64 columns).

@@ -44,13 +44,17 @@ constexpr int KBOX = 2, SLAB = BOX * KBOX;     // K bytes per stage
 constexpr int STAGES = 3;
 constexpr int NTHREADS = 320;                  // 10 warps
 constexpr int EPI_WARP0 = 2, NEPI = 8;
-constexpr int TMEM_COLS = 256;                 // two 128-column FP32 accumulators
+// Four 128-column FP32 accumulators (all of TMEM): the MMA thread can run
+// three diagonal groups ahead of the epilogue, which covers the post-additions
+// of one task while the next task's first groups accumulate.
+constexpr int NBUF = 4;
+constexpr int TMEM_COLS = NBUF * 128;
 constexpr int TASK_RING = 2;
 constexpr uint32_t STAGE_BYTES = 2u * TM * SLAB;
 
 struct __align__(8) Bars {
     unsigned long long full[STAGES], empty[STAGES];
-    unsigned long long accfull[2], accempty[2];
+    unsigned long long accfull[NBUF], accempty[NBUF];
     unsigned long long tfull[TASK_RING], tempty[TASK_RING];
     unsigned long long drain;
     unsigned long long epi_go, epi_done;  // epilogue hand-offs around each post-addition
@@ -138,6 +142,37 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+// v * 2^e rounded to nearest even, built with integer operations only (the
+// FP64 pipe is the GPU's scarcest unit).  Scaling by a power of two is exact,
+// so this equals RN(v) * 2^e whenever the result is a normal number; results
+// that would be subnormal are reported through `ok` and take the FP64 route.
+__device__ __forceinline__ double ldexp_i64_rn(long long v, int e, bool &ok) {
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+    unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int msb = 63 - __clzll((long long)a);
+    int E = msb + e;  // unbiased exponent of the leading bit
+    unsigned long long mant;
+    if (msb <= 52) {
+        mant = a << (52 - msb);
+    } else {
+        const int sh = msb - 52;
+        mant = a >> sh;
+        const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+        if (mant >> 53) {  // carried into a new leading bit
+            mant >>= 1;
+            ++E;
+        }
+    }
+    const int biased = E + 1023;
+    if (biased <= 0 || biased >= 2047) {
+        ok = false;
+        return 0.0;
+    }
+    return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1ull))));
+}
 __device__ __forceinline__ double scale2(double v, int sc) {
     while (sc > 1023) {
         v *= pow2(1023);
@@ -148,6 +183,150 @@ __device__ __forceinline__ double scale2(double v, int sc) {
         sc += 1022;
     }
     return v * pow2(sc);
+}
+
+// Epilogue of one tile task (product r, tile ti, tj), run by the NEPI epilogue
+// warps: folds the diagonal groups g = 2 .. s+1 from TMEM into int64 (each
+// thread owns one tile row and 64 columns) while the next group accumulates
+// in the other TMEM buffer, converts and scales once to FP64, then applies the
+// post-additions C_l (+)= W[l][r] P_r in ascending r, ordered by the per-tile
+// counters.  Groups are numbered globally per CTA (G0 = first group of this
+// task); group G lives in accumulator G mod NBUF.  release(buf) hands an
+// accumulator back to the MMA thread.  `emit` is false for the padding tile of a CTA pair (no rows of C):
+// its groups are still drained.  Returns false when the CTA must stop.
+template <int EW0, class Release>
+__device__ __forceinline__ bool epilogue_tile(const OzParams &P, unsigned long long *accfull,
+                                              unsigned long long *epi_go, unsigned long long *epi_done,
+                                              volatile int *abort, uint32_t tmem, int r, int ti, int tj, bool emit,
+                                              int G0, uint32_t &dphase, Release release) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int e = warp - EW0;            // 0..7
+    const int quad = warp & 3;           // TMEM lane quadrant of this warp
+    const int half = e >> 2;             // column half
+    const int row = quad * 32 + lane;    // tile row owned by this thread
+    const int col0 = half * 64;
+    const bool leader = tid == EW0 * 32;
+    const int s = P.s;
+    const int tiles = P.tiles_m * P.tiles_n;
+    const int t = ti * P.tiles_n + tj;
+
+    long long acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0;
+    for (int g = 2; g <= s + 1; ++g) {
+        // global group index G0 + g - 2 selects the accumulator and its use parity
+        const int G = G0 + g - 2;
+        const uint32_t buf = (uint32_t)(G % NBUF), bphase = (uint32_t)((G / NBUF) & 1);
+        if (!mbar_wait(&accfull[buf], bphase, abort, P.error, P.timeout_ns)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int sh = OB * (s + 1 - g) - P.L;
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + buf * TN + col0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint32_t v[16];
+            tmem_ld16(taddr + c * 16, v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const long long vi = (long long)__float2int_rn(__uint_as_float(v[j]));
+                acc[c * 16 + j] += sh >= 0 ? vi * (1LL << sh) : ((vi + (1LL << (-sh - 1))) >> (-sh));
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) release(buf);
+    }
+    if (!emit) return true;
+
+    // FP64 values of this thread's 64 elements of P_r, converted in place
+    // (the bits replace the int64 sums, so both never occupy registers at once)
+    const int rows = (int)min((long long)TM, P.m - (long long)ti * TM);
+    const int cols = (int)min((long long)TN, P.m - (long long)tj * TN);
+    const int ea = row < rows ? max(P.mxa[(long long)r * P.Mp + (long long)ti * TM + row], 1) - 1021 : 0;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+        const int col = col0 + j;
+        const int eb = col < cols ? max(P.mxb[(long long)r * P.Mp + (long long)tj * TN + col], 1) - 1021 : 0;
+        const int sc = ea + eb - OB * (s + 1) + P.L;
+        bool ok = true;
+        double v = ldexp_i64_rn(acc[j], sc, ok);
+        if (!ok) v = scale2(__ll2double_rn(acc[j]), sc);
+        acc[j] = __double_as_longlong(v);
+    }
+
+    // post-additions C_l (+)= W[l][r] P_r in ascending r (per-tile counters)
+    const int wc = P.w_ptr[r], nD = P.w_ptr[r + 1] - wc;
+    for (int d = 0; d < nD; ++d) {
+        const int4 en = P.w_ent[wc + d];
+        const long long br = en.x / P.P, bc = en.x % P.P;
+        double *dst = P.C + (br * P.m + (long long)ti * TM) * P.ldc + bc * P.m + (long long)tj * TN;
+        unsigned *chain = P.chain + (long long)en.x * tiles + t;
+        if (leader) {
+            if (en.z > 0 && !chain_wait(chain, (unsigned)en.z, P.error, P.timeout_ns)) *abort = 1;
+            mbar_arrive(epi_go);
+        }
+        if (!mbar_wait(epi_go, dphase, abort, P.error, P.timeout_ns) || *abort) return false;
+        const int cf = en.y;
+        const double cfd = (double)cf;
+        const int mode = en.z == 0 ? (cf == 1 ? 0 : (cf == -1 ? 1 : 2)) : (cf == 1 ? 3 : (cf == -1 ? 4 : 5));
+        if (row < rows) {
+            double *prow = dst + (long long)row * P.ldc + col0;
+            // whole 32-byte sectors per access when the row is aligned
+            const bool vec = (((unsigned long long)prow) & 31ull) == 0;
+            const int nv = vec ? max(0, min(64, cols - col0)) / 4 : 0;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                if (u >= nv) break;
+                double v0 = __longlong_as_double(acc[4 * u]), v1 = __longlong_as_double(acc[4 * u + 1]),
+                       v2 = __longlong_as_double(acc[4 * u + 2]), v3 = __longlong_as_double(acc[4 * u + 3]);
+                if (mode >= 3) {
+                    double o0, o1, o2, o3;
+                    asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];"
+                                 : "=d"(o0), "=d"(o1), "=d"(o2), "=d"(o3)
+                                 : "l"(prow + 4 * u));
+                    if (mode == 3) {
+                        v0 = o0 + v0; v1 = o1 + v1; v2 = o2 + v2; v3 = o3 + v3;
+                    } else if (mode == 4) {
+                        v0 = o0 - v0; v1 = o1 - v1; v2 = o2 - v2; v3 = o3 - v3;
+                    } else {
+                        v0 = fma(cfd, v0, o0); v1 = fma(cfd, v1, o1); v2 = fma(cfd, v2, o2); v3 = fma(cfd, v3, o3);
+                    }
+                } else if (mode == 1) {
+                    v0 = neg(v0); v1 = neg(v1); v2 = neg(v2); v3 = neg(v3);
+                } else if (mode == 2) {
+                    v0 *= cfd; v1 *= cfd; v2 *= cfd; v3 *= cfd;
+                }
+                asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(prow + 4 * u), "d"(v0), "d"(v1), "d"(v2),
+                             "d"(v3)
+                             : "memory");
+            }
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                if (j < 4 * nv) continue;
+                if (col0 + j >= cols) break;
+                const double v = __longlong_as_double(acc[j]);
+                double out;
+                switch (mode) {
+                    case 0: out = v; break;
+                    case 1: out = neg(v); break;
+                    case 2: out = cfd * v; break;
+                    case 3: out = __ldcg(prow + j) + v; break;
+                    case 4: out = __ldcg(prow + j) - v; break;
+                    default: out = fma(cfd, v, __ldcg(prow + j)); break;
+                }
+                prow[j] = out;
+            }
+        }
+        __threadfence();
+        mbar_arrive(epi_done);
+        if (leader) {
+            if (!mbar_wait(epi_done, dphase, abort, P.error, P.timeout_ns)) return false;
+            __threadfence();
+            atomicAdd(chain, 1u);
+        }
+        dphase ^= 1u;
+    }
+    return true;
 }
 
 // Ten warps put three warps on some of the SM's four register-file partitions
@@ -174,7 +353,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&B.full[i], 1);
             mbar_init(&B.empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NBUF; ++i) {
             mbar_init(&B.accfull[i], 1);
             mbar_init(&B.accempty[i], NEPI);
         }
@@ -321,7 +500,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     if (!ok) break;
                     mma_commit(&B.accfull[buf]);
-                    if (++buf == 2) {
+                    if (++buf == NBUF) {
                         buf = 0;
                         bphase ^= 1u;
                     }
@@ -338,16 +517,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int e = warp - EPI_WARP0;      // 0..7
-        const int quad = warp & 3;           // TMEM lane quadrant of this warp
-        const int half = e >> 2;             // column half
-        const int row = quad * 32 + lane;    // tile row owned by this thread
-        const int col0 = half * 64;
-        uint32_t buf = 0, bphase = 0;
-        int tslot = 0;
+        int tslot = 0, tseq = 0;
         uint32_t tphase = 0;
         uint32_t dphase = 0;  // parity of the post-addition hand-offs
-        const bool leader = tid == EPI_WARP0 * 32;
         while (!*abort) {
             if (!mbar_wait(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
             const long long task = B.task[tslot];
@@ -361,130 +533,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int r = (int)(task / tiles);
             const int t = (int)(task - (long long)r * tiles);
             const int ti = t / P.tiles_n, tj = t - ti * P.tiles_n;
-
-            long long acc[64];
-#pragma unroll
-            for (int j = 0; j < 64; ++j) acc[j] = 0;
-            bool ok = true;
-            for (int g = 2; g <= s + 1; ++g) {
-                if (!mbar_wait(&B.accfull[buf], bphase, abort, P.error, P.timeout_ns)) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int sh = OB * (s + 1 - g) - P.L;
-                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + buf * TN + col0;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    uint32_t v[16];
-                    tmem_ld16(taddr + c * 16, v);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const long long vi = (long long)__float2int_rn(__uint_as_float(v[j]));
-                        acc[c * 16 + j] += sh >= 0 ? vi * (1LL << sh) : ((vi + (1LL << (-sh - 1))) >> (-sh));
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&B.accempty[buf]);
-                if (++buf == 2) {
-                    buf = 0;
-                    bphase ^= 1u;
-                }
-            }
-            if (!ok) break;
-
-            // FP64 values of this thread's 64 elements of P_r
-            const int rows = (int)min((long long)TM, P.m - (long long)ti * TM);
-            const int cols = (int)min((long long)TN, P.m - (long long)tj * TN);
-            const int ea = row < rows ? max(P.mxa[(long long)r * P.Mp + (long long)ti * TM + row], 1) - 1021 : 0;
-            double pv[64];
-#pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const int col = col0 + j;
-                const int eb = col < cols ? max(P.mxb[(long long)r * P.Mp + (long long)tj * TN + col], 1) - 1021 : 0;
-                pv[j] = acc[j] == 0 ? 0.0 : scale2(__ll2double_rn(acc[j]), ea + eb - OB * (s + 1) + P.L);
-            }
-
-            // post-additions C_l (+)= W[l][r] P_r in ascending r (per-tile counters)
-            const int wc = P.w_ptr[r], nD = P.w_ptr[r + 1] - wc;
-            for (int d = 0; d < nD && ok; ++d) {
-                const int4 en = P.w_ent[wc + d];
-                const long long br = en.x / P.P, bc = en.x % P.P;
-                double *dst = P.C + (br * P.m + (long long)ti * TM) * P.ldc + bc * P.m + (long long)tj * TN;
-                unsigned *chain = P.chain + (long long)en.x * tiles + t;
-                if (leader) {
-                    if (en.z > 0 && !chain_wait(chain, (unsigned)en.z, P.error, P.timeout_ns)) *abort = 1;
-                    mbar_arrive(&B.epi_go);
-                }
-                if (!mbar_wait(&B.epi_go, dphase, abort, P.error, P.timeout_ns) || *abort) {
-                    ok = false;
-                    break;
-                }
-                const int cf = en.y;
-                const double cfd = (double)cf;
-                const int mode = en.z == 0 ? (cf == 1 ? 0 : (cf == -1 ? 1 : 2)) : (cf == 1 ? 3 : (cf == -1 ? 4 : 5));
-                if (row < rows) {
-                    double *prow = dst + (long long)row * P.ldc + col0;
-                    // whole 32-byte sectors per access when the row is aligned
-                    const bool vec = (((unsigned long long)prow) & 31ull) == 0;
-                    const int nv = vec ? max(0, min(64, cols - col0)) / 4 : 0;
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        if (u >= nv) break;
-                        double v0 = pv[4 * u], v1 = pv[4 * u + 1], v2 = pv[4 * u + 2], v3 = pv[4 * u + 3];
-                        if (mode >= 3) {
-                            double o0, o1, o2, o3;
-                            asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];"
-                                         : "=d"(o0), "=d"(o1), "=d"(o2), "=d"(o3)
-                                         : "l"(prow + 4 * u));
-                            if (mode == 3) {
-                                v0 = o0 + v0; v1 = o1 + v1; v2 = o2 + v2; v3 = o3 + v3;
-                            } else if (mode == 4) {
-                                v0 = o0 - v0; v1 = o1 - v1; v2 = o2 - v2; v3 = o3 - v3;
-                            } else {
-                                v0 = fma(cfd, v0, o0); v1 = fma(cfd, v1, o1); v2 = fma(cfd, v2, o2); v3 = fma(cfd, v3, o3);
-                            }
-                        } else if (mode == 1) {
-                            v0 = neg(v0); v1 = neg(v1); v2 = neg(v2); v3 = neg(v3);
-                        } else if (mode == 2) {
-                            v0 *= cfd; v1 *= cfd; v2 *= cfd; v3 *= cfd;
-                        }
-                        asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(prow + 4 * u), "d"(v0), "d"(v1),
-                                     "d"(v2), "d"(v3)
-                                     : "memory");
-                    }
-#pragma unroll
-                    for (int j = 0; j < 64; ++j) {
-                        if (j < 4 * nv) continue;
-                        if (col0 + j >= cols) break;
-                        const double v = pv[j];
-                        double out;
-                        switch (mode) {
-                            case 0: out = v; break;
-                            case 1: out = neg(v); break;
-                            case 2: out = cfd * v; break;
-                            case 3: out = __ldcg(prow + j) + v; break;
-                            case 4: out = __ldcg(prow + j) - v; break;
-                            default: out = fma(cfd, v, __ldcg(prow + j)); break;
-                        }
-                        prow[j] = out;
-                    }
-                }
-                __threadfence();
-                mbar_arrive(&B.epi_done);
-                if (leader) {
-                    if (!mbar_wait(&B.epi_done, dphase, abort, P.error, P.timeout_ns)) {
-                        ok = false;
-                    } else {
-                        __threadfence();
-                        atomicAdd(chain, 1u);
-                    }
-                }
-                dphase ^= 1u;
-            }
-            if (!ok) break;
+            if (!epilogue_tile<EPI_WARP0>(P, B.accfull, &B.epi_go, &B.epi_done, abort, tmem, r, ti, tj, true,
+                                          tseq * s, dphase, [&](uint32_t b) { mbar_arrive(&B.accempty[b]); }))
+                break;
+            ++tseq;
         }
     }
 
@@ -494,7 +546,372 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// ---------------------------------------------------------------- CTA pairs
+// Cluster helpers for the pair kernel (shared::cluster addressing).
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Arrive on an mbarrier of the peer CTA.  The release form orders this
+// thread's earlier memory accesses (a slot read, a remote store) before the
+// arrival; the relaxed form is used after tcgen05.wait::ld, where the TMEM
+// reads it must follow have already completed.
+__device__ __forceinline__ void arrive_remote_release(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+__device__ __forceinline__ void arrive_remote_relaxed(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+__device__ __forceinline__ void st_cluster_s64(uint32_t caddr, long long v) {
+    asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(caddr), "l"(v) : "memory");
+}
+// Bounded wait with cluster-scope acquire, for phases completed by the peer's release arrivals.
+__device__ __forceinline__ bool mbar_test_cl(unsigned long long *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cl(unsigned long long *b, uint32_t parity, volatile int *abort,
+                                             int *gerror, long long timeout_ns) {
+    if (mbar_test_cl(b, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_test_cl(b, parity)) return true;
+        if (*abort) return false;
+        if ((long long)(global_ns() - t0) > timeout_ns) {
+            *abort = 1;
+            atomicCAS(gerror, kDevOk, kDevTimeout);
+            return false;
+        }
+    }
+}
+// TMA load into this CTA's shared memory whose completion is signalled on the
+// leader CTA's mbarrier (caddr: shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int x, int y, uint32_t caddr) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(su32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(caddr)
+        : "memory");
+}
+// 2-SM MMA: M = 256 (128 rows in each CTA's TMEM), N = 128 (64 rows of B in each CTA's shared memory).
+constexpr uint32_t kIdescPair = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)((2 * TM) >> 4) << 24);
+__device__ __forceinline__ void mma_e4m3_pair(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(kIdescPair), "r"(accumulate)
+        : "memory");
+}
+// Arrives on the mbarrier at this offset in both CTAs of the pair once the MMAs issued so far complete.
+__device__ __forceinline__ void mma_commit_pair(unsigned long long *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            su32(bar)),
+        "h"((unsigned short)3)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair_local(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+constexpr int TNH = TN / 2;                                    // rows of B held by each CTA of a pair
+constexpr int NRING = 2, RSTAGES = 2;                          // two rings of two stages
+constexpr uint32_t P_STAGE_A = (uint32_t)KBOX * TM * BOX;      // 32 KB
+constexpr uint32_t P_STAGE_BYTES = P_STAGE_A + (uint32_t)KBOX * TNH * BOX;  // + 16 KB
+constexpr int P_EPI_WARP0 = 4;
+constexpr int P_NTHREADS = (P_EPI_WARP0 + NEPI) * 32;          // 12 warps
+
+struct __align__(8) PairBars {
+    unsigned long long full[NRING][RSTAGES], empty[NRING][RSTAGES];
+    unsigned long long accfull[NBUF], accempty[NBUF];
+    unsigned long long tfull[TASK_RING], tempty[TASK_RING];
+    unsigned long long drain[NRING];
+    unsigned long long epi_go, epi_done;
+    long long task[TASK_RING];
+    unsigned tmem_base;
+    int abort;
+};
+
+// Slice GEMM on CTA pairs (cluster of 2).  A task is product r, tile column
+// tj and the tile-row pair tp; CTA `rank` owns tile row ti = 2 tp + rank.
+// Each CTA streams its 128 rows of the left slices and its 64-row half of the
+// right slices; the leader's MMA threads issue 256 x 128 x 32 MMAs (tcgen05
+// cta_group::2) that read both CTAs' shared memory and accumulate into both
+// CTAs' TMEM.  Per SM this stages 3/4 of the operand bytes of the one-CTA
+// kernel per MMA flop.
+// The tensor pipe queues only about one MMA ahead of its issuing thread, so
+// every barrier wait of a lone issuer idles the pipe.  Two issuers therefore
+// alternate: diagonal groups are numbered globally (G), group G runs on ring
+// G mod 2 (its own producer, its own two stages, its own MMA thread) and
+// accumulates in TMEM buffer G mod 4; while one MMA thread waits, the other
+// issues.
+// Warps: 0, 1 producers of rings 0, 1 (both CTAs); 2, 3 MMA threads of rings
+// 0, 1 (leader; warp 2 also allocates TMEM in both CTAs); 4-11 epilogue.
+// Barriers (same offsets in both CTAs):
+//   full[q][k]   leader only: its producer's expect_tx plus both CTAs' bytes
+//   empty[q][k]  both: MMA thread q's commit (multicast) once stage k is read
+//   accfull[b]   both: the commit (multicast) closing the group in buffer b
+//   accempty[b]  leader only: 2 x NEPI epilogue warps (NEPI of them remote)
+//   tfull/tempty task ring: ring 0's producer in the leader fetches tasks and
+//                publishes them to both CTAs; every other role of both CTAs
+//                releases the slot on the leader's tempty.
+__global__ void __launch_bounds__(P_NTHREADS, 1)
+    ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_bh,
+                         const __grid_constant__ OzParams P) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
+    unsigned char *stage_mem = base;  // NRING x RSTAGES x (A 32 KB, B half 16 KB)
+    PairBars &B = *reinterpret_cast<PairBars *>(base + NRING * RSTAGES * P_STAGE_BYTES);
+    volatile int *abort = &B.abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t rank = cluster_rank();
+    const bool lead = rank == 0;
+    const int pairs_m = (P.tiles_m + 1) / 2;
+    const int ptiles = pairs_m * P.tiles_n;
+    const int nbox = P.Kp / BOX;
+    const int nkb = (nbox + KBOX - 1) / KBOX;
+    const int s = P.s;
+
+    if (tid == 0) {
+        for (int q = 0; q < NRING; ++q)
+            for (int i = 0; i < RSTAGES; ++i) {
+                mbar_init(&B.full[q][i], 1);
+                mbar_init(&B.empty[q][i], 1);
+            }
+        for (int i = 0; i < NBUF; ++i) {
+            mbar_init(&B.accfull[i], 1);
+            mbar_init(&B.accempty[i], 2 * NEPI);
+        }
+        // consumers of a task slot: leader (producer 1, two MMA threads, NEPI
+        // epilogue warps) and peer (two producers, NEPI epilogue warps)
+        for (int i = 0; i < TASK_RING; ++i) {
+            mbar_init(&B.tfull[i], 1);
+            mbar_init(&B.tempty[i], 5 + 2 * NEPI);
+        }
+        for (int q = 0; q < NRING; ++q) mbar_init(&B.drain[q], 1);
+        mbar_init(&B.epi_go, 1);
+        mbar_init(&B.epi_done, NEPI * 32);
+        B.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&B.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    cluster_sync();  // the peer's barriers and TMEM exist before any remote use
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = B.tmem_base;
+
+    if (warp < NRING) {
+        // ------------------------------------------------------------ producer of ring q (both CTAs)
+        const int q = warp;
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&map_a) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&map_bh) : "memory");
+            uint32_t stage = 0, sphase = 0;
+            int tslot = 0, tseq = 0;
+            uint32_t tphase = 0;
+            bool issued = false;
+            while (!*abort) {
+                long long task;
+                if (lead && q == 0) {
+                    task = (long long)atomicAdd(P.task_counter, 1ull);
+                    if (ld_volatile(P.error) != kDevOk) task = P.tasks;
+                    if (!mbar_wait_cl(&B.tempty[tslot], tphase ^ 1u, abort, P.error, P.timeout_ns)) break;
+                    B.task[tslot] = task;
+                    st_cluster_s64(mapa(su32(&B.task[tslot]), 1), task);
+                    mbar_arrive(&B.tfull[tslot]);
+                    arrive_remote_release(mapa(su32(&B.tfull[tslot]), 1));
+                } else {
+                    if (!mbar_wait_cl(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
+                    task = B.task[tslot];
+                    if (lead) mbar_arrive(&B.tempty[tslot]);
+                    else arrive_remote_release(mapa(su32(&B.tempty[tslot]), 0));
+                }
+                if (++tslot == TASK_RING) {
+                    tslot = 0;
+                    tphase ^= 1u;
+                }
+                if (task >= P.tasks) break;
+                const int r = (int)(task / ptiles);
+                const int t2 = (int)(task - (long long)r * ptiles);
+                const int tp = t2 / P.tiles_n, tj = t2 - tp * P.tiles_n;
+                const int ti = 2 * tp + (int)rank;
+                bool ok = true;
+                for (int g = 2; g <= s + 1 && ok; ++g) {
+                    if (((tseq * s + g - 2) & 1) != q) continue;
+                    for (int ta = max(1, g - s); ta <= min(s, g - 1) && ok; ++ta)
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            if (!mbar_wait(&B.empty[q][stage], sphase ^ 1u, abort, P.error, P.timeout_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            unsigned char *sa = stage_mem + (q * RSTAGES + stage) * P_STAGE_BYTES;
+                            unsigned char *sb = sa + P_STAGE_A;
+                            const int boxes = min(KBOX, nbox - kb * KBOX);
+                            const uint32_t full_lead = mapa(su32(&B.full[q][stage]), 0);
+                            if (lead) mbar_expect_tx(&B.full[q][stage], (uint32_t)(2 * boxes * (TM + TNH) * BOX));
+                            const int ya = (r * s + (ta - 1)) * P.Mp + ti * TM;
+                            const int yb = (r * s + (g - ta - 1)) * P.Mp + tj * TN + (int)rank * TNH;
+                            for (int bx = 0; bx < boxes; ++bx) {
+                                const int x = (kb * KBOX + bx) * BOX;
+                                tma_load_2d_pair(sa + bx * TM * BOX, &map_a, x, ya, full_lead);
+                                tma_load_2d_pair(sb + bx * TNH * BOX, &map_bh, x, yb, full_lead);
+                            }
+                            issued = true;
+                            if (++stage == RSTAGES) {
+                                stage = 0;
+                                sphase ^= 1u;
+                            }
+                        }
+                }
+                if (!ok) break;
+                ++tseq;
+            }
+            if (*abort && issued) {
+                // copies signal the leader's barriers, which this thread cannot
+                // wait on: give any copy still in flight time to land
+                const unsigned long long t0 = global_ns();
+                while ((long long)(global_ns() - t0) < 100000) {
+                }
+            }
+        }
+    } else if (warp < 2 * NRING) {
+        // ------------------------------------------------------------ MMA thread of ring q (leader CTA)
+        const int q = warp - NRING;
+        if (lead && lane == 0) {
+            uint32_t stage = 0, sphase = 0;
+            int tslot = 0, tseq = 0;
+            uint32_t tphase = 0;
+            const uint32_t sbase = su32(stage_mem) + (uint32_t)(q * RSTAGES) * P_STAGE_BYTES;
+            bool any = false;
+            while (!*abort) {
+                if (!mbar_wait(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
+                const long long task = B.task[tslot];
+                mbar_arrive(&B.tempty[tslot]);
+                if (++tslot == TASK_RING) {
+                    tslot = 0;
+                    tphase ^= 1u;
+                }
+                if (task >= P.tasks) break;
+                bool ok = true;
+                for (int g = 2; g <= s + 1 && ok; ++g) {
+                    const int G = tseq * s + g - 2;
+                    if ((G & 1) != q) continue;
+                    const uint32_t buf = (uint32_t)(G % NBUF), bphase = (uint32_t)((G / NBUF) & 1);
+                    if (!mbar_wait(&B.accempty[buf], bphase ^ 1u, abort, P.error, P.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dtm = tmem + buf * TN;
+                    bool first = true;
+                    for (int ta = max(1, g - s); ta <= min(s, g - 1) && ok; ++ta)
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            if (!mbar_wait(&B.full[q][stage], sphase, abort, P.error, P.timeout_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t sa = sbase + stage * P_STAGE_BYTES;
+                            const uint64_t da = desc_sw128(sa), db = desc_sw128(sa + P_STAGE_A);
+                            const int kmma = min(KBOX, nbox - kb * KBOX) * (BOX / 32);
+#pragma unroll
+                            for (int k = 0; k < SLAB / 32; ++k) {
+                                if (k >= kmma) break;
+                                // 32-byte K step inside a box; boxes 16 KB (A) and 8 KB (B half) apart
+                                const uint64_t adv = (uint64_t)(((k % (BOX / 32)) * 32) >> 4);
+                                const uint64_t boxa = (uint64_t)(((k / (BOX / 32)) * TM * BOX) >> 4);
+                                const uint64_t boxb = (uint64_t)(((k / (BOX / 32)) * TNH * BOX) >> 4);
+                                mma_e4m3_pair(dtm, da + boxa + adv, db + boxb + adv, first ? 0u : 1u);
+                                first = false;
+                            }
+                            mma_commit_pair(&B.empty[q][stage]);
+                            any = true;
+                            if (++stage == RSTAGES) {
+                                stage = 0;
+                                sphase ^= 1u;
+                            }
+                        }
+                    if (!ok) break;
+                    mma_commit_pair(&B.accfull[buf]);
+                }
+                if (!ok) break;
+                ++tseq;
+            }
+            if (any) {
+                // all MMAs complete before either CTA releases TMEM or shared memory
+                mma_commit_pair_local(&B.drain[q]);
+                const unsigned long long t0 = global_ns();
+                while (!mbar_test(&B.drain[q], 0) && (long long)(global_ns() - t0) < P.timeout_ns) {
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (both CTAs)
+        int tslot = 0, tseq = 0;
+        uint32_t tphase = 0;
+        uint32_t dphase = 0;
+        uint32_t accempty_lead[NBUF];
+#pragma unroll
+        for (int i = 0; i < NBUF; ++i) accempty_lead[i] = mapa(su32(&B.accempty[i]), 0);
+        while (!*abort) {
+            if (!mbar_wait_cl(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
+            const long long task = B.task[tslot];
+            __syncwarp();
+            if (lane == 0) {
+                if (lead) mbar_arrive(&B.tempty[tslot]);
+                else arrive_remote_release(mapa(su32(&B.tempty[tslot]), 0));
+            }
+            if (++tslot == TASK_RING) {
+                tslot = 0;
+                tphase ^= 1u;
+            }
+            if (task >= P.tasks) break;
+            const int r = (int)(task / ptiles);
+            const int t2 = (int)(task - (long long)r * ptiles);
+            const int tp = t2 / P.tiles_n, tj = t2 - tp * P.tiles_n;
+            const int ti = 2 * tp + (int)rank;
+            if (!epilogue_tile<P_EPI_WARP0>(P, B.accfull, &B.epi_go, &B.epi_done, abort, tmem, r, ti, tj,
+                                            ti < P.tiles_m, tseq * s, dphase, [&](uint32_t b) {
+                                                if (lead) mbar_arrive(&B.accempty[b]);
+                                                else arrive_remote_relaxed(accempty_lead[b]);
+                                            }))
+                break;
+            ++tseq;
+        }
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    cluster_sync();  // neither CTA leaves while the pair's MMAs or copies may touch it
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
 constexpr size_t kSmemBytes = 1024 + STAGES * STAGE_BYTES + sizeof(Bars);
+constexpr size_t kPairSmemBytes = 1024 + NRING * RSTAGES * P_STAGE_BYTES + sizeof(PairBars);
 
 }  // namespace
 
@@ -509,6 +926,61 @@ cudaError_t launch_ozaki_tc(const CUtensorMap &map_a, const CUtensorMap &map_b, 
     }
     ozaki_tc_kernel<<<grid, NTHREADS, kSmemBytes, s>>>(map_a, map_b, P);
     return cudaGetLastError();
+}
+
+cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_bh, const OzParams &P,
+                                 int pairs, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(ozaki_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kPairSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * pairs));
+    cfg.blockDim = dim3(P_NTHREADS);
+    cfg.dynamicSmemBytes = kPairSmemBytes;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ozaki_tc_pair_kernel, map_a, map_bh, P);
+}
+
+int ozaki_tc_max_pairs() {
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    if (cudaFuncSetAttribute(ozaki_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPairSmemBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cfg.gridDim = dim3((unsigned)(sms / 2 * 2));
+    cfg.blockDim = dim3(P_NTHREADS);
+    cfg.dynamicSmemBytes = kPairSmemBytes;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, ozaki_tc_pair_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cached = n;
+    return n;
 }
 
 }  // namespace fmm
