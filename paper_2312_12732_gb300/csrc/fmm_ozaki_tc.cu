@@ -144,34 +144,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
 // v * 2^e rounded to nearest even, built with integer operations only (the
-// FP64 pipe is the GPU's scarcest unit).  Scaling by a power of two is exact,
-// so this equals RN(v) * 2^e whenever the result is a normal number; results
-// that would be subnormal are reported through `ok` and take the FP64 route.
+// FP64 pipe is the GPU's scarcest unit) and without branches: normalise |v|
+// so its leading bit is bit 63, keep 53 bits, round on the guard bit with the
+// sticky bits and the last kept bit, and add the rounded significand (whose
+// leading bit is worth one exponent step) onto the exponent field, so that a
+// carry out of the significand bumps the exponent by itself.  Scaling by a
+// power of two is exact, so this equals RN(v) * 2^e whenever the result is a
+// normal number; `ok` is cleared otherwise and the caller takes the FP64 route.
 __device__ __forceinline__ double ldexp_i64_rn(long long v, int e, bool &ok) {
-    if (v == 0) return 0.0;
-    const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
-    unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    const int msb = 63 - __clzll((long long)a);
-    int E = msb + e;  // unbiased exponent of the leading bit
-    unsigned long long mant;
-    if (msb <= 52) {
-        mant = a << (52 - msb);
-    } else {
-        const int sh = msb - 52;
-        mant = a >> sh;
-        const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1ull))) ++mant;
-        if (mant >> 53) {  // carried into a new leading bit
-            mant >>= 1;
-            ++E;
-        }
-    }
-    const int biased = E + 1023;
-    if (biased <= 0 || biased >= 2047) {
-        ok = false;
-        return 0.0;
-    }
-    return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1ull))));
+    const unsigned long long sign = (unsigned long long)v & (1ull << 63);
+    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)a);
+    const unsigned long long m = a << (lz & 63);                 // leading bit at 63 (a != 0)
+    const unsigned long long keep = m >> 11;                     // 53 bits
+    const unsigned long long up = (m >> 10) & ((m & 0x3FFull) != 0 ? 1ull : (keep & 1ull));
+    const int E = 63 - lz + e;                                   // exponent of the leading bit
+    ok = (a == 0) || (E >= -1022 && E <= 1022);
+    const unsigned long long bits = ((unsigned long long)(E + 1022) << 52) + keep + up;
+    return a == 0 ? 0.0 : __longlong_as_double((long long)(sign | bits));
 }
 __device__ __forceinline__ double scale2(double v, int sc) {
     while (sc > 1023) {
@@ -243,15 +233,23 @@ __device__ __forceinline__ bool epilogue_tile(const OzParams &P, unsigned long l
     const int rows = (int)min((long long)TM, P.m - (long long)ti * TM);
     const int cols = (int)min((long long)TN, P.m - (long long)tj * TN);
     const int ea = row < rows ? max(P.mxa[(long long)r * P.Mp + (long long)ti * TM + row], 1) - 1021 : 0;
+    // column exponents: 64 consecutive ints, 16-byte aligned (Mp, TN and col0 are multiples of 64);
+    // padding columns hold zeros, which only ever scale zero sums
+    const int4 *mxb4 = reinterpret_cast<const int4 *>(P.mxb + (long long)r * P.Mp + (long long)tj * TN + col0);
+    const int base_sc = ea - 1021 - OB * (s + 1) + P.L;
 #pragma unroll
-    for (int j = 0; j < 64; ++j) {
-        const int col = col0 + j;
-        const int eb = col < cols ? max(P.mxb[(long long)r * P.Mp + (long long)tj * TN + col], 1) - 1021 : 0;
-        const int sc = ea + eb - OB * (s + 1) + P.L;
-        bool ok = true;
-        double v = ldexp_i64_rn(acc[j], sc, ok);
-        if (!ok) v = scale2(__ll2double_rn(acc[j]), sc);
-        acc[j] = __double_as_longlong(v);
+    for (int j4 = 0; j4 < 16; ++j4) {
+        const int4 e4 = __ldg(mxb4 + j4);
+        const int ebs[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = 4 * j4 + u;
+            const int sc = base_sc + max(ebs[u], 1);
+            bool ok;
+            double v = ldexp_i64_rn(acc[j], sc, ok);
+            if (!ok) v = scale2(__ll2double_rn(acc[j]), sc);
+            acc[j] = __double_as_longlong(v);
+        }
     }
 
     // post-additions C_l (+)= W[l][r] P_r in ascending r (per-tile counters)
@@ -275,30 +273,46 @@ __device__ __forceinline__ bool epilogue_tile(const OzParams &P, unsigned long l
             const bool vec = (((unsigned long long)prow) & 31ull) == 0;
             const int nv = vec ? max(0, min(64, cols - col0)) / 4 : 0;
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                if (u >= nv) break;
-                double v0 = __longlong_as_double(acc[4 * u]), v1 = __longlong_as_double(acc[4 * u + 1]),
-                       v2 = __longlong_as_double(acc[4 * u + 2]), v3 = __longlong_as_double(acc[4 * u + 3]);
-                if (mode >= 3) {
-                    double o0, o1, o2, o3;
+            for (int u0 = 0; u0 < 16; u0 += 2) {
+                if (u0 >= nv) break;
+                const bool two = u0 + 1 < nv;
+                double o[2][4];
+                if (mode >= 3) {  // both 32-byte sectors in flight before the first add
                     asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];"
-                                 : "=d"(o0), "=d"(o1), "=d"(o2), "=d"(o3)
-                                 : "l"(prow + 4 * u));
-                    if (mode == 3) {
-                        v0 = o0 + v0; v1 = o1 + v1; v2 = o2 + v2; v3 = o3 + v3;
-                    } else if (mode == 4) {
-                        v0 = o0 - v0; v1 = o1 - v1; v2 = o2 - v2; v3 = o3 - v3;
-                    } else {
-                        v0 = fma(cfd, v0, o0); v1 = fma(cfd, v1, o1); v2 = fma(cfd, v2, o2); v3 = fma(cfd, v3, o3);
-                    }
-                } else if (mode == 1) {
-                    v0 = neg(v0); v1 = neg(v1); v2 = neg(v2); v3 = neg(v3);
-                } else if (mode == 2) {
-                    v0 *= cfd; v1 *= cfd; v2 *= cfd; v3 *= cfd;
+                                 : "=d"(o[0][0]), "=d"(o[0][1]), "=d"(o[0][2]), "=d"(o[0][3])
+                                 : "l"(prow + 4 * u0));
+                    if (two)
+                        asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];"
+                                     : "=d"(o[1][0]), "=d"(o[1][1]), "=d"(o[1][2]), "=d"(o[1][3])
+                                     : "l"(prow + 4 * u0 + 4));
                 }
-                asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(prow + 4 * u), "d"(v0), "d"(v1), "d"(v2),
-                             "d"(v3)
-                             : "memory");
+#pragma unroll
+                for (int w = 0; w < 2; ++w) {
+                    if (w == 1 && !two) break;
+                    const int u = u0 + w;
+                    double v[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) v[c] = __longlong_as_double(acc[4 * u + c]);
+                    if (mode == 3) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[c] = o[w][c] + v[c];
+                    } else if (mode == 4) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[c] = o[w][c] - v[c];
+                    } else if (mode == 5) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[c] = fma(cfd, v[c], o[w][c]);
+                    } else if (mode == 1) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[c] = neg(v[c]);
+                    } else if (mode == 2) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[c] *= cfd;
+                    }
+                    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(prow + 4 * u), "d"(v[0]), "d"(v[1]),
+                                 "d"(v[2]), "d"(v[3])
+                                 : "memory");
+                }
             }
 #pragma unroll
             for (int j = 0; j < 64; ++j) {
@@ -631,9 +645,12 @@ __device__ __forceinline__ void mma_commit_pair_local(unsigned long long *bar) {
 }
 
 constexpr int TNH = TN / 2;                                    // rows of B held by each CTA of a pair
-constexpr int NRING = 2, RSTAGES = 2;                          // two rings of two stages
-constexpr uint32_t P_STAGE_A = (uint32_t)KBOX * TM * BOX;      // 32 KB
-constexpr uint32_t P_STAGE_BYTES = P_STAGE_A + (uint32_t)KBOX * TNH * BOX;  // + 16 KB
+// Two rings of four one-box stages (24 KB each per CTA): with two MMA threads
+// the per-stage waits hide behind the other thread's MMAs, and small stages
+// keep more of the ring's bytes in flight while one stage is being read.
+constexpr int NRING = 2, RSTAGES = 4, P_KBOX = 1, P_SLAB = BOX * P_KBOX;
+constexpr uint32_t P_STAGE_A = (uint32_t)P_KBOX * TM * BOX;    // 16 KB
+constexpr uint32_t P_STAGE_BYTES = P_STAGE_A + (uint32_t)P_KBOX * TNH * BOX;  // + 8 KB
 constexpr int P_EPI_WARP0 = 4;
 constexpr int P_NTHREADS = (P_EPI_WARP0 + NEPI) * 32;          // 12 warps
 
@@ -686,7 +703,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
     const int pairs_m = (P.tiles_m + 1) / 2;
     const int ptiles = pairs_m * P.tiles_n;
     const int nbox = P.Kp / BOX;
-    const int nkb = (nbox + KBOX - 1) / KBOX;
+    const int nkb = (nbox + P_KBOX - 1) / P_KBOX;
     const int s = P.s;
 
     if (tid == 0) {
@@ -769,13 +786,13 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                             }
                             unsigned char *sa = stage_mem + (q * RSTAGES + stage) * P_STAGE_BYTES;
                             unsigned char *sb = sa + P_STAGE_A;
-                            const int boxes = min(KBOX, nbox - kb * KBOX);
+                            const int boxes = min(P_KBOX, nbox - kb * P_KBOX);
                             const uint32_t full_lead = mapa(su32(&B.full[q][stage]), 0);
                             if (lead) mbar_expect_tx(&B.full[q][stage], (uint32_t)(2 * boxes * (TM + TNH) * BOX));
                             const int ya = (r * s + (ta - 1)) * P.Mp + ti * TM;
                             const int yb = (r * s + (g - ta - 1)) * P.Mp + tj * TN + (int)rank * TNH;
                             for (int bx = 0; bx < boxes; ++bx) {
-                                const int x = (kb * KBOX + bx) * BOX;
+                                const int x = (kb * P_KBOX + bx) * BOX;
                                 tma_load_2d_pair(sa + bx * TM * BOX, &map_a, x, ya, full_lead);
                                 tma_load_2d_pair(sb + bx * TNH * BOX, &map_bh, x, yb, full_lead);
                             }
@@ -836,9 +853,9 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                             const uint32_t sa = sbase + stage * P_STAGE_BYTES;
                             const uint64_t da = desc_sw128(sa), db = desc_sw128(sa + P_STAGE_A);
-                            const int kmma = min(KBOX, nbox - kb * KBOX) * (BOX / 32);
+                            const int kmma = min(P_KBOX, nbox - kb * P_KBOX) * (BOX / 32);
 #pragma unroll
-                            for (int k = 0; k < SLAB / 32; ++k) {
+                            for (int k = 0; k < P_SLAB / 32; ++k) {
                                 if (k >= kmma) break;
                                 // 32-byte K step inside a box; boxes 16 KB (A) and 8 KB (B half) apart
                                 const uint64_t adv = (uint64_t)(((k % (BOX / 32)) * 32) >> 4);
