@@ -292,6 +292,12 @@ def make_algo(fmm, name):
     return fmm.fmm_algo_builtin(name)
 
 
+def ozaki_launches(levels: int, peeled: bool) -> int:
+    """Kernels of one emulated-leaf call: a materialization per level and operand, row and column
+    slicing, the slice GEMM, the post-additions and (for peeled sizes) the FP64 peel tasks."""
+    return 2 * levels + 4 + (1 if peeled else 0)
+
+
 def materialized_bytes(n_core: int, p: int, R_total: int, depth: int, levels: int) -> float:
     """Algorithmic HBM bytes of the materialized pre-additions of both operands: level l reads the
     R^(l-1) blocks of side n_core/p^(l-1) once and writes R^l blocks of side n_core/p^l."""
@@ -569,7 +575,7 @@ def run_ours(a):
             "value": job_throughput(flops_eff, ws, e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
             "speedup_vs_classic": (flops_eff / (e_ms * 1e-3) / 1e12) / classic["value"] if classic else None,
             "normalised_error_sampled": e_err, "ozaki_slices": e_info["ozaki_slices"],
-            "gpu_launches": a.steps * (2 * e_info["materialized_levels"] + 5 + (1 if n % 4 else 0)),
+            "gpu_launches": a.steps * ozaki_launches(e_info["materialized_levels"], e_info["n_core"] < n),
             "roofline": {"bound": "tensor", "kernel": "ozaki_tc_kernel", "achieved": e_achieved, "peak": fp8_peak,
                          "unit": "TFLOP/s", "frac": e_achieved / fp8_peak, "peak_note": fp8_note,
                          "traffic": profile_traffic("ozaki_tc_kernel",
@@ -639,8 +645,8 @@ def run_ours(a):
         "normalised_error_sampled": err,
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": a.steps * ((1 + 2 * info["materialized_levels"]) if a.dtype == "f64" else
-                                   (2 * info["materialized_levels"] + 5 + (1 if q > 0 else 0))),
+        "gpu_launches": a.steps * ozaki_launches(info["materialized_levels"], q > 0) if a.dtype == "f64_ozaki"
+        else a.steps * (1 + 2 * info["materialized_levels"]),
         "roofline": roofline,
         "emulated_fp64": emulated,
         "cpu_baseline": cpu,

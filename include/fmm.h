@@ -227,7 +227,9 @@ fmm_status_t fmm_plan_last_kernel_ms(const fmm_plan_t *plan, float *leaf_ms, flo
  * call's stream: phases[0] counter reset and materialized pre-additions,
  * phases[1] exponents and slicing (FMM_F64_OZAKI; 0 otherwise), phases[2]
  * the leaf-product kernel, phases[3] the peel tasks run after an emulated
- * leaf (0 otherwise).  Fills min(count, 4) entries; waits for the call. */
+ * leaf (0 otherwise), phases[4] the post-additions C_l = sum_r W[l][r] P_r
+ * that the emulated leaf runs as a separate kernel (0 otherwise).  Fills
+ * min(count, 5) entries; waits for the call. */
 fmm_status_t fmm_plan_last_phase_ms(const fmm_plan_t *plan, float *phases, int count);
 
 /* Calibration, with no counterpart in the paper: measures the FP64

@@ -246,10 +246,10 @@ def fmm_measure_e4m3_peak(stream=None) -> float:
 
 
 def fmm_plan_last_phase_ms(plan: Plan) -> dict:
-    """{materialize, slice, leaf, peel} milliseconds of the plan's most recent fmm_gemm."""
-    arr = (ctypes.c_float * 4)()
-    _check(lib().fmm_plan_last_phase_ms(plan.handle, arr, 4), "fmm_plan_last_phase_ms")
-    return dict(zip(("materialize", "slice", "leaf", "peel"), (float(x) for x in arr)))
+    """{materialize, slice, leaf, peel, post} milliseconds of the plan's most recent fmm_gemm."""
+    arr = (ctypes.c_float * 5)()
+    _check(lib().fmm_plan_last_phase_ms(plan.handle, arr, 5), "fmm_plan_last_phase_ms")
+    return dict(zip(("materialize", "slice", "leaf", "peel", "post"), (float(x) for x in arr)))
 
 
 def fmm_plan_workspace_bytes(plan: Plan) -> int:

@@ -311,12 +311,16 @@ struct fmm_plan {
     const F64Geom *d_geom_peel = nullptr;              // FP64 peel-only geometry
     int oz_engine = 2;                                  // 2 = tcgen05 CTA pairs, 1 = tcgen05, 0 = mma.sync
     CUtensorMap oz_map_a{}, oz_map_b{}, oz_map_bh{};    // TMA maps over the slices (bh: 64-row boxes)
+    double *d_pout = nullptr;                           // [R][m][m] leaf products of the tcgen05 engines
+    const int *d_wl_ptr = nullptr;                      // per C block: products (r, coefficient) in ascending r
+    const int2 *d_wl_ent = nullptr;
     double flops_lowp = 0;
     // host-buffer path
     double *d_hostA = nullptr, *d_hostB = nullptr, *d_hostC = nullptr;
     // optional timing events: [0] call start, [1] leaf start, [2] leaf end,
-    // [3] after counter reset + materialization, [4] call end
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // [3] after counter reset + materialization, [4] call end, [5] after the
+    // separate post-additions of the emulated leaf
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool timed_once = false;
     // statistics
     double flops_leaf = 0, flops_exec = 0;
@@ -502,6 +506,15 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         w_ptr[c + 1] = w_ptr[c] + (int)wcols[c].size();
         for (const Entry &e : wcols[c]) w_ent.push_back(make_int4(e.blk, e.coef, w_row[e.blk]++, 0));
     }
+    // the same nonzeros by C block, products in ascending order (separate post-additions)
+    std::vector<int> wl_ptr((size_t)P * P + 1, 0);
+    std::vector<int2> wl_ent(w_ent.size());
+    for (size_t l = 0; l < (size_t)P * P; ++l) wl_ptr[l + 1] = wl_ptr[l] + w_row[l];
+    for (size_t c = 0; c < wcols.size(); ++c)
+        for (int k = w_ptr[c]; k < w_ptr[c + 1]; ++k) {
+            const int4 &e = w_ent[k];
+            wl_ent[wl_ptr[e.x] + e.z] = make_int2((int)c, e.y);
+        }
 
     // Task counts.
     const long long tiles = (long long)pl->tiles_m * pl->tiles_n;
@@ -561,6 +574,8 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     const size_t o_wptr = reserve(w_ptr.size() * sizeof(int));
     const size_t o_went = reserve(std::max<size_t>(1, w_ent.size()) * sizeof(int4));
     const size_t o_wrow = reserve(w_row.size() * sizeof(int));
+    const size_t o_wlptr = reserve(wl_ptr.size() * sizeof(int));
+    const size_t o_wlent = reserve(std::max<size_t>(1, wl_ent.size()) * sizeof(int2));
     size_t o_muptr = 0, o_muent = 0, o_mvptr = 0, o_mvent = 0;
     if (mat > 0) {
         o_muptr = reserve(mu_ptr.size() * sizeof(int));
@@ -582,6 +597,8 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     g.w_ptr = (const int *)(base + o_wptr);
     g.w_ent = (const int4 *)(base + o_went);
     g.w_row_nnz = (const int *)(base + o_wrow);
+    pl->d_wl_ptr = (const int *)(base + o_wlptr);
+    pl->d_wl_ent = (const int2 *)(base + o_wlent);
     std::vector<char> host(pl->tables_bytes, 0);
     auto put = [&](size_t o2, const void *src, size_t bytes) { if (bytes) std::memcpy(host.data() + o2, src, bytes); };
     put(o_uptr, u_ptr.data(), u_ptr.size() * sizeof(int));
@@ -591,6 +608,8 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     put(o_wptr, w_ptr.data(), w_ptr.size() * sizeof(int));
     put(o_went, w_ent.data(), w_ent.size() * sizeof(int4));
     put(o_wrow, w_row.data(), w_row.size() * sizeof(int));
+    put(o_wlptr, wl_ptr.data(), wl_ptr.size() * sizeof(int));
+    put(o_wlent, wl_ent.data(), wl_ent.size() * sizeof(int2));
     if (mat > 0) {
         put(o_muptr, mu_ptr.data(), mu_ptr.size() * sizeof(int));
         put(o_muent, mu_ent.data(), mu_ent.size() * sizeof(int4));
@@ -645,11 +664,12 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
             o_tb = ws; ws = align_up(ws + tbytes, 256);
         }
     }
-    size_t o_sla = 0, o_slb = 0, slice_bytes = 0;
+    size_t o_sla = 0, o_slb = 0, o_pout = 0, slice_bytes = 0;
     if (dtype == FMM_F64_OZAKI) {
         slice_bytes = (size_t)Rt * (size_t)oz_s * (size_t)pl->oz_Mp * (size_t)pl->oz_Mp;
         o_sla = ws; ws = align_up(ws + slice_bytes, 256);
         o_slb = ws; ws = align_up(ws + slice_bytes, 256);
+        o_pout = ws; ws = align_up(ws + (size_t)Rt * (size_t)pl->m * (size_t)pl->m * sizeof(double), 256);
     }
     pl->ws_bytes = ws;
     if (cudaMalloc(&pl->d_ws, ws) != cudaSuccess) {
@@ -676,6 +696,7 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         pl->d_mxb = pl->d_mxa + (size_t)Rt * pl->oz_Mp;
         pl->d_sla = (unsigned char *)(wsb + o_sla);
         pl->d_slb = (unsigned char *)(wsb + o_slb);
+        pl->d_pout = (double *)(wsb + o_pout);
         // engine: CTA pairs by default; FMM_OZAKI_ENGINE=tc1 (one CTA per tile) or mma_sync
         const char *eng = std::getenv("FMM_OZAKI_ENGINE");
         const std::string es = eng ? eng : "";
@@ -808,6 +829,7 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     P.mxb = pl->d_mxb;
     P.C = C;
     P.ldc = pl->n;
+    P.pout = pl->d_pout;
     P.m = m;
     P.Mp = Mp;
     P.Kp = Mp;
@@ -839,6 +861,11 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
         if (fmm::launch_ozaki_gemm(P, grid < 1 ? 1 : grid, st) != cudaSuccess) return FMM_ERR_CUDA;
     }
     if (pl->ev[2] && cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (pl->oz_engine >= 1 &&
+        fmm::launch_ozaki_postadd(pl->d_pout, m, (int)pl->P, pl->d_wl_ptr, pl->d_wl_ent, C, pl->n, pl->d_chain,
+                                  pl->geom.w_row_nnz, pl->tiles_m * pl->tiles_n, st) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    if (pl->ev[5] && cudaEventRecord(pl->ev[5], st) != cudaSuccess) return FMM_ERR_CUDA;
     const long long peel = pl->geom.tasks_right + pl->geom.tasks_bottom + pl->geom.tasks_rankq;
     if (peel > 0) {
         F64Launch<1> L{};
@@ -888,6 +915,7 @@ extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const do
     if (ls != FMM_OK) return ls;
     if (pl->ev[2]) {
         if (cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
+        if (cudaEventRecord(pl->ev[5], st) != cudaSuccess) return FMM_ERR_CUDA;
         if (cudaEventRecord(pl->ev[4], st) != cudaSuccess) return FMM_ERR_CUDA;
         const_cast<fmm_plan *>(pl)->timed_once = true;
     }
@@ -897,11 +925,13 @@ extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const do
 extern "C" fmm_status_t fmm_plan_last_phase_ms(const fmm_plan_t *pl, float *phases, int count) {
     if (!pl || !phases || count < 1 || !pl->ev[0] || !pl->timed_once) return FMM_ERR_INVALID;
     if (cudaEventSynchronize(pl->ev[4]) != cudaSuccess) return FMM_ERR_CUDA;
-    // [0] counter reset + materialization, [1] slicing (emulated leaf), [2] leaf kernel, [3] peel tasks
-    const cudaEvent_t marks[5] = {pl->ev[0], pl->ev[3], pl->ev[1], pl->ev[2], pl->ev[4]};
-    for (int i = 0; i < count && i < 4; ++i) {
+    // [0] counter reset + materialization, [1] slicing (emulated leaf), [2] leaf kernel, [3] peel tasks,
+    // [4] separate post-additions (emulated leaf)
+    const cudaEvent_t from[5] = {pl->ev[0], pl->ev[3], pl->ev[1], pl->ev[5], pl->ev[2]};
+    const cudaEvent_t to[5] = {pl->ev[3], pl->ev[1], pl->ev[2], pl->ev[4], pl->ev[5]};
+    for (int i = 0; i < count && i < 5; ++i) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, marks[i], marks[i + 1]) != cudaSuccess) return FMM_ERR_CUDA;
+        if (cudaEventElapsedTime(&ms, from[i], to[i]) != cudaSuccess) return FMM_ERR_CUDA;
         phases[i] = ms;
     }
     return FMM_OK;

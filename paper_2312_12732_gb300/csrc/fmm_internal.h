@@ -96,8 +96,9 @@ struct OzParams {
     const unsigned char *sb;  // right slices [R][s][Mp][Kp] (column j of T_r, K contiguous)
     const int *mxa;           // [R][Mp] largest biased exponent of each row of S_r
     const int *mxb;           // [R][Mp] ... of each column of T_r
-    double *C;
+    double *C;                // C (the mma.sync engine adds into it directly)
     long long ldc;
+    double *pout;             // [R][m][m] leaf products P_r (tcgen05 engines), leading dimension m
     long long m;              // leaf size
     int Mp, Kp;               // padded to multiples of 128
     int s;                    // slices per operand
@@ -133,6 +134,13 @@ cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &ma
                                  int pairs, cudaStream_t s);
 // Largest number of co-resident pairs of the pair kernel (0 if it cannot run).
 int ozaki_tc_max_pairs();
+// C_l = sum_r W[l][r] P_r for the P x P blocks of side m of C (leading
+// dimension ldc), in ascending r: wl_ptr / wl_ent list, per block l, the
+// products (r, coefficient) in ascending r.  Also sets the ordering counters
+// of the peel tasks: chain[l * tiles + t] = w_row_nnz[l].
+cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
+                                 double *C, long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
+                                 cudaStream_t s);
 
 // Kernel launchers (fmm_f64.cu).  Return cudaSuccess or the launch error.
 // bn selects the tile configuration (128 or 64 columns).

@@ -1,22 +1,26 @@
 // Emulated-FP64 slice GEMM on the 5th-generation tensor cores (tcgen05),
 // sm_103a.  Same arithmetic as the mma.sync kernel in fmm_ozaki.cu (Ozaki
 // scheme: diagonal groups D_g = sum_{t+u=g} Shat_t That_u of e4m3 slices,
-// exact in FP32, folded into int64, one FP64 conversion per element, FP64
-// post-additions in ascending product order), organised the Blackwell way:
+// exact in FP32, folded into int64, one correctly rounded conversion to FP64
+// per element), organised the Blackwell way, in two forms:
 //
-//   warp 0     TMA producer: fetches tile tasks in increasing order, streams
-//              128 x 256-byte slabs of both slice operands (two 128B-swizzled
-//              boxes each) into a 3-stage shared-memory ring with
-//              cp.async.bulk.tensor;
-//   warp 1     MMA issuer: one thread issues tcgen05.mma kind::f8f6f4
-//              (M = 128, N = 128, K = 32) from the ring into one of two TMEM
-//              accumulators (one per diagonal group in flight) and releases
-//              ring slots / hands finished groups over with tcgen05.commit;
-//   warps 2-9  epilogue: each thread owns one tile row and 64 columns, reads
-//              D_g with tcgen05.ld, folds it into 64 int64 registers while the
-//              next group accumulates in the other TMEM buffer, then scales to
-//              FP64 and applies the post-additions.
+//   ozaki_tc_kernel (one CTA per tile)
+//     warp 0     TMA producer: fetches tile tasks in increasing order, streams
+//                128 x 256-byte slabs of both slice operands (two 128B-swizzled
+//                boxes each) into a 3-stage shared-memory ring with
+//                cp.async.bulk.tensor;
+//     warp 1     MMA issuer: one thread issues tcgen05.mma kind::f8f6f4
+//                (M = 128, N = 128, K = 32) into one of four TMEM
+//                accumulators and releases ring slots / hands finished groups
+//                over with tcgen05.commit;
+//     warps 2-9  epilogue: each thread owns one tile row and 64 columns, reads
+//                D_g with tcgen05.ld, folds it into 64 int64 registers while
+//                later groups accumulate, converts to FP64 and stores the tile
+//                of P_r.
+//   ozaki_tc_pair_kernel (CTA pairs, tcgen05 cta_group::2; the default)
+//     described above the kernel.
 //
+// ozaki_postadd_kernel then forms C_l = sum_r W[l][r] P_r in ascending r.
 // Every mbarrier wait is bounded by %globaltimer; on expiry the CTA records a
 // timeout, stops issuing, waits (bounded) for its own copies and MMAs in
 // flight, frees its TMEM and returns.
@@ -29,10 +33,8 @@
 namespace fmm {
 namespace {
 
-using dev::chain_wait;
 using dev::global_ns;
 using dev::ld_volatile;
-using dev::neg;
 
 constexpr int OB = kOzDigitBits;
 constexpr int TM = 128, TN = 128, BOX = 128;  // tile rows, tile cols, K bytes per TMA box
@@ -44,9 +46,9 @@ constexpr int KBOX = 2, SLAB = BOX * KBOX;     // K bytes per stage
 constexpr int STAGES = 3;
 constexpr int NTHREADS = 320;                  // 10 warps
 constexpr int EPI_WARP0 = 2, NEPI = 8;
-// Four 128-column FP32 accumulators (all of TMEM): the MMA thread can run
-// three diagonal groups ahead of the epilogue, which covers the post-additions
-// of one task while the next task's first groups accumulate.
+// Four 128-column FP32 accumulators (all of TMEM): the MMA threads can run
+// three diagonal groups ahead of the epilogue, which covers the conversion and
+// store of one task while the next task's first groups accumulate.
 constexpr int NBUF = 4;
 constexpr int TMEM_COLS = NBUF * 128;
 constexpr int TASK_RING = 2;
@@ -57,7 +59,6 @@ struct __align__(8) Bars {
     unsigned long long accfull[NBUF], accempty[NBUF];
     unsigned long long tfull[TASK_RING], tempty[TASK_RING];
     unsigned long long drain;
-    unsigned long long epi_go, epi_done;  // epilogue hand-offs around each post-addition
     long long task[TASK_RING];
     unsigned tmem_base;
     int abort;
@@ -141,65 +142,62 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr));
 }
 
-__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
 // v * 2^e rounded to nearest even, built with integer operations only (the
-// FP64 pipe is the GPU's scarcest unit) and without branches: normalise |v|
-// so its leading bit is bit 63, keep 53 bits, round on the guard bit with the
-// sticky bits and the last kept bit, and add the rounded significand (whose
-// leading bit is worth one exponent step) onto the exponent field, so that a
-// carry out of the significand bumps the exponent by itself.  Scaling by a
-// power of two is exact, so this equals RN(v) * 2^e whenever the result is a
-// normal number; `ok` is cleared otherwise and the caller takes the FP64 route.
-__device__ __forceinline__ double ldexp_i64_rn(long long v, int e, bool &ok) {
+// FP64 pipe is the GPU's scarcest unit).  Normal results: normalise |v| so its
+// leading bit is bit 63, keep 53 bits, round on the guard bit with the sticky
+// bits and the last kept bit, and add the rounded significand (whose leading
+// bit is worth one exponent step) onto the exponent field, so that a carry out
+// of the significand bumps the exponent by itself (up to infinity).
+// Subnormal results: the significand is |v| scaled to units of 2^-1074 and
+// rounded once, the same way.
+__device__ __forceinline__ double ldexp_i64_rn(long long v, int e) {
     const unsigned long long sign = (unsigned long long)v & (1ull << 63);
     const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
     const int lz = __clzll((long long)a);
-    const unsigned long long m = a << (lz & 63);                 // leading bit at 63 (a != 0)
-    const unsigned long long keep = m >> 11;                     // 53 bits
-    const unsigned long long up = (m >> 10) & ((m & 0x3FFull) != 0 ? 1ull : (keep & 1ull));
-    const int E = 63 - lz + e;                                   // exponent of the leading bit
-    ok = (a == 0) || (E >= -1022 && E <= 1022);
-    const unsigned long long bits = ((unsigned long long)(E + 1022) << 52) + keep + up;
+    const int E = 63 - lz + e;  // exponent of the leading bit
+    unsigned long long bits;
+    if (E >= -1022) {
+        const unsigned long long m = a << (lz & 63);  // leading bit at 63
+        const unsigned long long keep = m >> 11;      // 53 bits
+        const unsigned long long up = (m >> 10) & ((m & 0x3FFull) != 0 ? 1ull : (keep & 1ull));
+        bits = E > 1023 ? 0x7FF0000000000000ull : ((unsigned long long)(E + 1022) << 52) + keep + up;
+    } else {
+        const int t = e + 1074;  // |v| * 2^t is the significand in units of 2^-1074
+        if (t >= 0) {
+            bits = a << t;
+        } else if (t <= -64) {
+            bits = 0;  // below half of the smallest subnormal (|v| < 2^63)
+        } else {
+            const int sh = -t;
+            const unsigned long long q = a >> sh, rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+            bits = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+        }
+    }
     return a == 0 ? 0.0 : __longlong_as_double((long long)(sign | bits));
-}
-__device__ __forceinline__ double scale2(double v, int sc) {
-    while (sc > 1023) {
-        v *= pow2(1023);
-        sc -= 1023;
-    }
-    while (sc < -1022) {
-        v *= pow2(-1022);
-        sc += 1022;
-    }
-    return v * pow2(sc);
 }
 
 // Epilogue of one tile task (product r, tile ti, tj), run by the NEPI epilogue
 // warps: folds the diagonal groups g = 2 .. s+1 from TMEM into int64 (each
-// thread owns one tile row and 64 columns) while the next group accumulates
-// in the other TMEM buffer, converts and scales once to FP64, then applies the
-// post-additions C_l (+)= W[l][r] P_r in ascending r, ordered by the per-tile
-// counters.  Groups are numbered globally per CTA (G0 = first group of this
+// thread owns one tile row and 64 columns) while later groups accumulate in
+// the other TMEM buffers, converts and scales once to FP64 and stores the
+// tile of P_r.  The post-additions C_l = sum_r W[l][r] P_r run afterwards in
+// ozaki_postadd_kernel: fused here they made the epilogue's per-task burst
+// longer than the MMA threads' lookahead.  Groups are numbered globally per CTA (G0 = first group of this
 // task); group G lives in accumulator G mod NBUF.  release(buf) hands an
 // accumulator back to the MMA thread.  `emit` is false for the padding tile of a CTA pair (no rows of C):
 // its groups are still drained.  Returns false when the CTA must stop.
 template <int EW0, class Release>
-__device__ __forceinline__ bool epilogue_tile(const OzParams &P, unsigned long long *accfull,
-                                              unsigned long long *epi_go, unsigned long long *epi_done,
-                                              volatile int *abort, uint32_t tmem, int r, int ti, int tj, bool emit,
-                                              int G0, uint32_t &dphase, Release release) {
+__device__ __forceinline__ bool epilogue_tile(const OzParams &P, unsigned long long *accfull, volatile int *abort,
+                                              uint32_t tmem, int r, int ti, int tj, bool emit, int G0,
+                                              Release release) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int e = warp - EW0;            // 0..7
     const int quad = warp & 3;           // TMEM lane quadrant of this warp
-    const int half = e >> 2;             // column half
     const int row = quad * 32 + lane;    // tile row owned by this thread
+    const int half = e >> 2;             // column half
     const int col0 = half * 64;
-    const bool leader = tid == EW0 * 32;
     const int s = P.s;
-    const int tiles = P.tiles_m * P.tiles_n;
-    const int t = ti * P.tiles_n + tj;
-
     long long acc[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) acc[j] = 0;
@@ -244,101 +242,30 @@ __device__ __forceinline__ bool epilogue_tile(const OzParams &P, unsigned long l
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = 4 * j4 + u;
-            const int sc = base_sc + max(ebs[u], 1);
-            bool ok;
-            double v = ldexp_i64_rn(acc[j], sc, ok);
-            if (!ok) v = scale2(__ll2double_rn(acc[j]), sc);
-            acc[j] = __double_as_longlong(v);
+            acc[j] = __double_as_longlong(ldexp_i64_rn(acc[j], base_sc + max(ebs[u], 1)));
         }
     }
 
-    // post-additions C_l (+)= W[l][r] P_r in ascending r (per-tile counters)
-    const int wc = P.w_ptr[r], nD = P.w_ptr[r + 1] - wc;
-    for (int d = 0; d < nD; ++d) {
-        const int4 en = P.w_ent[wc + d];
-        const long long br = en.x / P.P, bc = en.x % P.P;
-        double *dst = P.C + (br * P.m + (long long)ti * TM) * P.ldc + bc * P.m + (long long)tj * TN;
-        unsigned *chain = P.chain + (long long)en.x * tiles + t;
-        if (leader) {
-            if (en.z > 0 && !chain_wait(chain, (unsigned)en.z, P.error, P.timeout_ns)) *abort = 1;
-            mbar_arrive(epi_go);
+    // store this thread's 64 elements of the P_r tile (row-major, leading
+    // dimension m): whole 32-byte sectors when the row is aligned
+    if (row < rows) {
+        double *prow = P.pout + (long long)r * P.m * P.m + ((long long)ti * TM + row) * P.m + (long long)tj * TN + col0;
+        const bool vec = (((unsigned long long)prow) & 31ull) == 0;
+        const int nv = vec ? max(0, min(64, cols - col0)) / 4 : 0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            if (u >= nv) break;
+            asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(prow + 4 * u),
+                         "d"(__longlong_as_double(acc[4 * u])), "d"(__longlong_as_double(acc[4 * u + 1])),
+                         "d"(__longlong_as_double(acc[4 * u + 2])), "d"(__longlong_as_double(acc[4 * u + 3]))
+                         : "memory");
         }
-        if (!mbar_wait(epi_go, dphase, abort, P.error, P.timeout_ns) || *abort) return false;
-        const int cf = en.y;
-        const double cfd = (double)cf;
-        const int mode = en.z == 0 ? (cf == 1 ? 0 : (cf == -1 ? 1 : 2)) : (cf == 1 ? 3 : (cf == -1 ? 4 : 5));
-        if (row < rows) {
-            double *prow = dst + (long long)row * P.ldc + col0;
-            // whole 32-byte sectors per access when the row is aligned
-            const bool vec = (((unsigned long long)prow) & 31ull) == 0;
-            const int nv = vec ? max(0, min(64, cols - col0)) / 4 : 0;
 #pragma unroll
-            for (int u0 = 0; u0 < 16; u0 += 2) {
-                if (u0 >= nv) break;
-                const bool two = u0 + 1 < nv;
-                double o[2][4];
-                if (mode >= 3) {  // both 32-byte sectors in flight before the first add
-                    asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];"
-                                 : "=d"(o[0][0]), "=d"(o[0][1]), "=d"(o[0][2]), "=d"(o[0][3])
-                                 : "l"(prow + 4 * u0));
-                    if (two)
-                        asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];"
-                                     : "=d"(o[1][0]), "=d"(o[1][1]), "=d"(o[1][2]), "=d"(o[1][3])
-                                     : "l"(prow + 4 * u0 + 4));
-                }
-#pragma unroll
-                for (int w = 0; w < 2; ++w) {
-                    if (w == 1 && !two) break;
-                    const int u = u0 + w;
-                    double v[4];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) v[c] = __longlong_as_double(acc[4 * u + c]);
-                    if (mode == 3) {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) v[c] = o[w][c] + v[c];
-                    } else if (mode == 4) {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) v[c] = o[w][c] - v[c];
-                    } else if (mode == 5) {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) v[c] = fma(cfd, v[c], o[w][c]);
-                    } else if (mode == 1) {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) v[c] = neg(v[c]);
-                    } else if (mode == 2) {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) v[c] *= cfd;
-                    }
-                    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(prow + 4 * u), "d"(v[0]), "d"(v[1]),
-                                 "d"(v[2]), "d"(v[3])
-                                 : "memory");
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                if (j < 4 * nv) continue;
-                if (col0 + j >= cols) break;
-                const double v = __longlong_as_double(acc[j]);
-                double out;
-                switch (mode) {
-                    case 0: out = v; break;
-                    case 1: out = neg(v); break;
-                    case 2: out = cfd * v; break;
-                    case 3: out = __ldcg(prow + j) + v; break;
-                    case 4: out = __ldcg(prow + j) - v; break;
-                    default: out = fma(cfd, v, __ldcg(prow + j)); break;
-                }
-                prow[j] = out;
-            }
+        for (int j = 0; j < 64; ++j) {
+            if (j < 4 * nv) continue;
+            if (col0 + j >= cols) break;
+            prow[j] = __longlong_as_double(acc[j]);
         }
-        __threadfence();
-        mbar_arrive(epi_done);
-        if (leader) {
-            if (!mbar_wait(epi_done, dphase, abort, P.error, P.timeout_ns)) return false;
-            __threadfence();
-            atomicAdd(chain, 1u);
-        }
-        dphase ^= 1u;
     }
     return true;
 }
@@ -376,8 +303,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&B.tempty[i], 1 + NEPI);
         }
         mbar_init(&B.drain, 1);
-        mbar_init(&B.epi_go, 1);
-        mbar_init(&B.epi_done, NEPI * 32);
         B.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -533,7 +458,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------ epilogue
         int tslot = 0, tseq = 0;
         uint32_t tphase = 0;
-        uint32_t dphase = 0;  // parity of the post-addition hand-offs
         while (!*abort) {
             if (!mbar_wait(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
             const long long task = B.task[tslot];
@@ -547,8 +471,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int r = (int)(task / tiles);
             const int t = (int)(task - (long long)r * tiles);
             const int ti = t / P.tiles_n, tj = t - ti * P.tiles_n;
-            if (!epilogue_tile<EPI_WARP0>(P, B.accfull, &B.epi_go, &B.epi_done, abort, tmem, r, ti, tj, true,
-                                          tseq * s, dphase, [&](uint32_t b) { mbar_arrive(&B.accempty[b]); }))
+            if (!epilogue_tile<EPI_WARP0>(P, B.accfull, abort, tmem, r, ti, tj, true, tseq * s,
+                                          [&](uint32_t b) { mbar_arrive(&B.accempty[b]); }))
                 break;
             ++tseq;
         }
@@ -659,7 +583,6 @@ struct __align__(8) PairBars {
     unsigned long long accfull[NBUF], accempty[NBUF];
     unsigned long long tfull[TASK_RING], tempty[TASK_RING];
     unsigned long long drain[NRING];
-    unsigned long long epi_go, epi_done;
     long long task[TASK_RING];
     unsigned tmem_base;
     int abort;
@@ -723,8 +646,6 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
             mbar_init(&B.tempty[i], 5 + 2 * NEPI);
         }
         for (int q = 0; q < NRING; ++q) mbar_init(&B.drain[q], 1);
-        mbar_init(&B.epi_go, 1);
-        mbar_init(&B.epi_done, NEPI * 32);
         B.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -739,6 +660,14 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
     cluster_sync();  // the peer's barriers and TMEM exist before any remote use
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = B.tmem_base;
+
+    // Register split: the launch gives every thread 168 registers (384 x 168 =
+    // 64512).  The producer / MMA warpgroup (warps 0-3) hands back 112 each
+    // and the two epilogue warpgroups take them: 128 x 56 + 256 x 224 = 64512,
+    // so the increase can always be granted.  Every warp executes its step
+    // unconditionally here.
+    if (warp < P_EPI_WARP0) asm volatile("setmaxnreg.dec.sync.aligned.u32 56;" ::: "memory");
+    else asm volatile("setmaxnreg.inc.sync.aligned.u32 224;" ::: "memory");
 
     if (warp < NRING) {
         // ------------------------------------------------------------ producer of ring q (both CTAs)
@@ -889,10 +818,6 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
         // ------------------------------------------------------------ epilogue (both CTAs)
         int tslot = 0, tseq = 0;
         uint32_t tphase = 0;
-        uint32_t dphase = 0;
-        uint32_t accempty_lead[NBUF];
-#pragma unroll
-        for (int i = 0; i < NBUF; ++i) accempty_lead[i] = mapa(su32(&B.accempty[i]), 0);
         while (!*abort) {
             if (!mbar_wait_cl(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
             const long long task = B.task[tslot];
@@ -910,10 +835,10 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
             const int t2 = (int)(task - (long long)r * ptiles);
             const int tp = t2 / P.tiles_n, tj = t2 - tp * P.tiles_n;
             const int ti = 2 * tp + (int)rank;
-            if (!epilogue_tile<P_EPI_WARP0>(P, B.accfull, &B.epi_go, &B.epi_done, abort, tmem, r, ti, tj,
-                                            ti < P.tiles_m, tseq * s, dphase, [&](uint32_t b) {
+            if (!epilogue_tile<P_EPI_WARP0>(P, B.accfull, abort, tmem, r, ti, tj, ti < P.tiles_m, tseq * s,
+                                            [&](uint32_t b) {
                                                 if (lead) mbar_arrive(&B.accempty[b]);
-                                                else arrive_remote_relaxed(accempty_lead[b]);
+                                                else arrive_remote_relaxed(mapa(su32(&B.accempty[b]), 0));
                                             }))
                 break;
             ++tseq;
@@ -925,6 +850,87 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
     cluster_sync();  // neither CTA leaves while the pair's MMAs or copies may touch it
     if (warp == 2)
         asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// Post-additions of the emulated leaf: C_l = sum_r W[l][r] P_r for every C
+// block l, in ascending r, with the same operation sequence as ordered
+// read-modify-writes (first term w * P, then o + P, o - P or fma(w, P, o)),
+// so the result is the one the fused form gives.  blockIdx.y is the block,
+// CTAs stride over its rows, threads over column pairs.  Bound by the FP64
+// adds (nnz(W) - P^2 per element of a block) and the P_r reads.
+__global__ void __launch_bounds__(256) ozaki_postadd_kernel(const double *__restrict__ pout, long long m, int Pb,
+                                                            const int *__restrict__ wl_ptr,
+                                                            const int2 *__restrict__ wl_ent, double *__restrict__ C,
+                                                            long long ldc, unsigned *chain,
+                                                            const int *__restrict__ w_row_nnz, int tiles, int l0) {
+    const int l = l0 + (int)blockIdx.y;
+    const long long br = l / Pb, bc = l % Pb;
+    const int e0 = wl_ptr[l], e1 = wl_ptr[l + 1];
+    const long long mm = m * m;
+    if (chain != nullptr && blockIdx.x == 0)
+        for (int t = threadIdx.x; t < tiles; t += blockDim.x) chain[(long long)l * tiles + t] = (unsigned)w_row_nnz[l];
+    const bool pairs = (m & 1) == 0 && (ldc & 1) == 0;  // 16-byte aligned column pairs
+    constexpr int NB = 8;                                // terms whose loads are in flight together
+    for (long long i = blockIdx.x; i < m; i += gridDim.x) {
+        double *crow = C + (br * m + i) * ldc + bc * m;
+        const double *prow = pout + i * m;
+        if (pairs) {
+            for (long long j = 2 * (long long)threadIdx.x; j < m; j += 2 * blockDim.x) {
+                double2 c = make_double2(0.0, 0.0);
+                for (int eb = e0; eb < e1; eb += NB) {
+                    double2 v[NB];
+                    int cf[NB];
+#pragma unroll
+                    for (int k = 0; k < NB; ++k)
+                        if (eb + k < e1) {
+                            const int2 en = wl_ent[eb + k];  // {product r, coefficient}
+                            cf[k] = en.y;
+                            v[k] = __ldg(reinterpret_cast<const double2 *>(prow + (long long)en.x * mm + j));
+                        }
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        if (eb + k >= e1) break;
+                        if (eb + k == e0) {
+                            c = cf[k] == 1 ? v[k]
+                                : cf[k] == -1 ? make_double2(dev::neg(v[k].x), dev::neg(v[k].y))
+                                              : make_double2((double)cf[k] * v[k].x, (double)cf[k] * v[k].y);
+                        } else if (cf[k] == 1) {
+                            c.x = c.x + v[k].x; c.y = c.y + v[k].y;
+                        } else if (cf[k] == -1) {
+                            c.x = c.x - v[k].x; c.y = c.y - v[k].y;
+                        } else {
+                            c.x = fma((double)cf[k], v[k].x, c.x); c.y = fma((double)cf[k], v[k].y, c.y);
+                        }
+                    }
+                }
+                *reinterpret_cast<double2 *>(crow + j) = c;
+            }
+        } else {
+            for (long long j = threadIdx.x; j < m; j += blockDim.x) {
+                double c = 0.0;
+                for (int eb = e0; eb < e1; eb += NB) {
+                    double v[NB];
+                    int cf[NB];
+#pragma unroll
+                    for (int k = 0; k < NB; ++k)
+                        if (eb + k < e1) {
+                            const int2 en = wl_ent[eb + k];
+                            cf[k] = en.y;
+                            v[k] = __ldg(prow + (long long)en.x * mm + j);
+                        }
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        if (eb + k >= e1) break;
+                        if (eb + k == e0) c = cf[k] == 1 ? v[k] : (cf[k] == -1 ? dev::neg(v[k]) : (double)cf[k] * v[k]);
+                        else if (cf[k] == 1) c = c + v[k];
+                        else if (cf[k] == -1) c = c - v[k];
+                        else c = fma((double)cf[k], v[k], c);
+                    }
+                }
+                crow[j] = c;
+            }
+        }
+    }
 }
 
 constexpr size_t kSmemBytes = 1024 + STAGES * STAGE_BYTES + sizeof(Bars);
@@ -998,6 +1004,26 @@ int ozaki_tc_max_pairs() {
     }
     cached = n;
     return n;
+}
+
+cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
+                                 double *C, long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
+                                 cudaStream_t s) {
+    if (m <= 0 || P <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long bx = ((long long)sms * 16 + P * P - 1) / ((long long)P * P);
+    if (bx > m) bx = m;
+    if (bx < 1) bx = 1;
+    for (int l0 = 0; l0 < P * P; l0 += 65535) {
+        const int cnt = P * P - l0 < 65535 ? P * P - l0 : 65535;
+        dim3 grid((unsigned)bx, (unsigned)cnt);
+        ozaki_postadd_kernel<<<grid, 256, 0, s>>>(pout, m, P, wl_ptr, wl_ent, C, ldc, chain, w_row_nnz, tiles, l0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace fmm
