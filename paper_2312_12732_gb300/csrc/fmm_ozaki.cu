@@ -94,15 +94,15 @@ __device__ __forceinline__ unsigned char e4m3(int v) {
 // bits [8q, 8q + 8) of packed[t].
 __device__ __forceinline__ long long digit_offset(int s) { return ((1LL << (OB * s)) - 1) / 31 * 16; }
 
-__device__ __forceinline__ void pack_digits(long long Z, int s, const unsigned char *lut,
-                                            unsigned (&packed)[kOzMaxSlices], int q) {
+template <int S>
+__device__ __forceinline__ void pack_digits(long long Z, const unsigned char *lut, unsigned (&packed)[kOzMaxSlices],
+                                            int q) {
+    // S is a compile-time constant, so every field is a constant shift of Z
 #pragma unroll
-    for (int t = 0; t < kOzMaxSlices; ++t) {
-        if (t < s) {
-            const int sh = OB * (s - 1 - t);
-            const int z = t == 0 ? (int)(Z >> sh) : (int)((Z >> sh) & 31);
-            packed[t] |= (unsigned)lut[z] << (8 * q);
-        }
+    for (int t = 0; t < S; ++t) {
+        const int sh = OB * (S - 1 - t);
+        const int z = t == 0 ? (int)(Z >> sh) : (int)((Z >> sh) & 31);
+        packed[t] |= (unsigned)lut[z] << (8 * q);
     }
 }
 
@@ -122,9 +122,11 @@ __device__ __forceinline__ void fill_lut(unsigned char *lut) {
 // Left operand: one warp per row r of X (rows x cols, ld); lane j handles
 // elements 4(j + 32 i) .. +3, so each slice row is written with coalesced
 // 4-byte stores.
+template <int S>
 __global__ void slice_rows_kernel(const double *__restrict__ X, long long ld, long long mat_stride, int rows,
-                                  int cols, int *__restrict__ mx, int pitch, int s, int Mp, int Kp,
+                                  int cols, int *__restrict__ mx, int pitch, int Mp, int Kp,
                                   unsigned char *__restrict__ out) {
+    constexpr int s = S;
     __shared__ unsigned char lut[33];
     fill_lut(lut);
     __syncthreads();
@@ -152,7 +154,7 @@ __global__ void slice_rows_kernel(const double *__restrict__ X, long long ld, lo
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = c4 * 4 + q;
-                if (c < cols) pack_digits(to_fixed(__ldg(row + c), E, bs) + O, s, lut, packed, q);
+                if (c < cols) pack_digits<S>(to_fixed(__ldg(row + c), E, bs) + O, lut, packed, q);
             }
 #pragma unroll
             for (int t = 0; t < kOzMaxSlices; ++t)
@@ -165,9 +167,11 @@ __global__ void slice_rows_kernel(const double *__restrict__ X, long long ld, lo
 // (rows = K): the column maxima first, then 32 x 32 tiles whose digits are
 // transposed through shared memory so that slice row c (K contiguous) is
 // written with coalesced stores.
+template <int S>
 __global__ void slice_cols_kernel(const double *__restrict__ X, long long ld, long long mat_stride, int rows,
-                                  int cols, int *__restrict__ mx, int pitch, int s, int Mp, int Kp,
+                                  int cols, int *__restrict__ mx, int pitch, int Mp, int Kp,
                                   unsigned char *__restrict__ out) {
+    constexpr int s = S;
     __shared__ unsigned char tile[kOzMaxSlices][32][36];
     __shared__ int colmax[8][32];
     __shared__ unsigned char lut[33];
@@ -203,7 +207,7 @@ __global__ void slice_cols_kernel(const double *__restrict__ X, long long ld, lo
             unsigned packed[kOzMaxSlices];
 #pragma unroll
             for (int t = 0; t < kOzMaxSlices; ++t) packed[t] = 0u;
-            if (c < cols && k < rows) pack_digits(to_fixed(__ldg(Xm + (long long)k * ld + c), E, bs) + O, s, lut, packed, 0);
+            if (c < cols && k < rows) pack_digits<S>(to_fixed(__ldg(Xm + (long long)k * ld + c), E, bs) + O, lut, packed, 0);
 #pragma unroll
             for (int t = 0; t < kOzMaxSlices; ++t)
                 if (t < s) tile[t][tx][kk] = (unsigned char)packed[t];
@@ -499,6 +503,29 @@ __global__ void __launch_bounds__(NT, 1) ozaki_gemm_kernel(const __grid_constant
     }
 }
 
+// Instantiates the slicing kernels for the slice count s (1 .. kOzMaxSlices).
+template <bool ROWS, int S>
+void launch_slices_one(dim3 grid, cudaStream_t st, const double *X, long long ld, long long mat_stride, int rows,
+                       int cols, int *mx, int pitch, int Mp, int Kp, unsigned char *out) {
+    if (ROWS)
+        slice_rows_kernel<S><<<grid, 256, 0, st>>>(X, ld, mat_stride, rows, cols, mx, pitch, Mp, Kp, out);
+    else
+        slice_cols_kernel<S><<<grid, 256, 0, st>>>(X, ld, mat_stride, rows, cols, mx, pitch, Mp, Kp, out);
+}
+template <bool ROWS>
+void launch_slices_s(int s, dim3 grid, cudaStream_t st, const double *X, long long ld, long long mat_stride, int rows,
+                     int cols, int *mx, int pitch, int Mp, int Kp, unsigned char *out) {
+    switch (s) {
+#define FMM_SLICE_CASE(S_)                                                                              \
+    case S_: launch_slices_one<ROWS, S_>(grid, st, X, ld, mat_stride, rows, cols, mx, pitch, Mp, Kp, out); break;
+        FMM_SLICE_CASE(1) FMM_SLICE_CASE(2) FMM_SLICE_CASE(3) FMM_SLICE_CASE(4) FMM_SLICE_CASE(5) FMM_SLICE_CASE(6)
+        FMM_SLICE_CASE(7) FMM_SLICE_CASE(8) FMM_SLICE_CASE(9) FMM_SLICE_CASE(10) FMM_SLICE_CASE(11)
+        FMM_SLICE_CASE(12)
+#undef FMM_SLICE_CASE
+        default: break;
+    }
+}
+
 }  // namespace
 
 size_t ozaki_smem_bytes() { return sizeof(Smem); }
@@ -519,10 +546,10 @@ cudaError_t launch_ozaki_slices(const double *X, long long ld, long long mat_str
             const int cap = (sms * 16 + cnt - 1) / cnt;
             if (bx > cap) bx = cap;
             if (bx < 1) bx = 1;
-            slice_rows_kernel<<<dim3(bx, cnt), 256, 0, st>>>(Xm, ld, mat_stride, rows, cols, mxm, pitch, s, Mp, Kp, om);
+            launch_slices_s<true>(s, dim3(bx, cnt), st, Xm, ld, mat_stride, rows, cols, mxm, pitch, Mp, Kp, om);
         } else {
-            slice_cols_kernel<<<dim3((cols + 31) / 32, cnt), 256, 0, st>>>(Xm, ld, mat_stride, rows, cols, mxm,
-                                                                           pitch, s, Mp, Kp, om);
+            launch_slices_s<false>(s, dim3((cols + 31) / 32, cnt), st, Xm, ld, mat_stride, rows, cols, mxm, pitch, Mp,
+                                   Kp, om);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
