@@ -105,3 +105,23 @@ def test_ozaki_plan_info(fmm):
     assert info["flops_lowp"] == 2.0 * 49 * 45 * 256 ** 3
     with pytest.raises(fmm.FmmError):
         fmm.fmm_plan_create(64, fmm.fmm_algo_builtin("strassen"), 1, dtype="f64_ozaki", ozaki_slices=13)
+
+
+@pytest.mark.parametrize("engine", ["pair", "tc1", "mma_sync"])
+@pytest.mark.parametrize("name,depth,n", [("strassen", 1, 7), ("strassen", 0, 300), ("strassen", 2, 1000),
+                                          ("laderman", 1, 384)])
+def test_every_slice_gemm_engine(fmm, oracle_mod, monkeypatch, engine, name, depth, n):
+    """The CTA-pair kernel (default), the one-CTA tcgen05 kernel and the mma.sync kernel give the same
+    bit-exact integer results; the engine is read when the plan is created.  Sizes cover an odd number
+    of tile rows (a padding tile in the last pair), K not a multiple of 256 and a single tile."""
+    if engine == "pair":
+        monkeypatch.delenv("FMM_OZAKI_ENGINE", raising=False)
+    else:
+        monkeypatch.setenv("FMM_OZAKI_ENGINE", engine)
+    algo = fmm.fmm_algo_builtin(name)
+    plan = fmm.fmm_plan_create(n, algo, depth, dtype="f64_ozaki")
+    A, B = inputs.operands(n, "integer", seed=3 * n + depth)
+    assert np.array_equal(run(fmm, plan, A, B), oracle_mod.classic(A, B))
+    A, B = inputs.operands(n, "uniform", seed=n)
+    rows, cols, ref = ref_entries(oracle_mod, A, B)
+    assert nerr(run(fmm, plan, A, B)[rows, cols], ref, A, B) <= 1e-13
