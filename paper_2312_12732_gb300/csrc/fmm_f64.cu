@@ -427,32 +427,63 @@ __global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __gri
             const double cfd = (double)cf;  // used only when |cf| != 1
             // mode: 0 store v, 1 store -v, 2 store cf*v, 3 add, 4 subtract, 5 fma
             const int mode = first ? (cf == 1 ? 0 : (cf == -1 ? 1 : 2)) : (cf == 1 ? 3 : (cf == -1 ? 4 : 5));
+            // Column pairs (2 t4, 2 t4 + 1) are 16 bytes apart-aligned when the tile
+            // start and ldc are even.  Read-modify-writes load a whole subtile row
+            // (16 values) before the first store, so the loads overlap instead of
+            // waiting for each other behind possibly aliasing stores.
+            const bool pair_ok = ((((unsigned long long)dst.ptr) & 15ull) == 0) && ((ldc & 1) == 0);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i) {
+                double o[4][2][2];
+                if (mode >= 3) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int row = wm * 64 + i * 16 + g + 8 * h;
+                            const int col = wn * 32 + j * 8 + 2 * t4;
+                            const double *p = dst.ptr + row * ldc + col;
+                            o[j][h][0] = o[j][h][1] = 0.0;
+                            if (row >= rows || col >= cols) continue;
+                            if (pair_ok && col + 1 < cols) {
+                                const double2 q = __ldcg(reinterpret_cast<const double2 *>(p));
+                                o[j][h][0] = q.x;
+                                o[j][h][1] = q.y;
+                            } else {
+                                o[j][h][0] = __ldcg(p);
+                                if (col + 1 < cols) o[j][h][1] = __ldcg(p + 1);
+                            }
+                        }
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int row = wm * 64 + i * 16 + g + 8 * h;
-                        if (row >= rows) continue;
+                        const int col = wn * 32 + j * 8 + 2 * t4;
+                        if (row >= rows || col >= cols) continue;
+                        double *p = dst.ptr + row * ldc + col;
+                        double out[2];
 #pragma unroll
                         for (int c2 = 0; c2 < 2; ++c2) {
-                            const int col = wn * 32 + j * 8 + 2 * t4 + c2;
-                            if (col >= cols) continue;
-                            double *p = dst.ptr + row * ldc + col;
                             const double v = acc[i][j][2 * h + c2];
-                            double out;
                             switch (mode) {
-                                case 0: out = v; break;
-                                case 1: out = neg(v); break;
-                                case 2: out = cfd * v; break;
-                                case 3: out = __ldcg(p) + v; break;
-                                case 4: out = __ldcg(p) - v; break;
-                                default: out = fma(cfd, v, __ldcg(p)); break;
+                                case 0: out[c2] = v; break;
+                                case 1: out[c2] = neg(v); break;
+                                case 2: out[c2] = cfd * v; break;
+                                case 3: out[c2] = o[j][h][c2] + v; break;
+                                case 4: out[c2] = o[j][h][c2] - v; break;
+                                default: out[c2] = fma(cfd, v, o[j][h][c2]); break;
                             }
-                            *p = out;
+                        }
+                        if (pair_ok && col + 1 < cols) {
+                            *reinterpret_cast<double2 *>(p) = make_double2(out[0], out[1]);
+                        } else {
+                            p[0] = out[0];
+                            if (col + 1 < cols) p[1] = out[1];
                         }
                     }
+            }
             __syncthreads();
             if (tid == 0) {
                 if (dst.chain != nullptr) {
