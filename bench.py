@@ -354,7 +354,8 @@ def run_sweep(a):
     for algo in ("strassen", "winograd"):
         for d in (1, 2, 3):
             configs += [(algo, d, "fused", 0), (algo, d, "auto", 0)]
-    configs += [("strassen^2", 1, "fused", 0), ("strassen^2", 1, "auto", 0), ("strassen^2", 2, "auto", 0)]
+    configs += [("strassen^2", 1, "fused", 0), ("strassen^2", 1, "auto", 0), ("strassen^2", 2, "auto", 0),
+                ("strassen", 4, "auto", 0)]
     configs = [c + ("f64",) for c in configs]
     configs += [("strassen", d, "auto", 0, "f64_ozaki") for d in (0, 1, 2, 3)]
     n = a.n

@@ -300,9 +300,14 @@ struct fmm_plan {
     int *d_error = nullptr;
     double *d_SA = nullptr, *d_SB = nullptr;  // materialized sources (nullptr when fused)
     double *d_TA = nullptr, *d_TB = nullptr;  // intermediate level (materialized depth >= 2)
-    const int *d_mat_u_ptr = nullptr, *d_mat_v_ptr = nullptr;
-    const int4 *d_mat_u_ent = nullptr, *d_mat_v_ent = nullptr;
-    int64_t mat_outputs = 0;
+    // materialization steps, applied in order over all materialized levels:
+    // one per level, or the Kronecker factors of a composed level (fewer adds)
+    struct MatStep {
+        int p = 0, R = 0;
+        const int *uptr = nullptr, *vptr = nullptr;
+        const int4 *uent = nullptr, *vent = nullptr;
+    };
+    std::vector<MatStep> mat_steps;
     // emulated leaf (FMM_F64_OZAKI)
     int oz_s = 0, oz_L = 0;
     int64_t oz_Mp = 0;
@@ -387,6 +392,82 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // the levels one at a time shares each level's sums across all products below
 // it.  So every level whose operands combine more than one block on average
 // is materialized; algorithms whose columns are single blocks stay fused.
+// One recursion level's U and V, possibly a Kronecker factor of them.
+struct LevelFactor {
+    int p = 0, R = 0;
+    std::vector<int32_t> U, V;
+};
+
+// X (p^2 x R, row-major blocks, indexed as fmm_algo_compose builds products:
+// block (i1 p2 + i2, j1 p2 + j2), product r1 R2 + r2) as X1 (p1^2 x R1)
+// Kronecker X2 (p2^2 x R2) with integer entries.  The factors are read off a
+// +-1 entry and the product is then checked entry by entry.
+bool kron_split(const std::vector<int32_t> &X, int p, int R, int p1, int R1, std::vector<int32_t> &X1,
+                std::vector<int32_t> &X2) {
+    const int p2 = p / p1, R2 = R / R1;
+    auto at = [&](int i1, int j1, int i2, int j2, int r1, int r2) {
+        return X[((size_t)(i1 * p2 + i2) * p + (j1 * p2 + j2)) * R + (size_t)r1 * R2 + r2];
+    };
+    int a0 = -1, b0 = -1, c0 = -1, d0 = -1, v0 = 0;
+    for (int a = 0; a < p1 * p1 && v0 == 0; ++a)
+        for (int b = 0; b < p2 * p2 && v0 == 0; ++b)
+            for (int c = 0; c < R1 && v0 == 0; ++c)
+                for (int d = 0; d < R2 && v0 == 0; ++d) {
+                    const int v = at(a / p1, a % p1, b / p2, b % p2, c, d);
+                    if (v == 1 || v == -1) { a0 = a; b0 = b; c0 = c; d0 = d; v0 = v; }
+                }
+    if (v0 == 0) return false;
+    X1.assign((size_t)p1 * p1 * R1, 0);
+    X2.assign((size_t)p2 * p2 * R2, 0);
+    for (int a = 0; a < p1 * p1; ++a)
+        for (int c = 0; c < R1; ++c) X1[(size_t)a * R1 + c] = at(a / p1, a % p1, b0 / p2, b0 % p2, c, d0) * v0;
+    for (int b = 0; b < p2 * p2; ++b)
+        for (int d = 0; d < R2; ++d) X2[(size_t)b * R2 + d] = at(a0 / p1, a0 % p1, b / p2, b % p2, c0, d);
+    for (int a = 0; a < p1 * p1; ++a)
+        for (int b = 0; b < p2 * p2; ++b)
+            for (int c = 0; c < R1; ++c)
+                for (int d = 0; d < R2; ++d)
+                    if ((int64_t)X1[(size_t)a * R1 + c] * X2[(size_t)b * R2 + d] !=
+                        (int64_t)at(a / p1, a % p1, b / p2, b % p2, c, d))
+                        return false;
+    return true;
+}
+
+// FP64 adds of forming one level by the steps `seq`, per element of its input.
+double steps_cost(const std::vector<LevelFactor> &seq) {
+    double cost = 0, cnt = 1, area = 1;
+    for (const LevelFactor &f : seq) {
+        long long nu = 0, nv = 0;
+        for (int32_t x : f.U) nu += x != 0;
+        for (int32_t x : f.V) nv += x != 0;
+        area /= (double)f.p * f.p;
+        cost += cnt * (double)(nu - f.R + nv - f.R) * area;
+        cnt *= f.R;
+    }
+    return cost;
+}
+
+// Cheapest sequence of materialization steps for one level: the level itself,
+// or (recursively) Kronecker factors of its U and V with equal shapes.
+std::vector<LevelFactor> decompose_level(const LevelFactor &f) {
+    std::vector<LevelFactor> best{f};
+    double best_cost = steps_cost(best);
+    for (int p1 = 2; p1 < f.p; ++p1) {
+        if (f.p % p1) continue;
+        for (int R1 = 2; R1 < f.R; ++R1) {
+            if (f.R % R1) continue;
+            LevelFactor a, b;
+            a.p = p1; a.R = R1; b.p = f.p / p1; b.R = f.R / R1;
+            if (!kron_split(f.U, f.p, f.R, p1, R1, a.U, b.U) || !kron_split(f.V, f.p, f.R, p1, R1, a.V, b.V)) continue;
+            std::vector<LevelFactor> seq = decompose_level(a);
+            for (const LevelFactor &x : decompose_level(b)) seq.push_back(x);
+            const double c = steps_cost(seq);
+            if (c < best_cost) { best_cost = c; best = seq; }
+        }
+    }
+    return best;
+}
+
 int default_materialized_levels(int p, int R, const fmm_algo_t *a, int depth) {
     if (depth < 1) return 0;
     long long nnz_u = 0, nnz_v = 0;
@@ -471,10 +552,16 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     auto ucols = flatten(p, R, algo->U, depth - mat);
     auto vcols = flatten(p, R, algo->V, depth - mat);
     auto wcols = flatten(p, R, algo->W, depth);
-    std::vector<std::vector<Entry>> mu, mv;
-    if (mat > 0) {  // one level; applied `mat` times, level by level
-        mu = flatten(p, R, algo->U, 1);
-        mv = flatten(p, R, algo->V, 1);
+    // Materialization: each level formed by its cheapest sequence of Kronecker
+    // factors (the level itself when it has none); product and block order
+    // match the flattened algorithm because composition nests the same way.
+    std::vector<LevelFactor> steps;
+    if (mat > 0) {
+        LevelFactor lvl;
+        lvl.p = p; lvl.R = R;
+        lvl.U.assign(algo->U, algo->U + (size_t)p * p * R);
+        lvl.V.assign(algo->V, algo->V + (size_t)p * p * R);
+        steps = decompose_level(lvl);
     }
     size_t maxc = 0;
     for (auto &c : ucols) maxc = std::max(maxc, c.size());
@@ -489,17 +576,22 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
             for (const Entry &e : cols[c]) ent.push_back(make_int2(e.blk, e.coef));
         }
     };
-    std::vector<int> u_ptr, v_ptr, w_ptr, mu_ptr, mv_ptr, w_row((size_t)P * P, 0);
-    std::vector<int2> u_ent, v_ent, mu_ent2, mv_ent2;
-    std::vector<int4> mu_ent, mv_ent;
+    std::vector<int> u_ptr, v_ptr, w_ptr, w_row((size_t)P * P, 0);
+    std::vector<int2> u_ent, v_ent;
     std::vector<int4> w_ent;
     csc2(ucols, u_ptr, u_ent);
     csc2(vcols, v_ptr, v_ent);
-    if (mat > 0) {
-        csc2(mu, mu_ptr, mu_ent2);
-        csc2(mv, mv_ptr, mv_ent2);
-        for (const int2 &e : mu_ent2) mu_ent.push_back(make_int4(e.x / p, e.x % p, e.y, 0));
-        for (const int2 &e : mv_ent2) mv_ent.push_back(make_int4(e.x / p, e.x % p, e.y, 0));
+    // per materialization step: CSC over its products of {block row, block col, coef}
+    std::vector<std::vector<int>> st_uptr(steps.size()), st_vptr(steps.size());
+    std::vector<std::vector<int4>> st_uent(steps.size()), st_vent(steps.size());
+    for (size_t k = 0; k < steps.size(); ++k) {
+        const LevelFactor &f = steps[k];
+        std::vector<int2> tmp;
+        csc2(flatten(f.p, f.R, f.U.data(), 1), st_uptr[k], tmp);
+        for (const int2 &e : tmp) st_uent[k].push_back(make_int4(e.x / f.p, e.x % f.p, e.y, 0));
+        tmp.clear();
+        csc2(flatten(f.p, f.R, f.V.data(), 1), st_vptr[k], tmp);
+        for (const int2 &e : tmp) st_vent[k].push_back(make_int4(e.x / f.p, e.x % f.p, e.y, 0));
     }
     w_ptr.assign(wcols.size() + 1, 0);
     for (size_t c = 0; c < wcols.size(); ++c) {
@@ -551,10 +643,8 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         adds += (double)pl->nsub * ((double)(nnz_u - pl->R_src) * md * md * fused_factor_a +
                                     (double)(nnz_v - pl->R_src) * md * md * fused_factor_b);
         for (int lev = 1; lev <= mat; ++lev) {
-            const double bl = (double)(pl->n_core / ipow(p, lev));
-            const double cnt = (double)ipow(R, lev - 1);
-            adds += cnt * (double)((long long)mu_ent.size() - R) * bl * bl;
-            adds += cnt * (double)((long long)mv_ent.size() - R) * bl * bl;
+            const double bl = (double)(pl->n_core / ipow(p, lev - 1));  // input side of the level
+            adds += (double)ipow(R, lev - 1) * steps_cost(steps) * bl * bl;
         }
         adds += (double)((long long)w_ent.size() - (long long)P * P) * md * md;
     }
@@ -576,12 +666,12 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     const size_t o_wrow = reserve(w_row.size() * sizeof(int));
     const size_t o_wlptr = reserve(wl_ptr.size() * sizeof(int));
     const size_t o_wlent = reserve(std::max<size_t>(1, wl_ent.size()) * sizeof(int2));
-    size_t o_muptr = 0, o_muent = 0, o_mvptr = 0, o_mvent = 0;
-    if (mat > 0) {
-        o_muptr = reserve(mu_ptr.size() * sizeof(int));
-        o_muent = reserve(mu_ent.size() * sizeof(int4));
-        o_mvptr = reserve(mv_ptr.size() * sizeof(int));
-        o_mvent = reserve(mv_ent.size() * sizeof(int4));
+    std::vector<size_t> o_st(4 * steps.size());
+    for (size_t k = 0; k < steps.size(); ++k) {
+        o_st[4 * k] = reserve(st_uptr[k].size() * sizeof(int));
+        o_st[4 * k + 1] = reserve(std::max<size_t>(1, st_uent[k].size()) * sizeof(int4));
+        o_st[4 * k + 2] = reserve(st_vptr[k].size() * sizeof(int));
+        o_st[4 * k + 3] = reserve(std::max<size_t>(1, st_vent[k].size()) * sizeof(int4));
     }
     pl->tables_bytes = off;
     if (cudaMalloc(&pl->d_tables, pl->tables_bytes) != cudaSuccess) {
@@ -610,17 +700,23 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     put(o_wrow, w_row.data(), w_row.size() * sizeof(int));
     put(o_wlptr, wl_ptr.data(), wl_ptr.size() * sizeof(int));
     put(o_wlent, wl_ent.data(), wl_ent.size() * sizeof(int2));
-    if (mat > 0) {
-        put(o_muptr, mu_ptr.data(), mu_ptr.size() * sizeof(int));
-        put(o_muent, mu_ent.data(), mu_ent.size() * sizeof(int4));
-        put(o_mvptr, mv_ptr.data(), mv_ptr.size() * sizeof(int));
-        put(o_mvent, mv_ent.data(), mv_ent.size() * sizeof(int4));
-        pl->d_mat_u_ptr = (const int *)(base + o_muptr);
-        pl->d_mat_u_ent = (const int4 *)(base + o_muent);
-        pl->d_mat_v_ptr = (const int *)(base + o_mvptr);
-        pl->d_mat_v_ent = (const int4 *)(base + o_mvent);
-        pl->mat_outputs = (int64_t)mu.size();
+    for (size_t k = 0; k < steps.size(); ++k) {
+        put(o_st[4 * k], st_uptr[k].data(), st_uptr[k].size() * sizeof(int));
+        put(o_st[4 * k + 1], st_uent[k].data(), st_uent[k].size() * sizeof(int4));
+        put(o_st[4 * k + 2], st_vptr[k].data(), st_vptr[k].size() * sizeof(int));
+        put(o_st[4 * k + 3], st_vent[k].data(), st_vent[k].size() * sizeof(int4));
     }
+    for (int lev = 0; lev < mat; ++lev)
+        for (size_t k = 0; k < steps.size(); ++k) {
+            fmm_plan::MatStep ms;
+            ms.p = steps[k].p;
+            ms.R = steps[k].R;
+            ms.uptr = (const int *)(base + o_st[4 * k]);
+            ms.uent = (const int4 *)(base + o_st[4 * k + 1]);
+            ms.vptr = (const int *)(base + o_st[4 * k + 2]);
+            ms.vent = (const int4 *)(base + o_st[4 * k + 3]);
+            pl->mat_steps.push_back(ms);
+        }
     put(o_geom, &g, sizeof(F64Geom));
     {
         F64Geom gp = g;  // the peel tasks alone, run after the emulated leaf products
@@ -654,14 +750,25 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     size_t ws = pl->counters_bytes;
     size_t o_sa = 0, o_sb = 0, o_ta = 0, o_tb = 0;
     if (mat > 0) {
-        const size_t bytes = (size_t)pl->nsub * (size_t)pl->b_src * (size_t)pl->b_src * sizeof(double);
-        o_sa = ws; ws = align_up(ws + bytes, 256);
-        o_sb = ws; ws = align_up(ws + bytes, 256);
-        if (mat >= 2) {  // level mat-1 output; levels alternate between it and the final buffer
-            const size_t b1 = (size_t)(pl->n_core / ipow(p, mat - 1));
-            const size_t tbytes = (size_t)ipow(R, mat - 1) * b1 * b1 * sizeof(double);
-            o_ta = ws; ws = align_up(ws + tbytes, 256);
-            o_tb = ws; ws = align_up(ws + tbytes, 256);
+        // steps alternate between the final buffer and one temporary, ending in the final buffer
+        size_t fin_bytes = 0, tmp_bytes = 0;
+        {
+            const size_t K = pl->mat_steps.size();
+            double cnt = 1, side = (double)pl->n_core;
+            for (size_t k = 1; k <= K; ++k) {
+                const fmm_plan::MatStep &st = pl->mat_steps[k - 1];
+                cnt *= st.R;
+                side /= st.p;
+                const size_t bytes = (size_t)(cnt * side * side) * sizeof(double);
+                if ((K - k) % 2 == 0) fin_bytes = std::max(fin_bytes, bytes);
+                else tmp_bytes = std::max(tmp_bytes, bytes);
+            }
+        }
+        o_sa = ws; ws = align_up(ws + fin_bytes, 256);
+        o_sb = ws; ws = align_up(ws + fin_bytes, 256);
+        if (tmp_bytes > 0) {
+            o_ta = ws; ws = align_up(ws + tmp_bytes, 256);
+            o_tb = ws; ws = align_up(ws + tmp_bytes, 256);
         }
     }
     size_t o_sla = 0, o_slb = 0, o_pout = 0, slice_bytes = 0;
@@ -686,7 +793,7 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     if (mat > 0) {
         pl->d_SA = (double *)(wsb + o_sa);
         pl->d_SB = (double *)(wsb + o_sb);
-        if (mat >= 2) {
+        if (o_ta) {
             pl->d_TA = (double *)(wsb + o_ta);
             pl->d_TB = (double *)(wsb + o_tb);
         }
@@ -767,25 +874,26 @@ fmm_status_t prepare(const fmm_plan *pl, const double *A, const double *B, cudaS
         e = cudaMemsetAsync(pl->d_chain, 0xFF, sizeof(unsigned), st);
         if (e != cudaSuccess) return FMM_ERR_CUDA;
     }
-    // Level lev reads level lev-1 (level 0 = the n_core x n_core corner of the
-    // operand, ld n) and writes R^lev matrices of size n_core / p^lev; the last
-    // level lands in d_SA / d_SB, earlier ones alternate with d_TA / d_TB.
+    // Step k reads step k-1's output (step 0 = the n_core x n_core corner of
+    // the operand, ld n) and writes R_k times as many matrices of side 1/p_k;
+    // the last step lands in d_SA / d_SB, earlier ones alternate with d_TA / d_TB.
+    const int K = (int)pl->mat_steps.size();
     for (int side = 0; side < 2; ++side) {
         const double *src = side == 0 ? A : B;
         double *fin = side == 0 ? pl->d_SA : pl->d_SB;
         double *tmp = side == 0 ? pl->d_TA : pl->d_TB;
-        const int *ptr = side == 0 ? pl->d_mat_u_ptr : pl->d_mat_v_ptr;
-        const int4 *ent = side == 0 ? pl->d_mat_u_ent : pl->d_mat_v_ent;
-        long long ld_in = pl->n, b_in = pl->n_core;
-        for (int lev = 1; lev <= pl->mat_levels; ++lev) {
-            double *dst = ((pl->mat_levels - lev) % 2 == 0) ? fin : tmp;
-            const long long b_out = b_in / pl->p;
-            e = fmm::launch_materialize_level(src, ld_in, lev == 1 ? 0 : b_in * b_in, (int)ipow(pl->R, lev - 1), b_out,
-                                              pl->p, pl->R, ptr, ent, dst, st);
+        long long ld_in = pl->n, b_in = pl->n_core, n_in = 1;
+        for (int k = 1; k <= K; ++k) {
+            const fmm_plan::MatStep &ms = pl->mat_steps[k - 1];
+            double *dst = ((K - k) % 2 == 0) ? fin : tmp;
+            const long long b_out = b_in / ms.p;
+            e = fmm::launch_materialize_level(src, ld_in, k == 1 ? 0 : b_in * b_in, (int)n_in, b_out, ms.p, ms.R,
+                                              side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent, dst, st);
             if (e != cudaSuccess) return FMM_ERR_CUDA;
             src = dst;
             ld_in = b_out;
             b_in = b_out;
+            n_in *= ms.R;
         }
     }
     return FMM_OK;

@@ -200,3 +200,32 @@ def test_batched_grouped_launch(fmm, oracle_mod):
             assert np.array_equal(C, oracle_mod.classic(A, B))
         else:
             assert nerr(C, oracle_ref(oracle_mod, A, B, algo, depth), A, B) <= tol(depth)
+
+
+def test_composed_levels_materialize_by_factors(fmm):
+    """<4,4,4;49> = Strassen x Strassen: the planner forms each 4x4 level in two Strassen steps, so
+    depth 2 of the composed algorithm and depth 4 of Strassen execute the same adds and, with the same
+    operation order in every step, give bit-identical results on real inputs."""
+    n = 1024
+    comp = fmm.algorithm("strassen", 2)
+    p_comp = fmm.fmm_plan_create(n, comp, 2)
+    p_str = fmm.fmm_plan_create(n, fmm.fmm_algo_builtin("strassen"), 4)
+    i_comp, i_str = p_comp.info(), p_str.info()
+    assert i_comp["flops_executed"] == i_str["flops_executed"]
+    assert i_comp["R_total"] == i_str["R_total"] == 2401
+    A, B = inputs.operands(n, "uniform", seed=31)
+    assert np.array_equal(run(fmm, p_comp, A, B), run(fmm, p_str, A, B))
+
+
+@pytest.mark.parametrize("first,second,depth,n", [("laderman", "strassen", 1, 576), ("strassen", "laderman", 1, 576),
+                                                  ("strassen", "winograd", 2, 576)])
+def test_mixed_compositions(fmm, oracle_mod, first, second, depth, n):
+    """Kronecker products of different algorithms (p = 6, R = 161 and p = 4, R = 49 mixed): the
+    planner splits their levels into unequal factors; results match the oracle's recursion on the
+    composed tables."""
+    algo = fmm.fmm_algo_compose(fmm.fmm_algo_builtin(first), fmm.fmm_algo_builtin(second))
+    plan = fmm.fmm_plan_create(n, algo, depth)
+    A, B = inputs.operands(n, "integer", seed=n + depth)
+    assert np.array_equal(run(fmm, plan, A, B), oracle_mod.classic(A, B))
+    A, B = inputs.operands(n, "uniform", seed=depth + 5)
+    assert nerr(run(fmm, plan, A, B), oracle_ref(oracle_mod, A, B, algo, depth), A, B) <= tol(depth)
