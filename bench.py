@@ -293,10 +293,10 @@ def make_algo(fmm, name):
     return fmm.fmm_algo_builtin(name)
 
 
-def ozaki_launches(levels: int, peeled: bool) -> int:
-    """Kernels of one emulated-leaf call: a materialization per level and operand, row and column
+def ozaki_launches(passes: int, peeled: bool) -> int:
+    """Kernels of one emulated-leaf call: each materialization pass for both operands, row and column
     slicing, the slice GEMM, the post-additions and (for peeled sizes) the FP64 peel tasks."""
-    return 2 * levels + 4 + (1 if peeled else 0)
+    return 2 * passes + 4 + (1 if peeled else 0)
 
 
 def materialized_bytes(n_core: int, p: int, R_total: int, depth: int, levels: int) -> float:
@@ -577,7 +577,7 @@ def run_ours(a):
             "value": job_throughput(flops_eff, ws, e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
             "speedup_vs_classic": (flops_eff / (e_ms * 1e-3) / 1e12) / classic["value"] if classic else None,
             "normalised_error_sampled": e_err, "ozaki_slices": e_info["ozaki_slices"],
-            "gpu_launches": a.steps * ozaki_launches(e_info["materialized_levels"], e_info["n_core"] < n),
+            "gpu_launches": a.steps * ozaki_launches(e_info["materialize_passes"], e_info["n_core"] < n),
             "roofline": {"bound": "tensor", "kernel": "ozaki_tc_pair_kernel", "achieved": e_achieved, "peak": fp8_peak,
                          "unit": "TFLOP/s", "frac": e_achieved / fp8_peak, "peak_note": fp8_note,
                          "traffic": profile_traffic("ozaki_tc_pair_kernel",
@@ -647,8 +647,8 @@ def run_ours(a):
         "normalised_error_sampled": err,
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": a.steps * ozaki_launches(info["materialized_levels"], q > 0) if a.dtype == "f64_ozaki"
-        else a.steps * (1 + 2 * info["materialized_levels"]),
+        "gpu_launches": a.steps * ozaki_launches(info["materialize_passes"], q > 0) if a.dtype == "f64_ozaki"
+        else a.steps * (1 + 2 * info["materialize_passes"]),
         "roofline": roofline,
         "emulated_fp64": emulated,
         "cpu_baseline": cpu,

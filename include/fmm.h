@@ -112,6 +112,8 @@ typedef struct {
     int ozaki_slices;       /* FMM_F64_OZAKI: slices per operand (0 otherwise) */
     double flops_lowp;      /* FMM_F64_OZAKI: e4m3 tensor-core flops of the slice products */
     int tile_n;             /* leaf tile width of the FP64 kernel (128 or 64) */
+    int materialize_passes; /* kernel passes per operand that form the materialized S_r / T_r
+                               (a level, a Kronecker factor of one, or two 2 x 2 factors fused) */
 } fmm_plan_info_t;
 
 /* Status code to a static, NUL-terminated English string (never NULL). */

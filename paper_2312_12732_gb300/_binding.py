@@ -44,7 +44,7 @@ class fmm_plan_info_t(ctypes.Structure):
                 ("tasks", ctypes.c_int64), ("materialized_levels", ctypes.c_int),
                 ("flops_leaf", ctypes.c_double), ("flops_executed", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_size_t), ("ozaki_slices", ctypes.c_int), ("flops_lowp", ctypes.c_double),
-                ("tile_n", ctypes.c_int)]
+                ("tile_n", ctypes.c_int), ("materialize_passes", ctypes.c_int)]
 
 
 # (name, restype, argtypes) for every symbol declared in include/fmm.h.

@@ -306,6 +306,7 @@ struct fmm_plan {
         int p = 0, R = 0;
         const int *uptr = nullptr, *vptr = nullptr;
         const int4 *uent = nullptr, *vent = nullptr;
+        bool with_next = false;  // formed in one pass with the next step (both 2 x 2, at most 8 products)
     };
     std::vector<MatStep> mat_steps;
     // emulated leaf (FMM_F64_OZAKI)
@@ -717,6 +718,10 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
             ms.vent = (const int4 *)(base + o_st[4 * k + 3]);
             pl->mat_steps.push_back(ms);
         }
+    for (size_t k = 0; k + 1 < pl->mat_steps.size(); ++k) {
+        fmm_plan::MatStep &a = pl->mat_steps[k], &b = pl->mat_steps[k + 1];
+        if (a.p == 2 && b.p == 2 && a.R <= 8 && b.R <= 8 && !(k > 0 && pl->mat_steps[k - 1].with_next)) a.with_next = true;
+    }
     put(o_geom, &g, sizeof(F64Geom));
     {
         F64Geom gp = g;  // the peel tasks alone, run after the emulated leaf products
@@ -750,18 +755,22 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     size_t ws = pl->counters_bytes;
     size_t o_sa = 0, o_sb = 0, o_ta = 0, o_tb = 0;
     if (mat > 0) {
-        // steps alternate between the final buffer and one temporary, ending in the final buffer
+        // passes (a step, or two fused steps) alternate between the final buffer and one
+        // temporary, ending in the final buffer
         size_t fin_bytes = 0, tmp_bytes = 0;
         {
-            const size_t K = pl->mat_steps.size();
+            std::vector<size_t> outs;
             double cnt = 1, side = (double)pl->n_core;
-            for (size_t k = 1; k <= K; ++k) {
-                const fmm_plan::MatStep &st = pl->mat_steps[k - 1];
+            for (size_t k = 0; k < pl->mat_steps.size(); ++k) {
+                const fmm_plan::MatStep &st = pl->mat_steps[k];
                 cnt *= st.R;
                 side /= st.p;
-                const size_t bytes = (size_t)(cnt * side * side) * sizeof(double);
-                if ((K - k) % 2 == 0) fin_bytes = std::max(fin_bytes, bytes);
-                else tmp_bytes = std::max(tmp_bytes, bytes);
+                if (!st.with_next) outs.push_back((size_t)(cnt * side * side) * sizeof(double));
+            }
+            const size_t G = outs.size();
+            for (size_t g = 1; g <= G; ++g) {
+                if ((G - g) % 2 == 0) fin_bytes = std::max(fin_bytes, outs[g - 1]);
+                else tmp_bytes = std::max(tmp_bytes, outs[g - 1]);
             }
         }
         o_sa = ws; ws = align_up(ws + fin_bytes, 256);
@@ -874,26 +883,45 @@ fmm_status_t prepare(const fmm_plan *pl, const double *A, const double *B, cudaS
         e = cudaMemsetAsync(pl->d_chain, 0xFF, sizeof(unsigned), st);
         if (e != cudaSuccess) return FMM_ERR_CUDA;
     }
-    // Step k reads step k-1's output (step 0 = the n_core x n_core corner of
-    // the operand, ld n) and writes R_k times as many matrices of side 1/p_k;
-    // the last step lands in d_SA / d_SB, earlier ones alternate with d_TA / d_TB.
+    // Pass g (one step, or two steps fused) reads pass g-1's output (pass 0 =
+    // the n_core x n_core corner of the operand, ld n) and writes R times as
+    // many matrices of side 1/p per step; the last pass lands in d_SA / d_SB,
+    // earlier ones alternate with d_TA / d_TB.
     const int K = (int)pl->mat_steps.size();
+    int G = 0;
+    for (int k = 0; k < K; ++k) G += pl->mat_steps[k].with_next ? 0 : 1;
     for (int side = 0; side < 2; ++side) {
         const double *src = side == 0 ? A : B;
         double *fin = side == 0 ? pl->d_SA : pl->d_SB;
         double *tmp = side == 0 ? pl->d_TA : pl->d_TB;
         long long ld_in = pl->n, b_in = pl->n_core, n_in = 1;
-        for (int k = 1; k <= K; ++k) {
-            const fmm_plan::MatStep &ms = pl->mat_steps[k - 1];
-            double *dst = ((K - k) % 2 == 0) ? fin : tmp;
-            const long long b_out = b_in / ms.p;
-            e = fmm::launch_materialize_level(src, ld_in, k == 1 ? 0 : b_in * b_in, (int)n_in, b_out, ms.p, ms.R,
-                                              side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent, dst, st);
+        int g = 0;
+        for (int k = 0; k < K; ++k) {
+            const fmm_plan::MatStep &ms = pl->mat_steps[k];
+            ++g;
+            double *dst = ((G - g) % 2 == 0) ? fin : tmp;
+            const long long in_stride = (g == 1) ? 0 : b_in * b_in;
+            if (ms.with_next) {
+                const fmm_plan::MatStep &m2 = pl->mat_steps[k + 1];
+                const long long b_out = b_in / 4;
+                e = fmm::launch_materialize_two_steps(src, ld_in, in_stride, (int)n_in, b_out, ms.R,
+                                                      side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent,
+                                                      m2.R, side == 0 ? m2.uptr : m2.vptr,
+                                                      side == 0 ? m2.uent : m2.vent, dst, st);
+                n_in *= (long long)ms.R * m2.R;
+                b_in = b_out;
+                ++k;
+            } else {
+                const long long b_out = b_in / ms.p;
+                e = fmm::launch_materialize_level(src, ld_in, in_stride, (int)n_in, b_out, ms.p, ms.R,
+                                                  side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent, dst,
+                                                  st);
+                n_in *= ms.R;
+                b_in = b_out;
+            }
             if (e != cudaSuccess) return FMM_ERR_CUDA;
             src = dst;
-            ld_in = b_out;
-            b_in = b_out;
-            n_in *= ms.R;
+            ld_in = b_in;
         }
     }
     return FMM_OK;
@@ -1302,6 +1330,8 @@ extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t 
     info->ozaki_slices = pl->oz_s;
     info->tile_n = pl->bn;
     info->flops_lowp = pl->flops_lowp;
+    info->materialize_passes = 0;
+    for (const fmm_plan::MatStep &ms : pl->mat_steps) info->materialize_passes += ms.with_next ? 0 : 1;
     return FMM_OK;
 }
 

@@ -159,6 +159,11 @@ size_t f64_kernel_smem_bytes(int bn = kBN);
 cudaError_t launch_materialize_level(const double *in, long long ld_in, long long in_stride, int n_in,
                                      long long b_out, int p, int R, const int *ptr, const int4 *ent, double *out,
                                      cudaStream_t s);
+// Two consecutive steps with 2 x 2 block grids (at most 8 products each) in
+// one pass; out receives n_in * R1 * R2 matrices of side b2 (= input side / 4).
+cudaError_t launch_materialize_two_steps(const double *in, long long ld_in, long long in_stride, int n_in,
+                                         long long b2, int R1, const int *ptr1, const int4 *ent1, int R2,
+                                         const int *ptr2, const int4 *ent2, double *out, cudaStream_t s);
 
 // Calibration (fmm_calib.cu): FP64 throughput of DMMA (mma.sync m16n8k4) and
 // DFMA on the current device, in TFLOP/s, timed with CUDA events on `s`.

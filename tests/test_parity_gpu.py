@@ -229,3 +229,14 @@ def test_mixed_compositions(fmm, oracle_mod, first, second, depth, n):
     assert np.array_equal(run(fmm, plan, A, B), oracle_mod.classic(A, B))
     A, B = inputs.operands(n, "uniform", seed=depth + 5)
     assert nerr(run(fmm, plan, A, B), oracle_ref(oracle_mod, A, B, algo, depth), A, B) <= tol(depth)
+
+
+@pytest.mark.parametrize("name,power,depth,passes", [("strassen", 1, 1, 1), ("strassen", 1, 2, 1), ("strassen", 1, 3, 2),
+                                                     ("strassen", 2, 2, 2), ("laderman", 1, 2, 2),
+                                                     ("winograd", 1, 4, 2)])
+def test_materialization_passes(fmm, name, power, depth, passes):
+    """Pairs of 2 x 2 steps (Strassen-like factors) are formed in one pass; other steps one pass each."""
+    algo = fmm.algorithm(name, power)
+    n = algo.p ** depth * 8
+    assert fmm.fmm_plan_create(n, algo, depth, schedule="hybrid", materialize_levels=depth).info()[
+        "materialize_passes"] == passes
