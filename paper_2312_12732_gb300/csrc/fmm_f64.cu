@@ -75,12 +75,6 @@ using dev::neg;
 
 __device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
 
-// s (+)= c * v with the fewest FP64 operations: +-1 coefficients are adds.
-__device__ __forceinline__ double combine(double s, double v, int c, bool first) {
-    if (first) return c == 1 ? v : (c == -1 ? neg(v) : (double)c * v);
-    return c == 1 ? s + v : (c == -1 ? s - v : fma((double)c, v, s));
-}
-
 __device__ __forceinline__ void dmma_16x8x4(double (&d)[4], const double (&a)[2], double b) {
     asm volatile(
         "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
@@ -497,94 +491,6 @@ __global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __gri
     }
 }
 
-// One materialized recursion level.  blockIdx.y selects the input matrix;
-// CTAs stride over rows y of the b x b output blocks and threads over
-// columns x, so every load and store is coalesced and no index needs a
-// division.  All R outputs of a position are formed from the p^2 inputs.
-__global__ void materialize_level_kernel(const double *__restrict__ in, long long ld_in, long long in_stride,
-                                         long long b, int p, int R, const int *__restrict__ ptr,
-                                         const int4 *__restrict__ ent, double *__restrict__ out) {
-    const long long total = b * b;
-    const int c = blockIdx.y;
-    const double *src = in + (long long)c * in_stride;
-    double *dst = out + (long long)c * R * total;
-    for (long long y = blockIdx.x; y < b; y += gridDim.x) {
-        for (long long x = threadIdx.x; x < b; x += blockDim.x) {
-            const double *pos = src + y * ld_in + x;
-            for (int s = 0; s < R; ++s) {
-                double acc = 0.0;
-                const int e0 = ptr[s], e1 = ptr[s + 1];
-                for (int k = e0; k < e1; ++k) {
-                    const int4 en = ent[k];  // {block row, block col, coefficient, 0}
-                    const double v = __ldg(pos + (long long)en.x * b * ld_in + (long long)en.y * b);
-                    acc = combine(acc, v, en.z, k == e0);
-                }
-                dst[(long long)s * total + y * b + x] = acc;
-            }
-        }
-    }
-}
-
-
-// Two consecutive materialization steps with 2 x 2 block grids (Strassen-like
-// factors, at most 8 products each) in one pass: a thread reads the 16 inputs
-// of one output position, forms the first step's R1 x 4 sums in registers and
-// writes the R1 * R2 outputs.  The operations and their order are those of the
-// two separate steps, so the results are identical; the first step's output
-// never reaches HBM.  Entries: {block row, block col, coefficient, 0}.
-constexpr int kPairStepMaxR = 8;
-__global__ void materialize_two_steps_kernel(const double *__restrict__ in, long long ld_in, long long in_stride,
-                                             long long b2, int R1, const int *__restrict__ ptr1,
-                                             const int4 *__restrict__ ent1, int R2, const int *__restrict__ ptr2,
-                                             const int4 *__restrict__ ent2, double *__restrict__ out) {
-    const long long total = b2 * b2;
-    const long long b1 = 2 * b2;
-    const int c = blockIdx.y;
-    const double *src = in + (long long)c * in_stride;
-    double *dst = out + (long long)c * R1 * R2 * total;
-    for (long long y = blockIdx.x; y < b2; y += gridDim.x) {
-        for (long long x = threadIdx.x; x < b2; x += blockDim.x) {
-            // v[i1][j1][q]: input at outer block (i1, j1), inner block q = 2 i2 + j2
-            double v[2][2][4];
-#pragma unroll
-            for (int i1 = 0; i1 < 2; ++i1)
-#pragma unroll
-                for (int j1 = 0; j1 < 2; ++j1)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        v[i1][j1][q] = __ldg(src + (i1 * b1 + (q >> 1) * b2 + y) * ld_in + j1 * b1 + (q & 1) * b2 + x);
-            for (int r1 = 0; r1 < R1; ++r1) {
-                double t[4];
-                const int e0 = ptr1[r1], e1 = ptr1[r1 + 1];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) t[q] = 0.0;
-                for (int k = e0; k < e1; ++k) {
-                    const int4 en = ent1[k];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        // selects, not a pointer, keep v in registers
-                        const double w = en.x == 0 ? (en.y == 0 ? v[0][0][q] : v[0][1][q])
-                                                   : (en.y == 0 ? v[1][0][q] : v[1][1][q]);
-                        t[q] = combine(t[q], w, en.z, k == e0);
-                    }
-                }
-                double *o = dst + (long long)r1 * R2 * total + y * b2 + x;
-                for (int r2 = 0; r2 < R2; ++r2) {
-                    double acc = 0.0;
-                    const int f0 = ptr2[r2], f1 = ptr2[r2 + 1];
-                    for (int k = f0; k < f1; ++k) {
-                        const int4 en = ent2[k];
-                        const int q = 2 * en.x + en.y;
-                        const double w = q == 0 ? t[0] : (q == 1 ? t[1] : (q == 2 ? t[2] : t[3]));
-                        acc = combine(acc, w, en.z, k == f0);
-                    }
-                    o[(long long)r2 * total] = acc;
-                }
-            }
-        }
-    }
-}
-
 }  // namespace
 
 size_t f64_kernel_smem_bytes(int bn) { return bn == 64 ? sizeof(Smem<64>) : sizeof(Smem<128>); }
@@ -625,50 +531,6 @@ cudaError_t launch_f64_single(const F64Launch<1> &L, int grid, cudaStream_t s, i
 
 cudaError_t launch_f64_batch(const F64Launch<kMaxBatchPerLaunch> &L, int grid, cudaStream_t s, int bn) {
     return bn == 64 ? launch_cfg<kMaxBatchPerLaunch, 64>(L, grid, s) : launch_cfg<kMaxBatchPerLaunch, 128>(L, grid, s);
-}
-
-cudaError_t launch_materialize_level(const double *in, long long ld_in, long long in_stride, int n_in,
-                                     long long b_out, int p, int R, const int *ptr, const int4 *ent, double *out,
-                                     cudaStream_t s) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long bx = (long long)sms * 8 / (n_in > 0 ? n_in : 1);
-    if (bx > b_out) bx = b_out;
-    if (bx < 1) bx = 1;
-    const int threads = b_out >= 256 ? 256 : (int)((b_out + 31) / 32 * 32);
-    for (int c0 = 0; c0 < n_in; c0 += 65535) {
-        const int cnt = n_in - c0 < 65535 ? n_in - c0 : 65535;
-        dim3 grid((unsigned)bx, (unsigned)cnt);
-        materialize_level_kernel<<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride, b_out, p,
-                                                          R, ptr, ent, out + (long long)c0 * R * b_out * b_out);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-cudaError_t launch_materialize_two_steps(const double *in, long long ld_in, long long in_stride, int n_in,
-                                         long long b2, int R1, const int *ptr1, const int4 *ent1, int R2,
-                                         const int *ptr2, const int4 *ent2, double *out, cudaStream_t s) {
-    if (R1 > kPairStepMaxR || R2 > kPairStepMaxR) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long bx = (long long)sms * 8 / (n_in > 0 ? n_in : 1);
-    if (bx > b2) bx = b2;
-    if (bx < 1) bx = 1;
-    const int threads = b2 >= 256 ? 256 : (int)((b2 + 31) / 32 * 32);
-    for (int c0 = 0; c0 < n_in; c0 += 65535) {
-        const int cnt = n_in - c0 < 65535 ? n_in - c0 : 65535;
-        dim3 grid((unsigned)bx, (unsigned)cnt);
-        materialize_two_steps_kernel<<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride, b2, R1,
-                                                              ptr1, ent1, R2, ptr2, ent2,
-                                                              out + (long long)c0 * R1 * R2 * b2 * b2);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
 }
 
 }  // namespace fmm
