@@ -164,15 +164,17 @@ __global__ void slice_rows_kernel(const double *__restrict__ X, long long ld, lo
 }
 
 // Right operand: one CTA (32 x 8 threads) per strip of 32 columns of X
-// (rows = K): the column maxima first, then 32 x 32 tiles whose digits are
-// transposed through shared memory so that slice row c (K contiguous) is
-// written with coalesced stores.
+// (rows = K): the column maxima first, then 32 x 32 tiles.  Thread (tx, ty)
+// splits the four consecutive K rows 4 ty .. 4 ty + 3 of column tx, so each
+// of its digit planes is one 32-bit word; the words are transposed through
+// shared memory so that slice row c (K contiguous) is written with coalesced
+// stores.
 template <int S>
 __global__ void slice_cols_kernel(const double *__restrict__ X, long long ld, long long mat_stride, int rows,
                                   int cols, int *__restrict__ mx, int pitch, int Mp, int Kp,
                                   unsigned char *__restrict__ out) {
     constexpr int s = S;
-    __shared__ unsigned char tile[kOzMaxSlices][32][36];
+    __shared__ unsigned tile[S][32][9];  // [slice][column][K word], padded: conflict-free both ways
     __shared__ int colmax[8][32];
     __shared__ unsigned char lut[33];
     fill_lut(lut);
@@ -200,28 +202,21 @@ __global__ void slice_cols_kernel(const double *__restrict__ X, long long ld, lo
     const long long slice_stride = (long long)Mp * Kp;
     unsigned char *obase = out + ((long long)mat * s * Mp + c0 + cc) * Kp;
     for (int k0 = 0; k0 < rows; k0 += 32) {
+        unsigned packed[kOzMaxSlices];
+#pragma unroll
+        for (int t = 0; t < kOzMaxSlices; ++t) packed[t] = 0u;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int kk = ty + 8 * q;
-            const int k = k0 + kk;
-            unsigned packed[kOzMaxSlices];
-#pragma unroll
-            for (int t = 0; t < kOzMaxSlices; ++t) packed[t] = 0u;
-            if (c < cols && k < rows) pack_digits<S>(to_fixed(__ldg(Xm + (long long)k * ld + c), E, bs) + O, lut, packed, 0);
-#pragma unroll
-            for (int t = 0; t < kOzMaxSlices; ++t)
-                if (t < s) tile[t][tx][kk] = (unsigned char)packed[t];
+            const int k = k0 + 4 * ty + q;
+            if (c < cols && k < rows) pack_digits<S>(to_fixed(__ldg(Xm + (long long)k * ld + c), E, bs) + O, lut, packed, q);
         }
+#pragma unroll
+        for (int t = 0; t < S; ++t) tile[t][tx][ty] = packed[t];
         __syncthreads();
         if (c0 + cc < Mp && k0 + ch * 4 < Kp) {
 #pragma unroll
-            for (int t = 0; t < kOzMaxSlices; ++t)
-                if (t < s) {
-                    const unsigned v = (unsigned)tile[t][cc][ch * 4] | ((unsigned)tile[t][cc][ch * 4 + 1] << 8) |
-                                       ((unsigned)tile[t][cc][ch * 4 + 2] << 16) |
-                                       ((unsigned)tile[t][cc][ch * 4 + 3] << 24);
-                    *reinterpret_cast<unsigned *>(obase + t * slice_stride + k0 + ch * 4) = v;
-                }
+            for (int t = 0; t < S; ++t)
+                *reinterpret_cast<unsigned *>(obase + t * slice_stride + k0 + ch * 4) = tile[t][cc][ch];
         }
         __syncthreads();
     }
