@@ -13,6 +13,10 @@ Typical use::
     algo = fmm.fmm_algo_builtin("strassen")
     plan = fmm.fmm_plan_create(8192, algo, depth=2)
     fmm.fmm_gemm(plan, A, B, C)          # A, B, C: float64 CUDA tensors
+
+or, with a plan created on first use and kept for later calls of the same shape::
+
+    C = fmm.gemm(A, B, "strassen", depth=2)
 """
 from ._binding import (  # noqa: F401
     Algo,
@@ -53,3 +57,37 @@ def algorithm(name: str, power: int = 1):
     for _ in range(power - 1):
         out = fmm_algo_compose(out, a)
     return out
+
+
+_PLANS = {}
+
+
+def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None):
+    """C = A @ B for square float64 CUDA tensors by the bilinear algorithm ``algo`` (a built-in
+    name, ``"name^k"`` for its k-th Kronecker power, or an :class:`Algo`) at recursion ``depth``.
+
+    The plan for (n, algorithm, depth, dtype, device) is created on first use and cached; a cached
+    plan's workspace serves one call at a time, so calls on different streams that share a plan
+    must not overlap.  ``out`` (optional) receives the product; otherwise a new tensor does.
+    """
+    import torch
+
+    if not isinstance(A, torch.Tensor) or A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be a square 2-D torch.Tensor")
+    n = A.shape[0]
+    if isinstance(algo, str):
+        name, _, k = algo.partition("^")
+        alg = algorithm(name, int(k) if k else 1)
+        key_algo = algo
+    else:
+        alg = algo
+        key_algo = (alg.p, alg.U.tobytes(), alg.V.tobytes(), alg.W.tobytes())
+    key = (n, key_algo, depth, dtype, A.device.index)
+    plan = _PLANS.get(key)
+    if plan is None:
+        with torch.cuda.device(A.device):
+            plan = fmm_plan_create(n, alg, depth, dtype=dtype)
+        _PLANS[key] = plan
+    C = out if out is not None else torch.empty_like(A)
+    fmm_gemm(plan, A, B, C, stream)
+    return C

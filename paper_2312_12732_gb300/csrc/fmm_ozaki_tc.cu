@@ -578,6 +578,13 @@ constexpr uint32_t P_STAGE_BYTES = P_STAGE_A + (uint32_t)P_KBOX * TNH * BOX;  //
 constexpr int P_EPI_WARP0 = 4;
 constexpr int P_NTHREADS = (P_EPI_WARP0 + NEPI) * 32;          // 12 warps
 
+// Ring (and MMA thread) of global diagonal group G: the pattern 0, 1, 1, 0
+// repeating.  Group g of a task holds g - 1 slice pairs for g <= s + 1, so
+// with s = 12 each thread gets 39 of the 78 pairs (alternating 0, 1 gave 36
+// and 42, and the in-order epilogue made the lighter thread wait for the
+// other); thread 0 uses accumulators 0 and 3, thread 1 uses 1 and 2.
+__device__ __forceinline__ int ring_of_group(int G) { return ((G + 1) >> 1) & 1; }
+
 struct __align__(8) PairBars {
     unsigned long long full[NRING][RSTAGES], empty[NRING][RSTAGES];
     unsigned long long accfull[NBUF], accempty[NBUF];
@@ -597,10 +604,10 @@ struct __align__(8) PairBars {
 // kernel per MMA flop.
 // The tensor pipe queues only about one MMA ahead of its issuing thread, so
 // every barrier wait of a lone issuer idles the pipe.  Two issuers therefore
-// alternate: diagonal groups are numbered globally (G), group G runs on ring
-// G mod 2 (its own producer, its own two stages, its own MMA thread) and
-// accumulates in TMEM buffer G mod 4; while one MMA thread waits, the other
-// issues.
+// share the work: diagonal groups are numbered globally (G), group G runs on
+// ring ring_of_group(G) (its own producer, its own stages, its own MMA
+// thread) and accumulates in TMEM buffer G mod 4; while one MMA thread waits,
+// the other issues.
 // Warps: 0, 1 producers of rings 0, 1 (both CTAs); 2, 3 MMA threads of rings
 // 0, 1 (leader; warp 2 also allocates TMEM in both CTAs); 4-11 epilogue.
 // Barriers (same offsets in both CTAs):
@@ -706,7 +713,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                 const int ti = 2 * tp + (int)rank;
                 bool ok = true;
                 for (int g = 2; g <= s + 1 && ok; ++g) {
-                    if (((tseq * s + g - 2) & 1) != q) continue;
+                    if (ring_of_group(tseq * s + g - 2) != q) continue;
                     for (int ta = max(1, g - s); ta <= min(s, g - 1) && ok; ++ta)
                         for (int kb = 0; kb < nkb; ++kb) {
                             if (!mbar_wait(&B.empty[q][stage], sphase ^ 1u, abort, P.error, P.timeout_ns)) {
@@ -764,7 +771,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                 bool ok = true;
                 for (int g = 2; g <= s + 1 && ok; ++g) {
                     const int G = tseq * s + g - 2;
-                    if ((G & 1) != q) continue;
+                    if (ring_of_group(G) != q) continue;
                     const uint32_t buf = (uint32_t)(G % NBUF), bphase = (uint32_t)((G / NBUF) & 1);
                     if (!mbar_wait(&B.accempty[buf], bphase ^ 1u, abort, P.error, P.timeout_ns)) {
                         ok = false;

@@ -240,3 +240,19 @@ def test_materialization_passes(fmm, name, power, depth, passes):
     n = algo.p ** depth * 8
     assert fmm.fmm_plan_create(n, algo, depth, schedule="hybrid", materialize_levels=depth).info()[
         "materialize_passes"] == passes
+
+
+def test_gemm_convenience(fmm, oracle_mod):
+    """fmm.gemm creates a plan on first use, reuses it, accepts '<name>^k' and checks its operands."""
+    n = 256
+    A, B = inputs.operands(n, "integer", seed=77)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C1 = fmm.gemm(dA, dB, "strassen", depth=2)
+    C2 = fmm.gemm(dA, dB, "strassen^2", depth=1, out=torch.empty_like(dA))
+    C3 = fmm.gemm(dA, dB, "strassen", depth=2)
+    ref = oracle_mod.classic(A, B)
+    for C in (C1, C2, C3):
+        assert np.array_equal(C.cpu().numpy(), ref)
+    assert len([k for k in fmm._PLANS if k[0] == n]) >= 2
+    with pytest.raises(ValueError):
+        fmm.gemm(dA.float(), dB)
