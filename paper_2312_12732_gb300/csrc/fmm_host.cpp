@@ -316,7 +316,8 @@ struct fmm_plan {
     int *d_mxa = nullptr, *d_mxb = nullptr;            // exponents (zeroed per call with the counters)
     const F64Geom *d_geom_peel = nullptr;              // FP64 peel-only geometry
     int oz_engine = 2;                                  // 2 = tcgen05 CTA pairs, 1 = tcgen05, 0 = mma.sync
-    CUtensorMap oz_map_a{}, oz_map_b{}, oz_map_bh{};    // TMA maps over the slices (bh: 64-row boxes)
+    int oz_cluster = 4;                                 // CTAs per cluster of the pair engine (2 or 4)
+    CUtensorMap oz_map_a{}, oz_map_b{}, oz_map_bh{}, oz_map_ah{};  // TMA maps over the slices (h: 64-row boxes)
     double *d_pout = nullptr;                           // [R][m][m] leaf products of the tcgen05 engines
     const int *d_wl_ptr = nullptr;                      // per C block: products (r, coefficient) in ascending r
     const int2 *d_wl_ent = nullptr;
@@ -813,15 +814,19 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         pl->d_sla = (unsigned char *)(wsb + o_sla);
         pl->d_slb = (unsigned char *)(wsb + o_slb);
         pl->d_pout = (double *)(wsb + o_pout);
-        // engine: CTA pairs by default; FMM_OZAKI_ENGINE=tc1 (one CTA per tile) or mma_sync
+        // engine: CTA pairs in clusters of two pairs by default; FMM_OZAKI_ENGINE=pair2 (one pair
+        // per cluster), tc1 (one CTA per tile) or mma_sync
         const char *eng = std::getenv("FMM_OZAKI_ENGINE");
         const std::string es = eng ? eng : "";
         pl->oz_engine = es == "mma_sync" ? 0 : (es == "tc1" ? 1 : 2);
-        if (pl->oz_engine == 2 && fmm::ozaki_tc_max_pairs() < 1) pl->oz_engine = 1;
+        pl->oz_cluster = (es == "pair2" || pl->tiles_n < 2) ? 2 : 4;
+        if (pl->oz_engine == 2 && pl->oz_cluster == 4 && fmm::ozaki_tc_max_clusters(4) < 1) pl->oz_cluster = 2;
+        if (pl->oz_engine == 2 && fmm::ozaki_tc_max_clusters(2) < 1) pl->oz_engine = 1;
         const unsigned long long srows = (unsigned long long)Rt * oz_s * pl->oz_Mp;
         if (pl->oz_engine >= 1 && (!make_slice_map(&pl->oz_map_a, pl->d_sla, srows, pl->oz_Mp) ||
                                    !make_slice_map(&pl->oz_map_b, pl->d_slb, srows, pl->oz_Mp) ||
-                                   !make_slice_map(&pl->oz_map_bh, pl->d_slb, srows, pl->oz_Mp, 64))) {
+                                   !make_slice_map(&pl->oz_map_bh, pl->d_slb, srows, pl->oz_Mp, 64) ||
+                                   !make_slice_map(&pl->oz_map_ah, pl->d_sla, srows, pl->oz_Mp, 64))) {
             free_plan_memory(pl);
             delete pl;
             return FMM_ERR_CUDA;
@@ -983,10 +988,13 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     P.error = pl->d_error;
     P.timeout_ns = (long long)(pl->timeout_s * 1e9);
     if (pl->oz_engine == 2) {
-        // a task covers a pair of tile rows; the second row of the last pair may be padding
-        P.tasks = (long long)nmat * ((pl->tiles_m + 1) / 2) * pl->tiles_n;
-        const int pairs = (int)std::min<long long>(P.tasks, (long long)fmm::ozaki_tc_max_pairs());
-        if (fmm::launch_ozaki_tc_pair(pl->oz_map_a, pl->oz_map_bh, P, pairs < 1 ? 1 : pairs, st) != cudaSuccess)
+        // a task covers a pair of tile rows and oz_cluster / 2 tile columns; the last row or
+        // column of a task may be padding
+        const int cl = pl->oz_cluster, npair = cl / 2;
+        P.tasks = (long long)nmat * ((pl->tiles_m + 1) / 2) * ((pl->tiles_n + npair - 1) / npair);
+        const int clusters = (int)std::min<long long>(P.tasks, (long long)fmm::ozaki_tc_max_clusters(cl));
+        if (fmm::launch_ozaki_tc_pair(cl == 4 ? pl->oz_map_ah : pl->oz_map_a, pl->oz_map_bh, P,
+                                      clusters < 1 ? 1 : clusters, cl, st) != cudaSuccess)
             return FMM_ERR_CUDA;
     } else if (pl->oz_engine == 1) {
         const int grid = (int)std::min<long long>(P.tasks, (long long)pl->sms);

@@ -17,8 +17,9 @@
 //                D_g with tcgen05.ld, folds it into 64 int64 registers while
 //                later groups accumulate, converts to FP64 and stores the tile
 //                of P_r.
-//   ozaki_tc_pair_kernel (CTA pairs, tcgen05 cta_group::2; the default)
-//     described above the kernel.
+//   ozaki_tc_pair_kernel<CL> (CTA pairs, tcgen05 cta_group::2; clusters of one
+//     pair or of two pairs sharing their left-slice tiles by TMA multicast, the
+//     default) described above the kernel.
 //
 // ozaki_postadd_kernel then forms C_l = sum_r W[l][r] P_r in ascending r.
 // Every mbarrier wait is bounded by %globaltimer; on expiry the CTA records a
@@ -546,6 +547,16 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
         "l"(map), "r"(x), "r"(y), "r"(caddr)
         : "memory");
 }
+// The same, multicast: the box lands at this offset in every CTA of `mask`, and each destination
+// pair's leader barrier (same offset) is signalled.
+__device__ __forceinline__ void tma_load_2d_pair_mc(void *dst, const CUtensorMap *map, int x, int y, uint32_t caddr,
+                                                    uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::"
+        "cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(su32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(caddr), "h"(mask)
+        : "memory");
+}
 // 2-SM MMA: M = 256 (128 rows in each CTA's TMEM), N = 128 (64 rows of B in each CTA's shared memory).
 constexpr uint32_t kIdescPair = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)((2 * TM) >> 4) << 24);
 __device__ __forceinline__ void mma_e4m3_pair(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
@@ -555,12 +566,12 @@ __device__ __forceinline__ void mma_e4m3_pair(uint32_t tmem_d, uint64_t da, uint
         "l"(da), "l"(db), "r"(kIdescPair), "r"(accumulate)
         : "memory");
 }
-// Arrives on the mbarrier at this offset in both CTAs of the pair once the MMAs issued so far complete.
-__device__ __forceinline__ void mma_commit_pair(unsigned long long *bar) {
+// Arrives on the mbarrier at this offset in every CTA of `mask` once the MMAs issued so far complete.
+__device__ __forceinline__ void mma_commit_pair(unsigned long long *bar, unsigned short mask) {
     asm volatile(
         "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
             su32(bar)),
-        "h"((unsigned short)3)
+        "h"(mask)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit_pair_local(unsigned long long *bar) {
@@ -595,8 +606,14 @@ struct __align__(8) PairBars {
     int abort;
 };
 
-// Slice GEMM on CTA pairs (cluster of 2).  A task is product r, tile column
-// tj and the tile-row pair tp; CTA `rank` owns tile row ti = 2 tp + rank.
+// Slice GEMM on CTA pairs; CL = 2 (one pair per cluster) or 4 (two pairs
+// that share their left-slice tiles).  A task is product r, the tile-row
+// pair tp and CL / 2 adjacent tile columns; CTA (pair pc, rank-in-pair rp)
+// owns tile row ti = 2 tp + rp of tile column tj = (CL / 2) tj2 + pc.  With
+// CL = 4 each CTA loads half of its A box and multicasts it to the CTA with
+// the same rp in the other pair, which cuts each SM's L2 requests per stage
+// from 24 to 16 KB; the two pairs then run in lock-step, each stage being
+// released by both pairs' MMA threads.
 // Each CTA streams its 128 rows of the left slices and its 64-row half of the
 // right slices; the leader's MMA threads issue 256 x 128 x 32 MMAs (tcgen05
 // cta_group::2) that read both CTAs' shared memory and accumulate into both
@@ -618,9 +635,12 @@ struct __align__(8) PairBars {
 //   tfull/tempty task ring: ring 0's producer in the leader fetches tasks and
 //                publishes them to both CTAs; every other role of both CTAs
 //                releases the slot on the leader's tempty.
+template <int CL>
 __global__ void __launch_bounds__(P_NTHREADS, 1)
     ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_bh,
                          const __grid_constant__ OzParams P) {
+    static_assert(CL == 2 || CL == 4, "clusters of one or two CTA pairs");
+    constexpr int NPAIR = CL / 2;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
     unsigned char *stage_mem = base;  // NRING x RSTAGES x (A 32 KB, B half 16 KB)
@@ -629,9 +649,15 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t rank = cluster_rank();
-    const bool lead = rank == 0;
+    const int pc = (int)rank >> 1, rp = (int)rank & 1;
+    const bool lead = rp == 0;        // pair leader: MMA threads, full / accempty barriers
+    const bool fetcher = rank == 0;   // fetches tasks and publishes them to the cluster
+    const uint32_t pair_lead = rank & ~1u;
+    const unsigned short pair_mask = (unsigned short)(3u << pair_lead);
+    const unsigned short all_mask = (unsigned short)((1u << CL) - 1u);
     const int pairs_m = (P.tiles_m + 1) / 2;
-    const int ptiles = pairs_m * P.tiles_n;
+    const int tn2 = (P.tiles_n + NPAIR - 1) / NPAIR;
+    const int ptiles = pairs_m * tn2;
     const int nbox = P.Kp / BOX;
     const int nkb = (nbox + P_KBOX - 1) / P_KBOX;
     const int s = P.s;
@@ -640,17 +666,18 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
         for (int q = 0; q < NRING; ++q)
             for (int i = 0; i < RSTAGES; ++i) {
                 mbar_init(&B.full[q][i], 1);
-                mbar_init(&B.empty[q][i], 1);
+                mbar_init(&B.empty[q][i], NPAIR);  // every pair's MMA thread q releases the stage
             }
         for (int i = 0; i < NBUF; ++i) {
             mbar_init(&B.accfull[i], 1);
             mbar_init(&B.accempty[i], 2 * NEPI);
         }
-        // consumers of a task slot: leader (producer 1, two MMA threads, NEPI
-        // epilogue warps) and peer (two producers, NEPI epilogue warps)
+        // consumers of a task slot (counted on the fetcher): the fetcher's producer 1,
+        // two MMA threads and NEPI epilogue warps; two producers, NEPI epilogue warps
+        // and (pair leaders) two MMA threads in every other CTA
         for (int i = 0; i < TASK_RING; ++i) {
             mbar_init(&B.tfull[i], 1);
-            mbar_init(&B.tempty[i], 5 + 2 * NEPI);
+            mbar_init(&B.tempty[i], (3 + NEPI) + (CL - 1) * (2 + NEPI) + (NPAIR - 1) * 2);
         }
         for (int q = 0; q < NRING; ++q) mbar_init(&B.drain[q], 1);
         B.abort = 0;
@@ -688,18 +715,20 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
             bool issued = false;
             while (!*abort) {
                 long long task;
-                if (lead && q == 0) {
+                if (fetcher && q == 0) {
                     task = (long long)atomicAdd(P.task_counter, 1ull);
                     if (ld_volatile(P.error) != kDevOk) task = P.tasks;
                     if (!mbar_wait_cl(&B.tempty[tslot], tphase ^ 1u, abort, P.error, P.timeout_ns)) break;
                     B.task[tslot] = task;
-                    st_cluster_s64(mapa(su32(&B.task[tslot]), 1), task);
+#pragma unroll
+                    for (int c = 1; c < CL; ++c) st_cluster_s64(mapa(su32(&B.task[tslot]), c), task);
                     mbar_arrive(&B.tfull[tslot]);
-                    arrive_remote_release(mapa(su32(&B.tfull[tslot]), 1));
+#pragma unroll
+                    for (int c = 1; c < CL; ++c) arrive_remote_release(mapa(su32(&B.tfull[tslot]), c));
                 } else {
                     if (!mbar_wait_cl(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
                     task = B.task[tslot];
-                    if (lead) mbar_arrive(&B.tempty[tslot]);
+                    if (fetcher) mbar_arrive(&B.tempty[tslot]);
                     else arrive_remote_release(mapa(su32(&B.tempty[tslot]), 0));
                 }
                 if (++tslot == TASK_RING) {
@@ -709,8 +738,9 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                 if (task >= P.tasks) break;
                 const int r = (int)(task / ptiles);
                 const int t2 = (int)(task - (long long)r * ptiles);
-                const int tp = t2 / P.tiles_n, tj = t2 - tp * P.tiles_n;
-                const int ti = 2 * tp + (int)rank;
+                const int tp = t2 / tn2;
+                const int tj = NPAIR * (t2 - tp * tn2) + pc;
+                const int ti = 2 * tp + rp;
                 bool ok = true;
                 for (int g = 2; g <= s + 1 && ok; ++g) {
                     if (ring_of_group(tseq * s + g - 2) != q) continue;
@@ -723,13 +753,17 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                             unsigned char *sa = stage_mem + (q * RSTAGES + stage) * P_STAGE_BYTES;
                             unsigned char *sb = sa + P_STAGE_A;
                             const int boxes = min(P_KBOX, nbox - kb * P_KBOX);
-                            const uint32_t full_lead = mapa(su32(&B.full[q][stage]), 0);
+                            const uint32_t full_lead = mapa(su32(&B.full[q][stage]), pair_lead);
                             if (lead) mbar_expect_tx(&B.full[q][stage], (uint32_t)(2 * boxes * (TM + TNH) * BOX));
                             const int ya = (r * s + (ta - 1)) * P.Mp + ti * TM;
-                            const int yb = (r * s + (g - ta - 1)) * P.Mp + tj * TN + (int)rank * TNH;
+                            const int yb = (r * s + (g - ta - 1)) * P.Mp + tj * TN + rp * TNH;
                             for (int bx = 0; bx < boxes; ++bx) {
                                 const int x = (kb * P_KBOX + bx) * BOX;
-                                tma_load_2d_pair(sa + bx * TM * BOX, &map_a, x, ya, full_lead);
+                                if (CL == 4)  // my 64-row half of the A box, to both CTAs holding tile row ti
+                                    tma_load_2d_pair_mc(sa + bx * TM * BOX + pc * TNH * BOX, &map_a, x, ya + pc * TNH,
+                                                        full_lead, (unsigned short)((1u << rp) | (1u << (2 + rp))));
+                                else
+                                    tma_load_2d_pair(sa + bx * TM * BOX, &map_a, x, ya, full_lead);
                                 tma_load_2d_pair(sb + bx * TNH * BOX, &map_bh, x, yb, full_lead);
                             }
                             issued = true;
@@ -760,9 +794,10 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
             const uint32_t sbase = su32(stage_mem) + (uint32_t)(q * RSTAGES) * P_STAGE_BYTES;
             bool any = false;
             while (!*abort) {
-                if (!mbar_wait(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
+                if (!mbar_wait_cl(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
                 const long long task = B.task[tslot];
-                mbar_arrive(&B.tempty[tslot]);
+                if (fetcher) mbar_arrive(&B.tempty[tslot]);
+                else arrive_remote_release(mapa(su32(&B.tempty[tslot]), 0));
                 if (++tslot == TASK_RING) {
                     tslot = 0;
                     tphase ^= 1u;
@@ -800,7 +835,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                                 mma_e4m3_pair(dtm, da + boxa + adv, db + boxb + adv, first ? 0u : 1u);
                                 first = false;
                             }
-                            mma_commit_pair(&B.empty[q][stage]);
+                            mma_commit_pair(&B.empty[q][stage], all_mask);
                             any = true;
                             if (++stage == RSTAGES) {
                                 stage = 0;
@@ -808,7 +843,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                             }
                         }
                     if (!ok) break;
-                    mma_commit_pair(&B.accfull[buf]);
+                    mma_commit_pair(&B.accfull[buf], pair_mask);
                 }
                 if (!ok) break;
                 ++tseq;
@@ -830,7 +865,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
             const long long task = B.task[tslot];
             __syncwarp();
             if (lane == 0) {
-                if (lead) mbar_arrive(&B.tempty[tslot]);
+                if (fetcher) mbar_arrive(&B.tempty[tslot]);
                 else arrive_remote_release(mapa(su32(&B.tempty[tslot]), 0));
             }
             if (++tslot == TASK_RING) {
@@ -840,12 +875,13 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
             if (task >= P.tasks) break;
             const int r = (int)(task / ptiles);
             const int t2 = (int)(task - (long long)r * ptiles);
-            const int tp = t2 / P.tiles_n, tj = t2 - tp * P.tiles_n;
-            const int ti = 2 * tp + (int)rank;
-            if (!epilogue_tile<P_EPI_WARP0>(P, B.accfull, abort, tmem, r, ti, tj, ti < P.tiles_m, tseq * s,
-                                            [&](uint32_t b) {
+            const int tp = t2 / tn2;
+            const int tj = NPAIR * (t2 - tp * tn2) + pc;
+            const int ti = 2 * tp + rp;
+            if (!epilogue_tile<P_EPI_WARP0>(P, B.accfull, abort, tmem, r, ti, tj, ti < P.tiles_m && tj < P.tiles_n,
+                                            tseq * s, [&](uint32_t b) {
                                                 if (lead) mbar_arrive(&B.accempty[b]);
-                                                else arrive_remote_relaxed(mapa(su32(&B.accempty[b]), 0));
+                                                else arrive_remote_relaxed(mapa(su32(&B.accempty[b]), pair_lead));
                                             }))
                 break;
             ++tseq;
@@ -958,60 +994,67 @@ cudaError_t launch_ozaki_tc(const CUtensorMap &map_a, const CUtensorMap &map_b, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_bh, const OzParams &P,
-                                 int pairs, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(ozaki_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kPairSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+namespace {
+template <int CL>
+cudaLaunchConfig_t pair_config(cudaLaunchAttribute *at, int clusters, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.x = CL;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)(2 * pairs));
+    cfg.gridDim = dim3((unsigned)(CL * clusters));
     cfg.blockDim = dim3(P_NTHREADS);
     cfg.dynamicSmemBytes = kPairSmemBytes;
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ozaki_tc_pair_kernel, map_a, map_bh, P);
+    return cfg;
 }
 
-int ozaki_tc_max_pairs() {
+template <int CL>
+bool pair_attr() {
+    static int state = 0;  // 0 unset, 1 ok, -1 failed
+    if (state == 0)
+        state = cudaFuncSetAttribute(ozaki_tc_pair_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kPairSmemBytes) == cudaSuccess ? 1 : -1;
+    if (state < 0) cudaGetLastError();
+    return state > 0;
+}
+
+template <int CL>
+int max_clusters() {
     static int cached = -1;
     if (cached >= 0) return cached;
-    if (cudaFuncSetAttribute(ozaki_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kPairSmemBytes) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
+    if (!pair_attr<CL>()) return 0;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cfg.gridDim = dim3((unsigned)(sms / 2 * 2));
-    cfg.blockDim = dim3(P_NTHREADS);
-    cfg.dynamicSmemBytes = kPairSmemBytes;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = pair_config<CL>(at, sms / CL, nullptr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, ozaki_tc_pair_kernel, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, ozaki_tc_pair_kernel<CL>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     cached = n;
     return n;
 }
+}  // namespace
+
+cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_bh, const OzParams &P,
+                                 int clusters, int cluster_ctas, cudaStream_t s) {
+    cudaLaunchAttribute at[1];
+    if (cluster_ctas == 4) {
+        if (!pair_attr<4>()) return cudaErrorInvalidValue;
+        cudaLaunchConfig_t cfg = pair_config<4>(at, clusters, s);
+        return cudaLaunchKernelEx(&cfg, ozaki_tc_pair_kernel<4>, map_a, map_bh, P);
+    }
+    if (!pair_attr<2>()) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = pair_config<2>(at, clusters, s);
+    return cudaLaunchKernelEx(&cfg, ozaki_tc_pair_kernel<2>, map_a, map_bh, P);
+}
+
+int ozaki_tc_max_clusters(int cluster_ctas) { return cluster_ctas == 4 ? max_clusters<4>() : max_clusters<2>(); }
 
 cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
                                  double *C, long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
