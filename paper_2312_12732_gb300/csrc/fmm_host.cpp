@@ -820,8 +820,7 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
         const std::string es = eng ? eng : "";
         pl->oz_engine = es == "mma_sync" ? 0 : (es == "tc1" ? 1 : 2);
         pl->oz_cluster = (es == "pair2" || pl->tiles_n < 2) ? 2 : 4;
-        if (pl->oz_engine == 2 && pl->oz_cluster == 4 && fmm::ozaki_tc_max_clusters(4) < 1) pl->oz_cluster = 2;
-        if (pl->oz_engine == 2 && fmm::ozaki_tc_max_clusters(2) < 1) pl->oz_engine = 1;
+        if (pl->oz_engine == 2 && fmm::ozaki_tc_max_pairs() < 1) pl->oz_engine = 1;
         const unsigned long long srows = (unsigned long long)Rt * oz_s * pl->oz_Mp;
         if (pl->oz_engine >= 1 && (!make_slice_map(&pl->oz_map_a, pl->d_sla, srows, pl->oz_Mp) ||
                                    !make_slice_map(&pl->oz_map_b, pl->d_slb, srows, pl->oz_Mp) ||
@@ -988,13 +987,13 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     P.error = pl->d_error;
     P.timeout_ns = (long long)(pl->timeout_s * 1e9);
     if (pl->oz_engine == 2) {
-        // a task covers a pair of tile rows and oz_cluster / 2 tile columns; the last row or
-        // column of a task may be padding
-        const int cl = pl->oz_cluster, npair = cl / 2;
-        P.tasks = (long long)nmat * ((pl->tiles_m + 1) / 2) * ((pl->tiles_n + npair - 1) / npair);
-        const int clusters = (int)std::min<long long>(P.tasks, (long long)fmm::ozaki_tc_max_clusters(cl));
-        if (fmm::launch_ozaki_tc_pair(cl == 4 ? pl->oz_map_ah : pl->oz_map_a, pl->oz_map_bh, P,
-                                      clusters < 1 ? 1 : clusters, cl, st) != cudaSuccess)
+        // a task covers a pair of tile rows and two tile columns; the last row or column of a
+        // task may be padding.  One CTA per SM, in clusters of 4 where possible (oz_cluster = 4).
+        P.tasks = (long long)nmat * ((pl->tiles_m + 1) / 2) * ((pl->tiles_n + 1) / 2);
+        const long long pairs = std::min<long long>(2 * P.tasks, (long long)fmm::ozaki_tc_max_pairs());
+        const int ctas = (int)(pl->oz_cluster == 4 ? pairs / 2 * 4 : 2 * pairs);
+        if (fmm::launch_ozaki_tc_pair(pl->oz_map_a, pl->oz_map_ah, pl->oz_map_bh, P, ctas < 2 ? 2 : ctas,
+                                      pl->oz_cluster, st) != cudaSuccess)
             return FMM_ERR_CUDA;
     } else if (pl->oz_engine == 1) {
         const int grid = (int)std::min<long long>(P.tasks, (long long)pl->sms);

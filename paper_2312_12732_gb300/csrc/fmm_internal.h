@@ -128,15 +128,16 @@ size_t ozaki_smem_bytes();
 // maps over the slice buffers ([rows][Kp], 128 x 128 boxes, 128B swizzle).
 cudaError_t launch_ozaki_tc(const CUtensorMap &map_a, const CUtensorMap &map_b, const OzParams &P, int grid,
                             cudaStream_t s);
-// The same slice GEMM on CTA pairs (tcgen05 cta_group::2) in clusters of
-// cluster_ctas = 2 (one pair) or 4 (two pairs that share left-slice tiles by
-// TMA multicast; map_a then has 64-row boxes); map_bh has 64-row boxes over
-// the right slices.  P.tasks counts (product, tile-row pair, cluster_ctas / 2
-// tile columns) tasks; `clusters` clusters are launched.
-cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_bh, const OzParams &P,
-                                 int clusters, int cluster_ctas, cudaStream_t s);
-// Largest number of co-resident clusters of that size (0 if the kernel cannot run).
-int ozaki_tc_max_clusters(int cluster_ctas);
+// The same slice GEMM on CTA pairs (tcgen05 cta_group::2): `ctas` CTAs in
+// clusters of 2, or (cluster_ctas = 4) clusters of 4 where the GPU can form
+// them and of 2 on the remaining SMs.  A cluster of 4 is two pairs that share
+// left-slice tiles by TMA multicast and reads them through map_ah (64-row
+// boxes); pairs read map_a (128-row boxes); map_bh has 64-row boxes over the
+// right slices.  P.tasks counts (product, tile-row pair, two tile columns).
+cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_ah, const CUtensorMap &map_bh,
+                                 const OzParams &P, int ctas, int cluster_ctas, cudaStream_t s);
+// Largest number of co-resident CTA pairs of the pair kernel (0 if it cannot run).
+int ozaki_tc_max_pairs();
 // C_l = sum_r W[l][r] P_r for the P x P blocks of side m of C (leading
 // dimension ldc), in ascending r: wl_ptr / wl_ent list, per block l, the
 // products (r, coefficient) in ascending r.  Also sets the ordering counters

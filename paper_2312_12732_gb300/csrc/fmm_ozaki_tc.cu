@@ -17,8 +17,8 @@
 //                D_g with tcgen05.ld, folds it into 64 int64 registers while
 //                later groups accumulate, converts to FP64 and stores the tile
 //                of P_r.
-//   ozaki_tc_pair_kernel<CL> (CTA pairs, tcgen05 cta_group::2; clusters of one
-//     pair or of two pairs sharing their left-slice tiles by TMA multicast, the
+//   ozaki_tc_pair_kernel (CTA pairs, tcgen05 cta_group::2; clusters of one
+//     pair or of two pairs sharing their left-slice tiles by TMA multicast; the
 //     default) described above the kernel.
 //
 // ozaki_postadd_kernel then forms C_l = sum_r W[l][r] P_r in ascending r.
@@ -492,6 +492,11 @@ __device__ __forceinline__ uint32_t cluster_rank() {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
 }
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
 __device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
     uint32_t r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
@@ -606,14 +611,18 @@ struct __align__(8) PairBars {
     int abort;
 };
 
-// Slice GEMM on CTA pairs; CL = 2 (one pair per cluster) or 4 (two pairs
-// that share their left-slice tiles).  A task is product r, the tile-row
-// pair tp and CL / 2 adjacent tile columns; CTA (pair pc, rank-in-pair rp)
-// owns tile row ti = 2 tp + rp of tile column tj = (CL / 2) tj2 + pc.  With
-// CL = 4 each CTA loads half of its A box and multicasts it to the CTA with
-// the same rp in the other pair, which cuts each SM's L2 requests per stage
-// from 24 to 16 KB; the two pairs then run in lock-step, each stage being
-// released by both pairs' MMA threads.
+// Slice GEMM on CTA pairs, in clusters of CL = 2 (one pair) or 4 CTAs (two
+// pairs that share their left-slice tiles); the cluster size is read at run
+// time, so one launch can mix both (a preferred size of 4 where the GPU's
+// partitions allow it, pairs on the SMs left over).  A task is product r, the
+// tile-row pair tp and two adjacent tile columns 2 tj2, 2 tj2 + 1.  CTA (pair
+// pc, rank-in-pair rp) owns tile row ti = 2 tp + rp; in a cluster of 4 pair
+// pc takes column 2 tj2 + pc, a lone pair takes both columns one after the
+// other (the task is published as two items).  With CL = 4 each CTA loads
+// half of its A box and multicasts it to the CTA with the same rp in the
+// other pair, which cuts each SM's L2 requests per stage from 24 to 16 KB;
+// the two pairs then run in lock-step, each stage being released by both
+// pairs' MMA threads.
 // Each CTA streams its 128 rows of the left slices and its 64-row half of the
 // right slices; the leader's MMA threads issue 256 x 128 x 32 MMAs (tcgen05
 // cta_group::2) that read both CTAs' shared memory and accumulate into both
@@ -635,12 +644,12 @@ struct __align__(8) PairBars {
 //   tfull/tempty task ring: ring 0's producer in the leader fetches tasks and
 //                publishes them to both CTAs; every other role of both CTAs
 //                releases the slot on the leader's tempty.
-template <int CL>
 __global__ void __launch_bounds__(P_NTHREADS, 1)
-    ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_bh,
-                         const __grid_constant__ OzParams P) {
-    static_assert(CL == 2 || CL == 4, "clusters of one or two CTA pairs");
-    constexpr int NPAIR = CL / 2;
+    ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_ah,
+                         const __grid_constant__ CUtensorMap map_bh, const __grid_constant__ OzParams P) {
+    const int CL = (int)cluster_nctarank();  // 2 or 4
+    const int NPAIR = CL / 2;
+    const CUtensorMap *amap = CL == 4 ? &map_ah : &map_a;  // 64-row A boxes when the halves are shared
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
     unsigned char *stage_mem = base;  // NRING x RSTAGES x (A 32 KB, B half 16 KB)
@@ -656,7 +665,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
     const unsigned short pair_mask = (unsigned short)(3u << pair_lead);
     const unsigned short all_mask = (unsigned short)((1u << CL) - 1u);
     const int pairs_m = (P.tiles_m + 1) / 2;
-    const int tn2 = (P.tiles_n + NPAIR - 1) / NPAIR;
+    const int tn2 = (P.tiles_n + 1) / 2;
     const int ptiles = pairs_m * tn2;
     const int nbox = P.Kp / BOX;
     const int nkb = (nbox + P_KBOX - 1) / P_KBOX;
@@ -707,27 +716,33 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
         // ------------------------------------------------------------ producer of ring q (both CTAs)
         const int q = warp;
         if (lane == 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(&map_a) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(amap) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(&map_bh) : "memory");
             uint32_t stage = 0, sphase = 0;
             int tslot = 0, tseq = 0;
             uint32_t tphase = 0;
             bool issued = false;
+            long long pending = -1;  // a lone pair's second item of the current task
             while (!*abort) {
-                long long task;
+                long long item;  // 2 task + column offset (a lone pair's second column)
                 if (fetcher && q == 0) {
-                    task = (long long)atomicAdd(P.task_counter, 1ull);
-                    if (ld_volatile(P.error) != kDevOk) task = P.tasks;
+                    if (pending >= 0) {
+                        item = pending;
+                        pending = -1;
+                    } else {
+                        long long task = (long long)atomicAdd(P.task_counter, 1ull);
+                        if (ld_volatile(P.error) != kDevOk || task > P.tasks) task = P.tasks;
+                        item = 2 * task;
+                        if (CL == 2 && task < P.tasks && 2 * ((task % ptiles) % tn2) + 1 < P.tiles_n) pending = item + 1;
+                    }
                     if (!mbar_wait_cl(&B.tempty[tslot], tphase ^ 1u, abort, P.error, P.timeout_ns)) break;
-                    B.task[tslot] = task;
-#pragma unroll
-                    for (int c = 1; c < CL; ++c) st_cluster_s64(mapa(su32(&B.task[tslot]), c), task);
+                    B.task[tslot] = item;
+                    for (int c = 1; c < CL; ++c) st_cluster_s64(mapa(su32(&B.task[tslot]), c), item);
                     mbar_arrive(&B.tfull[tslot]);
-#pragma unroll
                     for (int c = 1; c < CL; ++c) arrive_remote_release(mapa(su32(&B.tfull[tslot]), c));
                 } else {
                     if (!mbar_wait_cl(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
-                    task = B.task[tslot];
+                    item = B.task[tslot];
                     if (fetcher) mbar_arrive(&B.tempty[tslot]);
                     else arrive_remote_release(mapa(su32(&B.tempty[tslot]), 0));
                 }
@@ -735,11 +750,12 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                     tslot = 0;
                     tphase ^= 1u;
                 }
+                const long long task = item >> 1;
                 if (task >= P.tasks) break;
                 const int r = (int)(task / ptiles);
                 const int t2 = (int)(task - (long long)r * ptiles);
                 const int tp = t2 / tn2;
-                const int tj = NPAIR * (t2 - tp * tn2) + pc;
+                const int tj = 2 * (t2 - tp * tn2) + (CL == 4 ? pc : (int)(item & 1));
                 const int ti = 2 * tp + rp;
                 bool ok = true;
                 for (int g = 2; g <= s + 1 && ok; ++g) {
@@ -760,10 +776,10 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                             for (int bx = 0; bx < boxes; ++bx) {
                                 const int x = (kb * P_KBOX + bx) * BOX;
                                 if (CL == 4)  // my 64-row half of the A box, to both CTAs holding tile row ti
-                                    tma_load_2d_pair_mc(sa + bx * TM * BOX + pc * TNH * BOX, &map_a, x, ya + pc * TNH,
+                                    tma_load_2d_pair_mc(sa + bx * TM * BOX + pc * TNH * BOX, amap, x, ya + pc * TNH,
                                                         full_lead, (unsigned short)((1u << rp) | (1u << (2 + rp))));
                                 else
-                                    tma_load_2d_pair(sa + bx * TM * BOX, &map_a, x, ya, full_lead);
+                                    tma_load_2d_pair(sa + bx * TM * BOX, amap, x, ya, full_lead);
                                 tma_load_2d_pair(sb + bx * TNH * BOX, &map_bh, x, yb, full_lead);
                             }
                             issued = true;
@@ -795,7 +811,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
             bool any = false;
             while (!*abort) {
                 if (!mbar_wait_cl(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
-                const long long task = B.task[tslot];
+                const long long task = B.task[tslot] >> 1;
                 if (fetcher) mbar_arrive(&B.tempty[tslot]);
                 else arrive_remote_release(mapa(su32(&B.tempty[tslot]), 0));
                 if (++tslot == TASK_RING) {
@@ -862,7 +878,8 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
         uint32_t tphase = 0;
         while (!*abort) {
             if (!mbar_wait_cl(&B.tfull[tslot], tphase, abort, P.error, P.timeout_ns)) break;
-            const long long task = B.task[tslot];
+            const long long item = B.task[tslot];
+            const long long task = item >> 1;
             __syncwarp();
             if (lane == 0) {
                 if (fetcher) mbar_arrive(&B.tempty[tslot]);
@@ -876,7 +893,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
             const int r = (int)(task / ptiles);
             const int t2 = (int)(task - (long long)r * ptiles);
             const int tp = t2 / tn2;
-            const int tj = NPAIR * (t2 - tp * tn2) + pc;
+            const int tj = 2 * (t2 - tp * tn2) + (CL == 4 ? pc : (int)(item & 1));
             const int ti = 2 * tp + rp;
             if (!epilogue_tile<P_EPI_WARP0>(P, B.accfull, abort, tmem, r, ti, tj, ti < P.tiles_m && tj < P.tiles_n,
                                             tseq * s, [&](uint32_t b) {
@@ -995,66 +1012,64 @@ cudaError_t launch_ozaki_tc(const CUtensorMap &map_a, const CUtensorMap &map_b, 
 }
 
 namespace {
-template <int CL>
-cudaLaunchConfig_t pair_config(cudaLaunchAttribute *at, int clusters, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CL;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)(CL * clusters));
-    cfg.blockDim = dim3(P_NTHREADS);
-    cfg.dynamicSmemBytes = kPairSmemBytes;
-    cfg.stream = s;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cfg;
-}
-
-template <int CL>
 bool pair_attr() {
     static int state = 0;  // 0 unset, 1 ok, -1 failed
     if (state == 0)
-        state = cudaFuncSetAttribute(ozaki_tc_pair_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        state = cudaFuncSetAttribute(ozaki_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kPairSmemBytes) == cudaSuccess ? 1 : -1;
     if (state < 0) cudaGetLastError();
     return state > 0;
 }
 
-template <int CL>
-int max_clusters() {
+// clusters of `cl` CTAs, or (preferred_cl = 4) clusters of 4 where possible and of cl elsewhere
+cudaLaunchConfig_t pair_config(cudaLaunchAttribute *at, int ctas, int cl, int preferred_cl, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.numAttrs = 1;
+    if (preferred_cl > cl) {
+        at[1].id = cudaLaunchAttributePreferredClusterDimension;
+        at[1].val.preferredClusterDim.x = preferred_cl;
+        at[1].val.preferredClusterDim.y = 1;
+        at[1].val.preferredClusterDim.z = 1;
+        cfg.numAttrs = 2;
+    }
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3(P_NTHREADS);
+    cfg.dynamicSmemBytes = kPairSmemBytes;
+    cfg.stream = s;
+    cfg.attrs = at;
+    return cfg;
+}
+}  // namespace
+
+cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_ah, const CUtensorMap &map_bh,
+                                 const OzParams &P, int ctas, int cluster_ctas, cudaStream_t s) {
+    if (!pair_attr()) return cudaErrorInvalidValue;
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg = pair_config(at, ctas, 2, cluster_ctas, s);
+    return cudaLaunchKernelEx(&cfg, ozaki_tc_pair_kernel, map_a, map_ah, map_bh, P);
+}
+
+int ozaki_tc_max_pairs() {
     static int cached = -1;
     if (cached >= 0) return cached;
-    if (!pair_attr<CL>()) return 0;
+    if (!pair_attr()) return 0;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaLaunchAttribute at[1];
-    cudaLaunchConfig_t cfg = pair_config<CL>(at, sms / CL, nullptr);
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg = pair_config(at, sms / 2 * 2, 2, 2, nullptr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, ozaki_tc_pair_kernel<CL>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, ozaki_tc_pair_kernel, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     cached = n;
     return n;
 }
-}  // namespace
-
-cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_bh, const OzParams &P,
-                                 int clusters, int cluster_ctas, cudaStream_t s) {
-    cudaLaunchAttribute at[1];
-    if (cluster_ctas == 4) {
-        if (!pair_attr<4>()) return cudaErrorInvalidValue;
-        cudaLaunchConfig_t cfg = pair_config<4>(at, clusters, s);
-        return cudaLaunchKernelEx(&cfg, ozaki_tc_pair_kernel<4>, map_a, map_bh, P);
-    }
-    if (!pair_attr<2>()) return cudaErrorInvalidValue;
-    cudaLaunchConfig_t cfg = pair_config<2>(at, clusters, s);
-    return cudaLaunchKernelEx(&cfg, ozaki_tc_pair_kernel<2>, map_a, map_bh, P);
-}
-
-int ozaki_tc_max_clusters(int cluster_ctas) { return cluster_ctas == 4 ? max_clusters<4>() : max_clusters<2>(); }
 
 cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
                                  double *C, long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
