@@ -14,6 +14,10 @@ Functions (each follows the passage cited in ``fmm_oracle.c``):
   `strassen`, level by level, with the peeling rule stated in the C source.
 * ``sample_dot2(A, B, rows, cols)`` -- compensated dot products (Ogita, Rump,
   Oishi 2005) for sampled reference entries.
+* ``axpby(alpha, P, beta, C)`` / ``scaled(alpha, A, B, beta, C, ...)`` -- the
+  update C = alpha A B + beta C (Section 3 states C = alpha A B; beta is the
+  BLAS extension), with beta = 0 leaving C unread and alpha = 0 leaving A B
+  unread.
 """
 from __future__ import annotations
 
@@ -59,6 +63,8 @@ def _load():
         lib.fmm_oracle_dot2.argtypes = [i64, dp, i64, dp, i64]
         lib.fmm_oracle_sample_dot2.restype = None
         lib.fmm_oracle_sample_dot2.argtypes = [i64, dp, i64, dp, i64, i64, ip64, ip64, dp]
+        lib.fmm_oracle_axpby.restype = None
+        lib.fmm_oracle_axpby.argtypes = [i64, ctypes.c_double, dp, ctypes.c_double, dp]
         _lib = lib
     return _lib
 
@@ -139,3 +145,22 @@ def sample_dot2(A, B, rows, cols) -> np.ndarray:
     _load().fmm_oracle_sample_dot2(K, _dp(A), K, _dp(B), N, rows.shape[0], rows.ctypes.data_as(ip64),
                                    cols.ctypes.data_as(ip64), _dp(out))
     return out
+
+
+def axpby(alpha: float, P, beta: float, C) -> np.ndarray:
+    """alpha * P + beta * C elementwise, in a new array; P is not read when alpha == 0
+    (it may be None) and C is not read when beta == 0."""
+    C = np.array(C, dtype=np.float64, order="C", copy=True)
+    pp = None
+    if alpha != 0.0:
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        assert P.shape == C.shape
+        pp = _dp(P)
+    _load().fmm_oracle_axpby(C.size, float(alpha), pp, float(beta), _dp(C))
+    return C
+
+
+def scaled(alpha: float, A, B, beta: float, C, p: int, U, V, W, depth: int) -> np.ndarray:
+    """alpha * bilinear(A, B, ...) + beta * C; the product is not formed when alpha == 0."""
+    P = bilinear(A, B, p, U, V, W, depth) if alpha != 0.0 else None
+    return axpby(alpha, P, beta, C)

@@ -198,6 +198,28 @@ int fmm_oracle_bilinear(int64_t n, const double *A, int64_t lda, const double *B
 }
 
 /* ------------------------------------------------------------------------- */
+/* Scaled update (Section 3 states the product as C = alpha A B; beta C is    */
+/* the usual BLAS extension of that statement).                               */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * C[t] = alpha * P[t] + beta * C[t] for t < count, each product rounded, then
+ * added.  beta == 0 leaves C unread and alpha == 0 leaves P unread (P may then
+ * be NULL), so NaN or infinity there does not reach the result.
+ */
+void fmm_oracle_axpby(int64_t count, double alpha, const double *P, double beta, double *C) {
+    for (int64_t t = 0; t < count; ++t) {
+        double x = 0.0;
+        if (alpha != 0.0) x = alpha * P[t];
+        if (beta != 0.0) {
+            double y = beta * C[t];
+            x = x + y;
+        }
+        C[t] = x;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Compensated dot products for sampled reference entries.                    */
 /* Ogita, Rump, Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.    */
 /* 26(6), 2005: TwoSum (Knuth), TwoProduct via FMA, and Dot2 (their Alg. 5.3). */

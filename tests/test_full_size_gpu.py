@@ -68,3 +68,34 @@ def test_peeled_full_sizes(fmm, oracle_mod, n, depth):
     assert np.array_equal(got, ref)
     got, ref, scale = sampled(fmm, oracle_mod, n, "strassen", depth, "normal", seed=9)
     assert np.max(np.abs(got - ref)) / (n * scale) <= tol(depth)
+
+
+@pytest.mark.parametrize("phi", [4, 8])
+def test_wide_range_emulated_leaf_at_full_size(fmm, oracle_mod, phi):
+    """Entries uniform[-1,1] * 10^U(-phi, phi) at n = 8192, Strassen depth 2: the emulated leaf stays
+    within the depth's tolerance and within 2x the FP64 path's error on the same sampled entries."""
+    n = 8192
+    algo = fmm.fmm_algo_builtin("strassen")
+    A, B = inputs.operands(n, "wide", seed=13, phi=phi)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    rows, cols = inputs.sample_indices(n, 4096, seed=21)
+    r_t, c_t = torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()
+    ref = oracle_mod.sample_dot2(A, B, rows, cols)
+    scale = n * float(np.abs(A).max() * np.abs(B).max())
+    errs = {}
+    for dtype in ("f64_ozaki", "f64"):
+        plan = fmm.fmm_plan_create(n, algo, 2, dtype=dtype)
+        dC = torch.full_like(dA, float("nan"))
+        fmm.fmm_gemm(plan, dA, dB, dC)
+        assert fmm.fmm_sync_status(plan) == 0
+        errs[dtype] = float(np.max(np.abs(dC[r_t, c_t].cpu().numpy() - ref))) / scale
+        del dC, plan
+        torch.cuda.empty_cache()
+    assert errs["f64_ozaki"] <= 1e-13
+    assert errs["f64_ozaki"] <= 2.0 * errs["f64"], errs
+
+
+def test_default_workload_normal_entries(fmm, oracle_mod):
+    """The default benchmark workload (<4,4,4;49> depth 2, n = 8192) on N(0,1) entries."""
+    got, ref, scale = sampled(fmm, oracle_mod, 8192, "strassen^2", 2, "normal", seed=17)
+    assert np.max(np.abs(got - ref)) / (8192 * scale) <= 1e-13

@@ -258,3 +258,45 @@ def test_sample_dot2_matches_classic_indices(oracle_mod):
     rows, cols = inputs.sample_indices(25, 100, seed=3)
     rows = rows % 30
     assert np.array_equal(oracle_mod.sample_dot2(A, B, rows, cols), (A @ B)[rows, cols])
+
+
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (2.0, -3.0), (-1.0, 1.0), (0.0, 5.0), (3.0, 0.0), (0.0, 0.0)])
+def test_scaled_update_exact_on_integers(oracle_mod, alpha, beta):
+    """alpha A B + beta C on integer inputs and small integer scalars equals the same
+    expression in exact int64 arithmetic (numpy integer matmul), at a peeled size."""
+    p, U, V, W = algos.paper_strassen()
+    n = 37
+    A, B = inputs.operands(n, "integer", seed=5)
+    C0 = inputs.matrix(n, "integer", seed=8)
+    ref = (int(alpha) * (A.astype(np.int64) @ B.astype(np.int64)) + int(beta) * C0.astype(np.int64))
+    got = oracle_mod.scaled(alpha, A, B, beta, C0, p, U, V, W, 2)
+    assert np.array_equal(got, ref.astype(np.float64))
+
+
+def test_scaled_update_does_not_read_what_is_scaled_by_zero(oracle_mod):
+    """beta = 0 ignores NaN in C; alpha = 0 ignores NaN in A (BLAS convention)."""
+    p, U, V, W = algos.paper_strassen()
+    A, B = inputs.operands(8, "integer", seed=6)
+    C0 = np.full((8, 8), np.nan)
+    assert np.array_equal(oracle_mod.scaled(2.0, A, B, 0.0, C0, p, U, V, W, 1), 2.0 * (A @ B))
+    A_nan = A.copy()
+    A_nan[3, 4] = np.nan
+    C1 = inputs.matrix(8, "integer", seed=9)
+    assert np.array_equal(oracle_mod.scaled(0.0, A_nan, B, -2.0, C1, p, U, V, W, 1), -2.0 * C1)
+    assert np.array_equal(oracle_mod.scaled(0.0, A_nan, B, 0.0, C0, p, U, V, W, 1), np.zeros((8, 8)))
+
+
+def test_scaled_update_rounds_each_term_once(oracle_mod):
+    """Real scalars: every entry is fl(fl(alpha p) + fl(beta c)), checked against exact
+    rational arithmetic on a few entries (error at most one rounding of the sum plus one of
+    each product, i.e. within 3 ulps of the exact value scaled by the terms)."""
+    rng = np.random.default_rng(11)
+    P = rng.standard_normal(64)
+    C = rng.standard_normal(64)
+    alpha, beta = 0.7, -1.3
+    got = oracle_mod.axpby(alpha, P, beta, C)
+    for t in range(64):
+        exact = Fraction(alpha) * Fraction(P[t]) + Fraction(beta) * Fraction(C[t])
+        bound = Fraction(3 * 2.0 ** -53) * (abs(Fraction(alpha) * Fraction(P[t])) + abs(Fraction(beta) * Fraction(C[t])))
+        assert abs(Fraction(got[t]) - exact) <= bound
+    assert not np.array_equal(oracle_mod.axpby(beta, P, alpha, C), got)  # the roles are not symmetric
