@@ -9,6 +9,9 @@ arrays.
 Functions (each follows the passage cited in ``fmm_oracle.c``):
 
 * ``brent_mismatches(p, U, V, W)`` -- exact Brent-equation check, Section 2.
+* ``brent_mismatches_rational(p, U, V, W, dens)`` / ``bilinear_rational(...)`` --
+  the same for coefficients U / den_u, V / den_v, W / den_w (Section 2: the
+  coefficients need not be integers).
 * ``classic(A, B)`` -- textbook triple loop, ascending k (Section 2).
 * ``bilinear(A, B, p, U, V, W, depth)`` -- recursive evaluation of equation
   `strassen`, level by level, with the peeling rule stated in the C source.
@@ -59,6 +62,11 @@ def _load():
         lib.fmm_oracle_bilinear.restype = ctypes.c_int
         lib.fmm_oracle_bilinear.argtypes = [i64, dp, i64, dp, i64, dp, i64, i32, i32, ip32, ip32,
                                             ip32, i32]
+        lib.fmm_oracle_brent_mismatches_rational.restype = i64
+        lib.fmm_oracle_brent_mismatches_rational.argtypes = [i32, i32, ip32, ip32, ip32, i32, i32, i32]
+        lib.fmm_oracle_bilinear_rational.restype = ctypes.c_int
+        lib.fmm_oracle_bilinear_rational.argtypes = [i64, dp, i64, dp, i64, dp, i64, i32, i32, ip32, ip32,
+                                                     ip32, i32, i32, i32, i32]
         lib.fmm_oracle_dot2.restype = ctypes.c_double
         lib.fmm_oracle_dot2.argtypes = [i64, dp, i64, dp, i64]
         lib.fmm_oracle_sample_dot2.restype = None
@@ -117,6 +125,30 @@ def bilinear(A, B, p: int, U, V, W, depth: int) -> np.ndarray:
     C = np.empty((n, n), dtype=np.float64)
     rc = _load().fmm_oracle_bilinear(n, _dp(A), n, _dp(B), n, _dp(C), n, p, R, _ip32(U), _ip32(V),
                                      _ip32(W), depth)
+    if rc != 0:
+        raise MemoryError("oracle: temporary allocation failed")
+    return C
+
+
+def brent_mismatches_rational(p: int, U, V, W, dens) -> int:
+    """Number of failed Brent equations of the rational algorithm (U / du, V / dv, W / dw)."""
+    U, V, W, R = _alg(p, U, V, W)
+    du, dv, dw = (int(d) for d in dens)
+    return int(_load().fmm_oracle_brent_mismatches_rational(p, R, _ip32(U), _ip32(V), _ip32(W), du, dv, dw))
+
+
+def bilinear_rational(A, B, p: int, U, V, W, dens, depth: int) -> np.ndarray:
+    """C = A B by `depth` recursive levels of the rational algorithm (U / du, V / dv, W / dw)."""
+    A, B = _mat(A), _mat(B)
+    n = A.shape[0]
+    assert A.shape == (n, n) and B.shape == (n, n)
+    U, V, W, R = _alg(p, U, V, W)
+    du, dv, dw = (int(d) for d in dens)
+    C = np.empty((n, n), dtype=np.float64)
+    rc = _load().fmm_oracle_bilinear_rational(n, _dp(A), n, _dp(B), n, _dp(C), n, p, R, _ip32(U), _ip32(V),
+                                              _ip32(W), du, dv, dw, depth)
+    if rc == -2:
+        raise ValueError("oracle: denominators must be positive")
     if rc != 0:
         raise MemoryError("oracle: temporary allocation failed")
     return C

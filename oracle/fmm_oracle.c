@@ -44,8 +44,27 @@
  * Sums are taken in int64, so the check is exact for any coefficients that
  * fit in int32 and any R below 2^31 / max|coefficient|^3.
  */
+int64_t fmm_oracle_brent_mismatches_rational(int p, int R, const int32_t *U, const int32_t *V,
+                                             const int32_t *W, int32_t den_u, int32_t den_v, int32_t den_w);
+
 int64_t fmm_oracle_brent_mismatches(int p, int R, const int32_t *U, const int32_t *V,
                                     const int32_t *W) {
+    return fmm_oracle_brent_mismatches_rational(p, R, U, V, W, 1, 1, 1);
+}
+
+/*
+ * Brent equations for rational coefficients U / den_u, V / den_v, W / den_w:
+ * multiplied through by den_u den_v den_w they read
+ *     sum_r U[(i,j)][r] V[(j2,k)][r] W[(i2,k2)][r]
+ *         = den_u den_v den_w delta(j, j2) delta(i, i2) delta(k, k2),
+ * an identity of integers, counted here in int64 (exact while R times the
+ * largest |U V W| and the denominators' product stay below 2^63; the callers'
+ * tables are far below).  Returns -1 for a denominator below 1.
+ */
+int64_t fmm_oracle_brent_mismatches_rational(int p, int R, const int32_t *U, const int32_t *V,
+                                             const int32_t *W, int32_t den_u, int32_t den_v, int32_t den_w) {
+    if (den_u < 1 || den_v < 1 || den_w < 1) return -1;
+    const int64_t one = (int64_t)den_u * den_v * den_w;
     int64_t bad = 0;
     for (int i = 0; i < p; ++i)
         for (int j = 0; j < p; ++j)
@@ -58,7 +77,7 @@ int64_t fmm_oracle_brent_mismatches(int p, int R, const int32_t *U, const int32_
                             const int32_t *w = W + (int64_t)(i2 * p + k2) * R;
                             int64_t s = 0;
                             for (int r = 0; r < R; ++r) s += (int64_t)u[r] * v[r] * w[r];
-                            int64_t want = (j == j2 && i == i2 && k == k2) ? 1 : 0;
+                            int64_t want = (j == j2 && i == i2 && k == k2) ? one : 0;
                             if (s != want) ++bad;
                         }
     return bad;
@@ -95,26 +114,34 @@ void fmm_oracle_classic(int64_t M, int64_t N, int64_t K, const double *A, int64_
 /* split factors).                                                             */
 /* ------------------------------------------------------------------------- */
 
+/* Coefficients are U[i][r] / den_u and so on (Section 2: they need not be
+ * integers); integer algorithms have every denominator 1. */
 typedef struct {
     int p, R;
     const int32_t *U, *V, *W;
+    int32_t den_u, den_v, den_w;
 } oracle_alg;
 
-/* dst[0:m,0:m] (ld m) = sum_i coef[i][r] * src block i, ascending i. */
-static void combine_blocks(int64_t m, int p, int R, const int32_t *coef, int r, const double *src,
+/* The coefficient c / den as a binary64 number (exact when den is a power of
+ * two and c is small; otherwise the nearest double), and whether it is +1 or
+ * -1, where the oracle adds or subtracts instead of multiplying. */
+static double coef_value(int32_t c, int32_t den) { return den == 1 ? (double)c : (double)c / (double)den; }
+
+/* dst[0:m,0:m] (ld m) = sum_i (coef[i][r] / den) * src block i, ascending i. */
+static void combine_blocks(int64_t m, int p, int R, const int32_t *coef, int32_t den, int r, const double *src,
                            int64_t ld, double *dst) {
     for (int64_t x = 0; x < m * m; ++x) dst[x] = 0.0;
     for (int i = 0; i < p * p; ++i) {
         const int32_t c = coef[(int64_t)i * R + r];
         if (c == 0) continue;
         const double *blk = src + (int64_t)(i / p) * m * ld + (int64_t)(i % p) * m;
-        const double cd = (double)c;
+        const double cd = coef_value(c, den);
         for (int64_t y = 0; y < m; ++y)
             for (int64_t x = 0; x < m; ++x) {
                 const double a = blk[y * ld + x];
-                if (c == 1)
+                if (cd == 1.0)
                     dst[y * m + x] += a;
-                else if (c == -1)
+                else if (cd == -1.0)
                     dst[y * m + x] -= a;
                 else
                     dst[y * m + x] += cd * a;
@@ -148,8 +175,8 @@ static int bilinear_rec(int64_t n, const double *A, int64_t lda, const double *B
     int rc = 0;
     for (int r = 0; r < R && rc == 0; ++r) {
         /* S_r = sum_i U[i][r] A_i,  T_r = sum_j V[j][r] B_j */
-        combine_blocks(m, p, R, alg->U, r, A, lda, S);
-        combine_blocks(m, p, R, alg->V, r, B, ldb, T);
+        combine_blocks(m, p, R, alg->U, alg->den_u, r, A, lda, S);
+        combine_blocks(m, p, R, alg->V, alg->den_v, r, B, ldb, T);
         /* P_r = S_r T_r, itself by the same algorithm one level down */
         rc = bilinear_rec(m, S, m, T, m, Pr, m, alg, depth - 1);
         /* C_l += W[l][r] P_r for every l (so each C_l sums in ascending r) */
@@ -157,13 +184,13 @@ static int bilinear_rec(int64_t n, const double *A, int64_t lda, const double *B
             const int32_t w = alg->W[(int64_t)l * R + r];
             if (w == 0) continue;
             double *cb = C + (int64_t)(l / p) * m * ldc + (int64_t)(l % p) * m;
-            const double wd = (double)w;
+            const double wd = coef_value(w, alg->den_w);
             for (int64_t y = 0; y < m; ++y)
                 for (int64_t x = 0; x < m; ++x) {
                     const double v = Pr[y * m + x];
-                    if (w == 1)
+                    if (wd == 1.0)
                         cb[y * ldc + x] += v;
-                    else if (w == -1)
+                    else if (wd == -1.0)
                         cb[y * ldc + x] -= v;
                     else
                         cb[y * ldc + x] += wd * v;
@@ -193,7 +220,22 @@ static int bilinear_rec(int64_t n, const double *A, int64_t lda, const double *B
 int fmm_oracle_bilinear(int64_t n, const double *A, int64_t lda, const double *B, int64_t ldb,
                         double *C, int64_t ldc, int p, int R, const int32_t *U, const int32_t *V,
                         const int32_t *W, int depth) {
-    oracle_alg alg = {p, R, U, V, W};
+    oracle_alg alg = {p, R, U, V, W, 1, 1, 1};
+    return bilinear_rec(n, A, lda, B, ldb, C, ldc, &alg, depth);
+}
+
+/*
+ * The same recursion for an algorithm with rational coefficients U / den_u,
+ * V / den_v, W / den_w (int32 numerators, positive denominators): every
+ * coefficient is applied where it stands, as the binary64 value of its
+ * fraction.  Returns 0, -1 if a temporary could not be allocated, -2 for a
+ * denominator below 1.
+ */
+int fmm_oracle_bilinear_rational(int64_t n, const double *A, int64_t lda, const double *B, int64_t ldb,
+                                 double *C, int64_t ldc, int p, int R, const int32_t *U, const int32_t *V,
+                                 const int32_t *W, int32_t den_u, int32_t den_v, int32_t den_w, int depth) {
+    if (den_u < 1 || den_v < 1 || den_w < 1) return -2;
+    oracle_alg alg = {p, R, U, V, W, den_u, den_v, den_w};
     return bilinear_rec(n, A, lda, B, ldb, C, ldc, &alg, depth);
 }
 

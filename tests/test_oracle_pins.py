@@ -300,3 +300,98 @@ def test_scaled_update_rounds_each_term_once(oracle_mod):
         bound = Fraction(3 * 2.0 ** -53) * (abs(Fraction(alpha) * Fraction(P[t])) + abs(Fraction(beta) * Fraction(C[t])))
         assert abs(Fraction(got[t]) - exact) <= bound
     assert not np.array_equal(oracle_mod.axpby(beta, P, alpha, C), got)  # the roles are not symmetric
+
+
+# --- rational coefficients (Section 2: the coefficients need not be integers) ---------------
+
+from golden import rational_algos  # noqa: E402
+
+RATIONAL = {"dyadic": rational_algos.strassen_dyadic, "thirds": rational_algos.strassen_thirds,
+            "halved": rational_algos.strassen_halved}
+
+
+@pytest.mark.parametrize("name", list(RATIONAL))
+def test_rational_brent_accepts_derived_algorithms_and_needs_the_denominators(oracle_mod, name):
+    p, U, V, W, dens = RATIONAL[name]()
+    assert oracle_mod.brent_mismatches_rational(p, U, V, W, dens) == 0
+    assert oracle_mod.brent_mismatches(p, U, V, W) > 0  # the numerators alone are not an algorithm
+    du, dv, dw = dens
+    assert oracle_mod.brent_mismatches_rational(p, U, V, W, (du * 2, dv, dw)) > 0
+
+
+@pytest.mark.parametrize("name", ["dyadic", "thirds"])
+def test_rational_brent_rejects_every_single_entry_change(oracle_mod, name):
+    p, U, V, W, dens = RATIONAL[name]()
+    for M in (U, V, W):
+        for idx in zip(*np.nonzero(M)):
+            M[idx] += 1
+            assert oracle_mod.brent_mismatches_rational(p, U, V, W, dens) > 0
+            M[idx] -= 1
+
+
+def test_rational_brent_with_unit_denominators_is_the_integer_check(oracle_mod):
+    for name in ("paper_strassen", "winograd", "laderman"):
+        p, U, V, W = all_algos()[name]
+        assert oracle_mod.brent_mismatches_rational(p, U, V, W, (1, 1, 1)) == oracle_mod.brent_mismatches(p, U, V, W)
+    p, U, V, W = algos.paper_strassen()
+    U2 = U.copy(); U2[0, 0] += 1
+    assert oracle_mod.brent_mismatches_rational(p, U2, V, W, (1, 1, 1)) == oracle_mod.brent_mismatches(p, U2, V, W) > 0
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+def test_rational_bilinear_exhaustive_basis_pairs_dyadic(oracle_mod, depth):
+    """Power-of-two denominators: every basis pair gives the exact elementary product."""
+    p, U, V, W, dens = rational_algos.strassen_dyadic()
+    n = p ** depth
+    for i, j, k, l in itertools.product(range(n), repeat=4):
+        C = oracle_mod.bilinear_rational(_basis(n, i, j), _basis(n, k, l), p, U, V, W, dens, depth)
+        want = _basis(n, i, l) if j == k else np.zeros((n, n))
+        assert np.array_equal(C, want), (i, j, k, l)
+
+
+def test_rational_bilinear_basis_pairs_thirds_within_rounding(oracle_mod):
+    """Denominators 3 and 9: the coefficients are rounded, so basis pairs come out within a few
+    ulps of the exact elementary product (and not exactly, which shows the fractions are used)."""
+    p, U, V, W, dens = rational_algos.strassen_thirds()
+    worst = 0.0
+    for i, j, k, l in itertools.product(range(2), repeat=4):
+        C = oracle_mod.bilinear_rational(_basis(2, i, j), _basis(2, k, l), p, U, V, W, dens, 1)
+        want = _basis(2, i, l) if j == k else np.zeros((2, 2))
+        worst = max(worst, float(np.max(np.abs(C - want))))
+    assert 0.0 < worst < 64 * 2.0 ** -53
+
+
+@pytest.mark.parametrize("n,depth", [(16, 1), (37, 2), (64, 3), (101, 2)])
+def test_rational_bilinear_bit_exact_on_integers_dyadic(oracle_mod, n, depth):
+    p, U, V, W, dens = rational_algos.strassen_dyadic()
+    A, B = inputs.operands(n, "integer", seed=n + depth)
+    assert np.array_equal(oracle_mod.bilinear_rational(A, B, p, U, V, W, dens, depth), A @ B)
+    p, U, V, W, dens = rational_algos.strassen_halved()
+    assert np.array_equal(oracle_mod.bilinear_rational(A, B, p, U, V, W, dens, depth), A @ B)
+
+
+def test_rational_bilinear_with_unit_denominators_equals_integer_bilinear(oracle_mod):
+    p, U, V, W = all_algos()["laderman"]
+    A, B = inputs.operands(81, "uniform", seed=3)
+    assert np.array_equal(oracle_mod.bilinear_rational(A, B, p, U, V, W, (1, 1, 1), 2),
+                          oracle_mod.bilinear(A, B, p, U, V, W, 2))
+
+
+def test_rational_bilinear_thirds_real_inputs_within_tolerance(oracle_mod):
+    p, U, V, W, dens = rational_algos.strassen_thirds()
+    n = 256
+    A, B = inputs.operands(n, "uniform", seed=23)
+    rows, cols = inputs.sample_indices(n, 2048, seed=7)
+    ref = oracle_mod.sample_dot2(A, B, rows, cols)
+    for depth in (1, 2):
+        C = oracle_mod.bilinear_rational(A, B, p, U, V, W, dens, depth)
+        assert np.max(np.abs(C[rows, cols] - ref)) / (n * np.abs(A).max() * np.abs(B).max()) <= 1e-13
+
+
+def test_rational_planted_denominator_mistake_is_detected(oracle_mod):
+    """Dropping a denominator (den_w = 1 instead of 2) scales the result and breaks exactness."""
+    p, U, V, W, (du, dv, dw) = rational_algos.strassen_dyadic()
+    A, B = inputs.operands(8, "integer", seed=2)
+    assert not np.array_equal(oracle_mod.bilinear_rational(A, B, p, U, V, W, (du, dv, 1), 1), A @ B)
+    with pytest.raises(ValueError):
+        oracle_mod.bilinear_rational(A, B, p, U, V, W, (0, dv, dw), 1)
