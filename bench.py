@@ -290,6 +290,12 @@ def run_reference(a):
 def make_algo(fmm, name):
     if name.endswith("^2"):
         return fmm.algorithm(name[:-2], 2)
+    if name in ("strassen_dyadic", "strassen_thirds"):
+        # Strassen in a basis with non-integer coefficients (exact change of basis, test fixture)
+        from tests.golden import rational_algos
+
+        p, U, V, W, dens = getattr(rational_algos, name)()
+        return fmm.RationalAlgo(p, U, V, W, dens, name=name)
     return fmm.fmm_algo_builtin(name)
 
 
@@ -358,6 +364,8 @@ def run_sweep(a):
                 ("strassen", 4, "auto", 0)]
     configs = [c + ("f64",) for c in configs]
     configs += [("strassen", d, "auto", 0, "f64_ozaki") for d in (0, 1, 2, 3)]
+    configs += [("strassen_dyadic", d, "auto", 0, "f64") for d in (1, 2, 3)]
+    configs += [("strassen_thirds", 2, "auto", 0, "f64"), ("strassen_dyadic", 2, "auto", 0, "f64_ozaki")]
     n = a.n
     A, B = inputs.operands(n, a.kind, seed=1)
     dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
@@ -526,14 +534,20 @@ def run_ours(a):
         fmm.fmm_gemm_host(plan, hA, hB, hC)  # allocates the plan's host-path buffers
         if dist is not None:
             dist.barrier()
-        t0 = time.perf_counter()
         k_e2e = max(2, a.steps // 2)
-        for _ in range(k_e2e):
-            fmm.fmm_gemm_host(plan, hA, hB, hC)
-        t1 = time.perf_counter()
+        dev_ms = []
+        sampler_e2e = ClockSampler(gpu_uuid(torch, dev))
+        with sampler_e2e:
+            t0 = time.perf_counter()
+            for _ in range(k_e2e):
+                fmm.fmm_gemm_host(plan, hA, hB, hC)
+                dev_ms.append(fmm.fmm_plan_last_kernel_ms(plan)[1])  # the call's device work, copies excluded
+            t1 = time.perf_counter()
         te = max_over_ranks((t1 - t0) / k_e2e, dist, dev)
         e2e = {"value": job_throughput(flops_eff, ws, te) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * n * n * 8,
                "d2h_bytes_per_step": n * n * 8, "ms_per_step": te * 1e3, "steps": k_e2e,
+               "device_ms_per_step": statistics.mean(dev_ms),
+               "clocks": sampler_e2e.summary(),
                "path": "fmm_gemm_host (pinned host buffers, copies inside the timed region)"}
 
     nc = info["n_core"]

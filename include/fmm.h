@@ -65,6 +65,20 @@ typedef struct {
     const int32_t *W;
 } fmm_algo_t;
 
+/* A bilinear algorithm <p,p,p;R> with rational coefficients (Section 2: the
+ * coefficients of a, b, c need not be integers): entry [i][r] of U is
+ * U[i*R + r] / den_u, likewise V over den_v and W over den_w.  Numerators are
+ * row-major p^2 x R int32 arrays; each denominator is one positive int32
+ * common to its matrix.  The library copies the numerators. */
+typedef struct {
+    int p;
+    int R;
+    const int32_t *U;
+    const int32_t *V;
+    const int32_t *W;
+    int32_t den_u, den_v, den_w;
+} fmm_algo_rational_t;
+
 typedef struct fmm_plan fmm_plan_t;
 
 /* How the pre-additions S_r / T_r of the recursion levels are formed.
@@ -114,6 +128,7 @@ typedef struct {
     int tile_n;             /* leaf tile width of the FP64 kernel (128 or 64) */
     int materialize_passes; /* kernel passes per operand that form the materialized S_r / T_r
                                (a level, a Kronecker factor of one, or two 2 x 2 factors fused) */
+    double coef_scale;      /* (den_u den_v den_w)^-depth for a rational plan, 1 otherwise */
 } fmm_plan_info_t;
 
 /* Status code to a static, NUL-terminated English string (never NULL). */
@@ -133,6 +148,14 @@ fmm_status_t fmm_algo_builtin(const char *name, fmm_algo_t *out);
  * in int64 (Section 2, equation `strassen` read entry-wise); 0 means the
  * algorithm multiplies exactly.  Host-only.  Returns -1 for invalid input. */
 int64_t fmm_algo_brent_mismatches(const fmm_algo_t *algo);
+
+/* The Brent equations of a rational algorithm, multiplied through by
+ * den_u den_v den_w: sum_r U V W = den_u den_v den_w delta delta delta over the
+ * numerators, exact in int64.  Returns the number of violated equations, or -1
+ * for invalid input (a NULL table, p < 2, R < 1, a denominator < 1, or
+ * numerators so large that R max|U| max|V| max|W| or the denominators'
+ * product reaches 2^62). */
+int64_t fmm_algo_rational_brent_mismatches(const fmm_algo_rational_t *algo);
 
 /* Relabel an algorithm given in the paper's printed format, where the rows of
  * c^t index the blocks of C transposed (Section 2: printed order C0, C2, C1,
@@ -160,6 +183,20 @@ fmm_status_t fmm_plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo
 fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
                                 fmm_dtype_t dtype, const fmm_plan_options_t *opts);
 
+/* A plan for a rational algorithm (opts may be NULL).  Checks the rational
+ * Brent equations (FMM_ERR_BRENT; FMM_ERR_INVALID for what
+ * fmm_algo_rational_brent_mismatches rejects), then plans the integer
+ * numerator tables as fmm_plan_create_ex does and applies the product of the
+ * denominators, (den_u den_v den_w)^-depth, once per leaf product in the
+ * post-additions (folded into alpha: w -> alpha * scale * w); the peel fix-ups
+ * of non-divisible sizes are plain products and are not scaled.  With
+ * power-of-two denominators the scale is exact, so integer-valued inputs still
+ * give exact results while every intermediate stays below 2^53.  Every call
+ * on the plan (fmm_gemm, fmm_gemm_ex, the batched calls) works as for an
+ * integer plan; fmm_plan_info_t.coef_scale reports the scale. */
+fmm_status_t fmm_plan_create_rational(fmm_plan_t **out, int64_t n, const fmm_algo_rational_t *algo, int depth,
+                                      fmm_dtype_t dtype, const fmm_plan_options_t *opts);
+
 /* C = A * B on `stream`.  A, B, C: device pointers to n x n row-major
  * binary64; C is overwritten; A and B are read only and must not overlap C.
  * Asynchronous.  Two calls on the same plan must not overlap in time (they
@@ -167,6 +204,19 @@ fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fmm_algo_t *a
  * launch fails.  Device-side wait timeouts surface at fmm_sync_status. */
 fmm_status_t fmm_gemm(const fmm_plan_t *plan, const double *A, const double *B, double *C,
                       void *stream);
+
+/* C = alpha * A * B + beta * C on `stream`: the scaled product as Section 3
+ * states it (C = alpha A B), with the BLAS beta term.  Same operands, plan
+ * rules and errors as fmm_gemm, which is alpha = 1, beta = 0.
+ *   - beta = 0: C is written without being read (NaN or Inf in C is dropped).
+ *   - alpha = 0: A and B are not read and no product runs; C = beta * C
+ *     (zeros for beta = 0), one elementwise kernel.
+ *   - otherwise every coefficient w of W is applied as alpha * w, and the first
+ *     contribution to each element of C adds it to beta * C (C read once);
+ *     the rest of the schedule, and its determinism, is that of fmm_gemm.
+ * FMM_ERR_INVALID for a NULL pointer or a non-finite alpha or beta. */
+fmm_status_t fmm_gemm_ex(const fmm_plan_t *plan, double alpha, const double *A, const double *B,
+                         double beta, double *C, void *stream);
 
 /* Same as fmm_gemm with HOST buffers: copies A and B to plan-owned device
  * buffers (allocated on first use, freed by fmm_plan_destroy), multiplies,
@@ -181,6 +231,14 @@ fmm_status_t fmm_gemm_host(fmm_plan_t *plan, const double *A_host, const double 
  * FMM_F64 and not in use by another call at the same time.  Asynchronous. */
 fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double *const *A,
                               const double *const *B, double *const *C, int count, void *stream);
+
+/* Batched C[i] = alpha[i] * A[i] * B[i] + beta[i] * C[i] with the rules of
+ * fmm_gemm_ex per product.  alpha and beta are HOST arrays of `count` values,
+ * or NULL for all ones (alpha) / all zeros (beta).  Products with alpha[i] = 0
+ * run as a scaling of C[i] before the grouped launch and are left out of it. */
+fmm_status_t fmm_gemm_batched_ex(fmm_plan_t *const *plans, const double *alpha, const double *const *A,
+                                 const double *const *B, const double *beta, double *const *C, int count,
+                                 void *stream);
 
 /* A batched multiplication captured once into a CUDA graph (the counter
  * resets, materialization passes and the one grouped leaf launch of

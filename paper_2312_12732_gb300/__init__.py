@@ -31,8 +31,11 @@ from ._binding import (  # noqa: F401
     fmm_algo_builtin,
     fmm_algo_compose,
     fmm_algo_from_transposed_c,
+    fmm_algo_rational_brent_mismatches,
+    RationalAlgo,
     fmm_gemm,
     fmm_gemm_batched,
+    fmm_gemm_ex,
     fmm_gemm_host,
     fmm_gemm_noalloc,
     fmm_plan_create,
@@ -62,13 +65,15 @@ def algorithm(name: str, power: int = 1):
 _PLANS = {}
 
 
-def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None):
-    """C = A @ B for square float64 CUDA tensors by the bilinear algorithm ``algo`` (a built-in
-    name, ``"name^k"`` for its k-th Kronecker power, or an :class:`Algo`) at recursion ``depth``.
+def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None, alpha=1.0, beta=0.0):
+    """C = alpha * A @ B + beta * out for square float64 CUDA tensors by the bilinear algorithm
+    ``algo`` (a built-in name, ``"name^k"`` for its k-th Kronecker power, or an :class:`Algo`) at
+    recursion ``depth``.
 
     The plan for (n, algorithm, depth, dtype, device) is created on first use and cached; a cached
     plan's workspace serves one call at a time, so calls on different streams that share a plan
-    must not overlap.  ``out`` (optional) receives the product; otherwise a new tensor does.
+    must not overlap.  ``out`` (optional) receives the result; otherwise a new tensor does, and
+    ``beta`` must then be 0.
     """
     import torch
 
@@ -81,13 +86,18 @@ def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None):
         key_algo = algo
     else:
         alg = algo
-        key_algo = (alg.p, alg.U.tobytes(), alg.V.tobytes(), alg.W.tobytes())
+        key_algo = (alg.p, alg.U.tobytes(), alg.V.tobytes(), alg.W.tobytes(), getattr(alg, "dens", None))
     key = (n, key_algo, depth, dtype, A.device.index)
     plan = _PLANS.get(key)
     if plan is None:
         with torch.cuda.device(A.device):
             plan = fmm_plan_create(n, alg, depth, dtype=dtype)
         _PLANS[key] = plan
+    if out is None and beta != 0.0:
+        raise ValueError("beta != 0 needs out")
     C = out if out is not None else torch.empty_like(A)
-    fmm_gemm(plan, A, B, C, stream)
+    if alpha == 1.0 and beta == 0.0:
+        fmm_gemm(plan, A, B, C, stream)
+    else:
+        fmm_gemm_ex(plan, alpha, A, B, beta, C, stream)
     return C

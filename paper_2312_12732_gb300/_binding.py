@@ -32,6 +32,11 @@ class fmm_algo_t(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("R", ctypes.c_int), ("U", _i32p), ("V", _i32p), ("W", _i32p)]
 
 
+class fmm_algo_rational_t(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("R", ctypes.c_int), ("U", _i32p), ("V", _i32p), ("W", _i32p),
+                ("den_u", ctypes.c_int32), ("den_v", ctypes.c_int32), ("den_w", ctypes.c_int32)]
+
+
 class fmm_plan_options_t(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int), ("materialize_levels", ctypes.c_int), ("ozaki_slices", ctypes.c_int),
                 ("wait_timeout_s", ctypes.c_double), ("debug_poison_chain", ctypes.c_int),
@@ -44,7 +49,7 @@ class fmm_plan_info_t(ctypes.Structure):
                 ("tasks", ctypes.c_int64), ("materialized_levels", ctypes.c_int),
                 ("flops_leaf", ctypes.c_double), ("flops_executed", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_size_t), ("ozaki_slices", ctypes.c_int), ("flops_lowp", ctypes.c_double),
-                ("tile_n", ctypes.c_int), ("materialize_passes", ctypes.c_int)]
+                ("tile_n", ctypes.c_int), ("materialize_passes", ctypes.c_int), ("coef_scale", ctypes.c_double)]
 
 
 # (name, restype, argtypes) for every symbol declared in include/fmm.h.
@@ -60,8 +65,18 @@ SIGNATURES = [
     ("fmm_plan_create_ex", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
                                           ctypes.POINTER(fmm_algo_t), ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(fmm_plan_options_t)]),
+    ("fmm_algo_rational_brent_mismatches", ctypes.c_int64, [ctypes.POINTER(fmm_algo_rational_t)]),
+    ("fmm_plan_create_rational", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                                                ctypes.POINTER(fmm_algo_rational_t), ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(fmm_plan_options_t)]),
     ("fmm_gemm", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_void_p]),
+    ("fmm_gemm_ex", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fmm_gemm_batched_ex", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.c_int, ctypes.c_void_p]),
     ("fmm_gemm_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p]),
     ("fmm_gemm_batched", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -144,6 +159,37 @@ class Algo:
         return f"Algo({self.name}, <{self.p},{self.p},{self.p};{self.R}>)"
 
 
+class RationalAlgo:
+    """An algorithm <p,p,p;R> with coefficients U / den_u, V / den_v, W / den_w (int32 numerators,
+    one positive denominator per matrix); keeps the numerator tables alive for the C struct."""
+
+    def __init__(self, p: int, U, V, W, dens, name: str = "rational"):
+        self.p = int(p)
+        self.U = np.ascontiguousarray(U, dtype=np.int32)
+        self.V = np.ascontiguousarray(V, dtype=np.int32)
+        self.W = np.ascontiguousarray(W, dtype=np.int32)
+        if not (self.U.shape == self.V.shape == self.W.shape and self.U.ndim == 2
+                and self.U.shape[0] == self.p * self.p):
+            raise ValueError("U, V, W must all be p^2 x R")
+        self.R = int(self.U.shape[1])
+        self.dens = tuple(int(d) for d in dens)
+        if len(self.dens) != 3:
+            raise ValueError("dens must be (den_u, den_v, den_w)")
+        self.name = name
+
+    def c_struct(self) -> fmm_algo_rational_t:
+        return fmm_algo_rational_t(self.p, self.R, self.U.ctypes.data_as(_i32p), self.V.ctypes.data_as(_i32p),
+                                   self.W.ctypes.data_as(_i32p), *self.dens)
+
+    def __repr__(self):
+        return f"RationalAlgo({self.name}, <{self.p},{self.p},{self.p};{self.R}>, dens={self.dens})"
+
+
+def fmm_algo_rational_brent_mismatches(algo: RationalAlgo) -> int:
+    a = algo.c_struct()
+    return int(lib().fmm_algo_rational_brent_mismatches(ctypes.byref(a)))
+
+
 def fmm_algo_builtin(name: str) -> Algo:
     a = fmm_algo_t()
     _check(lib().fmm_algo_builtin(name.encode(), ctypes.byref(a)), f"fmm_algo_builtin({name!r})")
@@ -201,13 +247,16 @@ class Plan:
 def fmm_plan_create(n: int, algo: Algo, depth: int, dtype: str = "f64", schedule: str = "auto",
                     materialize_levels: int = 0, ozaki_slices: int = 0, wait_timeout_s: float = 0.0,
                     debug_poison_chain: int = 0, record_kernel_time: bool = False, tile_n: int = 0) -> Plan:
+    """A plan for ``algo`` (an :class:`Algo`, or a :class:`RationalAlgo` through
+    fmm_plan_create_rational) with the given options."""
     h = ctypes.c_void_p()
     a = algo.c_struct()
     opts = fmm_plan_options_t(SCHEDULES[schedule], int(materialize_levels), int(ozaki_slices),
                               float(wait_timeout_s), int(debug_poison_chain), int(bool(record_kernel_time)),
                               int(tile_n))
-    _check(lib().fmm_plan_create_ex(ctypes.byref(h), int(n), ctypes.byref(a), int(depth), DTYPES[dtype],
-                                    ctypes.byref(opts)), f"fmm_plan_create(n={n}, {algo}, depth={depth})")
+    create = lib().fmm_plan_create_rational if isinstance(algo, RationalAlgo) else lib().fmm_plan_create_ex
+    _check(create(ctypes.byref(h), int(n), ctypes.byref(a), int(depth), DTYPES[dtype], ctypes.byref(opts)),
+           f"fmm_plan_create(n={n}, {algo}, depth={depth})")
     return Plan(h.value, int(n), algo, int(depth), dtype)
 
 
@@ -287,6 +336,17 @@ def fmm_gemm(plan: Plan, A, B, C, stream=None):
     return C
 
 
+def fmm_gemm_ex(plan: Plan, alpha: float, A, B, beta: float, C, stream=None):
+    """C = alpha * A @ B + beta * C on the GPU (beta = 0: C is not read; alpha = 0: A, B are not read)."""
+    n = plan.n
+    for X, nm in ((A, "A"), (B, "B"), (C, "C")):
+        _check_operand(X, n, nm)
+    _check(lib().fmm_gemm_ex(plan.handle, float(alpha), ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                             float(beta), ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+           "fmm_gemm_ex")
+    return C
+
+
 def fmm_gemm_host(plan: Plan, A, B, C, stream=None):
     """C = A @ B with host tensors; copies in and out inside the call (blocking)."""
     n = plan.n
@@ -310,7 +370,9 @@ def fmm_gemm_noalloc(algo: Algo, depth: int, A, B, C, stream=None):
     return C
 
 
-def fmm_gemm_batched(plans, As, Bs, Cs, stream=None):
+def fmm_gemm_batched(plans, As, Bs, Cs, stream=None, alphas=None, betas=None):
+    """C[i] = A[i] @ B[i] as one grouped launch; with ``alphas`` / ``betas`` (sequences of floats,
+    default all 1 / all 0) C[i] = alpha[i] * A[i] @ B[i] + beta[i] * C[i] (fmm_gemm_batched_ex)."""
     count = len(plans)
     if not (len(As) == len(Bs) == len(Cs) == count):
         raise ValueError("plans, A, B, C must have the same length")
@@ -324,7 +386,17 @@ def fmm_gemm_batched(plans, As, Bs, Cs, stream=None):
     ha = arr(*[A.data_ptr() for A in As])
     hb = arr(*[B.data_ptr() for B in Bs])
     hc = arr(*[C.data_ptr() for C in Cs])
-    _check(lib().fmm_gemm_batched(hp, ha, hb, hc, count, ctypes.c_void_p(_stream_ptr(stream))), "fmm_gemm_batched")
+    if alphas is None and betas is None:
+        _check(lib().fmm_gemm_batched(hp, ha, hb, hc, count, ctypes.c_void_p(_stream_ptr(stream))),
+               "fmm_gemm_batched")
+        return Cs
+    darr = ctypes.c_double * max(count, 1)
+    al = None if alphas is None else darr(*[float(x) for x in alphas])
+    be = None if betas is None else darr(*[float(x) for x in betas])
+    if (alphas is not None and len(alphas) != count) or (betas is not None and len(betas) != count):
+        raise ValueError("alphas and betas must have one entry per product")
+    _check(lib().fmm_gemm_batched_ex(hp, al, ha, hb, be, hc, count, ctypes.c_void_p(_stream_ptr(stream))),
+           "fmm_gemm_batched_ex")
     return Cs
 
 

@@ -14,8 +14,10 @@
 //   * the epilogue applies C_l (+)= W[l][r] P_r for every nonzero of column r
 //     of W (post-additions fused into the epilogue).  Contributions to one
 //     (C block, tile) are applied in ascending r, ordered by a per-tile
-//     counter, so results are deterministic; the first contributor stores,
-//     the others read-modify-write.
+//     counter, so results are deterministic; the first contributor stores
+//     (adding beta C when beta != 0), the others read-modify-write.  With
+//     alpha != 1 every coefficient is scaled by alpha (C = alpha A B + beta C,
+//     the BLAS form of Section 3's C = alpha A B).
 // Every wait points at a task with a lower index, tasks are handed out in
 // increasing order and only to running CTAs, so the lowest unfinished task can
 // always proceed: no co-residency assumption is needed.  Each wait is also
@@ -61,6 +63,7 @@ struct Smem {
     Dst dst[kMaxTerms];
     long long lda, ldb, ldc;
     long long task;
+    double alpha, beta;  // C = alpha A B + beta C of the task's problem
     int nA, nB, nD;
     int rows, cols, K;
     int ok;
@@ -132,11 +135,13 @@ __device__ void setup_task(Smem<BNT> &S, const F64Problem &pr, const F64Geom &g,
             S.rows = (int)lmin(BM, m - (long long)ti * BM);
             S.cols = (int)lmin(BN, m - (long long)tj * BN);
             S.K = (int)m;
+            S.alpha = pr.alpha; S.beta = pr.beta;
         }
         return;
     }
     local -= g.tasks_core;
     if (tid != 0) return;
+    S.alpha = pr.alpha_peel; S.beta = pr.beta;
     S.nA = S.nB = S.nD = 1;
     S.lda = n; S.ldb = n; S.ldc = n;
     S.srcA[0].coef = S.srcB[0].coef = 1;
@@ -418,9 +423,16 @@ __global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __gri
             const Dst dst = S.dst[d];
             const bool first = dst.pos == 0;
             const int cf = dst.coef;
-            const double cfd = (double)cf;  // used only when |cf| != 1
-            // mode: 0 store v, 1 store -v, 2 store cf*v, 3 add, 4 subtract, 5 fma
-            const int mode = first ? (cf == 1 ? 0 : (cf == -1 ? 1 : 2)) : (cf == 1 ? 3 : (cf == -1 ? 4 : 5));
+            const double alpha = S.alpha, beta = S.beta;
+            // With alpha = 1 the coefficient stays an integer test (+-1: add or
+            // subtract); otherwise every term is fma(alpha * cf, v, o).  The
+            // first contribution reads C only for beta != 0 and scales it by beta.
+            const int unit = alpha == 1.0 ? cf : 0;
+            const double cfd = alpha * (double)cf;  // used only when unit is not +-1
+            const bool load = !first || beta != 0.0;
+            const bool scale_old = first && beta != 1.0;
+            // mode: 0 store v, 1 store -v, 2 store cfd*v, 3 add, 4 subtract, 5 fma
+            const int mode = load ? (unit == 1 ? 3 : (unit == -1 ? 4 : 5)) : (unit == 1 ? 0 : (unit == -1 ? 1 : 2));
             // Column pairs (2 t4, 2 t4 + 1) are 16 bytes apart-aligned when the tile
             // start and ldc are even.  Read-modify-writes load a whole subtile row
             // (16 values) before the first store, so the loads overlap instead of
@@ -448,6 +460,15 @@ __global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __gri
                                 if (col + 1 < cols) o[j][h][1] = __ldcg(p + 1);
                             }
                         }
+                    if (scale_old) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                o[j][h][0] = beta * o[j][h][0];
+                                o[j][h][1] = beta * o[j][h][1];
+                            }
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j)

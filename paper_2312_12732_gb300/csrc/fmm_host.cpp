@@ -162,8 +162,9 @@ static bool algo_shape_ok(const fmm_algo_t *a) {
     return a && a->p >= 2 && a->R >= 1 && a->U && a->V && a->W && (long long)a->p * a->p * a->R < (1LL << 28);
 }
 
-extern "C" int64_t fmm_algo_brent_mismatches(const fmm_algo_t *a) {
-    if (!algo_shape_ok(a)) return -1;
+// Brent equations with right-hand side `one` on the diagonal (1 for integer
+// coefficients, the denominators' product for a rational algorithm's numerators).
+static int64_t brent_count(const fmm_algo_t *a, int64_t one) {
     const int p = a->p, R = a->R;
     int64_t bad = 0;
     // For each (i,j) of A, (j2,k) of B, (i2,k2) of C: sum_r U V W must equal
@@ -192,11 +193,34 @@ extern "C" int64_t fmm_algo_brent_mismatches(const fmm_algo_t *a) {
                 for (int k = 0; k < p; ++k)
                     for (int i2 = 0; i2 < p; ++i2)
                         for (int k2 = 0; k2 < p; ++k2) {
-                            const int64_t want = (j == j2 && i == i2 && k == k2) ? 1 : 0;
+                            const int64_t want = (j == j2 && i == i2 && k == k2) ? one : 0;
                             const size_t idx = ((size_t)(i * p + j) * p * p + (j2 * p + k)) * p * p + (i2 * p + k2);
                             if (acc[idx] != want) ++bad;
                         }
     return bad;
+}
+
+extern "C" int64_t fmm_algo_brent_mismatches(const fmm_algo_t *a) {
+    if (!algo_shape_ok(a)) return -1;
+    return brent_count(a, 1);
+}
+
+extern "C" int64_t fmm_algo_rational_brent_mismatches(const fmm_algo_rational_t *a) {
+    if (!a) return -1;
+    const fmm_algo_t num{a->p, a->R, a->U, a->V, a->W};
+    if (!algo_shape_ok(&num) || a->den_u < 1 || a->den_v < 1 || a->den_w < 1) return -1;
+    // every partial sum stays below 2^62 in magnitude: R * max|U| max|V| max|W| < 2^62
+    const size_t cnt = (size_t)a->p * a->p * a->R;
+    double mu = 0, mv = 0, mw = 0;
+    for (size_t x = 0; x < cnt; ++x) {
+        mu = std::max(mu, std::fabs((double)a->U[x]));
+        mv = std::max(mv, std::fabs((double)a->V[x]));
+        mw = std::max(mw, std::fabs((double)a->W[x]));
+    }
+    const double lim = 4611686018427387904.0;  // 2^62
+    if ((double)a->R * mu * mv * mw >= lim) return -1;
+    if ((double)a->den_u * a->den_v * a->den_w >= lim) return -1;
+    return brent_count(&num, (int64_t)a->den_u * a->den_v * a->den_w);
 }
 
 extern "C" fmm_status_t fmm_algo_from_transposed_c(int p, int R, const int32_t *ct, int32_t *W_out) {
@@ -288,6 +312,7 @@ struct fmm_plan {
     long long total_tasks = 0;
     double timeout_s = 5.0;
     int poison = 0;
+    double wscale = 1.0;  // (den_u den_v den_w)^-depth of a rational algorithm, applied with W
     // device memory
     void *d_tables = nullptr;     // geometry + CSC tables
     size_t tables_bytes = 0;
@@ -495,14 +520,25 @@ int default_tile_n(long long m, long long products) {
 
 }  // namespace
 
-extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
-                                           fmm_dtype_t dtype, const fmm_plan_options_t *opts) {
+namespace {
+
+// Plan creation for integer tables; `den` is the product of a rational
+// algorithm's denominators (1 for an integer algorithm, whose Brent equations
+// are checked here; a rational algorithm's are checked by the caller).
+fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth, fmm_dtype_t dtype,
+                         const fmm_plan_options_t *opts, int64_t den) {
     if (!out) return FMM_ERR_INVALID;
     *out = nullptr;
-    if (n < 1 || depth < 0 || depth > 8 || !algo_shape_ok(algo)) return FMM_ERR_INVALID;
+    if (n < 1 || depth < 0 || depth > 8 || !algo_shape_ok(algo) || den < 1) return FMM_ERR_INVALID;
     if (n > (1LL << 31) / 2) return FMM_ERR_UNSUPPORTED;
     if (dtype != FMM_F64 && dtype != FMM_F64_OZAKI) return FMM_ERR_UNSUPPORTED;
-    if (fmm_algo_brent_mismatches(algo) != 0) return FMM_ERR_BRENT;
+    if (den == 1 && fmm_algo_brent_mismatches(algo) != 0) return FMM_ERR_BRENT;
+    // the scale (den^depth)^-1, rounded once; den^depth must be an exact double
+    double den_d = 1.0;
+    for (int l = 0; l < depth; ++l) {
+        den_d *= (double)den;
+        if (den_d > 9007199254740992.0) return FMM_ERR_UNSUPPORTED;
+    }
     const int p = algo->p, R = algo->R;
     const long long P = ipow(p, depth);
     const long long Rt = ipow(R, depth);
@@ -530,6 +566,7 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     if (!pl) return FMM_ERR_OOM;
     cudaGetDevice(&pl->device);
     pl->n = n; pl->p = p; pl->R = R; pl->depth = depth; pl->dtype = dtype; pl->mat_levels = mat;
+    pl->wscale = 1.0 / den_d;
     pl->P = P; pl->R_total = Rt;
     pl->m = n / P;
     pl->n_core = P * pl->m;
@@ -870,9 +907,27 @@ extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fm
     return FMM_OK;
 }
 
+}  // namespace
+
+extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
+                                           fmm_dtype_t dtype, const fmm_plan_options_t *opts) {
+    return plan_create(out, n, algo, depth, dtype, opts, 1);
+}
+
 extern "C" fmm_status_t fmm_plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
                                         fmm_dtype_t dtype) {
     return fmm_plan_create_ex(out, n, algo, depth, dtype, nullptr);
+}
+
+extern "C" fmm_status_t fmm_plan_create_rational(fmm_plan_t **out, int64_t n, const fmm_algo_rational_t *algo,
+                                                 int depth, fmm_dtype_t dtype, const fmm_plan_options_t *opts) {
+    if (!out) return FMM_ERR_INVALID;
+    *out = nullptr;
+    const int64_t bad = fmm_algo_rational_brent_mismatches(algo);
+    if (bad < 0) return FMM_ERR_INVALID;
+    if (bad > 0) return FMM_ERR_BRENT;
+    const fmm_algo_t num{algo->p, algo->R, algo->U, algo->V, algo->W};
+    return plan_create(out, n, &num, depth, dtype, opts, (int64_t)algo->den_u * algo->den_v * algo->den_w);
 }
 
 namespace {
@@ -931,10 +986,14 @@ fmm_status_t prepare(const fmm_plan *pl, const double *A, const double *B, cudaS
     return FMM_OK;
 }
 
-F64Problem problem_of(const fmm_plan *pl, const double *A, const double *B, double *C, long long begin) {
+F64Problem problem_of(const fmm_plan *pl, const double *A, const double *B, double *C, long long begin,
+                      double alpha = 1.0, double beta = 0.0) {
     F64Problem pr{};
     pr.g = dev_geom(pl);
     pr.A = A; pr.B = B; pr.C = C;
+    pr.alpha = alpha * pl->wscale;
+    pr.alpha_peel = alpha;
+    pr.beta = beta;
     pr.SA = pl->mat_levels > 0 ? pl->d_SA : A;
     pr.SB = pl->mat_levels > 0 ? pl->d_SB : B;
     pr.chain = pl->d_chain;
@@ -948,7 +1007,8 @@ namespace {
 
 // Emulated leaf: FP64 pre-additions, exponents and slices of every S_r / T_r,
 // the slice GEMM with fused post-additions, then the FP64 peel tasks.
-fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, double *C, cudaStream_t st) {
+fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, double *C, double alpha, double beta,
+                        cudaStream_t st) {
     const long long m = pl->m;
     const int nmat = (int)pl->R_total;
     const double *S = pl->depth > 0 ? pl->d_SA : A;
@@ -986,6 +1046,8 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     P.task_counter = pl->d_task_counter;
     P.error = pl->d_error;
     P.timeout_ns = (long long)(pl->timeout_s * 1e9);
+    P.alpha = alpha * pl->wscale;
+    P.beta = beta;
     if (pl->oz_engine == 2) {
         // a task covers a pair of tile rows and two tile columns; the last row or column of a
         // task may be padding.  One CTA per SM, in clusters of 4 where possible (oz_cluster = 4).
@@ -1006,7 +1068,8 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     if (pl->ev[2] && cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
     if (pl->oz_engine >= 1 &&
         fmm::launch_ozaki_postadd(pl->d_pout, m, (int)pl->P, pl->d_wl_ptr, pl->d_wl_ent, C, pl->n, pl->d_chain,
-                                  pl->geom.w_row_nnz, pl->tiles_m * pl->tiles_n, st) != cudaSuccess)
+                                  pl->geom.w_row_nnz, pl->tiles_m * pl->tiles_n, alpha * pl->wscale, beta,
+                                  st) != cudaSuccess)
         return FMM_ERR_CUDA;
     if (pl->ev[5] && cudaEventRecord(pl->ev[5], st) != cudaSuccess) return FMM_ERR_CUDA;
     const long long peel = pl->geom.tasks_right + pl->geom.tasks_bottom + pl->geom.tasks_rankq;
@@ -1025,6 +1088,9 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
         L.probs[0].C = C;
         L.probs[0].chain = pl->d_chain;
         L.probs[0].task_begin = 0;
+        L.probs[0].alpha = alpha * pl->wscale;  // core tasks: none in this launch
+        L.probs[0].alpha_peel = alpha;
+        L.probs[0].beta = beta;
         const int g2 = (int)std::min<long long>(peel, (long long)pl->sms * fmm::f64_kernel_ctas_per_sm(pl->bn));
         if (fmm::launch_f64_single(L, g2 < 1 ? 1 : g2, st, pl->bn) != cudaSuccess) return FMM_ERR_CUDA;
     }
@@ -1034,14 +1100,20 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
 }  // namespace
 
 extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const double *B, double *C, void *stream) {
-    if (!pl || !A || !B || !C) return FMM_ERR_INVALID;
+    return fmm_gemm_ex(pl, 1.0, A, B, 0.0, C, stream);
+}
+
+extern "C" fmm_status_t fmm_gemm_ex(const fmm_plan_t *pl, double alpha, const double *A, const double *B, double beta,
+                                    double *C, void *stream) {
+    if (!pl || !A || !B || !C || !std::isfinite(alpha) || !std::isfinite(beta)) return FMM_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
+    if (alpha == 0.0) return cuda_status(fmm::launch_scale_c(C, pl->n, beta, st));  // A, B unread
     if (pl->ev[0] && cudaEventRecord(pl->ev[0], st) != cudaSuccess) return FMM_ERR_CUDA;
     fmm_status_t s = prepare(pl, A, B, st);
     if (s != FMM_OK) return s;
     if (pl->ev[3] && cudaEventRecord(pl->ev[3], st) != cudaSuccess) return FMM_ERR_CUDA;
     if (pl->dtype == FMM_F64_OZAKI) {
-        s = gemm_ozaki(pl, A, B, C, st);
+        s = gemm_ozaki(pl, A, B, C, alpha, beta, st);
         if (s == FMM_OK && pl->ev[4] && cudaEventRecord(pl->ev[4], st) != cudaSuccess) return FMM_ERR_CUDA;
         if (s == FMM_OK && pl->ev[2]) const_cast<fmm_plan *>(pl)->timed_once = true;
         return s;
@@ -1053,7 +1125,7 @@ extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const do
     L.task_counter = pl->d_task_counter;
     L.error = pl->d_error;
     L.timeout_ns = (long long)(pl->timeout_s * 1e9);
-    L.probs[0] = problem_of(pl, A, B, C, 0);
+    L.probs[0] = problem_of(pl, A, B, C, 0, alpha, beta);
     fmm_status_t ls = cuda_status(fmm::launch_f64_single(L, pl->grid, st, pl->bn));
     if (ls != FMM_OK) return ls;
     if (pl->ev[2]) {
@@ -1116,18 +1188,30 @@ extern "C" fmm_status_t fmm_gemm_host(fmm_plan_t *pl, const double *hA, const do
 
 extern "C" fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double *const *A, const double *const *B,
                                          double *const *C, int count, void *stream) {
+    return fmm_gemm_batched_ex(plans, nullptr, A, B, nullptr, C, count, stream);
+}
+
+extern "C" fmm_status_t fmm_gemm_batched_ex(fmm_plan_t *const *plans, const double *alpha, const double *const *A,
+                                            const double *const *B, const double *beta, double *const *C, int count,
+                                            void *stream) {
     if (count < 0 || (count > 0 && (!plans || !A || !B || !C))) return FMM_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     for (int i = 0; i < count; ++i) {
         if (!plans[i] || !A[i] || !B[i] || !C[i] || plans[i]->dtype != FMM_F64) return FMM_ERR_INVALID;
+        if ((alpha && !std::isfinite(alpha[i])) || (beta && !std::isfinite(beta[i]))) return FMM_ERR_INVALID;
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return FMM_ERR_INVALID;  // a plan's counters serve one product
     }
+    const auto al = [&](int i) { return alpha ? alpha[i] : 1.0; };
+    const auto be = [&](int i) { return beta ? beta[i] : 0.0; };
+    // problems with alpha = 0 only scale C (A and B unread); they join no launch
+    for (int i = 0; i < count; ++i)
+        if (al(i) == 0.0 && fmm::launch_scale_c(C[i], plans[i]->n, be(i), st) != cudaSuccess) return FMM_ERR_CUDA;
     // one grouped launch per tile width present in the batch
     for (int bn : {128, 64}) {
         std::vector<int> sel;
         for (int i = 0; i < count; ++i)
-            if (plans[i]->bn == bn) sel.push_back(i);
+            if (plans[i]->bn == bn && al(i) != 0.0) sel.push_back(i);
         for (size_t c0 = 0; c0 < sel.size(); c0 += fmm::kMaxBatchPerLaunch) {
             const int cnt = (int)std::min<size_t>(sel.size() - c0, fmm::kMaxBatchPerLaunch);
             F64Launch<fmm::kMaxBatchPerLaunch> *L = new (std::nothrow) F64Launch<fmm::kMaxBatchPerLaunch>();
@@ -1138,7 +1222,7 @@ extern "C" fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double 
                 const fmm_plan *pl = plans[i];
                 fmm_status_t s = prepare(pl, A[i], B[i], st);
                 if (s != FMM_OK) { delete L; return s; }
-                L->probs[k] = problem_of(pl, A[i], B[i], C[i], begin);
+                L->probs[k] = problem_of(pl, A[i], B[i], C[i], begin, al(i), be(i));
                 begin += pl->total_tasks;
             }
             const fmm_plan *lead = plans[sel[c0]];
@@ -1337,6 +1421,7 @@ extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t 
     info->ozaki_slices = pl->oz_s;
     info->tile_n = pl->bn;
     info->flops_lowp = pl->flops_lowp;
+    info->coef_scale = pl->wscale;
     info->materialize_passes = 0;
     for (const fmm_plan::MatStep &ms : pl->mat_steps) info->materialize_passes += ms.with_next ? 0 : 1;
     return FMM_OK;

@@ -61,6 +61,12 @@ struct F64Problem {
     double *C;           // output (ld = n)
     unsigned *chain;     // [P*P][tiles] post-add ordering counters
     long long task_begin;
+    // C = alpha A B + beta C (alpha = 0 never reaches a kernel).  Core tasks
+    // apply alpha times the plan's coefficient scale (a rational algorithm's
+    // 1 / denominators) to every W coefficient; peel tasks apply alpha_peel.
+    double alpha;
+    double alpha_peel;
+    double beta;         // beta = 0: C is written without being read
 };
 
 template <int MAXP>
@@ -113,6 +119,7 @@ struct OzParams {
     unsigned long long *task_counter;
     int *error;
     long long timeout_ns;
+    double alpha, beta;       // C = alpha A B + beta C (the mma.sync engine's epilogue)
 };
 
 // Exponents and slices of every row (by_rows) or column of the nmat matrices
@@ -138,13 +145,17 @@ cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &ma
                                  const OzParams &P, int ctas, int cluster_ctas, cudaStream_t s);
 // Largest number of co-resident CTA pairs of the pair kernel (0 if it cannot run).
 int ozaki_tc_max_pairs();
-// C_l = sum_r W[l][r] P_r for the P x P blocks of side m of C (leading
-// dimension ldc), in ascending r: wl_ptr / wl_ent list, per block l, the
-// products (r, coefficient) in ascending r.  Also sets the ordering counters
-// of the peel tasks: chain[l * tiles + t] = w_row_nnz[l].
+// C_l = alpha sum_r W[l][r] P_r + beta C_l for the P x P blocks of side m of
+// C (leading dimension ldc), in ascending r: wl_ptr / wl_ent list, per block
+// l, the products (r, coefficient) in ascending r.  beta = 0 writes C without
+// reading it.  Also sets the ordering counters of the peel tasks:
+// chain[l * tiles + t] = w_row_nnz[l].
 cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
                                  double *C, long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
-                                 cudaStream_t s);
+                                 double alpha, double beta, cudaStream_t s);
+// C = beta C over an n x n matrix (leading dimension n); beta = 0 stores zeros
+// without reading C (fmm_materialize.cu).
+cudaError_t launch_scale_c(double *C, long long n, double beta, cudaStream_t s);
 
 // Kernel launchers (fmm_f64.cu).  Return cudaSuccess or the launch error.
 // bn selects the tile configuration (128 or 64 columns).

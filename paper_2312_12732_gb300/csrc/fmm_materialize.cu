@@ -154,4 +154,24 @@ cudaError_t launch_materialize_two_steps(const double *in, long long ld_in, long
     return cudaSuccess;
 }
 
+// C = beta C (the whole update when alpha = 0: A and B are not read).  With
+// beta = 0 the kernel stores zeros without reading C, so NaN there is dropped.
+__global__ void __launch_bounds__(256) scale_c_kernel(double *C, long long count, double beta) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride)
+        C[t] = beta == 0.0 ? 0.0 : beta * C[t];
+}
+
+cudaError_t launch_scale_c(double *C, long long n, double beta, cudaStream_t s) {
+    const long long count = n * n;
+    if (count <= 0 || beta == 1.0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long grid = (count + 255) / 256;
+    if (grid > (long long)sms * 8) grid = (long long)sms * 8;
+    scale_c_kernel<<<(unsigned)grid, 256, 0, s>>>(C, count, beta);
+    return cudaGetLastError();
+}
+
 }  // namespace fmm

@@ -282,6 +282,9 @@ extern "C" fmm_status_t fmm_gemm_noalloc(int64_t n, const fmm_algo_t *algo, int 
     pr.A = A; pr.B = B; pr.SA = A; pr.SB = B; pr.C = C;
     pr.chain = (unsigned *)(dbase + 16);
     pr.task_begin = 0;
+    pr.alpha = 1.0;
+    pr.alpha_peel = 1.0;
+    pr.beta = 0.0;
     int sms = 0, devno = 0;
     cudaGetDevice(&devno);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devno);

@@ -460,8 +460,13 @@ __global__ void __launch_bounds__(NT, 1) ozaki_gemm_kernel(const __grid_constant
             __syncthreads();
             if (!S.ok) break;
             const int cf = dst.coef;
-            const double cfd = (double)cf;
-            const int mode = dst.pos == 0 ? (cf == 1 ? 0 : (cf == -1 ? 1 : 2)) : (cf == 1 ? 3 : (cf == -1 ? 4 : 5));
+            // C = alpha A B + beta C: alpha scales every coefficient; the first
+            // contribution reads C only for beta != 0 and scales it by beta.
+            const int unit = P.alpha == 1.0 ? cf : 0;
+            const double cfd = P.alpha * (double)cf;
+            const bool load = dst.pos != 0 || P.beta != 0.0;
+            const double oscale = dst.pos == 0 ? P.beta : 1.0;
+            const int mode = load ? (unit == 1 ? 3 : (unit == -1 ? 4 : 5)) : (unit == 1 ? 0 : (unit == -1 ? 1 : 2));
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -476,14 +481,19 @@ __global__ void __launch_bounds__(NT, 1) ozaki_gemm_kernel(const __grid_constant
                             if (col >= cols) continue;
                             double *p = dst.ptr + (long long)row * P.ldc + col;
                             const double v = pv[i][j][2 * h + c2];
+                            double o = 0.0;
+                            if (load) {
+                                o = __ldcg(p);
+                                if (oscale != 1.0) o = oscale * o;
+                            }
                             double out;
                             switch (mode) {
                                 case 0: out = v; break;
                                 case 1: out = neg(v); break;
                                 case 2: out = cfd * v; break;
-                                case 3: out = __ldcg(p) + v; break;
-                                case 4: out = __ldcg(p) - v; break;
-                                default: out = fma(cfd, v, __ldcg(p)); break;
+                                case 3: out = o + v; break;
+                                case 4: out = o - v; break;
+                                default: out = fma(cfd, v, o); break;
                             }
                             *p = out;
                         }

@@ -21,7 +21,7 @@
 //     pair or of two pairs sharing their left-slice tiles by TMA multicast; the
 //     default) described above the kernel.
 //
-// ozaki_postadd_kernel then forms C_l = sum_r W[l][r] P_r in ascending r.
+// ozaki_postadd_kernel (fmm_postadd.cu) then forms C_l = sum_r W[l][r] P_r in ascending r.
 // Every mbarrier wait is bounded by %globaltimer; on expiry the CTA records a
 // timeout, stops issuing, waits (bounded) for its own copies and MMAs in
 // flight, frees its TMEM and returns.
@@ -912,87 +912,6 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-// Post-additions of the emulated leaf: C_l = sum_r W[l][r] P_r for every C
-// block l, in ascending r, with the same operation sequence as ordered
-// read-modify-writes (first term w * P, then o + P, o - P or fma(w, P, o)),
-// so the result is the one the fused form gives.  blockIdx.y is the block,
-// CTAs stride over its rows, threads over column pairs.  Bound by the FP64
-// adds (nnz(W) - P^2 per element of a block) and the P_r reads.
-__global__ void __launch_bounds__(256) ozaki_postadd_kernel(const double *__restrict__ pout, long long m, int Pb,
-                                                            const int *__restrict__ wl_ptr,
-                                                            const int2 *__restrict__ wl_ent, double *__restrict__ C,
-                                                            long long ldc, unsigned *chain,
-                                                            const int *__restrict__ w_row_nnz, int tiles, int l0) {
-    const int l = l0 + (int)blockIdx.y;
-    const long long br = l / Pb, bc = l % Pb;
-    const int e0 = wl_ptr[l], e1 = wl_ptr[l + 1];
-    const long long mm = m * m;
-    if (chain != nullptr && blockIdx.x == 0)
-        for (int t = threadIdx.x; t < tiles; t += blockDim.x) chain[(long long)l * tiles + t] = (unsigned)w_row_nnz[l];
-    const bool pairs = (m & 1) == 0 && (ldc & 1) == 0;  // 16-byte aligned column pairs
-    constexpr int NB = 8;                                // terms whose loads are in flight together
-    for (long long i = blockIdx.x; i < m; i += gridDim.x) {
-        double *crow = C + (br * m + i) * ldc + bc * m;
-        const double *prow = pout + i * m;
-        if (pairs) {
-            for (long long j = 2 * (long long)threadIdx.x; j < m; j += 2 * blockDim.x) {
-                double2 c = make_double2(0.0, 0.0);
-                for (int eb = e0; eb < e1; eb += NB) {
-                    double2 v[NB];
-                    int cf[NB];
-#pragma unroll
-                    for (int k = 0; k < NB; ++k)
-                        if (eb + k < e1) {
-                            const int2 en = wl_ent[eb + k];  // {product r, coefficient}
-                            cf[k] = en.y;
-                            v[k] = __ldg(reinterpret_cast<const double2 *>(prow + (long long)en.x * mm + j));
-                        }
-#pragma unroll
-                    for (int k = 0; k < NB; ++k) {
-                        if (eb + k >= e1) break;
-                        if (eb + k == e0) {
-                            c = cf[k] == 1 ? v[k]
-                                : cf[k] == -1 ? make_double2(dev::neg(v[k].x), dev::neg(v[k].y))
-                                              : make_double2((double)cf[k] * v[k].x, (double)cf[k] * v[k].y);
-                        } else if (cf[k] == 1) {
-                            c.x = c.x + v[k].x; c.y = c.y + v[k].y;
-                        } else if (cf[k] == -1) {
-                            c.x = c.x - v[k].x; c.y = c.y - v[k].y;
-                        } else {
-                            c.x = fma((double)cf[k], v[k].x, c.x); c.y = fma((double)cf[k], v[k].y, c.y);
-                        }
-                    }
-                }
-                *reinterpret_cast<double2 *>(crow + j) = c;
-            }
-        } else {
-            for (long long j = threadIdx.x; j < m; j += blockDim.x) {
-                double c = 0.0;
-                for (int eb = e0; eb < e1; eb += NB) {
-                    double v[NB];
-                    int cf[NB];
-#pragma unroll
-                    for (int k = 0; k < NB; ++k)
-                        if (eb + k < e1) {
-                            const int2 en = wl_ent[eb + k];
-                            cf[k] = en.y;
-                            v[k] = __ldg(prow + (long long)en.x * mm + j);
-                        }
-#pragma unroll
-                    for (int k = 0; k < NB; ++k) {
-                        if (eb + k >= e1) break;
-                        if (eb + k == e0) c = cf[k] == 1 ? v[k] : (cf[k] == -1 ? dev::neg(v[k]) : (double)cf[k] * v[k]);
-                        else if (cf[k] == 1) c = c + v[k];
-                        else if (cf[k] == -1) c = c - v[k];
-                        else c = fma((double)cf[k], v[k], c);
-                    }
-                }
-                crow[j] = c;
-            }
-        }
-    }
-}
-
 constexpr size_t kSmemBytes = 1024 + STAGES * STAGE_BYTES + sizeof(Bars);
 constexpr size_t kPairSmemBytes = 1024 + NRING * RSTAGES * P_STAGE_BYTES + sizeof(PairBars);
 
@@ -1069,26 +988,6 @@ int ozaki_tc_max_pairs() {
     }
     cached = n;
     return n;
-}
-
-cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
-                                 double *C, long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
-                                 cudaStream_t s) {
-    if (m <= 0 || P <= 0) return cudaSuccess;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long bx = ((long long)sms * 16 + P * P - 1) / ((long long)P * P);
-    if (bx > m) bx = m;
-    if (bx < 1) bx = 1;
-    for (int l0 = 0; l0 < P * P; l0 += 65535) {
-        const int cnt = P * P - l0 < 65535 ? P * P - l0 : 65535;
-        dim3 grid((unsigned)bx, (unsigned)cnt);
-        ozaki_postadd_kernel<<<grid, 256, 0, s>>>(pout, m, P, wl_ptr, wl_ent, C, ldc, chain, w_row_nnz, tiles, l0);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
 }
 
 }  // namespace fmm

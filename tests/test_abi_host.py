@@ -119,3 +119,44 @@ def test_binding_requires_built_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_binding, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _binding.lib()
+
+
+def test_scaled_entry_points_validate_before_touching_the_gpu(fmm):
+    """fmm_gemm_ex rejects a NULL plan or operand, and an empty fmm_gemm_batched_ex is a no-op;
+    neither makes a CUDA call on these paths."""
+    lib = fmm.lib()
+    assert lib.fmm_gemm_ex(None, 1.0, None, None, 0.0, None, None) == 1
+    assert lib.fmm_gemm_batched_ex(None, None, None, None, None, None, 0, None) == 0
+    assert lib.fmm_gemm_batched_ex(None, None, None, None, None, None, -1, None) == 1
+
+
+def test_rational_brent_agrees_with_the_oracle(fmm, oracle_mod):
+    """The library's rational Brent check gives the oracle's count on the derived non-integer
+    algorithms, on single-entry changes and on a wrong denominator; bad input gives -1."""
+    from golden import rational_algos
+
+    for make in (rational_algos.strassen_dyadic, rational_algos.strassen_thirds, rational_algos.strassen_halved):
+        p, U, V, W, dens = make()
+        assert fmm.fmm_algo_rational_brent_mismatches(fmm.RationalAlgo(p, U, V, W, dens)) == 0
+        for wrong in ((dens[0] * 2, dens[1], dens[2]), (dens[0], dens[1], dens[2] + 1)):
+            assert (fmm.fmm_algo_rational_brent_mismatches(fmm.RationalAlgo(p, U, V, W, wrong))
+                    == oracle_mod.brent_mismatches_rational(p, U, V, W, wrong) > 0)
+        U2 = U.copy()
+        U2[1, 3] += 1
+        assert (fmm.fmm_algo_rational_brent_mismatches(fmm.RationalAlgo(p, U2, V, W, dens))
+                == oracle_mod.brent_mismatches_rational(p, U2, V, W, dens) > 0)
+        assert fmm.fmm_algo_rational_brent_mismatches(fmm.RationalAlgo(p, U, V, W, (0, 1, 1))) == -1
+    big = np.full((4, 7), 1 << 30, dtype=np.int32)
+    assert fmm.fmm_algo_rational_brent_mismatches(fmm.RationalAlgo(2, big, big, big, (1, 1, 1))) == -1
+
+
+def test_rational_plan_create_rejects_bad_algorithms_before_touching_the_gpu(fmm):
+    from golden import rational_algos
+
+    p, U, V, W, (du, dv, dw) = rational_algos.strassen_dyadic()
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_plan_create(64, fmm.RationalAlgo(p, U, V, W, (du, dv, dw * 2)), 1)
+    assert e.value.status == 2  # FMM_ERR_BRENT
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_plan_create(64, fmm.RationalAlgo(p, U, V, W, (du, 0, dw)), 1)
+    assert e.value.status == 1  # FMM_ERR_INVALID
