@@ -17,6 +17,10 @@ Functions (each follows the passage cited in ``fmm_oracle.c``):
   `strassen`, level by level, with the peeling rule stated in the C source.
 * ``sample_dot2(A, B, rows, cols)`` -- compensated dot products (Ogita, Rump,
   Oishi 2005) for sampled reference entries.
+* ``classic_complex(A, B)`` / ``bilinear_complex(A, B, p, U, V, W, depth)`` --
+  the same products for complex128 matrices (Section 1 names double complex
+  among the deployable types): real coefficients act on both parts alike,
+  leaf products use the textbook complex product.
 * ``axpby(alpha, P, beta, C)`` / ``scaled(alpha, A, B, beta, C, ...)`` -- the
   update C = alpha A B + beta C (Section 3 states C = alpha A B; beta is the
   BLAS extension), with beta = 0 leaving C unread and alpha = 0 leaving A B
@@ -71,6 +75,11 @@ def _load():
         lib.fmm_oracle_dot2.argtypes = [i64, dp, i64, dp, i64]
         lib.fmm_oracle_sample_dot2.restype = None
         lib.fmm_oracle_sample_dot2.argtypes = [i64, dp, i64, dp, i64, i64, ip64, ip64, dp]
+        lib.fmm_oracle_classic_complex.restype = None
+        lib.fmm_oracle_classic_complex.argtypes = [i64, i64, i64, dp, i64, dp, i64, dp, i64]
+        lib.fmm_oracle_bilinear_complex.restype = ctypes.c_int
+        lib.fmm_oracle_bilinear_complex.argtypes = [i64, dp, i64, dp, i64, dp, i64, i32, i32, ip32, ip32, ip32,
+                                                    i32]
         lib.fmm_oracle_axpby.restype = None
         lib.fmm_oracle_axpby.argtypes = [i64, ctypes.c_double, dp, ctypes.c_double, dp]
         _lib = lib
@@ -149,6 +158,41 @@ def bilinear_rational(A, B, p: int, U, V, W, dens, depth: int) -> np.ndarray:
                                               _ip32(W), du, dv, dw, depth)
     if rc == -2:
         raise ValueError("oracle: denominators must be positive")
+    if rc != 0:
+        raise MemoryError("oracle: temporary allocation failed")
+    return C
+
+
+def _cmat(A):
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    assert A.ndim == 2
+    return A
+
+
+def _cdp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def classic_complex(A, B) -> np.ndarray:
+    """C = A B for complex128 matrices by the ascending-k triple loop."""
+    A, B = _cmat(A), _cmat(B)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    C = np.empty((M, N), dtype=np.complex128)
+    _load().fmm_oracle_classic_complex(M, N, K, _cdp(A), K, _cdp(B), N, _cdp(C), N)
+    return C
+
+
+def bilinear_complex(A, B, p: int, U, V, W, depth: int) -> np.ndarray:
+    """C = A B (square complex128) by `depth` recursive levels of the integer algorithm (U, V, W)."""
+    A, B = _cmat(A), _cmat(B)
+    n = A.shape[0]
+    assert A.shape == (n, n) and B.shape == (n, n)
+    U, V, W, R = _alg(p, U, V, W)
+    C = np.empty((n, n), dtype=np.complex128)
+    rc = _load().fmm_oracle_bilinear_complex(n, _cdp(A), n, _cdp(B), n, _cdp(C), n, p, R, _ip32(U), _ip32(V),
+                                             _ip32(W), depth)
     if rc != 0:
         raise MemoryError("oracle: temporary allocation failed")
     return C

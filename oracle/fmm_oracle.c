@@ -240,6 +240,124 @@ int fmm_oracle_bilinear_rational(int64_t n, const double *A, int64_t lda, const 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Double complex (Section 1 lists single and double complex among the types  */
+/* the algorithms deploy to).  A complex matrix is stored interleaved: entry  */
+/* (i, j) is re at 2 (i ld + j), im right after it, ld counted in complex      */
+/* entries.  The bilinear algorithm's coefficients are real, so its pre- and   */
+/* post-additions act on the real and imaginary parts alike; only the leaf     */
+/* products multiply complex numbers.                                          */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * C = A B for complex M x K and K x N matrices.  Every C[i][j] starts at 0 and
+ * accumulates A[i][k] B[k][j] in ascending k, each product formed as
+ * (ac - bd) + (ad + bc) i with every product and difference rounded, then the
+ * two parts added to the running sums.
+ */
+void fmm_oracle_classic_complex(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda, const double *B,
+                                int64_t ldb, double *C, int64_t ldc) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < M; ++i) {
+        double *c = C + 2 * i * ldc;
+        for (int64_t j = 0; j < 2 * N; ++j) c[j] = 0.0;
+        for (int64_t k = 0; k < K; ++k) {
+            const double ar = A[2 * (i * lda + k)], ai = A[2 * (i * lda + k) + 1];
+            const double *b = B + 2 * k * ldb;
+            for (int64_t j = 0; j < N; ++j) {
+                const double br = b[2 * j], bi = b[2 * j + 1];
+                const double x = ar * br, y = ai * bi, u = ar * bi, v = ai * br;
+                c[2 * j] += x - y;
+                c[2 * j + 1] += u + v;
+            }
+        }
+    }
+}
+
+/* dst (m x m complex, ld m) = sum_i coef[i][r] * complex block i of src, ascending i. */
+static void combine_blocks_complex(int64_t m, int p, int R, const int32_t *coef, int r, const double *src,
+                                   int64_t ld, double *dst) {
+    for (int64_t x = 0; x < 2 * m * m; ++x) dst[x] = 0.0;
+    for (int i = 0; i < p * p; ++i) {
+        const int32_t c = coef[(int64_t)i * R + r];
+        if (c == 0) continue;
+        const double *blk = src + 2 * ((int64_t)(i / p) * m * ld + (int64_t)(i % p) * m);
+        const double cd = (double)c;
+        for (int64_t y = 0; y < m; ++y)
+            for (int64_t x = 0; x < 2 * m; ++x) {
+                const double a = blk[2 * y * ld + x];
+                if (c == 1)
+                    dst[2 * y * m + x] += a;
+                else if (c == -1)
+                    dst[2 * y * m + x] -= a;
+                else
+                    dst[2 * y * m + x] += cd * a;
+            }
+    }
+}
+
+static int bilinear_rec_complex(int64_t n, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+                                int64_t ldc, const oracle_alg *alg, int depth) {
+    const int p = alg->p, R = alg->R;
+    if (depth <= 0 || n < p) {
+        fmm_oracle_classic_complex(n, n, n, A, lda, B, ldb, C, ldc);
+        return 0;
+    }
+    /* the peeling rule of the real recursion, on complex entries */
+    const int64_t q = n % p, nc = n - q, m = nc / p;
+    double *S = (double *)malloc(sizeof(double) * 2 * m * m);
+    double *T = (double *)malloc(sizeof(double) * 2 * m * m);
+    double *Pr = (double *)malloc(sizeof(double) * 2 * m * m);
+    if (!S || !T || !Pr) {
+        free(S); free(T); free(Pr);
+        return -1;
+    }
+    for (int64_t y = 0; y < nc; ++y)
+        for (int64_t x = 0; x < 2 * nc; ++x) C[2 * y * ldc + x] = 0.0;
+    int rc = 0;
+    for (int r = 0; r < R && rc == 0; ++r) {
+        combine_blocks_complex(m, p, R, alg->U, r, A, lda, S);
+        combine_blocks_complex(m, p, R, alg->V, r, B, ldb, T);
+        rc = bilinear_rec_complex(m, S, m, T, m, Pr, m, alg, depth - 1);
+        for (int l = 0; l < p * p && rc == 0; ++l) {
+            const int32_t w = alg->W[(int64_t)l * R + r];
+            if (w == 0) continue;
+            double *cb = C + 2 * ((int64_t)(l / p) * m * ldc + (int64_t)(l % p) * m);
+            const double wd = (double)w;
+            for (int64_t y = 0; y < m; ++y)
+                for (int64_t x = 0; x < 2 * m; ++x) {
+                    const double v = Pr[2 * y * m + x];
+                    if (w == 1)
+                        cb[2 * y * ldc + x] += v;
+                    else if (w == -1)
+                        cb[2 * y * ldc + x] -= v;
+                    else
+                        cb[2 * y * ldc + x] += wd * v;
+                }
+        }
+    }
+    free(S); free(T); free(Pr);
+    if (rc != 0 || q == 0) return rc;
+
+    double *tmp = (double *)malloc(sizeof(double) * 2 * nc * nc);
+    if (!tmp) return -1;
+    fmm_oracle_classic_complex(nc, nc, q, A + 2 * nc, lda, B + 2 * nc * ldb, ldb, tmp, nc);
+    for (int64_t y = 0; y < nc; ++y)
+        for (int64_t x = 0; x < 2 * nc; ++x) C[2 * y * ldc + x] += tmp[2 * y * nc + x];
+    free(tmp);
+    fmm_oracle_classic_complex(nc, q, n, A, lda, B + 2 * nc, ldb, C + 2 * nc, ldc);
+    fmm_oracle_classic_complex(q, n, n, A + 2 * nc * lda, lda, B, ldb, C + 2 * nc * ldc, ldc);
+    return 0;
+}
+
+/* C = A B for complex n x n matrices by `depth` recursive levels of the (integer) algorithm. */
+int fmm_oracle_bilinear_complex(int64_t n, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+                                int64_t ldc, int p, int R, const int32_t *U, const int32_t *V, const int32_t *W,
+                                int depth) {
+    oracle_alg alg = {p, R, U, V, W, 1, 1, 1};
+    return bilinear_rec_complex(n, A, lda, B, ldb, C, ldc, &alg, depth);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Scaled update (Section 3 states the product as C = alpha A B; beta C is    */
 /* the usual BLAS extension of that statement).                               */
 /* ------------------------------------------------------------------------- */

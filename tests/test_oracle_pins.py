@@ -395,3 +395,81 @@ def test_rational_planted_denominator_mistake_is_detected(oracle_mod):
     assert not np.array_equal(oracle_mod.bilinear_rational(A, B, p, U, V, W, (du, dv, 1), 1), A @ B)
     with pytest.raises(ValueError):
         oracle_mod.bilinear_rational(A, B, p, U, V, W, (0, dv, dw), 1)
+
+
+# --- double complex (Section 1: single and double complex are among the deployable types) ------
+
+def _cint(n, seed, m=None):
+    return inputs.matrix(n, "integer", seed=seed, m=m) + 1j * inputs.matrix(n, "integer", seed=seed + 50, m=m)
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (7, 5, 3), (33, 17, 65)])
+def test_classic_complex_exact_on_integers_vs_numpy(oracle_mod, M, N, K):
+    A = _cint(M, 3, m=K)
+    B = _cint(K, 4, m=N)
+    assert np.array_equal(oracle_mod.classic_complex(A, B), A @ B)
+
+
+def test_classic_complex_reduces_to_the_real_oracle(oracle_mod):
+    """Zero imaginary parts give the real classic product bit for bit (and zero imaginary part);
+    a purely imaginary A gives i times it; conjugating both operands conjugates the result."""
+    A, B = inputs.operands(40, "uniform", seed=6)
+    C = oracle_mod.classic_complex(A + 0j, B + 0j)
+    assert np.array_equal(C.real, oracle_mod.classic(A, B)) and not C.imag.any()
+    C = oracle_mod.classic_complex(1j * A, B + 0j)
+    assert np.array_equal(C.imag, oracle_mod.classic(A, B)) and not C.real.any()
+    Z1 = A + 1j * inputs.matrix(40, "normal", seed=7)
+    Z2 = B + 1j * inputs.matrix(40, "normal", seed=8)
+    assert np.array_equal(oracle_mod.classic_complex(Z1.conj(), Z2.conj()), oracle_mod.classic_complex(Z1, Z2).conj())
+
+
+def test_classic_complex_within_rounding_of_dot2(oracle_mod):
+    """Each part of a complex dot product is a real dot product of length 2K (re: ar br - ai bi,
+    im: ar bi + ai br); compared with Dot2 of those vectors, within the dot-product bound."""
+    n = 64
+    Z1 = inputs.matrix(n, "uniform", seed=11) + 1j * inputs.matrix(n, "uniform", seed=12)
+    Z2 = inputs.matrix(n, "uniform", seed=13) + 1j * inputs.matrix(n, "uniform", seed=14)
+    C = oracle_mod.classic_complex(Z1, Z2)
+    for i, j in [(0, 0), (5, 9), (63, 63), (17, 40)]:
+        a, b = Z1[i, :], Z2[:, j]
+        re = oracle_mod.dot2(np.concatenate([a.real, -a.imag]), np.concatenate([b.real, b.imag]))
+        im = oracle_mod.dot2(np.concatenate([a.real, a.imag]), np.concatenate([b.imag, b.real]))
+        bound = 2 * n * 2.0 ** -53 * 2 * n
+        assert abs(C[i, j].real - re) <= bound and abs(C[i, j].imag - im) <= bound
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+def test_bilinear_complex_exhaustive_basis_pairs(oracle_mod, depth):
+    """(s E_ij)(t E_kl) = s t delta_jk E_il for s, t in {1, i}: every basis pair of both parts."""
+    p, U, V, W = algos.paper_strassen()
+    n = p ** depth
+    for i, j, k, l in itertools.product(range(n), repeat=4):
+        for s, t in ((1, 1j), (1j, 1), (1j, 1j)):
+            C = oracle_mod.bilinear_complex(s * _basis(n, i, j), t * _basis(n, k, l), p, U, V, W, depth)
+            want = (s * t * _basis(n, i, l)) if j == k else np.zeros((n, n), dtype=complex)
+            assert np.array_equal(C, want), (i, j, k, l, s, t)
+
+
+@pytest.mark.parametrize("name,n,depth", [("paper_strassen", 64, 3), ("winograd", 77, 2), ("laderman", 50, 2),
+                                          ("paper_strassen", 101, 2)])
+def test_bilinear_complex_bit_exact_on_integers(oracle_mod, name, n, depth):
+    p, U, V, W = all_algos()[name]
+    A, B = _cint(n, n), _cint(n, n + 1)
+    assert np.array_equal(oracle_mod.bilinear_complex(A, B, p, U, V, W, depth), A @ B)
+
+
+def test_bilinear_complex_real_parts_match_the_real_recursion(oracle_mod):
+    p, U, V, W = all_algos()["winograd"]
+    A, B = inputs.operands(96, "uniform", seed=15)
+    C = oracle_mod.bilinear_complex(A + 0j, B + 0j, p, U, V, W, 2)
+    assert np.array_equal(C.real, oracle_mod.bilinear(A, B, p, U, V, W, 2)) and not C.imag.any()
+
+
+def test_bilinear_complex_real_inputs_within_tolerance(oracle_mod):
+    p, U, V, W = algos.paper_strassen()
+    n = 128
+    Z1 = inputs.matrix(n, "uniform", seed=16) + 1j * inputs.matrix(n, "uniform", seed=17)
+    Z2 = inputs.matrix(n, "uniform", seed=18) + 1j * inputs.matrix(n, "uniform", seed=19)
+    C = oracle_mod.bilinear_complex(Z1, Z2, p, U, V, W, 2)
+    ref = oracle_mod.classic_complex(Z1, Z2)
+    assert np.max(np.abs(C - ref)) / (n * np.abs(Z1).max() * np.abs(Z2).max()) <= 1e-13
