@@ -335,7 +335,8 @@ def time_plan(torch, fmm, plan, dA, dB, dC, warmup, steps, dist=None, stream=Non
     for _ in range(steps):
         fmm.fmm_gemm(plan, dA, dB, dC, stream)
         leaf.append(fmm.fmm_plan_last_kernel_ms(plan)[0])
-        phases.append(fmm.fmm_plan_last_phase_ms(plan))
+        if plan.dtype not in ("c128", "c128_3m"):  # complex plans time the whole call only
+            phases.append(fmm.fmm_plan_last_phase_ms(plan))
     e1.record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -394,6 +395,34 @@ def run_sweep(a):
                           "leaf_ms": round(leaf, 3), "eff_tflops": round(2.0 * nn ** 3 / ms / 1e9, 4),
                           "exec_tflops_leaf_kernel": round(info["flops_leaf"] / leaf / 1e9, 4)}), flush=True)
         fmm.fmm_plan_destroy(plan)
+    if a.n == 8192:
+        # double complex: <4,4,4;49> depth 2 through four or three real fast products, and cuBLAS ZGEMM
+        # (torch.matmul on complex128) as context; effective complex flops 8 n^3
+        del cache
+        nn = 8192
+        Z1 = torch.complex(torch.from_numpy(inputs.matrix(nn, a.kind, seed=1)),
+                           torch.from_numpy(inputs.matrix(nn, a.kind, seed=3))).to(dev)
+        Z2 = torch.complex(torch.from_numpy(inputs.matrix(nn, a.kind, seed=2)),
+                           torch.from_numpy(inputs.matrix(nn, a.kind, seed=4))).to(dev)
+        Z3 = torch.empty_like(Z1)
+        for dt in ("c128", "c128_3m"):
+            plan = fmm.fmm_plan_create(nn, make_algo(fmm, "strassen^2"), 2, dtype=dt, record_kernel_time=True)
+            ms, _ = time_plan(torch, fmm, plan, Z1, Z2, Z3, 1, 2)
+            print(json.dumps({"n": nn, "algo": "strassen^2", "depth": 2, "schedule": "auto", "dtype": dt,
+                              "ms": round(ms, 3), "eff_complex_tflops": round(8.0 * nn ** 3 / ms / 1e9, 4)}),
+                  flush=True)
+            fmm.fmm_plan_destroy(plan)
+        torch.matmul(Z1, Z2, out=Z3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            torch.matmul(Z1, Z2, out=Z3)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 2
+        print(json.dumps({"n": nn, "algo": "cuBLAS ZGEMM (context)", "depth": 0, "schedule": "-", "dtype": "c128",
+                          "ms": round(ms, 3), "eff_complex_tflops": round(8.0 * nn ** 3 / ms / 1e9, 4)}), flush=True)
     return 0
 
 

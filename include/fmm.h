@@ -51,8 +51,18 @@ typedef enum {
 
 typedef enum {
     FMM_F64 = 0,       /* binary64 operands, FP64 tensor-core (DMMA) leaf products */
-    FMM_F64_OZAKI = 1  /* binary64 operands; S_r/T_r formed in FP64, leaf products emulated from
+    FMM_F64_OZAKI = 1, /* binary64 operands; S_r/T_r formed in FP64, leaf products emulated from
                           e4m3 slices (Ozaki scheme) on the tensor cores, post-additions in FP64 */
+    /* Double complex (Section 1 lists double complex among the types the
+     * algorithms deploy to): A, B, C are n x n row-major arrays of interleaved
+     * (re, im) binary64 pairs, 16-byte aligned, so each pointer addresses 2 n^2
+     * doubles.  The plan holds an FMM_F64 plan of the same algorithm and depth
+     * and splits the operands into real planes. */
+    FMM_C128 = 2,      /* four real fast products: Re C = Re A Re B - Im A Im B,
+                          Im C = Re A Im B + Im A Re B (each part as accurate as a real product) */
+    FMM_C128_3M = 3    /* three real fast products (Gauss): T1 = Re A Re B, T2 = Im A Im B,
+                          T3 = (Re A + Im A)(Re B + Im B); Re C = T1 - T2, Im C = (T3 - T1) - T2;
+                          25% fewer products, error bounded normwise rather than per part */
 } fmm_dtype_t;
 
 /* A bilinear algorithm <p,p,p;R>.  U, V, W are row-major p^2 x R int32

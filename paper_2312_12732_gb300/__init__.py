@@ -66,7 +66,7 @@ _PLANS = {}
 
 
 def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None, alpha=1.0, beta=0.0):
-    """C = alpha * A @ B + beta * out for square float64 CUDA tensors by the bilinear algorithm
+    """C = alpha * A @ B + beta * out for square float64 or complex128 CUDA tensors by the bilinear algorithm
     ``algo`` (a built-in name, ``"name^k"`` for its k-th Kronecker power, or an :class:`Algo`) at
     recursion ``depth``.
 
@@ -80,6 +80,8 @@ def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None, alp
     if not isinstance(A, torch.Tensor) or A.dim() != 2 or A.shape[0] != A.shape[1]:
         raise ValueError("A must be a square 2-D torch.Tensor")
     n = A.shape[0]
+    if A.is_complex() and dtype not in ("c128", "c128_3m"):
+        dtype = "c128"  # complex operands: four real fast products unless "c128_3m" is asked for
     if isinstance(algo, str):
         name, _, k = algo.partition("^")
         alg = algorithm(name, int(k) if k else 1)

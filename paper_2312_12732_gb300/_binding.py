@@ -19,10 +19,11 @@ LIB_PATH = os.path.join(_HERE, "libfmm.so")
 FMM_OK, FMM_ERR_INVALID, FMM_ERR_BRENT, FMM_ERR_UNSUPPORTED = 0, 1, 2, 3
 FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_NOT_FOUND = 4, 5, 6, 7
 FMM_ERR_SCRATCH_LIMIT = 8
-FMM_F64, FMM_F64_OZAKI = 0, 1
+FMM_F64, FMM_F64_OZAKI, FMM_C128, FMM_C128_3M = 0, 1, 2, 3
 FMM_SCHED_AUTO, FMM_SCHED_FUSED, FMM_SCHED_HYBRID = 0, 1, 2
 
-DTYPES = {"f64": FMM_F64, "f64_ozaki": FMM_F64_OZAKI}
+DTYPES = {"f64": FMM_F64, "f64_ozaki": FMM_F64_OZAKI, "c128": FMM_C128, "c128_3m": FMM_C128_3M}
+COMPLEX_DTYPES = ("c128", "c128_3m")
 SCHEDULES = {"auto": FMM_SCHED_AUTO, "fused": FMM_SCHED_FUSED, "hybrid": FMM_SCHED_HYBRID}
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -313,13 +314,14 @@ def _stream_ptr(stream) -> int:
     return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
 
 
-def _check_operand(X, n: int, name: str, device: bool = True):
+def _check_operand(X, n: int, name: str, device: bool = True, complex_: bool = False):
     import torch
 
     if not isinstance(X, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
-    if X.dtype != torch.float64 or X.shape != (n, n) or not X.is_contiguous():
-        raise ValueError(f"{name} must be a contiguous float64 tensor of shape ({n}, {n})")
+    want = torch.complex128 if complex_ else torch.float64
+    if X.dtype != want or X.shape != (n, n) or not X.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {str(want).replace('torch.', '')} tensor of shape ({n}, {n})")
     if device and not X.is_cuda:
         raise ValueError(f"{name} must live on a CUDA device")
     if not device and X.is_cuda:
@@ -327,20 +329,22 @@ def _check_operand(X, n: int, name: str, device: bool = True):
 
 
 def fmm_gemm(plan: Plan, A, B, C, stream=None):
-    """C = A @ B on the GPU (asynchronous on ``stream``, default: torch's current stream)."""
+    """C = A @ B on the GPU (asynchronous on ``stream``, default: torch's current stream); complex128
+    tensors for a "c128" / "c128_3m" plan, float64 otherwise."""
     n = plan.n
     for X, nm in ((A, "A"), (B, "B"), (C, "C")):
-        _check_operand(X, n, nm)
+        _check_operand(X, n, nm, complex_=plan.dtype in COMPLEX_DTYPES)
     _check(lib().fmm_gemm(plan.handle, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                           ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))), "fmm_gemm")
     return C
 
 
 def fmm_gemm_ex(plan: Plan, alpha: float, A, B, beta: float, C, stream=None):
-    """C = alpha * A @ B + beta * C on the GPU (beta = 0: C is not read; alpha = 0: A, B are not read)."""
+    """C = alpha * A @ B + beta * C on the GPU (beta = 0: C is not read; alpha = 0: A, B are not read);
+    real alpha and beta, also for complex plans."""
     n = plan.n
     for X, nm in ((A, "A"), (B, "B"), (C, "C")):
-        _check_operand(X, n, nm)
+        _check_operand(X, n, nm, complex_=plan.dtype in COMPLEX_DTYPES)
     _check(lib().fmm_gemm_ex(plan.handle, float(alpha), ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                              float(beta), ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
            "fmm_gemm_ex")
@@ -351,7 +355,7 @@ def fmm_gemm_host(plan: Plan, A, B, C, stream=None):
     """C = A @ B with host tensors; copies in and out inside the call (blocking)."""
     n = plan.n
     for X, nm in ((A, "A"), (B, "B"), (C, "C")):
-        _check_operand(X, n, nm, device=False)
+        _check_operand(X, n, nm, device=False, complex_=plan.dtype in COMPLEX_DTYPES)
     _check(lib().fmm_gemm_host(plan.handle, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                                ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
            "fmm_gemm_host")

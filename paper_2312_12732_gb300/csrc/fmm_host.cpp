@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -313,6 +314,9 @@ struct fmm_plan {
     double timeout_s = 5.0;
     int poison = 0;
     double wscale = 1.0;  // (den_u den_v den_w)^-depth of a rational algorithm, applied with W
+    // double complex (FMM_C128, FMM_C128_3M): the FP64 plan the real parts run on, and its planes
+    fmm_plan *inner = nullptr;
+    double *d_planes = nullptr;
     // device memory
     void *d_tables = nullptr;     // geometry + CSC tables
     size_t tables_bytes = 0;
@@ -399,6 +403,13 @@ bool make_slice_map(CUtensorMap *map, void *base, unsigned long long rows, unsig
 }
 
 void free_plan_memory(fmm_plan *pl) {
+    if (pl->inner) {
+        free_plan_memory(pl->inner);
+        delete pl->inner;
+        pl->inner = nullptr;
+    }
+    if (pl->d_planes) cudaFree(pl->d_planes);
+    pl->d_planes = nullptr;
     for (auto &e : pl->ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
     if (pl->d_tables) cudaFree(pl->d_tables);
@@ -531,6 +542,38 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     *out = nullptr;
     if (n < 1 || depth < 0 || depth > 8 || !algo_shape_ok(algo) || den < 1) return FMM_ERR_INVALID;
     if (n > (1LL << 31) / 2) return FMM_ERR_UNSUPPORTED;
+    if (dtype == FMM_C128 || dtype == FMM_C128_3M) {
+        // a real plan for the parts, and the planes: 4M splits A, B and C (6 planes),
+        // 3M splits A and B with their part sums and keeps three products (9 planes)
+        fmm_plan_t *inner = nullptr;
+        fmm_status_t st = plan_create(&inner, n, algo, depth, FMM_F64, opts, den);
+        if (st != FMM_OK) return st;
+        fmm_plan *pl = new (std::nothrow) fmm_plan();
+        if (!pl) {
+            fmm_plan_destroy(inner);
+            return FMM_ERR_OOM;
+        }
+        pl->inner = inner;
+        pl->device = inner->device;
+        pl->n = n; pl->p = inner->p; pl->R = inner->R; pl->depth = depth; pl->dtype = dtype;
+        pl->wscale = inner->wscale;
+        const size_t planes = dtype == FMM_C128 ? 6 : 9;
+        pl->ws_bytes = planes * (size_t)n * (size_t)n * sizeof(double);
+        if (cudaMalloc(&pl->d_planes, pl->ws_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            fmm_plan_destroy(pl);
+            return FMM_ERR_OOM;
+        }
+        if (opts && opts->record_kernel_time)
+            for (int e : {0, 1, 2})
+                if (cudaEventCreate(&pl->ev[e]) != cudaSuccess) {
+                    cudaGetLastError();
+                    fmm_plan_destroy(pl);
+                    return FMM_ERR_CUDA;
+                }
+        *out = pl;
+        return FMM_OK;
+    }
     if (dtype != FMM_F64 && dtype != FMM_F64_OZAKI) return FMM_ERR_UNSUPPORTED;
     if (den == 1 && fmm_algo_brent_mismatches(algo) != 0) return FMM_ERR_BRENT;
     // the scale (den^depth)^-1, rounded once; den^depth must be an exact double
@@ -1097,6 +1140,46 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     return FMM_OK;
 }
 
+// Double complex through real fast products on split planes (FMM_C128: four,
+// FMM_C128_3M: three; see fmm_dtype_t).  The 4M form accumulates its second
+// product of each part with beta = 1, so every part is one ordered sum.
+fmm_status_t gemm_complex(const fmm_plan *pl, double alpha, const double *A, const double *B, double beta, double *C,
+                          cudaStream_t st) {
+    const long long N = pl->n * pl->n;
+    double *P = pl->d_planes;
+    const fmm_plan *in = pl->inner;
+    if (pl->ev[0] && (cudaEventRecord(pl->ev[0], st) != cudaSuccess || cudaEventRecord(pl->ev[1], st) != cudaSuccess))
+        return FMM_ERR_CUDA;
+    fmm_status_t s = FMM_OK;
+    if (pl->dtype == FMM_C128) {
+        double *Ar = P, *Ai = P + N, *Br = P + 2 * N, *Bi = P + 3 * N, *Cr = P + 4 * N, *Ci = P + 5 * N;
+        if (fmm::launch_split_complex(A, N, Ar, Ai, nullptr, st) != cudaSuccess ||
+            fmm::launch_split_complex(B, N, Br, Bi, nullptr, st) != cudaSuccess ||
+            (beta != 0.0 && fmm::launch_split_complex(C, N, Cr, Ci, nullptr, st) != cudaSuccess))
+            return FMM_ERR_CUDA;
+        if ((s = fmm_gemm_ex(in, alpha, Ar, Br, beta, Cr, st)) != FMM_OK) return s;
+        if ((s = fmm_gemm_ex(in, -alpha, Ai, Bi, 1.0, Cr, st)) != FMM_OK) return s;
+        if ((s = fmm_gemm_ex(in, alpha, Ar, Bi, beta, Ci, st)) != FMM_OK) return s;
+        if ((s = fmm_gemm_ex(in, alpha, Ai, Br, 1.0, Ci, st)) != FMM_OK) return s;
+        if (fmm::launch_join_complex(Cr, Ci, C, N, st) != cudaSuccess) return FMM_ERR_CUDA;
+    } else {
+        double *Ar = P, *Ai = P + N, *As = P + 2 * N, *Br = P + 3 * N, *Bi = P + 4 * N, *Bs = P + 5 * N;
+        double *T1 = P + 6 * N, *T2 = P + 7 * N, *T3 = P + 8 * N;
+        if (fmm::launch_split_complex(A, N, Ar, Ai, As, st) != cudaSuccess ||
+            fmm::launch_split_complex(B, N, Br, Bi, Bs, st) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        if ((s = fmm_gemm(in, Ar, Br, T1, st)) != FMM_OK) return s;
+        if ((s = fmm_gemm(in, Ai, Bi, T2, st)) != FMM_OK) return s;
+        if ((s = fmm_gemm(in, As, Bs, T3, st)) != FMM_OK) return s;
+        if (fmm::launch_gauss_join(T1, T2, T3, C, N, alpha, beta, st) != cudaSuccess) return FMM_ERR_CUDA;
+    }
+    if (pl->ev[0]) {
+        if (cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
+        const_cast<fmm_plan *>(pl)->timed_once = true;
+    }
+    return FMM_OK;
+}
+
 }  // namespace
 
 extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const double *B, double *C, void *stream) {
@@ -1107,7 +1190,10 @@ extern "C" fmm_status_t fmm_gemm_ex(const fmm_plan_t *pl, double alpha, const do
                                     double *C, void *stream) {
     if (!pl || !A || !B || !C || !std::isfinite(alpha) || !std::isfinite(beta)) return FMM_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
-    if (alpha == 0.0) return cuda_status(fmm::launch_scale_c(C, pl->n, beta, st));  // A, B unread
+    const long long doubles = pl->n * pl->n * (pl->inner ? 2 : 1);
+    if (pl->inner && ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15) != 0) return FMM_ERR_INVALID;
+    if (alpha == 0.0) return cuda_status(fmm::launch_scale_c(C, doubles, beta, st));  // A, B unread
+    if (pl->inner) return gemm_complex(pl, alpha, A, B, beta, C, st);
     if (pl->ev[0] && cudaEventRecord(pl->ev[0], st) != cudaSuccess) return FMM_ERR_CUDA;
     fmm_status_t s = prepare(pl, A, B, st);
     if (s != FMM_OK) return s;
@@ -1138,7 +1224,7 @@ extern "C" fmm_status_t fmm_gemm_ex(const fmm_plan_t *pl, double alpha, const do
 }
 
 extern "C" fmm_status_t fmm_plan_last_phase_ms(const fmm_plan_t *pl, float *phases, int count) {
-    if (!pl || !phases || count < 1 || !pl->ev[0] || !pl->timed_once) return FMM_ERR_INVALID;
+    if (!pl || !phases || count < 1 || !pl->ev[0] || !pl->timed_once || pl->inner) return FMM_ERR_INVALID;
     if (cudaEventSynchronize(pl->ev[4]) != cudaSuccess) return FMM_ERR_CUDA;
     // [0] counter reset + materialization, [1] slicing (emulated leaf), [2] leaf kernel, [3] peel tasks,
     // [4] separate post-additions (emulated leaf)
@@ -1165,7 +1251,7 @@ extern "C" fmm_status_t fmm_plan_last_kernel_ms(const fmm_plan_t *pl, float *lea
 
 extern "C" fmm_status_t fmm_gemm_host(fmm_plan_t *pl, const double *hA, const double *hB, double *hC, void *stream) {
     if (!pl || !hA || !hB || !hC) return FMM_ERR_INVALID;
-    const size_t bytes = (size_t)pl->n * (size_t)pl->n * sizeof(double);
+    const size_t bytes = (size_t)pl->n * (size_t)pl->n * sizeof(double) * (pl->inner ? 2 : 1);
     if (!pl->d_hostA) {
         if (cudaMalloc(&pl->d_hostA, bytes) != cudaSuccess || cudaMalloc(&pl->d_hostB, bytes) != cudaSuccess ||
             cudaMalloc(&pl->d_hostC, bytes) != cudaSuccess) {
@@ -1392,6 +1478,7 @@ extern "C" fmm_status_t fmm_autotune(int64_t n, const fmm_algo_t *const *algos, 
 
 extern "C" fmm_status_t fmm_sync_status(const fmm_plan_t *pl, void *stream) {
     if (!pl) return FMM_ERR_INVALID;
+    if (pl->inner) return fmm_sync_status(pl->inner, stream);
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_ERR_CUDA;
     int err = 0;
@@ -1406,6 +1493,19 @@ extern "C" fmm_status_t fmm_sync_status(const fmm_plan_t *pl, void *stream) {
 
 extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t *info) {
     if (!pl || !info) return FMM_ERR_INVALID;
+    if (pl->inner) {
+        // a complex plan: its real plan's figures times the number of real products, plus the
+        // part sums and joins (4M: one add per element of each part; 3M: 2 n^2 sums, 3 n^2 joins)
+        fmm_status_t s = fmm_plan_get_info(pl->inner, info);
+        if (s != FMM_OK) return s;
+        const double k = pl->dtype == FMM_C128 ? 4.0 : 3.0;
+        const double n2 = (double)pl->n * (double)pl->n;
+        info->flops_leaf *= k;
+        info->flops_executed = k * info->flops_executed + (pl->dtype == FMM_C128 ? 2.0 : 5.0) * n2;
+        info->tasks = (int64_t)k * info->tasks;
+        info->workspace_bytes += pl->ws_bytes;
+        return FMM_OK;
+    }
     info->n = pl->n;
     info->p = pl->p;
     info->depth = pl->depth;
@@ -1435,7 +1535,9 @@ extern "C" fmm_status_t fmm_measure_e4m3_peak(void *stream, double *tflops) {
     return cuda_status(fmm::measure_e4m3_peak((cudaStream_t)stream, tflops));
 }
 
-extern "C" size_t fmm_plan_workspace_bytes(const fmm_plan_t *pl) { return pl ? pl->ws_bytes : 0; }
+extern "C" size_t fmm_plan_workspace_bytes(const fmm_plan_t *pl) {
+    return pl ? pl->ws_bytes + (pl->inner ? pl->inner->ws_bytes : 0) : 0;
+}
 
 extern "C" void fmm_plan_destroy(fmm_plan_t *pl) {
     if (!pl) return;

@@ -153,9 +153,20 @@ int ozaki_tc_max_pairs();
 cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
                                  double *C, long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
                                  double alpha, double beta, cudaStream_t s);
-// C = beta C over an n x n matrix (leading dimension n); beta = 0 stores zeros
-// without reading C (fmm_materialize.cu).
-cudaError_t launch_scale_c(double *C, long long n, double beta, cudaStream_t s);
+// C = beta C over `count` contiguous doubles; beta = 0 stores zeros without
+// reading C (fmm_materialize.cu).
+cudaError_t launch_scale_c(double *C, long long count, double beta, cudaStream_t s);
+
+// Double-complex planes (fmm_complex.cu); X and C are interleaved (re, im)
+// arrays of `count` complex entries, 16-byte aligned.
+// re, im (and sum = re + im when not null) <- X.
+cudaError_t launch_split_complex(const double *X, long long count, double *re, double *im, double *sum,
+                                 cudaStream_t s);
+// C <- (re, im).
+cudaError_t launch_join_complex(const double *re, const double *im, double *C, long long count, cudaStream_t s);
+// C <- alpha (T1 - T2, (T3 - T1) - T2) + beta C (beta = 0: C not read).
+cudaError_t launch_gauss_join(const double *T1, const double *T2, const double *T3, double *C, long long count,
+                              double alpha, double beta, cudaStream_t s);
 
 // Kernel launchers (fmm_f64.cu).  Return cudaSuccess or the launch error.
 // bn selects the tile configuration (128 or 64 columns).

@@ -162,8 +162,7 @@ __global__ void __launch_bounds__(256) scale_c_kernel(double *C, long long count
         C[t] = beta == 0.0 ? 0.0 : beta * C[t];
 }
 
-cudaError_t launch_scale_c(double *C, long long n, double beta, cudaStream_t s) {
-    const long long count = n * n;
+cudaError_t launch_scale_c(double *C, long long count, double beta, cudaStream_t s) {
     if (count <= 0 || beta == 1.0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
