@@ -393,7 +393,9 @@ def run_sweep(a):
                           "lowp_tflops_leaf_kernel": round(lowp, 1) if lowp else None,
                           "materialized": info["materialized_levels"], "ms": round(ms, 3),
                           "leaf_ms": round(leaf, 3), "eff_tflops": round(2.0 * nn ** 3 / ms / 1e9, 4),
-                          "exec_tflops_leaf_kernel": round(info["flops_leaf"] / leaf / 1e9, 4)}), flush=True)
+                          "exec_tflops_leaf_kernel": round(info["flops_leaf"] / leaf / 1e9, 4),
+                          "phases_ms": {k: round(v, 3) for k, v in (time_plan.last_phases or {}).items()}}),
+              flush=True)
         fmm.fmm_plan_destroy(plan)
     if a.n == 8192:
         # double complex: <4,4,4;49> depth 2 through four or three real fast products, and cuBLAS ZGEMM
@@ -564,18 +566,29 @@ def run_ours(a):
         if dist is not None:
             dist.barrier()
         k_e2e = max(2, a.steps // 2)
-        dev_ms = []
+        dev_ms, call_ms = [], []
         sampler_e2e = ClockSampler(gpu_uuid(torch, dev))
         with sampler_e2e:
             t0 = time.perf_counter()
             for _ in range(k_e2e):
+                tc = time.perf_counter()
                 fmm.fmm_gemm_host(plan, hA, hB, hC)
+                call_ms.append((time.perf_counter() - tc) * 1e3)
                 dev_ms.append(fmm.fmm_plan_last_kernel_ms(plan)[1])  # the call's device work, copies excluded
             t1 = time.perf_counter()
         te = max_over_ranks((t1 - t0) / k_e2e, dist, dev)
+        # the copies alone, same pinned buffers (context for the gap between e2e and device time)
+        torch.cuda.synchronize()
+        tc = time.perf_counter()
+        dA.copy_(hA, non_blocking=True)
+        dB.copy_(hB, non_blocking=True)
+        hC.copy_(dC, non_blocking=True)
+        torch.cuda.synchronize()
+        copy_ms = (time.perf_counter() - tc) * 1e3
         e2e = {"value": job_throughput(flops_eff, ws, te) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * n * n * 8,
                "d2h_bytes_per_step": n * n * 8, "ms_per_step": te * 1e3, "steps": k_e2e,
-               "device_ms_per_step": statistics.mean(dev_ms),
+               "device_ms_per_step": statistics.mean(dev_ms), "call_ms": [round(x, 2) for x in call_ms],
+               "device_ms": [round(x, 2) for x in dev_ms], "copies_alone_ms": round(copy_ms, 2),
                "clocks": sampler_e2e.summary(),
                "path": "fmm_gemm_host (pinned host buffers, copies inside the timed region)"}
 

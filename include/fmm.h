@@ -41,7 +41,7 @@ typedef enum {
     FMM_OK = 0,
     FMM_ERR_INVALID = 1,     /* bad argument: NULL pointer, n < 1, p < 2, R < 1, leaf size < 1 */
     FMM_ERR_BRENT = 2,       /* (U, V, W) fails the Brent equations in exact integer arithmetic */
-    FMM_ERR_UNSUPPORTED = 3, /* valid request this build does not implement (dtype, limits) */
+    FMM_ERR_UNSUPPORTED = 3, /* valid request the library does not implement (dtype, limits) */
     FMM_ERR_OOM = 4,         /* a device or host allocation failed */
     FMM_ERR_CUDA = 5,        /* a CUDA runtime call or kernel launch failed */
     FMM_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up (reported by fmm_sync_status) */

@@ -384,7 +384,7 @@ def fmm_gemm_batched(plans, As, Bs, Cs, stream=None, alphas=None, betas=None):
         raise ValueError("each product of a batch needs its own plan")
     for p, A, B, C in zip(plans, As, Bs, Cs):
         for X, nm in ((A, "A"), (B, "B"), (C, "C")):
-            _check_operand(X, p.n, nm)
+            _check_operand(X, p.n, nm, complex_=p.dtype in COMPLEX_DTYPES)  # the library rejects complex plans
     arr = ctypes.c_void_p * max(count, 1)
     hp = arr(*[p.handle.value for p in plans])
     ha = arr(*[A.data_ptr() for A in As])

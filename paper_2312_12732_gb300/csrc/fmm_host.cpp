@@ -369,7 +369,7 @@ namespace {
 
 fmm_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FMM_OK : FMM_ERR_CUDA; }
 
-// cuTensorMapEncodeTiled from the driver, without linking libcuda.
+// cuTensorMapEncodeTiled from the CUDA driver library, without linking libcuda.
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static bool tried = false;
