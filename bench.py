@@ -365,8 +365,13 @@ def run_sweep(a):
                 ("strassen", 4, "auto", 0)]
     configs = [c + ("f64",) for c in configs]
     configs += [("strassen", d, "auto", 0, "f64_ozaki") for d in (0, 1, 2, 3)]
-    configs += [("strassen_dyadic", d, "auto", 0, "f64") for d in (1, 2, 3)]
-    configs += [("strassen_thirds", 2, "auto", 0, "f64"), ("strassen_dyadic", 2, "auto", 0, "f64_ozaki")]
+    if a.n >= 16384:
+        # large sizes: the materialized schedules only (a fused row takes seconds per call)
+        configs = [c for c in configs if c[2] == "auto" and c[0] in ("strassen", "strassen^2", "winograd")
+                   and (c[0] != "winograd" or c[1] == 3)]
+    else:
+        configs += [("strassen_dyadic", d, "auto", 0, "f64") for d in (1, 2, 3)]
+        configs += [("strassen_thirds", 2, "auto", 0, "f64"), ("strassen_dyadic", 2, "auto", 0, "f64_ozaki")]
     n = a.n
     A, B = inputs.operands(n, a.kind, seed=1)
     dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
