@@ -288,8 +288,10 @@ fmm_status_t fmm_sync_status(const fmm_plan_t *plan, void *stream);
 /* Timing of the most recent fmm_gemm on a plan created with
  * record_kernel_time = 1: `leaf_ms` is the leaf-product kernel alone,
  * `total_ms` the whole call (counter reset, materialization, leaf kernel),
- * both measured with CUDA events on the call's stream.  Waits for the call's
- * end event.  FMM_ERR_INVALID if timing was not enabled or no call was made. */
+ * both measured with CUDA events on the call's stream.  For a complex plan
+ * (FMM_C128, FMM_C128_3M) both are the whole call: split, real products and
+ * join.  Waits for the call's end event.  FMM_ERR_INVALID if timing was not
+ * enabled or no call was made. */
 fmm_status_t fmm_plan_last_kernel_ms(const fmm_plan_t *plan, float *leaf_ms, float *total_ms);
 
 /* Phase times of the most recent fmm_gemm on a plan created with
@@ -299,7 +301,8 @@ fmm_status_t fmm_plan_last_kernel_ms(const fmm_plan_t *plan, float *leaf_ms, flo
  * the leaf-product kernel, phases[3] the peel tasks run after an emulated
  * leaf (0 otherwise), phases[4] the post-additions C_l = sum_r W[l][r] P_r
  * that the emulated leaf runs as a separate kernel (0 otherwise).  Fills
- * min(count, 5) entries; waits for the call. */
+ * min(count, 5) entries; waits for the call.  FMM_ERR_INVALID for a complex
+ * plan (its real plan records the phases of each real product separately). */
 fmm_status_t fmm_plan_last_phase_ms(const fmm_plan_t *plan, float *phases, int count);
 
 /* Calibration, with no counterpart in the paper: measures the FP64

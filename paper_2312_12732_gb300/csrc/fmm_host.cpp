@@ -1292,7 +1292,8 @@ extern "C" fmm_status_t fmm_gemm_batched_ex(fmm_plan_t *const *plans, const doub
     const auto be = [&](int i) { return beta ? beta[i] : 0.0; };
     // problems with alpha = 0 only scale C (A and B unread); they join no launch
     for (int i = 0; i < count; ++i)
-        if (al(i) == 0.0 && fmm::launch_scale_c(C[i], plans[i]->n, be(i), st) != cudaSuccess) return FMM_ERR_CUDA;
+        if (al(i) == 0.0 && fmm::launch_scale_c(C[i], plans[i]->n * plans[i]->n, be(i), st) != cudaSuccess)
+            return FMM_ERR_CUDA;
     // one grouped launch per tile width present in the batch
     for (int bn : {128, 64}) {
         std::vector<int> sel;
