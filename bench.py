@@ -402,11 +402,11 @@ def run_sweep(a):
                           "phases_ms": {k: round(v, 3) for k, v in (time_plan.last_phases or {}).items()}}),
               flush=True)
         fmm.fmm_plan_destroy(plan)
-    if a.n == 8192:
+    if a.n <= 8192:
         # double complex: <4,4,4;49> depth 2 through four or three real fast products, and cuBLAS ZGEMM
         # (torch.matmul on complex128) as context; effective complex flops 8 n^3
         del cache
-        nn = 8192
+        nn = a.n
         Z1 = torch.complex(torch.from_numpy(inputs.matrix(nn, a.kind, seed=1)),
                            torch.from_numpy(inputs.matrix(nn, a.kind, seed=3))).to(dev)
         Z2 = torch.complex(torch.from_numpy(inputs.matrix(nn, a.kind, seed=2)),
