@@ -4,9 +4,13 @@
  * Multiplication Algorithm Is Still Faster" (arXiv 2312.12732).
  *
  * The operation is C = A * B for square n x n binary64 matrices (Section 2,
- * definition of the matrix product; Section 3 states it as C = alpha A B, and
- * this library fixes alpha = 1 and overwrites C).  A bilinear algorithm
- * <p,p,p;R> is given by three integer p^2 x R matrices (U, V, W): with the
+ * definition of the matrix product).  Section 3 states it as C = alpha A B;
+ * fmm_gemm overwrites C with A B, and fmm_gemm_ex computes alpha A B + beta C.
+ * Double-complex operands are supported through the FMM_C128 dtypes
+ * (Section 1 lists double complex among the deployable types).  A bilinear
+ * algorithm <p,p,p;R> is given by three integer p^2 x R matrices (U, V, W),
+ * or by integer numerators over one denominator per matrix
+ * (fmm_algo_rational_t; Section 2 allows non-integer coefficients): with the
  * operands split by the factor p into row-major blocks A_0 .. A_{p^2-1}
  * (Section 2, the single-index partition), product r is
  *     P_r = S_r * T_r,   S_r = sum_i U[i][r] A_i,   T_r = sum_j V[j][r] B_j,

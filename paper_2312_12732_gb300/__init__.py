@@ -80,6 +80,8 @@ def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None, alp
     if not isinstance(A, torch.Tensor) or A.dim() != 2 or A.shape[0] != A.shape[1]:
         raise ValueError("A must be a square 2-D torch.Tensor")
     n = A.shape[0]
+    if out is None and beta != 0.0:
+        raise ValueError("beta != 0 needs out")
     if A.is_complex() and dtype not in ("c128", "c128_3m"):
         dtype = "c128"  # complex operands: four real fast products unless "c128_3m" is asked for
     if isinstance(algo, str):
@@ -95,8 +97,6 @@ def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None, alp
         with torch.cuda.device(A.device):
             plan = fmm_plan_create(n, alg, depth, dtype=dtype)
         _PLANS[key] = plan
-    if out is None and beta != 0.0:
-        raise ValueError("beta != 0 needs out")
     C = out if out is not None else torch.empty_like(A)
     if alpha == 1.0 and beta == 0.0:
         fmm_gemm(plan, A, B, C, stream)

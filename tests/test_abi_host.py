@@ -160,3 +160,31 @@ def test_rational_plan_create_rejects_bad_algorithms_before_touching_the_gpu(fmm
     with pytest.raises(fmm.FmmError) as e:
         fmm.fmm_plan_create(64, fmm.RationalAlgo(p, U, V, W, (du, 0, dw)), 1)
     assert e.value.status == 1  # FMM_ERR_INVALID
+
+
+def test_binding_checks_operands_before_calling_the_library(fmm):
+    """Tensor checks happen in the binding, before any C call: dtype (float64 for real plans,
+    complex128 for complex ones), shape, contiguity, and device."""
+    import torch
+
+    n = 8
+    real = fmm.Plan(0, n, None, 1, "f64")
+    cplx = fmm.Plan(0, n, None, 1, "c128")
+    X = torch.zeros(n, n, dtype=torch.float64)
+    Z = torch.zeros(n, n, dtype=torch.complex128)
+    with pytest.raises(ValueError, match="CUDA device"):
+        fmm.fmm_gemm(real, X, X, X)
+    with pytest.raises(ValueError, match="float64"):
+        fmm.fmm_gemm(real, Z, Z, Z)
+    with pytest.raises(ValueError, match="complex128"):
+        fmm.fmm_gemm_ex(cplx, 1.0, X, X, 0.0, X)
+    with pytest.raises(ValueError, match="shape"):
+        fmm.fmm_gemm(real, torch.zeros(n, n + 1, dtype=torch.float64), X, X)
+    with pytest.raises(ValueError, match="contiguous"):
+        fmm.fmm_gemm(real, X.t().contiguous().t()[:, :], X.t(), X)
+    with pytest.raises(ValueError, match="float64"):
+        fmm.fmm_gemm_host(real, Z, Z, Z)  # host path: a complex tensor for a real plan
+    with pytest.raises(ValueError, match="needs out"):
+        fmm.gemm(X, X, beta=1.0)
+    real.handle = None
+    cplx.handle = None
