@@ -17,6 +17,10 @@ Functions (each follows the passage cited in ``fmm_oracle.c``):
   `strassen`, level by level, with the peeling rule stated in the C source.
 * ``sample_dot2(A, B, rows, cols)`` -- compensated dot products (Ogita, Rump,
   Oishi 2005) for sampled reference entries.
+* ``rect_brent_mismatches(pm, pk, pn, U, V, W)`` / ``rect_bilinear(A, B, levels)``
+  -- rectangular algorithms <pm,pk,pn;R> (the factor-6 and factor-12 discussion
+  of Section 2), checked exactly and evaluated level by level, one algorithm per
+  level, on M x K times K x N operands.
 * ``classic_complex(A, B)`` / ``bilinear_complex(A, B, p, U, V, W, depth)`` --
   the same products for complex128 matrices (Section 1 names double complex
   among the deployable types): real coefficients act on both parts alike,
@@ -75,6 +79,12 @@ def _load():
         lib.fmm_oracle_dot2.argtypes = [i64, dp, i64, dp, i64]
         lib.fmm_oracle_sample_dot2.restype = None
         lib.fmm_oracle_sample_dot2.argtypes = [i64, dp, i64, dp, i64, i64, ip64, ip64, dp]
+        lib.fmm_oracle_rect_brent_mismatches.restype = i64
+        lib.fmm_oracle_rect_brent_mismatches.argtypes = [i32, i32, i32, i32, ip32, ip32, ip32]
+        pp32 = ctypes.POINTER(ip32)
+        lib.fmm_oracle_rect_bilinear.restype = ctypes.c_int
+        lib.fmm_oracle_rect_bilinear.argtypes = [i64, i64, i64, dp, i64, dp, i64, dp, i64, i32, ip32, pp32, pp32,
+                                                 pp32]
         lib.fmm_oracle_classic_complex.restype = None
         lib.fmm_oracle_classic_complex.argtypes = [i64, i64, i64, dp, i64, dp, i64, dp, i64]
         lib.fmm_oracle_bilinear_complex.restype = ctypes.c_int
@@ -158,6 +168,45 @@ def bilinear_rational(A, B, p: int, U, V, W, dens, depth: int) -> np.ndarray:
                                               _ip32(W), du, dv, dw, depth)
     if rc == -2:
         raise ValueError("oracle: denominators must be positive")
+    if rc != 0:
+        raise MemoryError("oracle: temporary allocation failed")
+    return C
+
+
+def _rect(alg):
+    pm, pk, pn, U, V, W = alg
+    U = np.ascontiguousarray(U, dtype=np.int32)
+    V = np.ascontiguousarray(V, dtype=np.int32)
+    W = np.ascontiguousarray(W, dtype=np.int32)
+    R = U.shape[1]
+    assert U.shape == (pm * pk, R) and V.shape == (pk * pn, R) and W.shape == (pm * pn, R)
+    return int(pm), int(pk), int(pn), R, U, V, W
+
+
+def rect_brent_mismatches(pm: int, pk: int, pn: int, U, V, W) -> int:
+    """Failed Brent equations of the rectangular algorithm <pm,pk,pn;R> (exact)."""
+    pm, pk, pn, R, U, V, W = _rect((pm, pk, pn, U, V, W))
+    return int(_load().fmm_oracle_rect_brent_mismatches(pm, pk, pn, R, _ip32(U), _ip32(V), _ip32(W)))
+
+
+def rect_bilinear(A, B, levels) -> np.ndarray:
+    """C = A B (M x K times K x N) by one recursion level per entry of ``levels``, each a
+    rectangular algorithm (pm, pk, pn, U, V, W), outermost first."""
+    A, B = _mat(A), _mat(B)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    lv = [_rect(a) for a in levels]
+    ip32 = ctypes.POINTER(ctypes.c_int32)
+    arr = ip32 * max(len(lv), 1)
+    dims = np.array([[a[0], a[1], a[2], a[3]] for a in lv] or [[1, 1, 1, 1]], dtype=np.int32).ravel()
+    Us = arr(*[_ip32(a[4]) for a in lv])
+    Vs = arr(*[_ip32(a[5]) for a in lv])
+    Ws = arr(*[_ip32(a[6]) for a in lv])
+    C = np.empty((M, N), dtype=np.float64)
+    rc = _load().fmm_oracle_rect_bilinear(M, K, N, _dp(A), K, _dp(B), N, _dp(C), N, len(lv), _ip32(dims), Us, Vs, Ws)
+    if rc == -2:
+        raise ValueError("oracle: bad level description")
     if rc != 0:
         raise MemoryError("oracle: temporary allocation failed")
     return C

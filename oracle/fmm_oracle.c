@@ -240,6 +240,145 @@ int fmm_oracle_bilinear_rational(int64_t n, const double *A, int64_t lda, const 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Rectangular algorithms <pm,pk,pn;R> (Section 2 and its discussion of split  */
+/* factors: a square problem of factor 6 or 12 can be solved by composing     */
+/* non-square basic products, 2x3x3 with 3x2x3 and so on).  A is split into a */
+/* pm x pk grid of blocks, B into pk x pn, C into pm x pn, all indexed         */
+/* row-major; U is (pm pk) x R, V is (pk pn) x R, W is (pm pn) x R.            */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Counts the index tuples (i, j, j2, k, i2, k2) with i, i2 < pm, j, j2 < pk,
+ * k, k2 < pn for which sum_r U[(i,j)][r] V[(j2,k)][r] W[(i2,k2)][r] differs
+ * from delta(j, j2) delta(i, i2) delta(k, k2); exact in int64.
+ */
+int64_t fmm_oracle_rect_brent_mismatches(int pm, int pk, int pn, int R, const int32_t *U, const int32_t *V,
+                                         const int32_t *W) {
+    int64_t bad = 0;
+    for (int i = 0; i < pm; ++i)
+        for (int j = 0; j < pk; ++j)
+            for (int j2 = 0; j2 < pk; ++j2)
+                for (int k = 0; k < pn; ++k)
+                    for (int i2 = 0; i2 < pm; ++i2)
+                        for (int k2 = 0; k2 < pn; ++k2) {
+                            const int32_t *u = U + (int64_t)(i * pk + j) * R;
+                            const int32_t *v = V + (int64_t)(j2 * pn + k) * R;
+                            const int32_t *w = W + (int64_t)(i2 * pn + k2) * R;
+                            int64_t sum = 0;
+                            for (int r = 0; r < R; ++r) sum += (int64_t)u[r] * v[r] * w[r];
+                            const int64_t want = (j == j2 && i == i2 && k == k2) ? 1 : 0;
+                            if (sum != want) ++bad;
+                        }
+    return bad;
+}
+
+typedef struct {
+    int pm, pk, pn, R;
+    const int32_t *U, *V, *W;
+} oracle_rect_alg;
+
+/* dst[0:rows,0:cols] (ld cols) = sum_i coef[i][r] * block i of src, ascending i;
+ * src is split into a gr x gc grid of rows x cols blocks. */
+static void combine_rect(int64_t rows, int64_t cols, int gr, int gc, int R, const int32_t *coef, int r,
+                         const double *src, int64_t ld, double *dst) {
+    for (int64_t x = 0; x < rows * cols; ++x) dst[x] = 0.0;
+    for (int i = 0; i < gr * gc; ++i) {
+        const int32_t c = coef[(int64_t)i * R + r];
+        if (c == 0) continue;
+        const double *blk = src + (int64_t)(i / gc) * rows * ld + (int64_t)(i % gc) * cols;
+        const double cd = (double)c;
+        for (int64_t y = 0; y < rows; ++y)
+            for (int64_t x = 0; x < cols; ++x) {
+                const double a = blk[y * ld + x];
+                if (c == 1)
+                    dst[y * cols + x] += a;
+                else if (c == -1)
+                    dst[y * cols + x] -= a;
+                else
+                    dst[y * cols + x] += cd * a;
+            }
+    }
+}
+
+/*
+ * C (M x N, ld ldc) = A (M x K) B (K x N) with level l of the recursion using
+ * algorithm levels[l] (l = 0 outermost); classic products below the last level
+ * or when a dimension is smaller than its split factor.  Peeling per
+ * dimension, as in the square recursion: with M', K', N' the largest
+ * multiples of pm, pk, pn,
+ *   C[:M',:N'] = fast(A[:M',:K'], B[:K',:N']) + A[:M',K':] B[K':,:N'],
+ *   C[:M',N':] = A[:M',:] B[:,N':],   C[M':,:] = A[M':,:] B.
+ */
+static int rect_rec(int64_t M, int64_t K, int64_t N, const double *A, int64_t lda, const double *B, int64_t ldb,
+                    double *C, int64_t ldc, const oracle_rect_alg *levels, int nlevels) {
+    if (nlevels <= 0 || M < levels[0].pm || K < levels[0].pk || N < levels[0].pn) {
+        fmm_oracle_classic(M, N, K, A, lda, B, ldb, C, ldc);
+        return 0;
+    }
+    const oracle_rect_alg *alg = &levels[0];
+    const int64_t Mc = M - M % alg->pm, Kc = K - K % alg->pk, Nc = N - N % alg->pn;
+    const int64_t bm = Mc / alg->pm, bk = Kc / alg->pk, bn = Nc / alg->pn;
+    double *S = (double *)malloc(sizeof(double) * bm * bk);
+    double *T = (double *)malloc(sizeof(double) * bk * bn);
+    double *Pr = (double *)malloc(sizeof(double) * bm * bn);
+    if (!S || !T || !Pr) {
+        free(S); free(T); free(Pr);
+        return -1;
+    }
+    for (int64_t y = 0; y < Mc; ++y)
+        for (int64_t x = 0; x < Nc; ++x) C[y * ldc + x] = 0.0;
+    int rc = 0;
+    for (int r = 0; r < alg->R && rc == 0; ++r) {
+        combine_rect(bm, bk, alg->pm, alg->pk, alg->R, alg->U, r, A, lda, S);
+        combine_rect(bk, bn, alg->pk, alg->pn, alg->R, alg->V, r, B, ldb, T);
+        rc = rect_rec(bm, bk, bn, S, bk, T, bn, Pr, bn, levels + 1, nlevels - 1);
+        for (int l = 0; l < alg->pm * alg->pn && rc == 0; ++l) {
+            const int32_t w = alg->W[(int64_t)l * alg->R + r];
+            if (w == 0) continue;
+            double *cb = C + (int64_t)(l / alg->pn) * bm * ldc + (int64_t)(l % alg->pn) * bn;
+            const double wd = (double)w;
+            for (int64_t y = 0; y < bm; ++y)
+                for (int64_t x = 0; x < bn; ++x) {
+                    const double v = Pr[y * bn + x];
+                    if (w == 1)
+                        cb[y * ldc + x] += v;
+                    else if (w == -1)
+                        cb[y * ldc + x] -= v;
+                    else
+                        cb[y * ldc + x] += wd * v;
+                }
+        }
+    }
+    free(S); free(T); free(Pr);
+    if (rc != 0) return rc;
+    if (K > Kc && Mc > 0 && Nc > 0) {
+        double *tmp = (double *)malloc(sizeof(double) * Mc * Nc);
+        if (!tmp) return -1;
+        fmm_oracle_classic(Mc, Nc, K - Kc, A + Kc, lda, B + Kc * ldb, ldb, tmp, Nc);
+        for (int64_t y = 0; y < Mc; ++y)
+            for (int64_t x = 0; x < Nc; ++x) C[y * ldc + x] += tmp[y * Nc + x];
+        free(tmp);
+    }
+    if (N > Nc) fmm_oracle_classic(Mc, N - Nc, K, A, lda, B + Nc, ldb, C + Nc, ldc);
+    if (M > Mc) fmm_oracle_classic(M - Mc, N, K, A + Mc * lda, lda, B, ldb, C + Mc * ldc, ldc);
+    return 0;
+}
+
+/* The recursion above; tables[l] = {pm, pk, pn, R} of level l, U/V/W[l] its tables. */
+int fmm_oracle_rect_bilinear(int64_t M, int64_t K, int64_t N, const double *A, int64_t lda, const double *B,
+                             int64_t ldb, double *C, int64_t ldc, int nlevels, const int32_t *dims,
+                             const int32_t *const *U, const int32_t *const *V, const int32_t *const *W) {
+    oracle_rect_alg lv[16];
+    if (nlevels < 0 || nlevels > 16) return -2;
+    for (int l = 0; l < nlevels; ++l) {
+        lv[l].pm = dims[4 * l]; lv[l].pk = dims[4 * l + 1]; lv[l].pn = dims[4 * l + 2]; lv[l].R = dims[4 * l + 3];
+        lv[l].U = U[l]; lv[l].V = V[l]; lv[l].W = W[l];
+        if (lv[l].pm < 1 || lv[l].pk < 1 || lv[l].pn < 1 || lv[l].R < 1) return -2;
+    }
+    return rect_rec(M, K, N, A, lda, B, ldb, C, ldc, lv, nlevels);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Double complex (Section 1 lists single and double complex among the types  */
 /* the algorithms deploy to).  A complex matrix is stored interleaved: entry  */
 /* (i, j) is re at 2 (i ld + j), im right after it, ld counted in complex      */

@@ -473,3 +473,104 @@ def test_bilinear_complex_real_inputs_within_tolerance(oracle_mod):
     C = oracle_mod.bilinear_complex(Z1, Z2, p, U, V, W, 2)
     ref = oracle_mod.classic_complex(Z1, Z2)
     assert np.max(np.abs(C - ref)) / (n * np.abs(Z1).max() * np.abs(Z2).max()) <= 1e-13
+
+
+# --- rectangular algorithms <m,k,n;R> (Section 2: factor-6 and factor-12 problems through
+#     non-square basic products composed by Kronecker products) ---------------------------------
+
+from golden import rect_algos  # noqa: E402
+
+
+def _rect_family():
+    s = rect_algos.strassen_223()
+    return {"classic_232": rect_algos.classic(2, 3, 2), "classic_314": rect_algos.classic(3, 1, 4),
+            "strassen_223": s, "transpose_322": rect_algos.transpose(s), "cyclic_232": rect_algos.cyclic(s),
+            "cyclic2_322": rect_algos.cyclic(rect_algos.cyclic(s)),
+            "compose_466": rect_algos.compose(s, rect_algos.cyclic(s))}
+
+
+@pytest.mark.parametrize("name", list(_rect_family()))
+def test_rect_brent_accepts_constructed_algorithms(oracle_mod, name):
+    m, k, n, U, V, W = _rect_family()[name]
+    assert oracle_mod.rect_brent_mismatches(m, k, n, U, V, W) == 0
+
+
+def test_rect_brent_rejects_every_single_entry_change(oracle_mod):
+    m, k, n, U, V, W = rect_algos.strassen_223()
+    for M in (U, V, W):
+        for idx in itertools.product(range(M.shape[0]), range(M.shape[1])):
+            M[idx] += 1
+            assert oracle_mod.rect_brent_mismatches(m, k, n, U, V, W) > 0
+            M[idx] -= 1
+
+
+def test_rect_brent_on_square_tables_is_the_square_check(oracle_mod):
+    for name in ("paper_strassen", "winograd", "laderman"):
+        p, U, V, W = all_algos()[name]
+        assert oracle_mod.rect_brent_mismatches(p, p, p, U, V, W) == oracle_mod.brent_mismatches(p, U, V, W) == 0
+        U2 = U.copy(); U2[1, 2] += 1
+        assert oracle_mod.rect_brent_mismatches(p, p, p, U2, V, W) == oracle_mod.brent_mismatches(p, U2, V, W) > 0
+
+
+def test_rect_symmetries_need_their_grid_transposes(oracle_mod):
+    """Swapping U and V without transposing their block grids, or a Kronecker product without the
+    row-major re-indexing, is not an algorithm."""
+    m, k, n, U, V, W = rect_algos.strassen_223()
+    assert oracle_mod.rect_brent_mismatches(n, k, m, V, U, W.copy()) > 0
+    s = rect_algos.strassen_223()
+    c = rect_algos.cyclic(s)
+    plain = (4, 6, 6, np.kron(s[3], c[3]).astype(np.int32), np.kron(s[4], c[4]).astype(np.int32),
+             np.kron(s[5], c[5]).astype(np.int32))
+    # np.kron of the rows orders the composed block index (a1, b1, a2, b2), not row-major (a1, a2, b1, b2)
+    assert oracle_mod.rect_brent_mismatches(*plain) > 0
+
+
+def test_rect_bilinear_exhaustive_basis_pairs(oracle_mod):
+    s = rect_algos.strassen_223()
+    for i, j, k, l in itertools.product(range(2), range(2), range(2), range(3)):
+        A = np.zeros((2, 2)); A[i, j] = 1.0
+        B = np.zeros((2, 3)); B[k, l] = 1.0
+        want = np.zeros((2, 3))
+        if j == k:
+            want[i, l] = 1.0
+        assert np.array_equal(oracle_mod.rect_bilinear(A, B, [s]), want), (i, j, k, l)
+
+
+@pytest.mark.parametrize("M,K,N,levels", [(8, 8, 12, 1), (37, 29, 41, 2), (24, 36, 36, 2), (5, 3, 2, 3)])
+def test_rect_bilinear_bit_exact_on_integers(oracle_mod, M, K, N, levels):
+    s = rect_algos.strassen_223()
+    seq = [s, rect_algos.cyclic(s), rect_algos.cyclic(rect_algos.cyclic(s))][:levels]
+    A = inputs.matrix(M, "integer", seed=M, m=K)
+    B = inputs.matrix(K, "integer", seed=N, m=N)
+    assert np.array_equal(oracle_mod.rect_bilinear(A, B, seq), A @ B)
+
+
+def test_rect_bilinear_with_square_levels_is_the_square_recursion(oracle_mod):
+    p, U, V, W = algos.paper_strassen()
+    A, B = inputs.operands(101, "uniform", seed=12)
+    sq = (p, p, p, U, V, W)
+    assert np.array_equal(oracle_mod.rect_bilinear(A, B, [sq, sq, sq]), oracle_mod.bilinear(A, B, p, U, V, W, 3))
+
+
+def test_composed_rect_algorithm_equals_nested_levels(oracle_mod):
+    """One level of compose(a, b) computes exactly what level a over level b computes (exact on
+    integers; within rounding on real inputs, where the summation orders differ)."""
+    s = rect_algos.strassen_223()
+    c = rect_algos.cyclic(s)
+    comp = rect_algos.compose(s, c)
+    A = inputs.matrix(40, "integer", seed=3, m=60)
+    B = inputs.matrix(60, "integer", seed=4, m=60)
+    assert np.array_equal(oracle_mod.rect_bilinear(A, B, [comp]), oracle_mod.rect_bilinear(A, B, [s, c]))
+    A = inputs.matrix(40, "uniform", seed=5, m=60)
+    B = inputs.matrix(60, "uniform", seed=6, m=60)
+    d = oracle_mod.rect_bilinear(A, B, [comp]) - oracle_mod.rect_bilinear(A, B, [s, c])
+    assert np.max(np.abs(d)) <= 1e-13 * 60
+
+
+def test_square_12_from_three_rotations(oracle_mod):
+    """<2,2,3;11> (x) <2,3,2;11> (x) <3,2,2;11> is a square <12;1331> that the square recursion runs."""
+    m, k, n, U, V, W = rect_algos.strassen_12()
+    assert (m, k, n, U.shape[1]) == (12, 12, 12, 1331)
+    assert oracle_mod.brent_mismatches(12, U, V, W) == 0
+    A, B = inputs.operands(24, "integer", seed=9)
+    assert np.array_equal(oracle_mod.bilinear(A, B, 12, U, V, W, 1), A @ B)
