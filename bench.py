@@ -60,6 +60,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cublas", action="store_true", help="skip the cuBLAS DGEMM context timing")
     ap.add_argument("--cpu-n", type=int, default=4096, help="size of the CPU-oracle sample")
     ap.add_argument("--sweep", action="store_true", help="print one JSON line per algorithm/depth/schedule")
+    ap.add_argument("--only", default="", help="sweep: comma-separated algorithm names to keep (default: all)")
     ap.add_argument("--batched", action="store_true",
                     help="batched workload: 256 products, n log-uniform in [128, 4096], one captured graph")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -290,6 +291,16 @@ def run_reference(a):
 def make_algo(fmm, name):
     if name.endswith("^2"):
         return fmm.algorithm(name[:-2], 2)
+    if name in ("rect_12", "rect_6"):
+        # square algorithms composed from rectangular ones: <2,2,3;11> (x) <2,3,2;11> (x) <3,2,2;11> = <12;1331>,
+        # <2,2,3;11> (x) classic <3,3,2;18> = <6;198>
+        s = fmm.fmm_algo_rect_builtin("strassen_2x2x3")
+        c = fmm.fmm_algo_rect_cyclic(s)
+        if name == "rect_12":
+            r = fmm.fmm_algo_rect_compose(fmm.fmm_algo_rect_compose(s, c), fmm.fmm_algo_rect_cyclic(c))
+        else:
+            r = fmm.fmm_algo_rect_compose(s, fmm.fmm_algo_rect_classic(3, 3, 2))
+        return fmm.fmm_algo_rect_as_square(r)
     if name in ("strassen_dyadic", "strassen_thirds"):
         # Strassen in a basis with non-integer coefficients (exact change of basis, test fixture)
         from tests.golden import rational_algos
@@ -372,6 +383,10 @@ def run_sweep(a):
     else:
         configs += [("strassen_dyadic", d, "auto", 0, "f64") for d in (1, 2, 3)]
         configs += [("strassen_thirds", 2, "auto", 0, "f64"), ("strassen_dyadic", 2, "auto", 0, "f64_ozaki")]
+        configs += [("rect_12", 1, "auto", 0, "f64"), ("rect_6", 1, "auto", 0, "f64"), ("rect_6", 2, "auto", 0, "f64")]
+    if a.only:
+        keep = set(a.only.split(","))
+        configs = [c for c in configs if c[0] in keep]
     n = a.n
     A, B = inputs.operands(n, a.kind, seed=1)
     dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
@@ -381,6 +396,8 @@ def run_sweep(a):
         rows += [(6912, ("laderman", d, s, 0, "f64")) for d in (1, 2) for s in ("fused", "auto")]
         rows += [(6912, ("strassen", 0, "auto", 0, "f64"))]
         rows += [(16384, ("strassen", d, "auto", 0, "f64_ozaki")) for d in (0, 2)]
+    if a.only:
+        rows = [r for r in rows if r[1][0] in set(a.only.split(","))]
     cache = {n: (dA, dB, dC)}
     for nn, (algo_name, depth, sched, ml, dt) in rows:
         if nn not in cache:
@@ -402,7 +419,7 @@ def run_sweep(a):
                           "phases_ms": {k: round(v, 3) for k, v in (time_plan.last_phases or {}).items()}}),
               flush=True)
         fmm.fmm_plan_destroy(plan)
-    if a.n <= 8192:
+    if a.n <= 8192 and (not a.only or "complex" in a.only.split(",")):
         # double complex: <4,4,4;49> depth 2 through four or three real fast products, and cuBLAS ZGEMM
         # (torch.matmul on complex128) as context; effective complex flops 8 n^3
         del cache

@@ -163,6 +163,62 @@ fmm_status_t fmm_algo_builtin(const char *name, fmm_algo_t *out);
  * algorithm multiplies exactly.  Host-only.  Returns -1 for invalid input. */
 int64_t fmm_algo_brent_mismatches(const fmm_algo_t *algo);
 
+/* Rectangular algorithms <m,k,n;R> (Section 2: a square problem of split
+ * factor 6 or 12 can be solved through non-square basic products, 2x3x3 with
+ * 3x2x3 and so on, composed by Kronecker products).  A is split into an m x k
+ * grid of blocks, B into k x n, C into m x n, each indexed row-major; U is
+ * (m k) x R, V is (k n) x R, W is (m n) x R, int32, entry [i][r] at i*R + r.
+ * Plans multiply square operands: a rectangular algorithm reaches them as a
+ * factor of a square composition (fmm_algo_rect_compose, then
+ * fmm_algo_rect_as_square). */
+typedef struct {
+    int m, k, n;
+    int R;
+    const int32_t *U;
+    const int32_t *V;
+    const int32_t *W;
+} fmm_algo_rect_t;
+
+/* Failed Brent equations of a rectangular algorithm: the (m k n)^2 index
+ * triples (i,j) of A, (j2,l) of B, (i2,l2) of C for which
+ * sum_r U V W != delta(j,j2) delta(i,i2) delta(l,l2), summed exactly in int64
+ * over the nonzeros of each product (exact for coefficients below 2^21 in
+ * magnitude).  -1 for invalid input. */
+int64_t fmm_algo_rect_brent_mismatches(const fmm_algo_rect_t *algo);
+
+/* Built-in rectangular algorithms (tables owned by the library):
+ * "strassen_2x2x3" is <2,2,3;11>, Strassen's seven products on the first two
+ * block columns of B and C plus the four classic products A_i0 B_02,
+ * A_i1 B_12 for the third.  FMM_ERR_NOT_FOUND for other names. */
+fmm_status_t fmm_algo_rect_builtin(const char *name, fmm_algo_rect_t *out);
+
+/* The classic <m,k,n; m k n> into caller arrays U[(m k) (m k n)],
+ * V[(k n) (m k n)], W[(m n) (m k n)] (product (i,j,l) = A_ij B_jl into C_il).
+ * FMM_ERR_UNSUPPORTED for m k n > 2^20. */
+fmm_status_t fmm_algo_rect_classic(int m, int k, int n, int32_t *U, int32_t *V, int32_t *W, fmm_algo_rect_t *out);
+
+/* Symmetries every algorithm has, into caller arrays of the input's sizes:
+ * transpose gives <n,k,m> from (A B)^T = B^T A^T (tables V^T, U^T, W^T, with
+ * ^T transposing the block grid); cyclic gives <k,n,m> from the rotation of
+ * the trilinear form sum A_ab B_bd C_ad (tables V, W^T, U^T). */
+fmm_status_t fmm_algo_rect_transpose(const fmm_algo_rect_t *in, int32_t *U, int32_t *V, int32_t *W,
+                                     fmm_algo_rect_t *out);
+fmm_status_t fmm_algo_rect_cyclic(const fmm_algo_rect_t *in, int32_t *U, int32_t *V, int32_t *W,
+                                  fmm_algo_rect_t *out);
+
+/* Kronecker composition <m1 m2, k1 k2, n1 n2; R1 R2> into caller arrays of
+ * (m k) R, (k n) R and (m n) R entries; composed blocks are re-indexed
+ * row-major (block (a1 r2 + a2, b1 c2 + b2) of each grid) and product
+ * (r1, r2) is r1 R2 + r2, so the first factor is the outer recursion level
+ * (Section 2: the order of the factors changes temporary space and error).
+ * FMM_ERR_UNSUPPORTED if a table would reach 2^30 entries. */
+fmm_status_t fmm_algo_rect_compose(const fmm_algo_rect_t *first, const fmm_algo_rect_t *second, int32_t *U,
+                                   int32_t *V, int32_t *W, fmm_algo_rect_t *out);
+
+/* A square view <p,p,p;R> (p = m = k = n) of a rectangular algorithm, sharing
+ * its tables; FMM_ERR_UNSUPPORTED unless m = k = n. */
+fmm_status_t fmm_algo_rect_as_square(const fmm_algo_rect_t *in, fmm_algo_t *out);
+
 /* The Brent equations of a rational algorithm, multiplied through by
  * den_u den_v den_w: sum_r U V W = den_u den_v den_w delta delta delta over the
  * numerators, exact in int64.  Returns the number of violated equations, or -1

@@ -32,7 +32,15 @@ from ._binding import (  # noqa: F401
     fmm_algo_compose,
     fmm_algo_from_transposed_c,
     fmm_algo_rational_brent_mismatches,
+    fmm_algo_rect_as_square,
+    fmm_algo_rect_brent_mismatches,
+    fmm_algo_rect_builtin,
+    fmm_algo_rect_classic,
+    fmm_algo_rect_compose,
+    fmm_algo_rect_cyclic,
+    fmm_algo_rect_transpose,
     RationalAlgo,
+    RectAlgo,
     fmm_gemm,
     fmm_gemm_batched,
     fmm_gemm_ex,

@@ -33,6 +33,11 @@ class fmm_algo_t(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("R", ctypes.c_int), ("U", _i32p), ("V", _i32p), ("W", _i32p)]
 
 
+class fmm_algo_rect_t(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("k", ctypes.c_int), ("n", ctypes.c_int), ("R", ctypes.c_int), ("U", _i32p),
+                ("V", _i32p), ("W", _i32p)]
+
+
 class fmm_algo_rational_t(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("R", ctypes.c_int), ("U", _i32p), ("V", _i32p), ("W", _i32p),
                 ("den_u", ctypes.c_int32), ("den_v", ctypes.c_int32), ("den_w", ctypes.c_int32)]
@@ -67,6 +72,17 @@ SIGNATURES = [
                                           ctypes.POINTER(fmm_algo_t), ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(fmm_plan_options_t)]),
     ("fmm_algo_rational_brent_mismatches", ctypes.c_int64, [ctypes.POINTER(fmm_algo_rational_t)]),
+    ("fmm_algo_rect_brent_mismatches", ctypes.c_int64, [ctypes.POINTER(fmm_algo_rect_t)]),
+    ("fmm_algo_rect_builtin", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(fmm_algo_rect_t)]),
+    ("fmm_algo_rect_classic", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _i32p,
+                                             ctypes.POINTER(fmm_algo_rect_t)]),
+    ("fmm_algo_rect_transpose", ctypes.c_int, [ctypes.POINTER(fmm_algo_rect_t), _i32p, _i32p, _i32p,
+                                               ctypes.POINTER(fmm_algo_rect_t)]),
+    ("fmm_algo_rect_cyclic", ctypes.c_int, [ctypes.POINTER(fmm_algo_rect_t), _i32p, _i32p, _i32p,
+                                            ctypes.POINTER(fmm_algo_rect_t)]),
+    ("fmm_algo_rect_compose", ctypes.c_int, [ctypes.POINTER(fmm_algo_rect_t), ctypes.POINTER(fmm_algo_rect_t), _i32p,
+                                             _i32p, _i32p, ctypes.POINTER(fmm_algo_rect_t)]),
+    ("fmm_algo_rect_as_square", ctypes.c_int, [ctypes.POINTER(fmm_algo_rect_t), ctypes.POINTER(fmm_algo_t)]),
     ("fmm_plan_create_rational", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
                                                 ctypes.POINTER(fmm_algo_rational_t), ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(fmm_plan_options_t)]),
@@ -184,6 +200,103 @@ class RationalAlgo:
 
     def __repr__(self):
         return f"RationalAlgo({self.name}, <{self.p},{self.p},{self.p};{self.R}>, dens={self.dens})"
+
+
+class RectAlgo:
+    """A rectangular algorithm <m,k,n;R> (U over A's m x k block grid, V over B's k x n grid, W over
+    C's m x n grid, row-major); keeps its int32 tables alive for the C struct."""
+
+    def __init__(self, m: int, k: int, n: int, U, V, W, name: str = "rect"):
+        self.m, self.k, self.n = int(m), int(k), int(n)
+        self.U = np.ascontiguousarray(U, dtype=np.int32)
+        self.V = np.ascontiguousarray(V, dtype=np.int32)
+        self.W = np.ascontiguousarray(W, dtype=np.int32)
+        R = self.U.shape[1] if self.U.ndim == 2 else -1
+        if not (self.U.shape == (self.m * self.k, R) and self.V.shape == (self.k * self.n, R)
+                and self.W.shape == (self.m * self.n, R)):
+            raise ValueError("U, V, W must be (m k) x R, (k n) x R and (m n) x R")
+        self.R = int(R)
+        self.name = name
+
+    def c_struct(self) -> fmm_algo_rect_t:
+        return fmm_algo_rect_t(self.m, self.k, self.n, self.R, self.U.ctypes.data_as(_i32p),
+                               self.V.ctypes.data_as(_i32p), self.W.ctypes.data_as(_i32p))
+
+    def __repr__(self):
+        return f"RectAlgo({self.name}, <{self.m},{self.k},{self.n};{self.R}>)"
+
+
+def _rect_from(out: fmm_algo_rect_t, name: str) -> RectAlgo:
+    m, k, n, R = out.m, out.k, out.n, out.R
+    U = np.ctypeslib.as_array(out.U, shape=(m * k * R,)).reshape(m * k, R).copy()
+    V = np.ctypeslib.as_array(out.V, shape=(k * n * R,)).reshape(k * n, R).copy()
+    W = np.ctypeslib.as_array(out.W, shape=(m * n * R,)).reshape(m * n, R).copy()
+    return RectAlgo(m, k, n, U, V, W, name=name)
+
+
+def fmm_algo_rect_builtin(name: str) -> RectAlgo:
+    out = fmm_algo_rect_t()
+    _check(lib().fmm_algo_rect_builtin(name.encode(), ctypes.byref(out)), f"fmm_algo_rect_builtin({name!r})")
+    return _rect_from(out, name)
+
+
+def fmm_algo_rect_classic(m: int, k: int, n: int) -> RectAlgo:
+    R = m * k * n
+    U = np.empty((m * k, R), dtype=np.int32)
+    V = np.empty((k * n, R), dtype=np.int32)
+    W = np.empty((m * n, R), dtype=np.int32)
+    out = fmm_algo_rect_t()
+    _check(lib().fmm_algo_rect_classic(m, k, n, U.ctypes.data_as(_i32p), V.ctypes.data_as(_i32p),
+                                       W.ctypes.data_as(_i32p), ctypes.byref(out)), "fmm_algo_rect_classic")
+    return RectAlgo(m, k, n, U, V, W, name=f"classic_{m}x{k}x{n}")
+
+
+def fmm_algo_rect_brent_mismatches(algo: RectAlgo) -> int:
+    a = algo.c_struct()
+    return int(lib().fmm_algo_rect_brent_mismatches(ctypes.byref(a)))
+
+
+def _rect_unary(fn, algo: RectAlgo, sizes, tag: str) -> RectAlgo:
+    U = np.empty(sizes[0], dtype=np.int32)
+    V = np.empty(sizes[1], dtype=np.int32)
+    W = np.empty(sizes[2], dtype=np.int32)
+    a, out = algo.c_struct(), fmm_algo_rect_t()
+    _check(fn(ctypes.byref(a), U.ctypes.data_as(_i32p), V.ctypes.data_as(_i32p), W.ctypes.data_as(_i32p),
+              ctypes.byref(out)), tag)
+    return RectAlgo(out.m, out.k, out.n, U.reshape(out.m * out.k, out.R), V.reshape(out.k * out.n, out.R),
+                    W.reshape(out.m * out.n, out.R), name=f"{tag}({algo.name})")
+
+
+def fmm_algo_rect_transpose(algo: RectAlgo) -> RectAlgo:
+    """<n,k,m> from (A B)^T = B^T A^T."""
+    m, k, n, R = algo.m, algo.k, algo.n, algo.R
+    return _rect_unary(lib().fmm_algo_rect_transpose, algo, (n * k * R, k * m * R, n * m * R), "transpose")
+
+
+def fmm_algo_rect_cyclic(algo: RectAlgo) -> RectAlgo:
+    """<k,n,m> from the rotation of the trilinear form."""
+    m, k, n, R = algo.m, algo.k, algo.n, algo.R
+    return _rect_unary(lib().fmm_algo_rect_cyclic, algo, (k * n * R, n * m * R, k * m * R), "cyclic")
+
+
+def fmm_algo_rect_compose(first: RectAlgo, second: RectAlgo) -> RectAlgo:
+    """<m1 m2, k1 k2, n1 n2; R1 R2>, the first factor outermost."""
+    m, k, n, R = first.m * second.m, first.k * second.k, first.n * second.n, first.R * second.R
+    U = np.empty((m * k, R), dtype=np.int32)
+    V = np.empty((k * n, R), dtype=np.int32)
+    W = np.empty((m * n, R), dtype=np.int32)
+    a1, a2, out = first.c_struct(), second.c_struct(), fmm_algo_rect_t()
+    _check(lib().fmm_algo_rect_compose(ctypes.byref(a1), ctypes.byref(a2), U.ctypes.data_as(_i32p),
+                                       V.ctypes.data_as(_i32p), W.ctypes.data_as(_i32p), ctypes.byref(out)),
+           "fmm_algo_rect_compose")
+    return RectAlgo(m, k, n, U, V, W, name=f"{first.name}x{second.name}")
+
+
+def fmm_algo_rect_as_square(algo: RectAlgo) -> Algo:
+    """The square algorithm <p,p,p;R> of a rectangular one with m = k = n (plans take square ones)."""
+    a, out = algo.c_struct(), fmm_algo_t()
+    _check(lib().fmm_algo_rect_as_square(ctypes.byref(a), ctypes.byref(out)), "fmm_algo_rect_as_square")
+    return Algo(algo.m, algo.U, algo.V, algo.W, name=algo.name)
 
 
 def fmm_algo_rational_brent_mismatches(algo: RationalAlgo) -> int:

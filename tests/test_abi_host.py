@@ -188,3 +188,57 @@ def test_binding_checks_operands_before_calling_the_library(fmm):
         fmm.gemm(X, X, beta=1.0)
     real.handle = None
     cplx.handle = None
+
+
+def test_rect_tables_match_the_golden_constructions(fmm, oracle_mod):
+    """The library's <2,2,3;11>, its transpose and rotations, compositions and classic tables equal
+    the independent constructions in tests/golden/rect_algos.py entry for entry, and both Brent
+    implementations accept them."""
+    from golden import rect_algos
+
+    def same(lib_alg, gold):
+        m, k, n, U, V, W = gold
+        assert (lib_alg.m, lib_alg.k, lib_alg.n) == (m, k, n)
+        assert np.array_equal(lib_alg.U, U) and np.array_equal(lib_alg.V, V) and np.array_equal(lib_alg.W, W)
+        assert fmm.fmm_algo_rect_brent_mismatches(lib_alg) == 0 == oracle_mod.rect_brent_mismatches(*gold)
+
+    s = fmm.fmm_algo_rect_builtin("strassen_2x2x3")
+    g = rect_algos.strassen_223()
+    same(s, g)
+    same(fmm.fmm_algo_rect_transpose(s), rect_algos.transpose(g))
+    same(fmm.fmm_algo_rect_cyclic(s), rect_algos.cyclic(g))
+    c, gc = fmm.fmm_algo_rect_cyclic(s), rect_algos.cyclic(g)
+    same(fmm.fmm_algo_rect_compose(s, c), rect_algos.compose(g, gc))
+    same(fmm.fmm_algo_rect_classic(3, 1, 4), rect_algos.classic(3, 1, 4))
+    sq = fmm.fmm_algo_rect_compose(fmm.fmm_algo_rect_compose(s, c), fmm.fmm_algo_rect_cyclic(c))
+    same(sq, rect_algos.strassen_12())
+    a = fmm.fmm_algo_rect_as_square(sq)
+    assert (a.p, a.R) == (12, 1331) and fmm.fmm_algo_brent_mismatches(a) == 0
+
+
+def test_rect_brent_agrees_with_the_oracle_on_changes(fmm, oracle_mod):
+    s = fmm.fmm_algo_rect_builtin("strassen_2x2x3")
+    for M in ("U", "V", "W"):
+        for idx in [(0, 0), (1, 7), (3, 10)] if M == "U" else [(2, 7), (5, 10), (4, 3)]:
+            t = fmm.RectAlgo(s.m, s.k, s.n, s.U.copy(), s.V.copy(), s.W.copy())
+            getattr(t, M)[idx] += 1
+            got = fmm.fmm_algo_rect_brent_mismatches(t)
+            assert got == oracle_mod.rect_brent_mismatches(t.m, t.k, t.n, t.U, t.V, t.W) > 0
+
+
+def test_rect_compose_of_square_tables_is_the_square_compose(fmm):
+    a = fmm.fmm_algo_builtin("strassen")
+    b = fmm.fmm_algo_builtin("laderman")
+    ra = fmm.RectAlgo(2, 2, 2, a.U, a.V, a.W)
+    rb = fmm.RectAlgo(3, 3, 3, b.U, b.V, b.W)
+    rc = fmm.fmm_algo_rect_compose(ra, rb)
+    sc = fmm.fmm_algo_compose(a, b)
+    assert np.array_equal(rc.U, sc.U) and np.array_equal(rc.V, sc.V) and np.array_equal(rc.W, sc.W)
+
+
+def test_rect_as_square_rejects_non_square(fmm):
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_algo_rect_as_square(fmm.fmm_algo_rect_builtin("strassen_2x2x3"))
+    assert e.value.status == 3  # FMM_ERR_UNSUPPORTED
+    with pytest.raises(fmm.FmmError):
+        fmm.fmm_algo_rect_builtin("no_such_algorithm")
