@@ -346,7 +346,7 @@ def time_plan(torch, fmm, plan, dA, dB, dC, warmup, steps, dist=None, stream=Non
     for _ in range(steps):
         fmm.fmm_gemm(plan, dA, dB, dC, stream)
         leaf.append(fmm.fmm_plan_last_kernel_ms(plan)[0])
-        if plan.dtype not in ("c128", "c128_3m"):  # complex plans time the whole call only
+        if plan.dtype in ("f64", "f64_ozaki"):  # complex and f32 plans time the whole call only
             phases.append(fmm.fmm_plan_last_phase_ms(plan))
     e1.record(stream)
     torch.cuda.synchronize()
@@ -447,6 +447,33 @@ def run_sweep(a):
         ms = e0.elapsed_time(e1) / 2
         print(json.dumps({"n": nn, "algo": "cuBLAS ZGEMM (context)", "depth": 0, "schedule": "-", "dtype": "c128",
                           "ms": round(ms, 3), "eff_complex_tflops": round(8.0 * nn ** 3 / ms / 1e9, 4)}), flush=True)
+        del Z1, Z2, Z3
+    if a.n <= 8192 and (not a.only or "f32" in a.only.split(",")):
+        # single precision through the emulated leaf (6 slices), and cuBLAS SGEMM in true FP32 (TF32 off) as context
+        nn = a.n
+        X1 = torch.from_numpy(inputs.matrix(nn, a.kind, seed=1)).float().to(dev)
+        X2 = torch.from_numpy(inputs.matrix(nn, a.kind, seed=2)).float().to(dev)
+        X3 = torch.empty_like(X1)
+        for d in (0, 1, 2, 3):
+            plan = fmm.fmm_plan_create(nn, make_algo(fmm, "strassen"), d, dtype="f32", record_kernel_time=True)
+            ms, _ = time_plan(torch, fmm, plan, X1, X2, X3, 1, 2)
+            print(json.dumps({"n": nn, "algo": "strassen", "depth": d, "schedule": "auto", "dtype": "f32",
+                              "ozaki_slices": plan.info()["ozaki_slices"], "ms": round(ms, 3),
+                              "eff_tflops": round(2.0 * nn ** 3 / ms / 1e9, 4)}), flush=True)
+            fmm.fmm_plan_destroy(plan)
+        torch.backends.cuda.matmul.allow_tf32 = False
+        torch.matmul(X1, X2, out=X3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            torch.matmul(X1, X2, out=X3)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        print(json.dumps({"n": nn, "algo": "cuBLAS SGEMM, TF32 off (context)", "depth": 0, "schedule": "-",
+                          "dtype": "f32", "ms": round(ms, 3), "eff_tflops": round(2.0 * nn ** 3 / ms / 1e9, 4)}),
+              flush=True)
     return 0
 
 

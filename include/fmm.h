@@ -64,9 +64,14 @@ typedef enum {
      * and splits the operands into real planes. */
     FMM_C128 = 2,      /* four real fast products: Re C = Re A Re B - Im A Im B,
                           Im C = Re A Im B + Im A Re B (each part as accurate as a real product) */
-    FMM_C128_3M = 3    /* three real fast products (Gauss): T1 = Re A Re B, T2 = Im A Im B,
+    FMM_C128_3M = 3,   /* three real fast products (Gauss): T1 = Re A Re B, T2 = Im A Im B,
                           T3 = (Re A + Im A)(Re B + Im B); Re C = T1 - T2, Im C = (T3 - T1) - T2;
                           25% fewer products, error bounded normwise rather than per part */
+    FMM_F32 = 4        /* binary32 operands (Section 1 lists single precision among the deployable
+                          types), run through fmm_gemm_f32_ex only: A and B widen exactly to binary64,
+                          the product runs as an FMM_F64_OZAKI plan with 6 slices by default (30 bits
+                          for 24-bit significands; opts->ozaki_slices overrides), and C is rounded to
+                          nearest binary32 once */
 } fmm_dtype_t;
 
 /* A bilinear algorithm <p,p,p;R>.  U, V, W are row-major p^2 x R int32
@@ -288,9 +293,20 @@ fmm_status_t fmm_gemm(const fmm_plan_t *plan, const double *A, const double *B, 
 fmm_status_t fmm_gemm_ex(const fmm_plan_t *plan, double alpha, const double *A, const double *B,
                          double beta, double *C, void *stream);
 
+/* C = alpha * A * B + beta * C for an FMM_F32 plan: A, B, C are n x n
+ * row-major binary32 device arrays, alpha and beta binary32 (the scalar rules
+ * of fmm_gemm_ex: beta = 0 leaves C unread, alpha = 0 leaves A and B unread).
+ * The plan's three binary64 planes hold the widened operands and the product
+ * before its single rounding.  FMM_ERR_INVALID for another dtype; fmm_gemm
+ * and fmm_gemm_ex return FMM_ERR_INVALID for an FMM_F32 plan. */
+fmm_status_t fmm_gemm_f32_ex(const fmm_plan_t *plan, float alpha, const float *A, const float *B, float beta,
+                             float *C, void *stream);
+
 /* Same as fmm_gemm with HOST buffers: copies A and B to plan-owned device
  * buffers (allocated on first use, freed by fmm_plan_destroy), multiplies,
  * copies C back and synchronizes `stream` before returning.  Blocking.
+ * For an FMM_C128 plan the buffers hold interleaved complex pairs and for an
+ * FMM_F32 plan binary32 values (pass their addresses cast to these types).
  * Page-locked host buffers copy at the host link's rate (about 200 GB/s on
  * GB300); pageable ones, or page-locked buffers allocated before the process
  * forked (a subprocess, for instance), copy at about 25 GB/s. */

@@ -44,6 +44,7 @@ from ._binding import (  # noqa: F401
     fmm_gemm,
     fmm_gemm_batched,
     fmm_gemm_ex,
+    fmm_gemm_f32_ex,
     fmm_gemm_host,
     fmm_gemm_noalloc,
     fmm_plan_create,
@@ -74,7 +75,7 @@ _PLANS = {}
 
 
 def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None, alpha=1.0, beta=0.0):
-    """C = alpha * A @ B + beta * out for square float64 or complex128 CUDA tensors by the bilinear algorithm
+    """C = alpha * A @ B + beta * out for square float64, complex128 or float32 CUDA tensors by the bilinear algorithm
     ``algo`` (a built-in name, ``"name^k"`` for its k-th Kronecker power, or an :class:`Algo`) at
     recursion ``depth``.
 
@@ -92,6 +93,8 @@ def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None, alp
         raise ValueError("beta != 0 needs out")
     if A.is_complex() and dtype not in ("c128", "c128_3m"):
         dtype = "c128"  # complex operands: four real fast products unless "c128_3m" is asked for
+    if A.dtype == torch.float32:
+        dtype = "f32"
     if isinstance(algo, str):
         name, _, k = algo.partition("^")
         alg = algorithm(name, int(k) if k else 1)

@@ -19,10 +19,10 @@ LIB_PATH = os.path.join(_HERE, "libfmm.so")
 FMM_OK, FMM_ERR_INVALID, FMM_ERR_BRENT, FMM_ERR_UNSUPPORTED = 0, 1, 2, 3
 FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_NOT_FOUND = 4, 5, 6, 7
 FMM_ERR_SCRATCH_LIMIT = 8
-FMM_F64, FMM_F64_OZAKI, FMM_C128, FMM_C128_3M = 0, 1, 2, 3
+FMM_F64, FMM_F64_OZAKI, FMM_C128, FMM_C128_3M, FMM_F32 = 0, 1, 2, 3, 4
 FMM_SCHED_AUTO, FMM_SCHED_FUSED, FMM_SCHED_HYBRID = 0, 1, 2
 
-DTYPES = {"f64": FMM_F64, "f64_ozaki": FMM_F64_OZAKI, "c128": FMM_C128, "c128_3m": FMM_C128_3M}
+DTYPES = {"f64": FMM_F64, "f64_ozaki": FMM_F64_OZAKI, "c128": FMM_C128, "c128_3m": FMM_C128_3M, "f32": FMM_F32}
 COMPLEX_DTYPES = ("c128", "c128_3m")
 SCHEDULES = {"auto": FMM_SCHED_AUTO, "fused": FMM_SCHED_FUSED, "hybrid": FMM_SCHED_HYBRID}
 
@@ -94,6 +94,8 @@ SIGNATURES = [
                                            ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
                                            ctypes.c_int, ctypes.c_void_p]),
+    ("fmm_gemm_f32_ex", ctypes.c_int, [ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     ("fmm_gemm_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p]),
     ("fmm_gemm_batched", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -427,12 +429,12 @@ def _stream_ptr(stream) -> int:
     return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
 
 
-def _check_operand(X, n: int, name: str, device: bool = True, complex_: bool = False):
+def _check_operand(X, n: int, name: str, device: bool = True, complex_: bool = False, f32: bool = False):
     import torch
 
     if not isinstance(X, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
-    want = torch.complex128 if complex_ else torch.float64
+    want = torch.complex128 if complex_ else (torch.float32 if f32 else torch.float64)
     if X.dtype != want or X.shape != (n, n) or not X.is_contiguous():
         raise ValueError(f"{name} must be a contiguous {str(want).replace('torch.', '')} tensor of shape ({n}, {n})")
     if device and not X.is_cuda:
@@ -443,7 +445,10 @@ def _check_operand(X, n: int, name: str, device: bool = True, complex_: bool = F
 
 def fmm_gemm(plan: Plan, A, B, C, stream=None):
     """C = A @ B on the GPU (asynchronous on ``stream``, default: torch's current stream); complex128
-    tensors for a "c128" / "c128_3m" plan, float64 otherwise."""
+    tensors for a "c128" / "c128_3m" plan, float32 for "f32" (through fmm_gemm_f32_ex), float64
+    otherwise."""
+    if plan.dtype == "f32":
+        return fmm_gemm_f32_ex(plan, 1.0, A, B, 0.0, C, stream)
     n = plan.n
     for X, nm in ((A, "A"), (B, "B"), (C, "C")):
         _check_operand(X, n, nm, complex_=plan.dtype in COMPLEX_DTYPES)
@@ -454,7 +459,9 @@ def fmm_gemm(plan: Plan, A, B, C, stream=None):
 
 def fmm_gemm_ex(plan: Plan, alpha: float, A, B, beta: float, C, stream=None):
     """C = alpha * A @ B + beta * C on the GPU (beta = 0: C is not read; alpha = 0: A, B are not read);
-    real alpha and beta, also for complex plans."""
+    real alpha and beta, also for complex plans; an "f32" plan goes through fmm_gemm_f32_ex."""
+    if plan.dtype == "f32":
+        return fmm_gemm_f32_ex(plan, alpha, A, B, beta, C, stream)
     n = plan.n
     for X, nm in ((A, "A"), (B, "B"), (C, "C")):
         _check_operand(X, n, nm, complex_=plan.dtype in COMPLEX_DTYPES)
@@ -464,11 +471,22 @@ def fmm_gemm_ex(plan: Plan, alpha: float, A, B, beta: float, C, stream=None):
     return C
 
 
+def fmm_gemm_f32_ex(plan: Plan, alpha: float, A, B, beta: float, C, stream=None):
+    """C = alpha * A @ B + beta * C for float32 CUDA tensors and an "f32" plan."""
+    n = plan.n
+    for X, nm in ((A, "A"), (B, "B"), (C, "C")):
+        _check_operand(X, n, nm, f32=True)
+    _check(lib().fmm_gemm_f32_ex(plan.handle, float(alpha), ctypes.c_void_p(A.data_ptr()),
+                                 ctypes.c_void_p(B.data_ptr()), float(beta), ctypes.c_void_p(C.data_ptr()),
+                                 ctypes.c_void_p(_stream_ptr(stream))), "fmm_gemm_f32_ex")
+    return C
+
+
 def fmm_gemm_host(plan: Plan, A, B, C, stream=None):
     """C = A @ B with host tensors; copies in and out inside the call (blocking)."""
     n = plan.n
     for X, nm in ((A, "A"), (B, "B"), (C, "C")):
-        _check_operand(X, n, nm, device=False, complex_=plan.dtype in COMPLEX_DTYPES)
+        _check_operand(X, n, nm, device=False, complex_=plan.dtype in COMPLEX_DTYPES, f32=plan.dtype == "f32")
     _check(lib().fmm_gemm_host(plan.handle, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                                ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
            "fmm_gemm_host")
@@ -497,7 +515,8 @@ def fmm_gemm_batched(plans, As, Bs, Cs, stream=None, alphas=None, betas=None):
         raise ValueError("each product of a batch needs its own plan")
     for p, A, B, C in zip(plans, As, Bs, Cs):
         for X, nm in ((A, "A"), (B, "B"), (C, "C")):
-            _check_operand(X, p.n, nm, complex_=p.dtype in COMPLEX_DTYPES)  # the library rejects complex plans
+            _check_operand(X, p.n, nm, complex_=p.dtype in COMPLEX_DTYPES,
+                           f32=p.dtype == "f32")  # the library rejects complex and f32 plans
     arr = ctypes.c_void_p * max(count, 1)
     hp = arr(*[p.handle.value for p in plans])
     ha = arr(*[A.data_ptr() for A in As])

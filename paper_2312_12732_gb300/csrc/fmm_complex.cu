@@ -1,5 +1,6 @@
-// Element-wise kernels of the double-complex products (Section 1 lists double
-// complex among the types the algorithms deploy to).  A complex n x n matrix
+// Element-wise kernels of the double-complex and single-precision products
+// (Section 1 lists single precision and double complex among the types the
+// algorithms deploy to).  A complex n x n matrix
 // is interleaved (re, im) binary64; a complex plan splits its operands into
 // real planes, runs real fast products on them and joins the result:
 //   4M:  Re C = Re A Re B - Im A Im B,  Im C = Re A Im B + Im A Re B;
@@ -55,6 +56,29 @@ __global__ void __launch_bounds__(256) gauss_join_kernel(const double *__restric
     }
 }
 
+// Single precision operands (FMM_F32): exact widening to binary64, rounding
+// back to nearest binary32, and C = beta C on binary32 (beta = 0: zeros, C not
+// read).  HBM-bound streams like the complex planes.
+__global__ void __launch_bounds__(256) f32_to_f64_kernel(const float *__restrict__ X, long long count,
+                                                         double *__restrict__ out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride)
+        out[t] = (double)__ldg(X + t);
+}
+
+__global__ void __launch_bounds__(256) f64_to_f32_kernel(const double *__restrict__ X, long long count,
+                                                         float *__restrict__ out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride)
+        out[t] = __double2float_rn(X[t]);
+}
+
+__global__ void __launch_bounds__(256) scale_f32_kernel(float *C, long long count, float beta) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride)
+        C[t] = beta == 0.0f ? 0.0f : beta * C[t];
+}
+
 int stream_grid(long long count) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -84,6 +108,24 @@ cudaError_t launch_gauss_join(const double *T1, const double *T2, const double *
     if (count <= 0) return cudaSuccess;
     gauss_join_kernel<<<stream_grid(count), 256, 0, s>>>(T1, T2, T3, reinterpret_cast<double2 *>(C), count, alpha,
                                                          beta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(const float *X, long long count, double *out, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    f32_to_f64_kernel<<<stream_grid(count), 256, 0, s>>>(X, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_to_f32(const double *X, long long count, float *out, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    f64_to_f32_kernel<<<stream_grid(count), 256, 0, s>>>(X, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_f32(float *C, long long count, float beta, cudaStream_t s) {
+    if (count <= 0 || beta == 1.0f) return cudaSuccess;
+    scale_f32_kernel<<<stream_grid(count), 256, 0, s>>>(C, count, beta);
     return cudaGetLastError();
 }
 

@@ -542,6 +542,40 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     *out = nullptr;
     if (n < 1 || depth < 0 || depth > 8 || !algo_shape_ok(algo) || den < 1) return FMM_ERR_INVALID;
     if (n > (1LL << 31) / 2) return FMM_ERR_UNSUPPORTED;
+    if (dtype == FMM_F32) {
+        // an emulated-FP64 plan with fewer slices (6 by default: 30 bits for 24-bit operands) and
+        // three binary64 planes for A, B and C
+        fmm_plan_options_t o2{};
+        if (opts) o2 = *opts;
+        if (!o2.ozaki_slices) o2.ozaki_slices = 6;
+        fmm_plan_t *inner = nullptr;
+        fmm_status_t st = plan_create(&inner, n, algo, depth, FMM_F64_OZAKI, &o2, den);
+        if (st != FMM_OK) return st;
+        fmm_plan *pl = new (std::nothrow) fmm_plan();
+        if (!pl) {
+            fmm_plan_destroy(inner);
+            return FMM_ERR_OOM;
+        }
+        pl->inner = inner;
+        pl->device = inner->device;
+        pl->n = n; pl->p = inner->p; pl->R = inner->R; pl->depth = depth; pl->dtype = dtype;
+        pl->wscale = inner->wscale;
+        pl->ws_bytes = 3 * (size_t)n * (size_t)n * sizeof(double);
+        if (cudaMalloc(&pl->d_planes, pl->ws_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            fmm_plan_destroy(pl);
+            return FMM_ERR_OOM;
+        }
+        if (opts && opts->record_kernel_time)
+            for (int e : {0, 1, 2})
+                if (cudaEventCreate(&pl->ev[e]) != cudaSuccess) {
+                    cudaGetLastError();
+                    fmm_plan_destroy(pl);
+                    return FMM_ERR_CUDA;
+                }
+        *out = pl;
+        return FMM_OK;
+    }
     if (dtype == FMM_C128 || dtype == FMM_C128_3M) {
         // a real plan for the parts, and the planes: 4M splits A, B and C (6 planes),
         // 3M splits A and B with their part sums and keeps three products (9 planes)
@@ -1189,6 +1223,7 @@ extern "C" fmm_status_t fmm_gemm(const fmm_plan_t *pl, const double *A, const do
 extern "C" fmm_status_t fmm_gemm_ex(const fmm_plan_t *pl, double alpha, const double *A, const double *B, double beta,
                                     double *C, void *stream) {
     if (!pl || !A || !B || !C || !std::isfinite(alpha) || !std::isfinite(beta)) return FMM_ERR_INVALID;
+    if (pl->dtype == FMM_F32) return FMM_ERR_INVALID;  // binary32 operands go through fmm_gemm_f32_ex
     cudaStream_t st = (cudaStream_t)stream;
     const long long doubles = pl->n * pl->n * (pl->inner ? 2 : 1);
     if (pl->inner && ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15) != 0) return FMM_ERR_INVALID;
@@ -1223,6 +1258,30 @@ extern "C" fmm_status_t fmm_gemm_ex(const fmm_plan_t *pl, double alpha, const do
     return FMM_OK;
 }
 
+extern "C" fmm_status_t fmm_gemm_f32_ex(const fmm_plan_t *pl, float alpha, const float *A, const float *B,
+                                        float beta, float *C, void *stream) {
+    if (!pl || !A || !B || !C || pl->dtype != FMM_F32 || !std::isfinite(alpha) || !std::isfinite(beta))
+        return FMM_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long N = pl->n * pl->n;
+    if (alpha == 0.0f) return cuda_status(fmm::launch_scale_f32(C, N, beta, st));  // A, B unread
+    double *Ad = pl->d_planes, *Bd = pl->d_planes + N, *Cd = pl->d_planes + 2 * N;
+    if (pl->ev[0] && (cudaEventRecord(pl->ev[0], st) != cudaSuccess || cudaEventRecord(pl->ev[1], st) != cudaSuccess))
+        return FMM_ERR_CUDA;
+    if (fmm::launch_f32_to_f64(A, N, Ad, st) != cudaSuccess || fmm::launch_f32_to_f64(B, N, Bd, st) != cudaSuccess ||
+        (beta != 0.0f && fmm::launch_f32_to_f64(C, N, Cd, st) != cudaSuccess))
+        return FMM_ERR_CUDA;
+    // binary32 scalars widen exactly; the product is formed in binary64 and rounded once
+    fmm_status_t s = fmm_gemm_ex(pl->inner, (double)alpha, Ad, Bd, (double)beta, Cd, st);
+    if (s != FMM_OK) return s;
+    if (fmm::launch_f64_to_f32(Cd, N, C, st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (pl->ev[0]) {
+        if (cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
+        const_cast<fmm_plan *>(pl)->timed_once = true;
+    }
+    return FMM_OK;
+}
+
 extern "C" fmm_status_t fmm_plan_last_phase_ms(const fmm_plan_t *pl, float *phases, int count) {
     if (!pl || !phases || count < 1 || !pl->ev[0] || !pl->timed_once || pl->inner) return FMM_ERR_INVALID;
     if (cudaEventSynchronize(pl->ev[4]) != cudaSuccess) return FMM_ERR_CUDA;
@@ -1251,7 +1310,8 @@ extern "C" fmm_status_t fmm_plan_last_kernel_ms(const fmm_plan_t *pl, float *lea
 
 extern "C" fmm_status_t fmm_gemm_host(fmm_plan_t *pl, const double *hA, const double *hB, double *hC, void *stream) {
     if (!pl || !hA || !hB || !hC) return FMM_ERR_INVALID;
-    const size_t bytes = (size_t)pl->n * (size_t)pl->n * sizeof(double) * (pl->inner ? 2 : 1);
+    const size_t elem = pl->dtype == FMM_F32 ? sizeof(float) : sizeof(double) * (pl->inner ? 2 : 1);
+    const size_t bytes = (size_t)pl->n * (size_t)pl->n * elem;
     if (!pl->d_hostA) {
         if (cudaMalloc(&pl->d_hostA, bytes) != cudaSuccess || cudaMalloc(&pl->d_hostB, bytes) != cudaSuccess ||
             cudaMalloc(&pl->d_hostC, bytes) != cudaSuccess) {
@@ -1266,7 +1326,11 @@ extern "C" fmm_status_t fmm_gemm_host(fmm_plan_t *pl, const double *hA, const do
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemcpyAsync(pl->d_hostA, hA, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FMM_ERR_CUDA;
     if (cudaMemcpyAsync(pl->d_hostB, hB, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FMM_ERR_CUDA;
-    fmm_status_t s = fmm_gemm(pl, pl->d_hostA, pl->d_hostB, pl->d_hostC, stream);
+    fmm_status_t s = pl->dtype == FMM_F32
+                         ? fmm_gemm_f32_ex(pl, 1.0f, reinterpret_cast<const float *>(pl->d_hostA),
+                                           reinterpret_cast<const float *>(pl->d_hostB),
+                                           0.0f, reinterpret_cast<float *>(pl->d_hostC), stream)
+                         : fmm_gemm(pl, pl->d_hostA, pl->d_hostB, pl->d_hostC, stream);
     if (s != FMM_OK) return s;
     if (cudaMemcpyAsync(hC, pl->d_hostC, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return FMM_ERR_CUDA;
     return cuda_status(cudaStreamSynchronize(st));
@@ -1499,6 +1563,10 @@ extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t 
         // part sums and joins (4M: one add per element of each part; 3M: 2 n^2 sums, 3 n^2 joins)
         fmm_status_t s = fmm_plan_get_info(pl->inner, info);
         if (s != FMM_OK) return s;
+        if (pl->dtype == FMM_F32) {  // one emulated product; the widening and rounding add no flops
+            info->workspace_bytes += pl->ws_bytes;
+            return FMM_OK;
+        }
         const double k = pl->dtype == FMM_C128 ? 4.0 : 3.0;
         const double n2 = (double)pl->n * (double)pl->n;
         info->flops_leaf *= k;

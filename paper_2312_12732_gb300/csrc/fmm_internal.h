@@ -164,6 +164,11 @@ cudaError_t launch_split_complex(const double *X, long long count, double *re, d
                                  cudaStream_t s);
 // C <- (re, im).
 cudaError_t launch_join_complex(const double *re, const double *im, double *C, long long count, cudaStream_t s);
+// Single precision (fmm_complex.cu): out <- (double) X; out <- round-to-nearest
+// (float) X; C <- beta C on `count` floats (beta = 0: zeros, C not read).
+cudaError_t launch_f32_to_f64(const float *X, long long count, double *out, cudaStream_t s);
+cudaError_t launch_f64_to_f32(const double *X, long long count, float *out, cudaStream_t s);
+cudaError_t launch_scale_f32(float *C, long long count, float beta, cudaStream_t s);
 // C <- alpha (T1 - T2, (T3 - T1) - T2) + beta C (beta = 0: C not read).
 cudaError_t launch_gauss_join(const double *T1, const double *T2, const double *T3, double *C, long long count,
                               double alpha, double beta, cudaStream_t s);

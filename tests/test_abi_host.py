@@ -242,3 +242,13 @@ def test_rect_as_square_rejects_non_square(fmm):
     assert e.value.status == 3  # FMM_ERR_UNSUPPORTED
     with pytest.raises(fmm.FmmError):
         fmm.fmm_algo_rect_builtin("no_such_algorithm")
+
+
+def test_f32_entry_point_validates_before_touching_the_gpu(fmm):
+    import torch
+
+    assert fmm.lib().fmm_gemm_f32_ex(None, 1.0, None, None, 0.0, None, None) == 1
+    plan = fmm.Plan(0, 8, None, 1, "f32")
+    with pytest.raises(ValueError, match="float32"):
+        fmm.fmm_gemm(plan, *(torch.zeros(8, 8, dtype=torch.float64) for _ in range(3)))
+    plan.handle = None
