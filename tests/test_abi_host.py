@@ -252,3 +252,18 @@ def test_f32_entry_point_validates_before_touching_the_gpu(fmm):
     with pytest.raises(ValueError, match="float32"):
         fmm.fmm_gemm(plan, *(torch.zeros(8, 8, dtype=torch.float64) for _ in range(3)))
     plan.handle = None
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_ozaki", "c128", "c128_3m", "f32"])
+def test_every_dtype_rejects_a_broken_algorithm_before_touching_the_gpu(fmm, dtype):
+    """The complex and single-precision plans wrap a real plan whose exact Brent check runs first,
+    so a broken table fails the same way for every dtype, with no CUDA call."""
+    a = fmm.fmm_algo_builtin("strassen")
+    U = a.U.copy()
+    U[0, 0] += 1
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_plan_create(64, fmm.Algo(2, U, a.V, a.W), 1, dtype=dtype)
+    assert e.value.status == 2  # FMM_ERR_BRENT
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_plan_create(0, a, 1, dtype=dtype)
+    assert e.value.status == 1  # FMM_ERR_INVALID
