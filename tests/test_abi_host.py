@@ -267,3 +267,33 @@ def test_every_dtype_rejects_a_broken_algorithm_before_touching_the_gpu(fmm, dty
     with pytest.raises(fmm.FmmError) as e:
         fmm.fmm_plan_create(0, a, 1, dtype=dtype)
     assert e.value.status == 1  # FMM_ERR_INVALID
+
+
+def test_random_symmetry_and_composition_chains(fmm, oracle_mod):
+    """Seeded random chains of transposes, rotations and compositions of <2,2,3;11> and classic
+    tables: the library and the independent golden construction give the same tables, and both
+    Brent implementations accept every result."""
+    from golden import rect_algos
+
+    rng = np.random.default_rng(2024)
+    base_lib = [fmm.fmm_algo_rect_builtin("strassen_2x2x3"), fmm.fmm_algo_rect_classic(1, 2, 2),
+                fmm.fmm_algo_rect_classic(2, 1, 1)]
+    base_gold = [rect_algos.strassen_223(), rect_algos.classic(1, 2, 2), rect_algos.classic(2, 1, 1)]
+    for _ in range(12):
+        i = int(rng.integers(len(base_lib)))
+        lib_a, gold_a = base_lib[i], base_gold[i]
+        for _step in range(int(rng.integers(1, 4))):
+            op = int(rng.integers(3))
+            if op == 0:
+                lib_a, gold_a = fmm.fmm_algo_rect_transpose(lib_a), rect_algos.transpose(gold_a)
+            elif op == 1:
+                lib_a, gold_a = fmm.fmm_algo_rect_cyclic(lib_a), rect_algos.cyclic(gold_a)
+            elif lib_a.R * 11 <= 1500:
+                j = int(rng.integers(len(base_lib)))
+                lib_a = fmm.fmm_algo_rect_compose(lib_a, base_lib[j])
+                gold_a = rect_algos.compose(gold_a, base_gold[j])
+        m, k, n, U, V, W = gold_a
+        assert (lib_a.m, lib_a.k, lib_a.n) == (m, k, n)
+        assert np.array_equal(lib_a.U, U) and np.array_equal(lib_a.V, V) and np.array_equal(lib_a.W, W)
+        assert fmm.fmm_algo_rect_brent_mismatches(lib_a) == 0
+        assert oracle_mod.rect_brent_mismatches(m, k, n, U, V, W) == 0

@@ -574,3 +574,17 @@ def test_square_12_from_three_rotations(oracle_mod):
     assert oracle_mod.brent_mismatches(12, U, V, W) == 0
     A, B = inputs.operands(24, "integer", seed=9)
     assert np.array_equal(oracle_mod.bilinear(A, B, 12, U, V, W, 1), A @ B)
+
+
+def test_rect_bilinear_random_shapes_exact_on_integers(oracle_mod):
+    """Seeded random shapes (including ones smaller than a split factor and ones needing peeling in
+    every dimension) and random level sequences of <2,2,3;11> rotations: exact on integers."""
+    rng = np.random.default_rng(77)
+    s = rect_algos.strassen_223()
+    rots = [s, rect_algos.cyclic(s), rect_algos.cyclic(rect_algos.cyclic(s)), rect_algos.transpose(s)]
+    for _ in range(15):
+        M, K, N = (int(x) for x in rng.integers(1, 40, size=3))
+        levels = [rots[int(i)] for i in rng.integers(len(rots), size=int(rng.integers(0, 4)))]
+        A = rng.integers(-16, 17, size=(M, K)).astype(np.float64)
+        B = rng.integers(-16, 17, size=(K, N)).astype(np.float64)
+        assert np.array_equal(oracle_mod.rect_bilinear(A, B, levels), A @ B), (M, K, N, len(levels))
