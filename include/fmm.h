@@ -107,8 +107,9 @@ typedef struct fmm_plan fmm_plan_t;
  *   FMM_SCHED_HYBRID -- the top `materialize_levels` levels are formed level
  *                       by level in plan workspace by an elementwise pass,
  *                       the remaining levels are fused into staging.
- * The post-additions C_l = sum_r W[l][r] P_r are always fused into the
- * leaf-product epilogue. */
+ * The post-additions C_l = sum_r W[l][r] P_r are fused into the FP64 leaf
+ * kernel's epilogue; the emulated leaf (FMM_F64_OZAKI, FMM_F32) stores its
+ * leaf products and applies them in a separate kernel, in the same order. */
 typedef enum { FMM_SCHED_AUTO = 0, FMM_SCHED_FUSED = 1, FMM_SCHED_HYBRID = 2 } fmm_schedule_t;
 
 /* Optional knobs for fmm_plan_create_ex.  Zero-initialise, then set fields;
@@ -116,9 +117,10 @@ typedef enum { FMM_SCHED_AUTO = 0, FMM_SCHED_FUSED = 1, FMM_SCHED_HYBRID = 2 } f
 typedef struct {
     fmm_schedule_t schedule;
     int materialize_levels;  /* FMM_SCHED_HYBRID: 0 .. depth */
-    int ozaki_slices;        /* FMM_F64_OZAKI: slices per operand, 2..12 (default 12:
-                                60 bits, within 2x of the FP64 path's error on uniform,
-                                normal and wide-exponent inputs) */
+    int ozaki_slices;        /* FMM_F64_OZAKI and FMM_F32: slices per operand, 2..12
+                                (default 12 for FMM_F64_OZAKI: 60 bits, within 2x of the
+                                FP64 path's error on uniform, normal and wide-exponent
+                                inputs; default 6 for FMM_F32: 30 bits) */
     double wait_timeout_s;   /* bound on every device-side wait (default 5 s) */
     int debug_poison_chain;  /* testing only: 1 = after the per-call reset, set one
                                 post-addition ordering counter to a value no task
