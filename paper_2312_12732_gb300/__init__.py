@@ -75,9 +75,10 @@ _PLANS = {}
 
 
 def gemm(A, B, algo="strassen", depth=1, dtype="f64", out=None, stream=None, alpha=1.0, beta=0.0):
-    """C = alpha * A @ B + beta * out for square float64, complex128 or float32 CUDA tensors by the bilinear algorithm
-    ``algo`` (a built-in name, ``"name^k"`` for its k-th Kronecker power, or an :class:`Algo`) at
-    recursion ``depth``.
+    """C = alpha * A @ B + beta * out for square float64, complex128 or float32 CUDA tensors by the
+    bilinear algorithm ``algo`` (a built-in name, ``"name^k"`` for its k-th Kronecker power, or an
+    :class:`Algo`) at recursion ``depth``.  Complex operands use the "c128" plan (or "c128_3m" when
+    asked for), float32 operands the "f32" plan.
 
     The plan for (n, algorithm, depth, dtype, device) is created on first use and cached; a cached
     plan's workspace serves one call at a time, so calls on different streams that share a plan
