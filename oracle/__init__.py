@@ -25,6 +25,7 @@ Functions (each follows the passage cited in ``fmm_oracle.c``):
   the same products for complex128 matrices (Section 1 names double complex
   among the deployable types): real coefficients act on both parts alike,
   leaf products use the textbook complex product.
+* ``set_num_threads(k)`` -- OpenMP threads used by the loops (timing only).
 * ``axpby(alpha, P, beta, C)`` / ``scaled(alpha, A, B, beta, C, ...)`` -- the
   update C = alpha A B + beta C (Section 3 states C = alpha A B; beta is the
   BLAS extension), with beta = 0 leaving C unread and alpha = 0 leaving A B
@@ -92,6 +93,8 @@ def _load():
                                                     i32]
         lib.fmm_oracle_axpby.restype = None
         lib.fmm_oracle_axpby.argtypes = [i64, ctypes.c_double, dp, ctypes.c_double, dp]
+        lib.fmm_oracle_set_num_threads.restype = None
+        lib.fmm_oracle_set_num_threads.argtypes = [i32]
         _lib = lib
     return _lib
 
@@ -283,6 +286,11 @@ def axpby(alpha: float, P, beta: float, C) -> np.ndarray:
         pp = _dp(P)
     _load().fmm_oracle_axpby(C.size, float(alpha), pp, float(beta), _dp(C))
     return C
+
+
+def set_num_threads(threads: int) -> None:
+    """OpenMP threads of the parallel loops (classic, Dot2 samples); results do not depend on it."""
+    _load().fmm_oracle_set_num_threads(int(threads))
 
 
 def scaled(alpha: float, A, B, beta: float, C, p: int, U, V, W, depth: int) -> np.ndarray:

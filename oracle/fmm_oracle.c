@@ -562,3 +562,19 @@ void fmm_oracle_sample_dot2(int64_t K, const double *A, int64_t lda, const doubl
     for (int64_t t = 0; t < count; ++t)
         out[t] = fmm_oracle_dot2(K, A + rows[t] * lda, 1, B + cols[t], ldb);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Thread count of the OpenMP loops above (timing only; results do not depend */
+/* on it: every parallel loop writes disjoint outputs in a fixed order).      */
+/* ------------------------------------------------------------------------- */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+void fmm_oracle_set_num_threads(int threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+}

@@ -136,13 +136,11 @@ size_t ozaki_smem_bytes();
 cudaError_t launch_ozaki_tc(const CUtensorMap &map_a, const CUtensorMap &map_b, const OzParams &P, int grid,
                             cudaStream_t s);
 // The same slice GEMM on CTA pairs (tcgen05 cta_group::2): `ctas` CTAs in
-// clusters of 2, or (cluster_ctas = 4) clusters of 4 where the GPU can form
-// them and of 2 on the remaining SMs.  A cluster of 4 is two pairs that share
-// left-slice tiles by TMA multicast and reads them through map_ah (64-row
-// boxes); pairs read map_a (128-row boxes); map_bh has 64-row boxes over the
-// right slices.  P.tasks counts (product, tile-row pair, two tile columns).
-cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_ah, const CUtensorMap &map_bh,
-                                 const OzParams &P, int ctas, int cluster_ctas, cudaStream_t s);
+// clusters of 2 (one pair each).  map_a has 128-row boxes over the left
+// slices, map_bh 64-row boxes over the right slices; each CTA loads its own
+// boxes.  P.tasks counts (product, tile-row pair, two tile columns).
+cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_bh, const OzParams &P, int ctas,
+                                 cudaStream_t s);
 // Largest number of co-resident CTA pairs of the pair kernel (0 if it cannot run).
 int ozaki_tc_max_pairs();
 // C_l = alpha sum_r W[l][r] P_r + beta C_l for the P x P blocks of side m of

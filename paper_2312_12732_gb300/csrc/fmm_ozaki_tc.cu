@@ -17,9 +17,9 @@
 //                D_g with tcgen05.ld, folds it into 64 int64 registers while
 //                later groups accumulate, converts to FP64 and stores the tile
 //                of P_r.
-//   ozaki_tc_pair_kernel (CTA pairs, tcgen05 cta_group::2; clusters of one
-//     pair or of two pairs sharing their left-slice tiles by TMA multicast; the
-//     default) described above the kernel.
+//   ozaki_tc_pair_kernel (CTA pairs, tcgen05 cta_group::2, one pair per
+//     cluster; every CTA fetches its own tiles; the default) described above
+//     the kernel.
 //
 // ozaki_postadd_kernel (fmm_postadd.cu) then forms C_l = sum_r W[l][r] P_r in ascending r.
 // Every mbarrier wait is bounded by %globaltimer; on expiry the CTA records a
@@ -492,11 +492,6 @@ __device__ __forceinline__ uint32_t cluster_rank() {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
 }
-__device__ __forceinline__ uint32_t cluster_nctarank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return r;
-}
 __device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
     uint32_t r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
@@ -552,16 +547,6 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
         "l"(map), "r"(x), "r"(y), "r"(caddr)
         : "memory");
 }
-// The same, multicast: the box lands at this offset in every CTA of `mask`, and each destination
-// pair's leader barrier (same offset) is signalled.
-__device__ __forceinline__ void tma_load_2d_pair_mc(void *dst, const CUtensorMap *map, int x, int y, uint32_t caddr,
-                                                    uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::"
-        "cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(su32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(caddr), "h"(mask)
-        : "memory");
-}
 // 2-SM MMA: M = 256 (128 rows in each CTA's TMEM), N = 128 (64 rows of B in each CTA's shared memory).
 constexpr uint32_t kIdescPair = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)((2 * TM) >> 4) << 24);
 __device__ __forceinline__ void mma_e4m3_pair(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
@@ -571,7 +556,8 @@ __device__ __forceinline__ void mma_e4m3_pair(uint32_t tmem_d, uint64_t da, uint
         "l"(da), "l"(db), "r"(kIdescPair), "r"(accumulate)
         : "memory");
 }
-// Arrives on the mbarrier at this offset in every CTA of `mask` once the MMAs issued so far complete.
+// Arrives on the mbarrier at this offset in both CTAs of the pair (`mask` = 3) once the MMAs issued
+// so far complete.
 __device__ __forceinline__ void mma_commit_pair(unsigned long long *bar, unsigned short mask) {
     asm volatile(
         "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
@@ -611,18 +597,12 @@ struct __align__(8) PairBars {
     int abort;
 };
 
-// Slice GEMM on CTA pairs, in clusters of CL = 2 (one pair) or 4 CTAs (two
-// pairs that share their left-slice tiles); the cluster size is read at run
-// time, so one launch can mix both (a preferred size of 4 where the GPU's
-// partitions allow it, pairs on the SMs left over).  A task is product r, the
-// tile-row pair tp and two adjacent tile columns 2 tj2, 2 tj2 + 1.  CTA (pair
-// pc, rank-in-pair rp) owns tile row ti = 2 tp + rp; in a cluster of 4 pair
-// pc takes column 2 tj2 + pc, a lone pair takes both columns one after the
-// other (the task is published as two items).  With CL = 4 each CTA loads
-// half of its A box and multicasts it to the CTA with the same rp in the
-// other pair, which cuts each SM's L2 requests per stage from 24 to 16 KB;
-// the two pairs then run in lock-step, each stage being released by both
-// pairs' MMA threads.
+// Slice GEMM on CTA pairs, one pair per cluster of two CTAs.  A task is
+// product r, the tile-row pair tp and two adjacent tile columns 2 tj2,
+// 2 tj2 + 1; CTA rp of the pair owns tile row ti = 2 tp + rp, and the pair
+// takes the two columns one after the other (the task is published as two
+// items).  Every CTA fetches its own tiles from global memory: no copy lands
+// in another CTA's shared memory except through the pair's own 2-SM copies.
 // Each CTA streams its 128 rows of the left slices and its 64-row half of the
 // right slices; the leader's MMA threads issue 256 x 128 x 32 MMAs (tcgen05
 // cta_group::2) that read both CTAs' shared memory and accumulate into both
@@ -638,18 +618,16 @@ struct __align__(8) PairBars {
 // 0, 1 (leader; warp 2 also allocates TMEM in both CTAs); 4-11 epilogue.
 // Barriers (same offsets in both CTAs):
 //   full[q][k]   leader only: its producer's expect_tx plus both CTAs' bytes
-//   empty[q][k]  both: MMA thread q's commit (multicast) once stage k is read
-//   accfull[b]   both: the commit (multicast) closing the group in buffer b
+//   empty[q][k]  both: MMA thread q's commit (to both CTAs) once stage k is read
+//   accfull[b]   both: the commit (to both CTAs) closing the group in buffer b
 //   accempty[b]  leader only: 2 x NEPI epilogue warps (NEPI of them remote)
 //   tfull/tempty task ring: ring 0's producer in the leader fetches tasks and
 //                publishes them to both CTAs; every other role of both CTAs
 //                releases the slot on the leader's tempty.
 __global__ void __launch_bounds__(P_NTHREADS, 1)
-    ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_ah,
-                         const __grid_constant__ CUtensorMap map_bh, const __grid_constant__ OzParams P) {
-    const int CL = (int)cluster_nctarank();  // 2 or 4
-    const int NPAIR = CL / 2;
-    const CUtensorMap *amap = CL == 4 ? &map_ah : &map_a;  // 64-row A boxes when the halves are shared
+    ozaki_tc_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_bh,
+                         const __grid_constant__ OzParams P) {
+    constexpr int CL = 2;  // the pair is the cluster
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
     unsigned char *stage_mem = base;  // NRING x RSTAGES x (A 32 KB, B half 16 KB)
@@ -658,12 +636,11 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t rank = cluster_rank();
-    const int pc = (int)rank >> 1, rp = (int)rank & 1;
+    const int rp = (int)rank & 1;
     const bool lead = rp == 0;        // pair leader: MMA threads, full / accempty barriers
-    const bool fetcher = rank == 0;   // fetches tasks and publishes them to the cluster
-    const uint32_t pair_lead = rank & ~1u;
-    const unsigned short pair_mask = (unsigned short)(3u << pair_lead);
-    const unsigned short all_mask = (unsigned short)((1u << CL) - 1u);
+    const bool fetcher = rank == 0;   // fetches tasks and publishes them to the peer
+    constexpr uint32_t pair_lead = 0;
+    constexpr unsigned short pair_mask = 3;
     const int pairs_m = (P.tiles_m + 1) / 2;
     const int tn2 = (P.tiles_n + 1) / 2;
     const int ptiles = pairs_m * tn2;
@@ -675,18 +652,18 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
         for (int q = 0; q < NRING; ++q)
             for (int i = 0; i < RSTAGES; ++i) {
                 mbar_init(&B.full[q][i], 1);
-                mbar_init(&B.empty[q][i], NPAIR);  // every pair's MMA thread q releases the stage
+                mbar_init(&B.empty[q][i], 1);  // the pair's MMA thread q releases the stage
             }
         for (int i = 0; i < NBUF; ++i) {
             mbar_init(&B.accfull[i], 1);
             mbar_init(&B.accempty[i], 2 * NEPI);
         }
         // consumers of a task slot (counted on the fetcher): the fetcher's producer 1,
-        // two MMA threads and NEPI epilogue warps; two producers, NEPI epilogue warps
-        // and (pair leaders) two MMA threads in every other CTA
+        // two MMA threads and NEPI epilogue warps; the peer's two producers and NEPI
+        // epilogue warps
         for (int i = 0; i < TASK_RING; ++i) {
             mbar_init(&B.tfull[i], 1);
-            mbar_init(&B.tempty[i], (3 + NEPI) + (CL - 1) * (2 + NEPI) + (NPAIR - 1) * 2);
+            mbar_init(&B.tempty[i], (3 + NEPI) + (CL - 1) * (2 + NEPI));
         }
         for (int q = 0; q < NRING; ++q) mbar_init(&B.drain[q], 1);
         B.abort = 0;
@@ -716,7 +693,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
         // ------------------------------------------------------------ producer of ring q (both CTAs)
         const int q = warp;
         if (lane == 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(amap) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&map_a) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(&map_bh) : "memory");
             uint32_t stage = 0, sphase = 0;
             int tslot = 0, tseq = 0;
@@ -733,7 +710,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                         long long task = (long long)atomicAdd(P.task_counter, 1ull);
                         if (ld_volatile(P.error) != kDevOk || task > P.tasks) task = P.tasks;
                         item = 2 * task;
-                        if (CL == 2 && task < P.tasks && 2 * ((task % ptiles) % tn2) + 1 < P.tiles_n) pending = item + 1;
+                        if (task < P.tasks && 2 * ((task % ptiles) % tn2) + 1 < P.tiles_n) pending = item + 1;
                     }
                     if (!mbar_wait_cl(&B.tempty[tslot], tphase ^ 1u, abort, P.error, P.timeout_ns)) break;
                     B.task[tslot] = item;
@@ -755,7 +732,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                 const int r = (int)(task / ptiles);
                 const int t2 = (int)(task - (long long)r * ptiles);
                 const int tp = t2 / tn2;
-                const int tj = 2 * (t2 - tp * tn2) + (CL == 4 ? pc : (int)(item & 1));
+                const int tj = 2 * (t2 - tp * tn2) + (int)(item & 1);
                 const int ti = 2 * tp + rp;
                 bool ok = true;
                 for (int g = 2; g <= s + 1 && ok; ++g) {
@@ -775,11 +752,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                             const int yb = (r * s + (g - ta - 1)) * P.Mp + tj * TN + rp * TNH;
                             for (int bx = 0; bx < boxes; ++bx) {
                                 const int x = (kb * P_KBOX + bx) * BOX;
-                                if (CL == 4)  // my 64-row half of the A box, to both CTAs holding tile row ti
-                                    tma_load_2d_pair_mc(sa + bx * TM * BOX + pc * TNH * BOX, amap, x, ya + pc * TNH,
-                                                        full_lead, (unsigned short)((1u << rp) | (1u << (2 + rp))));
-                                else
-                                    tma_load_2d_pair(sa + bx * TM * BOX, amap, x, ya, full_lead);
+                                tma_load_2d_pair(sa + bx * TM * BOX, &map_a, x, ya, full_lead);
                                 tma_load_2d_pair(sb + bx * TNH * BOX, &map_bh, x, yb, full_lead);
                             }
                             issued = true;
@@ -851,7 +824,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                                 mma_e4m3_pair(dtm, da + boxa + adv, db + boxb + adv, first ? 0u : 1u);
                                 first = false;
                             }
-                            mma_commit_pair(&B.empty[q][stage], all_mask);
+                            mma_commit_pair(&B.empty[q][stage], pair_mask);
                             any = true;
                             if (++stage == RSTAGES) {
                                 stage = 0;
@@ -893,7 +866,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
             const int r = (int)(task / ptiles);
             const int t2 = (int)(task - (long long)r * ptiles);
             const int tp = t2 / tn2;
-            const int tj = 2 * (t2 - tp * tn2) + (CL == 4 ? pc : (int)(item & 1));
+            const int tj = 2 * (t2 - tp * tn2) + (int)(item & 1);
             const int ti = 2 * tp + rp;
             if (!epilogue_tile<P_EPI_WARP0>(P, B.accfull, abort, tmem, r, ti, tj, ti < P.tiles_m && tj < P.tiles_n,
                                             tseq * s, [&](uint32_t b) {
@@ -940,21 +913,14 @@ bool pair_attr() {
     return state > 0;
 }
 
-// clusters of `cl` CTAs, or (preferred_cl = 4) clusters of 4 where possible and of cl elsewhere
-cudaLaunchConfig_t pair_config(cudaLaunchAttribute *at, int ctas, int cl, int preferred_cl, cudaStream_t s) {
+// clusters of two CTAs (one pair each)
+cudaLaunchConfig_t pair_config(cudaLaunchAttribute *at, int ctas, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.x = 2;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.numAttrs = 1;
-    if (preferred_cl > cl) {
-        at[1].id = cudaLaunchAttributePreferredClusterDimension;
-        at[1].val.preferredClusterDim.x = preferred_cl;
-        at[1].val.preferredClusterDim.y = 1;
-        at[1].val.preferredClusterDim.z = 1;
-        cfg.numAttrs = 2;
-    }
     cfg.gridDim = dim3((unsigned)ctas);
     cfg.blockDim = dim3(P_NTHREADS);
     cfg.dynamicSmemBytes = kPairSmemBytes;
@@ -964,12 +930,12 @@ cudaLaunchConfig_t pair_config(cudaLaunchAttribute *at, int ctas, int cl, int pr
 }
 }  // namespace
 
-cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_ah, const CUtensorMap &map_bh,
-                                 const OzParams &P, int ctas, int cluster_ctas, cudaStream_t s) {
+cudaError_t launch_ozaki_tc_pair(const CUtensorMap &map_a, const CUtensorMap &map_bh, const OzParams &P, int ctas,
+                                 cudaStream_t s) {
     if (!pair_attr()) return cudaErrorInvalidValue;
-    cudaLaunchAttribute at[2];
-    cudaLaunchConfig_t cfg = pair_config(at, ctas, 2, cluster_ctas, s);
-    return cudaLaunchKernelEx(&cfg, ozaki_tc_pair_kernel, map_a, map_ah, map_bh, P);
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = pair_config(at, ctas, s);
+    return cudaLaunchKernelEx(&cfg, ozaki_tc_pair_kernel, map_a, map_bh, P);
 }
 
 int ozaki_tc_max_pairs() {
@@ -979,8 +945,8 @@ int ozaki_tc_max_pairs() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaLaunchAttribute at[2];
-    cudaLaunchConfig_t cfg = pair_config(at, sms / 2 * 2, 2, 2, nullptr);
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = pair_config(at, sms / 2 * 2, nullptr);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, ozaki_tc_pair_kernel, &cfg) != cudaSuccess) {
         cudaGetLastError();

@@ -107,14 +107,13 @@ def test_ozaki_plan_info(fmm):
         fmm.fmm_plan_create(64, fmm.fmm_algo_builtin("strassen"), 1, dtype="f64_ozaki", ozaki_slices=13)
 
 
-@pytest.mark.parametrize("engine", ["pair", "pair2", "tc1", "mma_sync"])
+@pytest.mark.parametrize("engine", ["pair", "tc1", "mma_sync"])
 @pytest.mark.parametrize("name,depth,n", [("strassen", 1, 7), ("strassen", 0, 300), ("strassen", 2, 1000),
                                           ("laderman", 1, 384)])
 def test_every_slice_gemm_engine(fmm, oracle_mod, monkeypatch, engine, name, depth, n):
-    """The CTA-pair kernel in clusters of two pairs (default), in single pairs, the one-CTA tcgen05 kernel
-    and the mma.sync kernel give the same bit-exact integer results; the engine is read when the plan is
-    created.  Sizes cover an odd number of tile rows and columns (padding tiles in the last pair and
-    cluster), K not a multiple of 256 and a single tile."""
+    """The CTA-pair kernel (default), the one-CTA tcgen05 kernel and the mma.sync kernel give the same
+    bit-exact integer results; the engine is read when the plan is created.  Sizes cover an odd number of
+    tile rows and columns (padding tiles in the last pair), K not a multiple of 256 and a single tile."""
     if engine == "pair":
         monkeypatch.delenv("FMM_OZAKI_ENGINE", raising=False)
     else:

@@ -57,7 +57,7 @@ def test_scaled_fp64_bit_exact_on_integers(fmm, oracle_mod, name, depth, n):
         assert np.array_equal(got, oracle_mod.axpby(alpha, AB, beta, C0)), (alpha, beta)
 
 
-@pytest.mark.parametrize("engine", ["pair", "pair2", "tc1", "mma_sync"])
+@pytest.mark.parametrize("engine", ["pair", "tc1", "mma_sync"])
 @pytest.mark.parametrize("name,depth,n", [("strassen", 1, 301), ("strassen", 2, 1000), ("strassen", 0, 200)])
 def test_scaled_emulated_bit_exact_on_integers(fmm, oracle_mod, monkeypatch, engine, name, depth, n):
     """Every slice-GEMM engine: the tcgen05 ones apply alpha and beta in the post-addition gather,
