@@ -418,21 +418,50 @@ fmm_status_t fmm_measure_e4m3_peak(void *stream, double *tflops);
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Each call copies its tables into the array and clears the counters on
- * `stream` before launching; the copy from host memory first waits for work
- * already queued on `stream`.  Every call shares the one array, which keeps
- * the last call's contents: calls that overlap on the GPU (for example on
- * different streams) race and give wrong results.  Host calls are serialized
- * by a mutex.  Device-side wait timeouts end the kernel but are not reported
- * by this entry point.
+ * Each call copies its tables into the array and clears the counters and the
+ * error word on `stream` before launching; the copy comes from one host
+ * buffer that the next call rewrites, so a call made while `stream` is being
+ * captured into a CUDA graph returns FMM_ERR_UNSUPPORTED and enqueues
+ * nothing.  Every call shares the one array, which keeps the last call's
+ * contents: calls that overlap on the GPU (for example on different streams)
+ * race and give wrong results.  Host calls are serialized by a mutex.  A
+ * device-side wait that times out ends the kernel with C unspecified; read it
+ * with fmm_noalloc_sync_status before the next call.
  *
  * Errors: FMM_ERR_INVALID (NULL pointer, n < 1, p < 2, R < 1, depth < 0,
  * leaf size < 1), FMM_ERR_BRENT, FMM_ERR_SCRATCH_LIMIT (p > 4, depth > 4, or
  * tables plus counters larger than FMM_NOALLOC_SCRATCH_BYTES),
- * FMM_ERR_UNSUPPORTED (a flattened column with more than 256 terms, or
- * n > 2^30), FMM_ERR_CUDA. */
+ * FMM_ERR_UNSUPPORTED (a flattened column with more than 256 terms, n > 2^30,
+ * p^2 R >= 2^28, R max|U| max|V| max|W| >= 2^62, max|X|^depth >= 2^31 for a
+ * table X, or `stream` capturing), FMM_ERR_CUDA. */
 fmm_status_t fmm_gemm_noalloc(int64_t n, const fmm_algo_t *algo, int depth, const double *A, const double *B,
                               double *C, void *stream);
+
+/* Device status of the most recent fmm_gemm_noalloc call on the current
+ * device, without allocating (no counterpart in the paper): synchronizes
+ * `stream` (the stream of that call), reads the error word kept at the start
+ * of the static scratch array and clears it.  FMM_OK, FMM_ERR_TIMEOUT (a
+ * bounded device-side wait expired; that call's C is unspecified) or
+ * FMM_ERR_CUDA.  Only the latest call's status is kept: each call clears it. */
+fmm_status_t fmm_noalloc_sync_status(void *stream);
+
+/* Testing only (no counterpart in the paper): the bound on every device-side
+ * wait of later fmm_gemm_noalloc calls (default 5 s), and poison_chain = 1 to
+ * set one post-addition ordering counter, after each call's reset, to a value
+ * no task writes, so that its waiters time out.  FMM_ERR_INVALID unless
+ * 0 < wait_timeout_s <= 3600. */
+fmm_status_t fmm_noalloc_set_debug(double wait_timeout_s, int poison_chain);
+
+/* Testing only (no counterpart in the paper): make the k-th next allocation
+ * the library requests fail (k = 0: the next one; k < 0: none), counting every
+ * device, page-locked host and plan-object allocation of fmm_plan_create*,
+ * fmm_gemm_host, fmm_gemm_batched*, fmm_batch_graph_create and fmm_autotune.
+ * The failing call returns FMM_ERR_OOM after releasing what it had taken. */
+void fmm_debug_fail_allocation(int64_t k);
+
+/* Testing only: the number of those allocations currently live (0 when no
+ * plan, batch graph or call is outstanding). */
+int64_t fmm_debug_live_allocations(void);
 
 /* Describe a plan.  Host-only. */
 fmm_status_t fmm_plan_get_info(const fmm_plan_t *plan, fmm_plan_info_t *info);

@@ -46,7 +46,11 @@ from ._binding import (  # noqa: F401
     fmm_gemm_ex,
     fmm_gemm_f32_ex,
     fmm_gemm_host,
+    fmm_debug_fail_allocation,
+    fmm_debug_live_allocations,
     fmm_gemm_noalloc,
+    fmm_noalloc_set_debug,
+    fmm_noalloc_sync_status,
     fmm_plan_create,
     fmm_plan_destroy,
     fmm_plan_get_info,

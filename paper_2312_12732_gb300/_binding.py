@@ -116,6 +116,10 @@ SIGNATURES = [
     ("fmm_gemm_noalloc", ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(fmm_algo_t), ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fmm_measure_e4m3_peak", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    ("fmm_noalloc_sync_status", ctypes.c_int, [ctypes.c_void_p]),
+    ("fmm_debug_fail_allocation", None, [ctypes.c_int64]),
+    ("fmm_debug_live_allocations", ctypes.c_int64, []),
+    ("fmm_noalloc_set_debug", ctypes.c_int, [ctypes.c_double, ctypes.c_int]),
     ("fmm_plan_last_phase_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     ("fmm_plan_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fmm_plan_info_t)]),
     ("fmm_plan_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
@@ -503,6 +507,26 @@ def fmm_gemm_noalloc(algo: Algo, depth: int, A, B, C, stream=None):
                                   ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
                                   ctypes.c_void_p(_stream_ptr(stream))), "fmm_gemm_noalloc")
     return C
+
+
+def fmm_debug_fail_allocation(k: int):
+    """Testing only: the k-th next allocation of the library fails (k < 0: none)."""
+    lib().fmm_debug_fail_allocation(int(k))
+
+
+def fmm_debug_live_allocations() -> int:
+    """Testing only: allocations of the library currently live."""
+    return int(lib().fmm_debug_live_allocations())
+
+
+def fmm_noalloc_sync_status(stream=None) -> int:
+    """Synchronizes the stream and returns the device status of the latest fmm_gemm_noalloc call (0 = ok)."""
+    return int(lib().fmm_noalloc_sync_status(ctypes.c_void_p(_stream_ptr(stream))))
+
+
+def fmm_noalloc_set_debug(wait_timeout_s: float = 5.0, poison_chain: bool = False):
+    """Testing only: wait bound and counter poisoning of later fmm_gemm_noalloc calls."""
+    _check(lib().fmm_noalloc_set_debug(float(wait_timeout_s), int(bool(poison_chain))), "fmm_noalloc_set_debug")
 
 
 def fmm_gemm_batched(plans, As, Bs, Cs, stream=None, alphas=None, betas=None):

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -345,8 +346,7 @@ struct fmm_plan {
     int *d_mxa = nullptr, *d_mxb = nullptr;            // exponents (zeroed per call with the counters)
     const F64Geom *d_geom_peel = nullptr;              // FP64 peel-only geometry
     int oz_engine = 2;                                  // 2 = tcgen05 CTA pairs, 1 = tcgen05, 0 = mma.sync
-    int oz_cluster = 4;                                 // CTAs per cluster of the pair engine (2 or 4)
-    CUtensorMap oz_map_a{}, oz_map_b{}, oz_map_bh{}, oz_map_ah{};  // TMA maps over the slices (h: 64-row boxes)
+    CUtensorMap oz_map_a{}, oz_map_b{}, oz_map_bh{};    // TMA maps over the slices (h: 64-row boxes)
     double *d_pout = nullptr;                           // [R][m][m] leaf products of the tcgen05 engines
     const int *d_wl_ptr = nullptr;                      // per C block: products (r, coefficient) in ascending r
     const int2 *d_wl_ent = nullptr;
@@ -368,6 +368,69 @@ struct fmm_plan {
 namespace {
 
 fmm_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? FMM_OK : FMM_ERR_CUDA; }
+
+// Every allocation the library makes for plans, the host-buffer path and the
+// autotuner goes through these three functions, which keep a count of what is
+// live and can be told to fail the k-th next request (fmm_debug_fail_allocation),
+// so that each error path can be tested without exhausting a device.
+std::atomic<long long> g_live_allocs{0};
+std::atomic<long long> g_fail_countdown{-1};
+
+bool inject_failure() {
+    long long k = g_fail_countdown.load();
+    while (k >= 0) {
+        if (g_fail_countdown.compare_exchange_weak(k, k - 1)) return k == 0;
+    }
+    return false;
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (inject_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ++g_live_allocs;
+    else cudaGetLastError();
+    return e;
+}
+template <class T>
+cudaError_t dev_alloc(T **p, size_t bytes) {
+    void *q = nullptr;
+    const cudaError_t e = dev_alloc(&q, bytes);
+    *p = static_cast<T *>(q);
+    return e;
+}
+void dev_free(void *p) {
+    if (!p) return;
+    cudaFree(p);
+    --g_live_allocs;
+}
+cudaError_t pinned_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (inject_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaHostAlloc(p, bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) ++g_live_allocs;
+    else cudaGetLastError();
+    return e;
+}
+void pinned_free(void *p) {
+    if (!p) return;
+    cudaFreeHost(p);
+    --g_live_allocs;
+}
+// Host objects of the library (plans, batch graphs, launch descriptors).
+template <class T>
+T *host_new() {
+    if (inject_failure()) return nullptr;
+    T *x = new (std::nothrow) T();
+    if (x) ++g_live_allocs;
+    return x;
+}
+template <class T>
+void host_delete(T *x) {
+    if (!x) return;
+    delete x;
+    --g_live_allocs;
+}
 
 // cuTensorMapEncodeTiled from the CUDA driver library, without linking libcuda.
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -405,18 +468,18 @@ bool make_slice_map(CUtensorMap *map, void *base, unsigned long long rows, unsig
 void free_plan_memory(fmm_plan *pl) {
     if (pl->inner) {
         free_plan_memory(pl->inner);
-        delete pl->inner;
+        host_delete(pl->inner);
         pl->inner = nullptr;
     }
-    if (pl->d_planes) cudaFree(pl->d_planes);
+    dev_free(pl->d_planes);
     pl->d_planes = nullptr;
     for (auto &e : pl->ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
-    if (pl->d_tables) cudaFree(pl->d_tables);
-    if (pl->d_ws) cudaFree(pl->d_ws);
-    if (pl->d_hostA) cudaFree(pl->d_hostA);
-    if (pl->d_hostB) cudaFree(pl->d_hostB);
-    if (pl->d_hostC) cudaFree(pl->d_hostC);
+    dev_free(pl->d_tables);
+    dev_free(pl->d_ws);
+    dev_free(pl->d_hostA);
+    dev_free(pl->d_hostB);
+    dev_free(pl->d_hostC);
     pl->d_tables = pl->d_ws = nullptr;
     pl->d_hostA = pl->d_hostB = pl->d_hostC = nullptr;
 }
@@ -551,7 +614,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         fmm_plan_t *inner = nullptr;
         fmm_status_t st = plan_create(&inner, n, algo, depth, FMM_F64_OZAKI, &o2, den);
         if (st != FMM_OK) return st;
-        fmm_plan *pl = new (std::nothrow) fmm_plan();
+        fmm_plan *pl = host_new<fmm_plan>();
         if (!pl) {
             fmm_plan_destroy(inner);
             return FMM_ERR_OOM;
@@ -561,8 +624,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         pl->n = n; pl->p = inner->p; pl->R = inner->R; pl->depth = depth; pl->dtype = dtype;
         pl->wscale = inner->wscale;
         pl->ws_bytes = 3 * (size_t)n * (size_t)n * sizeof(double);
-        if (cudaMalloc(&pl->d_planes, pl->ws_bytes) != cudaSuccess) {
-            cudaGetLastError();
+        if (dev_alloc(&pl->d_planes, pl->ws_bytes) != cudaSuccess) {
             fmm_plan_destroy(pl);
             return FMM_ERR_OOM;
         }
@@ -582,7 +644,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         fmm_plan_t *inner = nullptr;
         fmm_status_t st = plan_create(&inner, n, algo, depth, FMM_F64, opts, den);
         if (st != FMM_OK) return st;
-        fmm_plan *pl = new (std::nothrow) fmm_plan();
+        fmm_plan *pl = host_new<fmm_plan>();
         if (!pl) {
             fmm_plan_destroy(inner);
             return FMM_ERR_OOM;
@@ -593,8 +655,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         pl->wscale = inner->wscale;
         const size_t planes = dtype == FMM_C128 ? 6 : 9;
         pl->ws_bytes = planes * (size_t)n * (size_t)n * sizeof(double);
-        if (cudaMalloc(&pl->d_planes, pl->ws_bytes) != cudaSuccess) {
-            cudaGetLastError();
+        if (dev_alloc(&pl->d_planes, pl->ws_bytes) != cudaSuccess) {
             fmm_plan_destroy(pl);
             return FMM_ERR_OOM;
         }
@@ -639,7 +700,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         if (n / P > (1LL << 30) / 128) return FMM_ERR_UNSUPPORTED;
     }
 
-    fmm_plan *pl = new (std::nothrow) fmm_plan();
+    fmm_plan *pl = host_new<fmm_plan>();
     if (!pl) return FMM_ERR_OOM;
     cudaGetDevice(&pl->device);
     pl->n = n; pl->p = p; pl->R = R; pl->depth = depth; pl->dtype = dtype; pl->mat_levels = mat;
@@ -655,7 +716,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     if (dtype == FMM_F64_OZAKI) {
         pl->bn = fmm::kBN;  // the slice GEMM and its counters use 128 x 128 tiles
     } else if (o.tile_n) {
-        if (o.tile_n != 64 && o.tile_n != 128) { delete pl; return FMM_ERR_INVALID; }
+        if (o.tile_n != 64 && o.tile_n != 128) { host_delete(pl); return FMM_ERR_INVALID; }
         pl->bn = o.tile_n;
     } else {
         pl->bn = default_tile_n(pl->m, pl->total_products_hint = Rt);
@@ -683,7 +744,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     for (auto &c : ucols) maxc = std::max(maxc, c.size());
     for (auto &c : vcols) maxc = std::max(maxc, c.size());
     for (auto &c : wcols) maxc = std::max(maxc, c.size());
-    if (maxc > (size_t)fmm::kMaxTerms) { delete pl; return FMM_ERR_UNSUPPORTED; }
+    if (maxc > (size_t)fmm::kMaxTerms) { host_delete(pl); return FMM_ERR_UNSUPPORTED; }
 
     auto csc2 = [](const std::vector<std::vector<Entry>> &cols, std::vector<int> &ptr, std::vector<int2> &ent) {
         ptr.assign(cols.size() + 1, 0);
@@ -790,9 +851,8 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         o_st[4 * k + 3] = reserve(std::max<size_t>(1, st_vent[k].size()) * sizeof(int4));
     }
     pl->tables_bytes = off;
-    if (cudaMalloc(&pl->d_tables, pl->tables_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        delete pl;
+    if (dev_alloc(&pl->d_tables, pl->tables_bytes) != cudaSuccess) {
+        host_delete(pl);
         return FMM_ERR_OOM;
     }
     char *base = (char *)pl->d_tables;
@@ -847,7 +907,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     if (cudaMemcpy(pl->d_tables, host.data(), pl->tables_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         free_plan_memory(pl);
-        delete pl;
+        host_delete(pl);
         return FMM_ERR_CUDA;
     }
 
@@ -903,10 +963,9 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         o_pout = ws; ws = align_up(ws + (size_t)Rt * (size_t)pl->m * (size_t)pl->m * sizeof(double), 256);
     }
     pl->ws_bytes = ws;
-    if (cudaMalloc(&pl->d_ws, ws) != cudaSuccess) {
-        cudaGetLastError();
+    if (dev_alloc(&pl->d_ws, ws) != cudaSuccess) {
         free_plan_memory(pl);
-        delete pl;
+        host_delete(pl);
         return FMM_ERR_OOM;
     }
     char *wsb = (char *)pl->d_ws;
@@ -928,34 +987,32 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         pl->d_sla = (unsigned char *)(wsb + o_sla);
         pl->d_slb = (unsigned char *)(wsb + o_slb);
         pl->d_pout = (double *)(wsb + o_pout);
-        // engine: CTA pairs in clusters of two pairs by default; FMM_OZAKI_ENGINE=pair2 (one pair
-        // per cluster), tc1 (one CTA per tile) or mma_sync
+        // engine: CTA pairs (one pair per cluster) by default; FMM_OZAKI_ENGINE=tc1 (one CTA per
+        // tile) or mma_sync
         const char *eng = std::getenv("FMM_OZAKI_ENGINE");
         const std::string es = eng ? eng : "";
         pl->oz_engine = es == "mma_sync" ? 0 : (es == "tc1" ? 1 : 2);
-        pl->oz_cluster = (es == "pair2" || pl->tiles_n < 2) ? 2 : 4;
         if (pl->oz_engine == 2 && fmm::ozaki_tc_max_pairs() < 1) pl->oz_engine = 1;
         const unsigned long long srows = (unsigned long long)Rt * oz_s * pl->oz_Mp;
         if (pl->oz_engine >= 1 && (!make_slice_map(&pl->oz_map_a, pl->d_sla, srows, pl->oz_Mp) ||
                                    !make_slice_map(&pl->oz_map_b, pl->d_slb, srows, pl->oz_Mp) ||
-                                   !make_slice_map(&pl->oz_map_bh, pl->d_slb, srows, pl->oz_Mp, 64) ||
-                                   !make_slice_map(&pl->oz_map_ah, pl->d_sla, srows, pl->oz_Mp, 64))) {
+                                   !make_slice_map(&pl->oz_map_bh, pl->d_slb, srows, pl->oz_Mp, 64))) {
             free_plan_memory(pl);
-            delete pl;
+            host_delete(pl);
             return FMM_ERR_CUDA;
         }
         // padding rows/columns of the slices are never written by the kernels
         if (cudaMemset(pl->d_sla, 0, slice_bytes) != cudaSuccess || cudaMemset(pl->d_slb, 0, slice_bytes) != cudaSuccess) {
             cudaGetLastError();
             free_plan_memory(pl);
-            delete pl;
+            host_delete(pl);
             return FMM_ERR_CUDA;
         }
     }
     if (cudaMemset(pl->d_ws, 0, pl->counters_bytes) != cudaSuccess) {
         cudaGetLastError();
         free_plan_memory(pl);
-        delete pl;
+        host_delete(pl);
         return FMM_ERR_CUDA;
     }
 
@@ -965,7 +1022,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     if (per_sm <= 0 || fmm::f64_kernel_ctas_per_sm(pl->bn) <= 0) {
         cudaGetLastError();
         free_plan_memory(pl);
-        delete pl;
+        host_delete(pl);
         return FMM_ERR_CUDA;
     }
     pl->grid = (int)std::min<long long>(pl->total_tasks, (long long)sms * per_sm);
@@ -976,7 +1033,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             if (cudaEventCreate(&e) != cudaSuccess) {
                 cudaGetLastError();
                 free_plan_memory(pl);
-                delete pl;
+                host_delete(pl);
                 return FMM_ERR_CUDA;
             }
     }
@@ -1127,12 +1184,11 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     P.beta = beta;
     if (pl->oz_engine == 2) {
         // a task covers a pair of tile rows and two tile columns; the last row or column of a
-        // task may be padding.  One CTA per SM, in clusters of 4 where possible (oz_cluster = 4).
+        // task may be padding.  One CTA per SM, one pair per cluster.
         P.tasks = (long long)nmat * ((pl->tiles_m + 1) / 2) * ((pl->tiles_n + 1) / 2);
         const long long pairs = std::min<long long>(2 * P.tasks, (long long)fmm::ozaki_tc_max_pairs());
-        const int ctas = (int)(pl->oz_cluster == 4 ? pairs / 2 * 4 : 2 * pairs);
-        if (fmm::launch_ozaki_tc_pair(pl->oz_map_a, pl->oz_map_ah, pl->oz_map_bh, P, ctas < 2 ? 2 : ctas,
-                                      pl->oz_cluster, st) != cudaSuccess)
+        const int ctas = (int)(2 * pairs);
+        if (fmm::launch_ozaki_tc_pair(pl->oz_map_a, pl->oz_map_bh, P, ctas < 2 ? 2 : ctas, st) != cudaSuccess)
             return FMM_ERR_CUDA;
     } else if (pl->oz_engine == 1) {
         const int grid = (int)std::min<long long>(P.tasks, (long long)pl->sms);
@@ -1365,14 +1421,14 @@ extern "C" fmm_status_t fmm_gemm_batched_ex(fmm_plan_t *const *plans, const doub
             if (plans[i]->bn == bn && al(i) != 0.0) sel.push_back(i);
         for (size_t c0 = 0; c0 < sel.size(); c0 += fmm::kMaxBatchPerLaunch) {
             const int cnt = (int)std::min<size_t>(sel.size() - c0, fmm::kMaxBatchPerLaunch);
-            F64Launch<fmm::kMaxBatchPerLaunch> *L = new (std::nothrow) F64Launch<fmm::kMaxBatchPerLaunch>();
+            F64Launch<fmm::kMaxBatchPerLaunch> *L = host_new<F64Launch<fmm::kMaxBatchPerLaunch>>();
             if (!L) return FMM_ERR_OOM;
             long long begin = 0;
             for (int k = 0; k < cnt; ++k) {
                 const int i = sel[c0 + k];
                 const fmm_plan *pl = plans[i];
                 fmm_status_t s = prepare(pl, A[i], B[i], st);
-                if (s != FMM_OK) { delete L; return s; }
+                if (s != FMM_OK) { host_delete(L); return s; }
                 L->probs[k] = problem_of(pl, A[i], B[i], C[i], begin, al(i), be(i));
                 begin += pl->total_tasks;
             }
@@ -1407,7 +1463,7 @@ extern "C" fmm_status_t fmm_gemm_batched_ex(fmm_plan_t *const *plans, const doub
             int grid = (int)std::min<long long>(begin, (long long)sms * fmm::f64_kernel_ctas_per_sm(bn));
             if (grid < 1) grid = 1;
             cudaError_t e = fmm::launch_f64_batch(*L, grid, st, bn);
-            delete L;
+            host_delete(L);
             if (e != cudaSuccess) return FMM_ERR_CUDA;
         }
     }
@@ -1428,7 +1484,7 @@ extern "C" fmm_status_t fmm_batch_graph_create(fmm_batch_graph_t **out, fmm_plan
     if (fmm::f64_kernel_ctas_per_sm(128) <= 0 || fmm::f64_kernel_ctas_per_sm(64) <= 0) return FMM_ERR_CUDA;
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return FMM_ERR_CUDA;
-    fmm_batch_graph *g = new (std::nothrow) fmm_batch_graph();
+    fmm_batch_graph *g = host_new<fmm_batch_graph>();
     if (!g) {
         cudaStreamDestroy(cs);
         return FMM_ERR_OOM;
@@ -1449,7 +1505,7 @@ extern "C" fmm_status_t fmm_batch_graph_create(fmm_batch_graph_t **out, fmm_plan
         cudaGetLastError();
         if (g->exec) cudaGraphExecDestroy(g->exec);
         if (g->graph) cudaGraphDestroy(g->graph);
-        delete g;
+        host_delete(g);
         return st;
     }
     *out = g;
@@ -1465,7 +1521,7 @@ extern "C" void fmm_batch_graph_destroy(fmm_batch_graph_t *g) {
     if (!g) return;
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
-    delete g;
+    host_delete(g);
 }
 
 namespace {
@@ -1489,12 +1545,11 @@ extern "C" fmm_status_t fmm_autotune(int64_t n, const fmm_algo_t *const *algos, 
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
     double *A = nullptr, *B = nullptr, *C = nullptr;
-    if (cudaMalloc(&A, bytes) != cudaSuccess || cudaMalloc(&B, bytes) != cudaSuccess ||
-        cudaMalloc(&C, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(A);
-        cudaFree(B);
-        cudaFree(C);
+    if (dev_alloc(&A, bytes) != cudaSuccess || dev_alloc(&B, bytes) != cudaSuccess ||
+        dev_alloc(&C, bytes) != cudaSuccess) {
+        dev_free(A);
+        dev_free(B);
+        dev_free(C);
         return FMM_ERR_OOM;
     }
     fill_kernel<<<256, 256, 0, st>>>(A, (long long)n * n, 11);
@@ -1534,9 +1589,9 @@ extern "C" fmm_status_t fmm_autotune(int64_t n, const fmm_algo_t *const *algos, 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(A);
-    cudaFree(B);
-    cudaFree(C);
+    dev_free(A);
+    dev_free(B);
+    dev_free(C);
     if (cudaGetLastError() != cudaSuccess) return FMM_ERR_CUDA;
     return result;
 }
@@ -1611,5 +1666,9 @@ extern "C" size_t fmm_plan_workspace_bytes(const fmm_plan_t *pl) {
 extern "C" void fmm_plan_destroy(fmm_plan_t *pl) {
     if (!pl) return;
     free_plan_memory(pl);
-    delete pl;
+    host_delete(pl);
 }
+
+extern "C" void fmm_debug_fail_allocation(int64_t k) { g_fail_countdown.store(k < 0 ? -1 : (long long)k); }
+
+extern "C" int64_t fmm_debug_live_allocations(void) { return (int64_t)g_live_allocs.load(); }

@@ -36,6 +36,11 @@ constexpr int kMaxDevices = 64;
 static void *g_dev_ptr[kMaxDevices];
 static bool g_dev_ready[kMaxDevices];
 
+// Testing hooks for the next calls (fmm_noalloc_set_debug): the bound on
+// every device-side wait, and whether one ordering counter is poisoned.
+static double g_wait_timeout_s = 5.0;
+static int g_poison_chain = 0;
+
 constexpr int kMaxP = 4;                     // split factor
 constexpr int kMaxDepth = 4;                 // recursion levels
 constexpr long long kMaxBlocks = 1LL << 16;  // (p^depth)^2 C blocks
@@ -46,6 +51,29 @@ long long ipow(long long b, int e) {
     long long r = 1;
     while (e-- > 0) r *= b;
     return r;
+}
+
+// Coefficient bounds that keep the checks and the flattened tables exact:
+// p^2 R below 2^28 (int indices), R max|U| max|V| max|W| below 2^62 (every
+// partial Brent sum fits int64), and max|X|^depth below 2^31 for each table
+// (flattened coefficients are products of `depth` entries and stay int32).
+bool coefficients_in_range(const fmm_algo_t *a, int depth) {
+    const long long cnt = (long long)a->p * a->p * a->R;
+    if (cnt >= (1LL << 28)) return false;
+    double mx[3] = {0, 0, 0};
+    const int32_t *X[3] = {a->U, a->V, a->W};
+    for (int t = 0; t < 3; ++t)
+        for (long long x = 0; x < cnt; ++x) {
+            const double v = X[t][x] < 0 ? -(double)X[t][x] : (double)X[t][x];
+            if (v > mx[t]) mx[t] = v;
+        }
+    if ((double)a->R * mx[0] * mx[1] * mx[2] >= 4611686018427387904.0) return false;  // 2^62
+    for (int t = 0; t < 3; ++t) {
+        double pw = 1.0;
+        for (int l = 0; l < depth; ++l) pw *= mx[t];
+        if (pw >= 2147483648.0) return false;  // 2^31
+    }
+    return true;
 }
 
 // Exact Brent check without heap storage: every one of the p^6 equations.
@@ -146,6 +174,7 @@ extern "C" fmm_status_t fmm_gemm_noalloc(int64_t n, const fmm_algo_t *algo, int 
     if (n > (1LL << 31) / 2) return FMM_ERR_UNSUPPORTED;
     const int p = algo->p, R0 = algo->R;
     if (p > kMaxP || depth > kMaxDepth) return FMM_ERR_SCRATCH_LIMIT;
+    if (!coefficients_in_range(algo, depth)) return FMM_ERR_UNSUPPORTED;
     if (!brent_ok(algo)) return FMM_ERR_BRENT;
     const long long P = ipow(p, depth), Rt = ipow(R0, depth);
     if (P > n) return FMM_ERR_INVALID;
@@ -265,18 +294,25 @@ extern "C" fmm_status_t fmm_gemm_noalloc(int64_t n, const fmm_algo_t *algo, int 
     std::memcpy(img + o_geom, &g, sizeof(g));
 
     cudaStream_t st = (cudaStream_t)stream;
+    // The tables are copied from g_host_image, which the next call rewrites: a
+    // copy recorded into a graph would read whatever the last call left there.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return FMM_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return FMM_ERR_UNSUPPORTED;
     // Tables and geometry (the source is copied out before the call returns),
-    // then the counters, which must start at zero on every call.
+    // then the counters and the error word, which must start at zero on every call.
     if (cudaMemcpyAsync(dbase + o_geom, img + o_geom, total - o_geom, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FMM_ERR_CUDA;
     if (cudaMemsetAsync(dbase, 0, counters_bytes, st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (g_poison_chain && cudaMemsetAsync(dbase + 16, 0xFF, sizeof(unsigned), st) != cudaSuccess)
+        return FMM_ERR_CUDA;
 
     fmm::F64Launch<1> L{};
     L.nprobs = 1;
     L.total_tasks = g.tasks_core + g.tasks_right + g.tasks_bottom + g.tasks_rankq;
     L.task_counter = (unsigned long long *)(dbase + 8);
     L.error = (int *)dbase;
-    L.timeout_ns = 5000000000LL;
+    L.timeout_ns = (long long)(g_wait_timeout_s * 1e9);
     fmm::F64Problem &pr = L.probs[0];
     pr.g = (const fmm::F64Geom *)(dbase + o_geom);
     pr.A = A; pr.B = B; pr.SA = A; pr.SB = B; pr.C = C;
@@ -294,4 +330,28 @@ extern "C" fmm_status_t fmm_gemm_noalloc(int64_t n, const fmm_algo_t *algo, int 
     if (grid > L.total_tasks) grid = L.total_tasks;
     if (grid < 1) grid = 1;
     return fmm::launch_f64_single(L, (int)grid, st) == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
+}
+
+extern "C" fmm_status_t fmm_noalloc_sync_status(void *stream) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return FMM_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    // offset 0 of the array on the current device holds the last call's error word
+    int err = 0;
+    if (cudaMemcpyFromSymbol(&err, g_fmm_noalloc_scratch, sizeof(int), 0, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    if (err != fmm::kDevOk) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbol(g_fmm_noalloc_scratch, &zero, sizeof(int), 0, cudaMemcpyHostToDevice) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        return FMM_ERR_TIMEOUT;
+    }
+    return FMM_OK;
+}
+
+extern "C" fmm_status_t fmm_noalloc_set_debug(double wait_timeout_s, int poison_chain) {
+    if (!(wait_timeout_s > 0.0) || wait_timeout_s > 3600.0) return FMM_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_wait_timeout_s = wait_timeout_s;
+    g_poison_chain = poison_chain ? 1 : 0;
+    return FMM_OK;
 }

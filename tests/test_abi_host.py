@@ -297,3 +297,22 @@ def test_random_symmetry_and_composition_chains(fmm, oracle_mod):
         assert np.array_equal(lib_a.U, U) and np.array_equal(lib_a.V, V) and np.array_equal(lib_a.W, W)
         assert fmm.fmm_algo_rect_brent_mismatches(lib_a) == 0
         assert oracle_mod.rect_brent_mismatches(m, k, n, U, V, W) == 0
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_ozaki", "c128", "c128_3m", "f32"])
+def test_injected_allocation_failure_returns_oom_and_leaks_nothing(fmm, dtype):
+    """The library's allocation shim fails the k-th next request on demand.  k = 0 fails the plan object
+    itself, k = 1 the first device allocation (the coefficient tables, or an inner plan's object); both
+    are injected before any CUDA call, so this runs without a GPU.  Each must give FMM_ERR_OOM and leave
+    no allocation live."""
+    s = fmm.fmm_algo_builtin("strassen")
+    base = fmm.fmm_debug_live_allocations()
+    try:
+        for k in (0, 1):
+            fmm.fmm_debug_fail_allocation(k)
+            with pytest.raises(fmm.FmmError) as e:
+                fmm.fmm_plan_create(256, s, 1, dtype=dtype)
+            assert e.value.status == 4, (k, e.value)
+            assert fmm.fmm_debug_live_allocations() == base, k
+    finally:
+        fmm.fmm_debug_fail_allocation(-1)
