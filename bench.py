@@ -66,6 +66,8 @@ def parse_args(argv=None):
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-emulated", action="store_true",
                     help="skip the emulated-FP64 (Ozaki, Strassen depth 2) measurement added to the JSON line")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched workload (256 autotuned products in one graph) added to the JSON line")
     return ap.parse_args(argv)
 
 
@@ -121,8 +123,11 @@ def source_digest(kernel: str):
 
 
 def profile_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch recorded by an ncu capture in profiles/, if it was
-    taken on the current kernel source and this workload; else None."""
+    """DRAM bytes per launch of `kernel` on `workload` from an ncu capture summarised in profiles/, if it
+    was taken on the current kernel source; else None.  A capture of a smaller case of the same kernel
+    names the bench workload it scales to (`scaled_workload`) and the scaled bytes
+    (`scaled_dram_bytes_per_launch`, by the units of work the launch processes, as the summary states);
+    a capture of the workload itself gives `dram_bytes_per_launch` directly."""
     digest = source_digest(kernel)
     if digest is None:
         return None
@@ -137,11 +142,15 @@ def profile_traffic(kernel: str, workload: str):
             if line.startswith("- ") and ":" in line:
                 k, v = line[2:].split(":", 1)
                 kv[k.strip()] = v.strip().strip("`")
-        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source_sha256_16") == digest:
-            try:
+        if kv.get("kernel") != kernel or kv.get("source_sha256_16") != digest:
+            continue
+        try:
+            if kv.get("scaled_workload") == workload:
+                return float(kv["scaled_dram_bytes_per_launch"])
+            if kv.get("workload") == workload:
                 return float(kv["dram_bytes_per_launch"])
-            except (KeyError, ValueError):
-                return None
+        except (KeyError, ValueError):
+            return None
     return None
 
 
@@ -357,11 +366,14 @@ def materialized_bytes(n_core: int, p: int, R_total: int, depth: int, levels: in
     return 2 * 8 * total
 
 
-def time_plan(torch, fmm, plan, dA, dB, dC, warmup, steps, dist=None, stream=None):
-    """(ms per step over the timed region, mean leaf-kernel ms per launch)."""
+def time_plan(torch, fmm, plan, dA, dB, dC, warmup, steps, dist=None, stream=None, after=None):
+    """(ms per step over the timed region, mean leaf-kernel ms per launch).  `after(dC)` runs after every
+    call on the same stream (the sum of the shards' partial products when the product is sharded)."""
     stream = stream or torch.cuda.current_stream()
     for _ in range(warmup):
         fmm.fmm_gemm(plan, dA, dB, dC, stream)
+        if after is not None:
+            after(dC)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -373,6 +385,8 @@ def time_plan(torch, fmm, plan, dA, dB, dC, warmup, steps, dist=None, stream=Non
     e0.record(stream)
     for _ in range(steps):
         fmm.fmm_gemm(plan, dA, dB, dC, stream)
+        if after is not None:
+            after(dC)
         leaf.append(fmm.fmm_plan_last_kernel_ms(plan)[0])
         if plan.dtype in ("f64", "f64_ozaki"):  # complex and f32 plans time the whole call only
             phases.append(fmm.fmm_plan_last_phase_ms(plan))
@@ -505,72 +519,102 @@ def run_sweep(a):
     return 0
 
 
-def run_batched(a):
+def batched_measurement(torch, fmm, dev, count: int, steps: int, warmup: int, tune_reps: int = 5):
+    """The batched workload: `count` products with n_i log-uniform in [128, 4096] (SplitMix64 seed 3),
+    entries uniform[-1, 1] (seeded on the device), each planned with its bucket's autotuned (algorithm,
+    depth, leaf tile, schedule), all of them run by one CUDA graph (per-plan counter resets and
+    materialization passes, then one grouped persistent leaf launch per tile width).  Returns the
+    measurement as a dict; the same batch at depth 0 in one graph is timed beside it."""
     import collections
 
-    import torch
+    from paper_2312_12732_gb300 import autotune, inputs
 
-    import paper_2312_12732_gb300 as fmm
-    from paper_2312_12732_gb300 import _build, autotune, inputs
-
-    _build.build()
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    sizes = inputs.batch_sizes(a.batch_count, 128, 4096, seed=3)
+    sizes = inputs.batch_sizes(count, 128, 4096, seed=3)
     t0 = time.perf_counter()
-    plans, picks = autotune.plan_batch(sizes, candidates=("strassen", "winograd"), max_depth=3, min_leaf=128)
+    plans, picks = autotune.plan_batch(sizes, candidates=("strassen", "winograd"), max_depth=3, min_leaf=128,
+                                       reps=tune_reps)
     tune_s = time.perf_counter() - t0
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1000)
     As, Bs, Cs = [], [], []
-    for i, n in enumerate(sizes):
-        A, B = inputs.operands(n, "uniform", seed=1000 + 2 * i)
-        As.append(torch.from_numpy(A).to(dev))
-        Bs.append(torch.from_numpy(B).to(dev))
+    for n in sizes:
+        As.append(torch.rand(n, n, dtype=torch.float64, device=dev, generator=gen) * 2 - 1)
+        Bs.append(torch.rand(n, n, dtype=torch.float64, device=dev, generator=gen) * 2 - 1)
         Cs.append(torch.empty_like(As[-1]))
     flops = sum(2.0 * n ** 3 for n in sizes)
     flops_exec = sum(p.info()["flops_executed"] for p in plans)
 
-    def time_graph(g, steps, warm):
+    def time_graph(g, k, warm):
         stream = torch.cuda.current_stream()
         for _ in range(warm):
             fmm.fmm_batch_graph_launch(g, stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(steps):
+        for _ in range(k):
             fmm.fmm_batch_graph_launch(g, stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
+        return e0.elapsed_time(e1) / k
 
     g = fmm.fmm_batch_graph_create(plans, As, Bs, Cs)
     sampler = ClockSampler(gpu_uuid(torch, dev))
     with sampler:
-        ms = time_graph(g, a.steps, max(a.warmup, 3))
+        ms = time_graph(g, steps, max(warmup, 3))
     st = fmm.fmm_sync_status(plans[0])
     if st != 0:
         raise RuntimeError("device status: " + fmm.fmm_status_string(st))
-    # spot check: a few products against a float64 GPU product
+    # accuracy: 64 sampled entries of eight products against the oracle's Dot2 references
     errs = []
     for i in range(0, len(sizes), max(1, len(sizes) // 8)):
-        ref = As[i] @ Bs[i]
-        errs.append(((Cs[i] - ref).abs().max() / (sizes[i] * As[i].abs().max() * Bs[i].abs().max())).item())
+        A, B = As[i].cpu().numpy(), Bs[i].cpu().numpy()
+        rows, cols = inputs.sample_indices(sizes[i], 64, seed=11 + i)
+        got = Cs[i].cpu().numpy()[rows, cols]
+        errs.append(oracle_error(A, B, got, rows, cols))
     plans0 = [fmm.fmm_plan_create(n, fmm.fmm_algo_builtin("strassen"), 0) for n in sizes]
     g0 = fmm.fmm_batch_graph_create(plans0, As, Bs, Cs)
-    ms0 = time_graph(g0, max(2, a.steps // 2), 1)
-    hist = collections.Counter(f"{nm}:d{d}" for nm, d in picks)
-    line = {
-        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps,
-        "warmup": max(a.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"batched_{len(sizes)}_loguniform_128_4096_uniform_fp64", "products": len(sizes),
-                   "sizes_min_max": [min(sizes), max(sizes)], "picks": dict(hist), "autotune_s": tune_s,
-                   "launch": "one CUDA graph: per-plan counter resets and materialization passes, then one "
-                             "grouped persistent leaf launch"},
+    ms0 = time_graph(g0, max(2, steps // 2), 1)
+    hist = collections.Counter(f"{p['algo']}:d{p['depth']}:t{p['tile_n']}:{p['schedule']}" for p in picks)
+    launches = 0
+    for p in plans:
+        launches += 2 * p.info()["materialize_passes"]
+    launches += len({p.info()["tile_n"] for p in plans})
+    return {
+        "workload": f"batched_{len(sizes)}_loguniform_128_4096_uniform_fp64", "value": flops / (ms * 1e-3) / 1e12,
+        "unit": "TFLOP/s", "ms_per_step": ms, "steps": steps, "warmup": max(warmup, 3), "products": len(sizes),
+        "sizes_min_max": [min(sizes), max(sizes)], "picks": dict(hist), "autotune_s": round(tune_s, 2),
+        "autotune_buckets": len({autotune.bucket(n) for n in sizes}),
+        "launch": "one CUDA graph: per-plan counter resets and materialization passes, then one grouped "
+                  "persistent leaf launch per tile width",
+        "gpu_launches": steps * launches,
         "classic_depth0_graph": {"value": flops / (ms0 * 1e-3) / 1e12, "ms_per_step": ms0},
-        "flops_executed_per_step": flops_exec, "executed_tflops": flops_exec / (ms * 1e-3) / 1e12,
         "speedup_vs_classic": ms0 / ms,
+        "flops_executed_per_step": flops_exec, "executed_tflops": flops_exec / (ms * 1e-3) / 1e12,
         "normalised_error_sampled_max": max(errs),
         "clocks": sampler.summary(),
+    }
+
+
+def run_batched(a):
+    import torch
+
+    import paper_2312_12732_gb300 as fmm
+    from paper_2312_12732_gb300 import _build
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    b = batched_measurement(torch, fmm, dev, a.batch_count, a.steps, a.warmup)
+    line = {
+        "metric": METRIC, "value": b["value"], "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps,
+        "warmup": b["warmup"], "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": b["workload"], "products": b["products"], "sizes_min_max": b["sizes_min_max"],
+                   "picks": b["picks"], "autotune_s": b["autotune_s"], "launch": b["launch"]},
+        "classic_depth0_graph": b["classic_depth0_graph"], "flops_executed_per_step": b["flops_executed_per_step"],
+        "executed_tflops": b["executed_tflops"], "speedup_vs_classic": b["speedup_vs_classic"],
+        "normalised_error_sampled_max": b["normalised_error_sampled_max"], "clocks": b["clocks"],
+        "gpu_launches": b["gpu_launches"],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -603,22 +647,29 @@ def run_ours(a):
     A, B = inputs.operands(n, a.kind, seed=1, phi=a.phi)
     dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
     dC = torch.empty_like(dA)
+    # one GPU: the whole product; N GPUs: rank k computes shard k of the leaf products and the partial
+    # products are summed by one all-reduce per step (strong scaling: one product per step for the job)
+    sharded = ws > 1
+    from paper_2312_12732_gb300 import sharded as shard_mod
+
     plan = fmm.fmm_plan_create(n, algo, a.depth, dtype=a.dtype, schedule=a.schedule,
                                materialize_levels=a.materialize_levels, ozaki_slices=a.slices,
-                               record_kernel_time=True)
+                               record_kernel_time=True, shard_count=ws if sharded else 0,
+                               shard_index=rank if sharded else 0)
+    after = shard_mod.reduce_partials if sharded else None
     info = plan.info()
 
     dmma_peak, dfma_peak = fmm.fmm_measure_fp64_peak()
     e4m3_peak = fmm.fmm_measure_e4m3_peak() if a.dtype == "f64_ozaki" else None
     sampler = ClockSampler(gpu_uuid(torch, dev))
     with sampler:
-        ms, leaf_ms = time_plan(torch, fmm, plan, dA, dB, dC, max(a.warmup, 3), a.steps, dist)
+        ms, leaf_ms = time_plan(torch, fmm, plan, dA, dB, dC, max(a.warmup, 3), a.steps, dist, after=after)
     clocks = sampler.summary()
     main_phases = time_plan.last_phases
 
     ms = max_over_ranks(ms, dist, dev)
     flops_eff = 2.0 * n ** 3
-    value = job_throughput(flops_eff, ws, ms * 1e-3) / 1e12
+    value = (flops_eff / (ms * 1e-3) if sharded else job_throughput(flops_eff, ws, ms * 1e-3)) / 1e12
 
     # accuracy: 4096 sampled entries against the oracle's compensated dot products of the same inputs
     s_rows, s_cols = inputs.sample_indices(n, 4096, seed=7)
@@ -626,7 +677,7 @@ def run_ours(a):
     err = oracle_error(A, B, dC[t_rows, t_cols].cpu().numpy(), s_rows, s_cols) if rank == 0 else None
 
     classic = None
-    if not a.no_classic and a.depth > 0:
+    if not a.no_classic and a.depth > 0 and not sharded:
         p0 = fmm.fmm_plan_create(n, algo, 0, record_kernel_time=True)
         ms0, leaf0 = time_plan(torch, fmm, p0, dA, dB, dC, 1, max(2, a.steps // 2), dist)
         classic = {"value": flops_eff / (ms0 * 1e-3) / 1e12, "ms_per_step": ms0, "leaf_kernel_ms": leaf0}
@@ -647,18 +698,33 @@ def run_ours(a):
             hC = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
             hA.copy_(torch.from_numpy(A))
             hB.copy_(torch.from_numpy(B))
-            fmm.fmm_gemm_host(plan, hA, hB, hC)  # allocates the plan's host-path buffers
+
+            def e2e_step():
+                if not sharded:
+                    fmm.fmm_gemm_host(plan, hA, hB, hC)
+                    return
+                # every rank copies in both operands, computes its shard, the partials are summed on the
+                # device, and rank 0 copies the product back
+                dA.copy_(hA, non_blocking=True)
+                dB.copy_(hB, non_blocking=True)
+                shard_mod.gemm_sharded(plan, dA, dB, dC)
+                if rank == 0:
+                    hC.copy_(dC, non_blocking=True)
+                torch.cuda.synchronize()
+
+            e2e_step()  # the plan's host-path buffers are allocated by the first call
             if dist is not None:
                 dist.barrier()
             t0 = time.perf_counter()
             for _ in range(k_e2e):
                 tc = time.perf_counter()
-                fmm.fmm_gemm_host(plan, hA, hB, hC)
+                e2e_step()
                 call_ms.append((time.perf_counter() - tc) * 1e3)
                 dev_ms.append(fmm.fmm_plan_last_kernel_ms(plan)[1])  # the call's device work, copies excluded
             t1 = time.perf_counter()
         te = max_over_ranks((t1 - t0) / k_e2e, dist, dev)
-        # the copies alone, same pinned buffers (context for the gap between e2e and device time)
+        # the copies alone, same pinned buffers (context for the gap between e2e and device time), and the
+        # host link's rate in each direction measured with CUDA events on the same buffers
         torch.cuda.synchronize()
         tc = time.perf_counter()
         dA.copy_(hA, non_blocking=True)
@@ -666,12 +732,27 @@ def run_ours(a):
         hC.copy_(dC, non_blocking=True)
         torch.cuda.synchronize()
         copy_ms = (time.perf_counter() - tc) * 1e3
-        e2e = {"value": job_throughput(flops_eff, ws, te) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 2 * n * n * 8,
-               "d2h_bytes_per_step": n * n * 8, "ms_per_step": te * 1e3, "steps": k_e2e,
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        dA.copy_(hA, non_blocking=True)
+        ev[1].record()
+        dB.copy_(hB, non_blocking=True)
+        ev[2].record()
+        hC.copy_(dC, non_blocking=True)
+        ev[3].record()
+        torch.cuda.synchronize()
+        gbs = [n * n * 8 / (ev[i].elapsed_time(ev[i + 1]) * 1e-3) / 1e9 for i in range(3)]
+        h2d_gbs, d2h_gbs = min(gbs[0], gbs[1]), gbs[2]
+        e2e = {"value": (flops_eff / te if sharded else job_throughput(flops_eff, ws, te)) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": ws * 2 * n * n * 8, "d2h_bytes_per_step": (1 if sharded else ws) * n * n * 8,
+               "ms_per_step": te * 1e3, "steps": k_e2e,
                "device_ms_per_step": statistics.mean(dev_ms), "call_ms": [round(x, 2) for x in call_ms],
                "device_ms": [round(x, 2) for x in dev_ms], "copies_alone_ms": round(copy_ms, 2),
+               "h2d_gbs": round(h2d_gbs, 1), "d2h_gbs": round(d2h_gbs, 1),
+               "copy_gbs_A_B_C": [round(x, 1) for x in gbs],
                "clocks": sampler_e2e.summary(),
-               "path": "fmm_gemm_host (pinned host buffers, copies inside the timed region)"}
+               "path": "fmm_gemm_host (pinned host buffers, copies inside the timed region)" if not sharded else
+               "per rank: copies of A and B in, its shard (fmm_gemm), all-reduce of C, rank 0 copies C out"}
 
     nc = info["n_core"]
     q = n - nc
@@ -698,7 +779,7 @@ def run_ours(a):
                 "frac_of_instruction_rate_measured_here": achieved / ref_rate if ref_rate else None, **extra}
 
     emulated = None
-    if a.dtype == "f64" and not a.no_emulated:
+    if a.dtype == "f64" and not a.no_emulated and not sharded:
         e_algo = fmm.fmm_algo_builtin("strassen")
         e_plan = fmm.fmm_plan_create(n, e_algo, 2, dtype="f64_ozaki", record_kernel_time=True)
         e_ms, e_leaf = time_plan(torch, fmm, e_plan, dA, dB, dC, max(a.warmup, 3), a.steps, dist)
@@ -725,9 +806,15 @@ def run_ours(a):
                     f"{e_info['ozaki_slices']} e4m3 slices with exact FP32/int64 sums (precision configuration)"}
         fmm.fmm_plan_destroy(e_plan)
 
+    # the batched workload (256 autotuned products of log-uniform size in one CUDA graph), three timed steps
+    batched = None
+    if a.dtype == "f64" and not a.no_batched and not sharded:
+        batched = batched_measurement(torch, fmm, dev, a.batch_count, 3, 3)
+        batched["gpu_launches_note"] = "counted separately from the main step's gpu_launches"
+
     # context only, not on the product path: the vendor FP64 GEMM (cuBLAS DGEMM through torch.matmul)
     dgemm = None
-    if not a.no_cublas:
+    if not a.no_cublas and not sharded:
         torch.matmul(dA, dB, out=dC)
         torch.cuda.synchronize()
         c0 = torch.cuda.Event(enable_timing=True)
@@ -777,16 +864,19 @@ def run_ours(a):
 
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": a.steps,
-        "warmup": max(a.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": max(a.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "n": n, "algorithm": a.algo, "depth": a.depth,
                    "leaf": "fp64 DMMA" if a.dtype == "f64" else f"emulated FP64, {info['ozaki_slices']} e4m3 slices",
                    "schedule": a.schedule, "materialized_levels": info["materialized_levels"],
                    "leaf_m": info["m"], "products": info["R_total"], "entries": a.kind,
                    "l2": "inputs 3 x %.0f MiB > L2 (129 MB), no flush" % (n * n * 8 / 2 ** 20),
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+                   "parallelism": f"{ws} GPUs, leaf products sharded (ranges {info['product_begin']}.."
+                                  f"{info['product_end']} on rank {rank}), one all-reduce of C per step"
+                   if sharded else "single GPU"},
         "classic_depth0": classic,
-        "speedup_vs_classic": (value / ws) / classic["value"] if classic else None,
+        "speedup_vs_classic": value / classic["value"] if classic else None,
         "context_cublas_dgemm": dgemm,
         "hbm": hbm,
         "normalised_error_sampled": err,
@@ -796,6 +886,7 @@ def run_ours(a):
         else a.steps * (1 + 2 * info["materialize_passes"]),
         "roofline": roofline,
         "emulated_fp64": emulated,
+        "batched": batched,
         "cpu_baseline": cpu,
         "flops_executed_per_step": info["flops_executed"],
         "executed_tflops": info["flops_executed"] / (ms * 1e-3) / 1e12,

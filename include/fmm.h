@@ -129,6 +129,22 @@ typedef struct {
                                 its stream (see fmm_plan_last_kernel_ms) */
     int tile_n;              /* FMM_F64 leaf tile width: 128 (one 8-warp CTA per SM)
                                 or 64 (two 4-warp CTAs per SM); 0 = planner's choice */
+    /* Product sharding (Section 2: the R^depth leaf products are independent,
+     * each can be computed on its own).  shard_count > 1 makes an FMM_F64
+     * plan compute only shard `shard_index` of its leaf products: the
+     * R^materialized_levels sub-problems are split into shard_count
+     * contiguous ranges of sizes differing by at most one
+     * (fmm_shard_range), and the plan's C is the sum over its own products
+     * of W[l][r] P_r, zero elsewhere; the shard whose range starts at product
+     * 0 also runs the peel fix-ups of a non-divisible n.  The full product is
+     * the elementwise sum of the shard_count partial C's (for example an
+     * all-reduce across GPUs, one shard per GPU).  A sharded plan takes
+     * beta = 0 only and cannot join a batched launch.  0 or 1 = the whole
+     * product.  FMM_ERR_UNSUPPORTED for another dtype, or for more shards
+     * than sub-problems (a fused schedule has one); FMM_ERR_INVALID for
+     * shard_index outside [0, shard_count). */
+    int shard_count;
+    int shard_index;
 } fmm_plan_options_t;
 
 /* Read-only description of a plan (all sizes in elements). */
@@ -150,7 +166,17 @@ typedef struct {
     int materialize_passes; /* kernel passes per operand that form the materialized S_r / T_r
                                (a level, a Kronecker factor of one, or two 2 x 2 factors fused) */
     double coef_scale;      /* (den_u den_v den_w)^-depth for a rational plan, 1 otherwise */
+    int64_t product_begin;  /* leaf products [product_begin, product_end) of this plan's shard */
+    int64_t product_end;    /* (0 and R_total for an unsharded plan) */
 } fmm_plan_info_t;
+
+/* The contiguous range [*begin, *end) of `units` work units that shard
+ * shard_index of shard_count takes: shard k starts at floor(k units /
+ * shard_count), so range sizes differ by at most one and the ranges cover
+ * [0, units) in order.  Host-only, no GPU work (the partition a sharded plan
+ * uses, in units of sub-problems).  FMM_ERR_INVALID for units < 0,
+ * shard_count < 1, shard_index outside [0, shard_count) or a NULL output. */
+fmm_status_t fmm_shard_range(int64_t units, int shard_count, int shard_index, int64_t *begin, int64_t *end);
 
 /* Status code to a static, NUL-terminated English string (never NULL). */
 const char *fmm_status_string(fmm_status_t s);
@@ -307,11 +333,16 @@ fmm_status_t fmm_gemm_f32_ex(const fmm_plan_t *plan, float alpha, const float *A
 /* Same as fmm_gemm with HOST buffers: copies A and B to plan-owned device
  * buffers (allocated on first use, freed by fmm_plan_destroy), multiplies,
  * copies C back and synchronizes `stream` before returning.  Blocking.
- * For an FMM_C128 plan the buffers hold interleaved complex pairs and for an
- * FMM_F32 plan binary32 values (pass their addresses cast to these types).
- * Page-locked host buffers copy at the host link's rate (about 200 GB/s on
- * GB300); pageable ones, or page-locked buffers allocated before the process
- * forked (a subprocess, for instance), copy at about 25 GB/s. */
+ * For an FMM_F64 or FMM_F64_OZAKI plan, B is copied on a plan-owned stream
+ * (created on first use) while A's copy and A's pre-addition passes run on
+ * `stream`; B's passes wait for its copy.  With page-locked sources the two
+ * overlap; a pageable source's copy returns only once it is done.  For an
+ * FMM_C128 plan the buffers hold interleaved complex pairs and for an
+ * FMM_F32 plan binary32 values (pass their addresses cast to these types);
+ * both copy A, then B, on `stream`.  On GB300 (Grace host) page-locked
+ * buffers copy at about 210 GB/s host to device and 190 GB/s back, pageable
+ * ones at 180-200 GB/s.  FMM_ERR_OOM if the device buffers cannot be
+ * allocated, FMM_ERR_CUDA if a copy or launch fails. */
 fmm_status_t fmm_gemm_host(fmm_plan_t *plan, const double *A_host, const double *B_host,
                            double *C_host, void *stream);
 
@@ -346,20 +377,32 @@ fmm_status_t fmm_batch_graph_launch(const fmm_batch_graph_t *g, void *stream);
 void fmm_batch_graph_destroy(fmm_batch_graph_t *g);
 
 /* Autotuner, with no counterpart in the paper beyond its observation that the
- * best algorithm depends on the problem size (Section 3): times one
- * multiplication of size n on scratch operands for every candidate algorithm
- * (index into `algos`) at every depth 0..max_depth whose leaf is at least
- * min_leaf, with the default schedule and FMM_F64, and returns the fastest
- * choice.  Depth 0 (the classic product) is always a candidate.  Blocking;
- * allocates and frees 3 n^2 doubles and the candidate plans on the current
- * device. */
+ * best algorithm depends on the problem size and that each call has a fixed
+ * overhead (Section 3): times one FMM_F64 multiplication of size n on scratch
+ * operands for every candidate configuration and returns the fastest.  The
+ * candidates are
+ *   - depth 0 (the classic product, algos[0]'s split factor is irrelevant);
+ *   - every algorithm (index into `algos`) at every depth 1..max_depth whose
+ *     leaf n / p^depth is at least min_leaf;
+ *   - for each of those, both leaf tile widths (tile_n 64 and 128) and, at
+ *     depth 1 when the planner would materialize it, both the default
+ *     (materialized) and the fused schedule.
+ * Each candidate runs once untimed, then up to `reps` timed runs (CUDA events
+ * on `stream`; reps < 1 means 5); its time is the median.  A candidate whose
+ * first timed run is more than 1.5 times the best median so far stops there.
+ * Blocking; allocates and frees 3 n^2 doubles and the candidate plans on the
+ * current device. */
 typedef struct {
-    int algo_index;   /* index into the candidate list */
+    int algo_index;          /* index into the candidate list */
     int depth;
-    double ms;        /* measured time of the best candidate */
+    double ms;               /* median time of the best candidate */
+    int tile_n;              /* its leaf tile width (64 or 128) */
+    fmm_schedule_t schedule; /* its schedule (FMM_SCHED_AUTO or FMM_SCHED_FUSED) */
+    double depth0_ms;        /* median time of the best depth-0 candidate */
+    int candidates;          /* configurations timed */
 } fmm_tune_result_t;
 fmm_status_t fmm_autotune(int64_t n, const fmm_algo_t *const *algos, int nalgos, int max_depth, int64_t min_leaf,
-                          void *stream, fmm_tune_result_t *best);
+                          int reps, void *stream, fmm_tune_result_t *best);
 
 /* Synchronize `stream`, then read and clear the plan's device error flag:
  * FMM_OK, FMM_ERR_TIMEOUT (a bounded wait expired; C is unspecified) or

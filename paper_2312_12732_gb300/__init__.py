@@ -59,6 +59,7 @@ from ._binding import (  # noqa: F401
     fmm_measure_e4m3_peak,
     fmm_measure_fp64_peak,
     fmm_plan_workspace_bytes,
+    fmm_shard_range,
     fmm_status_string,
     fmm_sync_status,
     lib,

@@ -46,7 +46,8 @@ class fmm_algo_rational_t(ctypes.Structure):
 class fmm_plan_options_t(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int), ("materialize_levels", ctypes.c_int), ("ozaki_slices", ctypes.c_int),
                 ("wait_timeout_s", ctypes.c_double), ("debug_poison_chain", ctypes.c_int),
-                ("record_kernel_time", ctypes.c_int), ("tile_n", ctypes.c_int)]
+                ("record_kernel_time", ctypes.c_int), ("tile_n", ctypes.c_int), ("shard_count", ctypes.c_int),
+                ("shard_index", ctypes.c_int)]
 
 
 class fmm_plan_info_t(ctypes.Structure):
@@ -55,12 +56,15 @@ class fmm_plan_info_t(ctypes.Structure):
                 ("tasks", ctypes.c_int64), ("materialized_levels", ctypes.c_int),
                 ("flops_leaf", ctypes.c_double), ("flops_executed", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_size_t), ("ozaki_slices", ctypes.c_int), ("flops_lowp", ctypes.c_double),
-                ("tile_n", ctypes.c_int), ("materialize_passes", ctypes.c_int), ("coef_scale", ctypes.c_double)]
+                ("tile_n", ctypes.c_int), ("materialize_passes", ctypes.c_int), ("coef_scale", ctypes.c_double),
+                ("product_begin", ctypes.c_int64), ("product_end", ctypes.c_int64)]
 
 
 # (name, restype, argtypes) for every symbol declared in include/fmm.h.
 SIGNATURES = [
     ("fmm_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("fmm_shard_range", ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64)]),
     ("fmm_algo_builtin", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(fmm_algo_t)]),
     ("fmm_algo_brent_mismatches", ctypes.c_int64, [ctypes.POINTER(fmm_algo_t)]),
     ("fmm_algo_from_transposed_c", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p]),
@@ -108,7 +112,7 @@ SIGNATURES = [
     ("fmm_batch_graph_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("fmm_batch_graph_destroy", None, [ctypes.c_void_p]),
     ("fmm_autotune", ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.POINTER(fmm_algo_t)), ctypes.c_int,
-                                    ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+                                    ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("fmm_plan_last_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
                                                ctypes.POINTER(ctypes.c_float)]),
     ("fmm_measure_fp64_peak", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -158,6 +162,14 @@ def _check(status: int, what: str):
 
 def fmm_status_string(status: int) -> str:
     return lib().fmm_status_string(int(status)).decode()
+
+
+def fmm_shard_range(units: int, shard_count: int, shard_index: int) -> tuple[int, int]:
+    """[begin, end) of `units` work units taken by shard `shard_index` of `shard_count` (host only)."""
+    b, e = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().fmm_shard_range(int(units), int(shard_count), int(shard_index), ctypes.byref(b), ctypes.byref(e)),
+           "fmm_shard_range")
+    return int(b.value), int(e.value)
 
 
 class Algo:
@@ -366,14 +378,16 @@ class Plan:
 
 def fmm_plan_create(n: int, algo: Algo, depth: int, dtype: str = "f64", schedule: str = "auto",
                     materialize_levels: int = 0, ozaki_slices: int = 0, wait_timeout_s: float = 0.0,
-                    debug_poison_chain: int = 0, record_kernel_time: bool = False, tile_n: int = 0) -> Plan:
+                    debug_poison_chain: int = 0, record_kernel_time: bool = False, tile_n: int = 0,
+                    shard_count: int = 0, shard_index: int = 0) -> Plan:
     """A plan for ``algo`` (an :class:`Algo`, or a :class:`RationalAlgo` through
-    fmm_plan_create_rational) with the given options."""
+    fmm_plan_create_rational) with the given options; ``shard_count`` > 1 makes it compute shard
+    ``shard_index`` of the leaf products only (see fmm_plan_options_t)."""
     h = ctypes.c_void_p()
     a = algo.c_struct()
     opts = fmm_plan_options_t(SCHEDULES[schedule], int(materialize_levels), int(ozaki_slices),
                               float(wait_timeout_s), int(debug_poison_chain), int(bool(record_kernel_time)),
-                              int(tile_n))
+                              int(tile_n), int(shard_count), int(shard_index))
     create = lib().fmm_plan_create_rational if isinstance(algo, RationalAlgo) else lib().fmm_plan_create_ex
     _check(create(ctypes.byref(h), int(n), ctypes.byref(a), int(depth), DTYPES[dtype], ctypes.byref(opts)),
            f"fmm_plan_create(n={n}, {algo}, depth={depth})")
@@ -600,17 +614,25 @@ def fmm_batch_graph_destroy(graph: BatchGraph):
 
 
 class fmm_tune_result_t(ctypes.Structure):
-    _fields_ = [("algo_index", ctypes.c_int), ("depth", ctypes.c_int), ("ms", ctypes.c_double)]
+    _fields_ = [("algo_index", ctypes.c_int), ("depth", ctypes.c_int), ("ms", ctypes.c_double),
+                ("tile_n", ctypes.c_int), ("schedule", ctypes.c_int), ("depth0_ms", ctypes.c_double),
+                ("candidates", ctypes.c_int)]
 
 
-def fmm_autotune(n: int, algos, max_depth: int = 3, min_leaf: int = 64, stream=None):
-    """(best algorithm, depth, ms) for size n among the candidates (the first also gives depth 0)."""
+_SCHEDULE_NAMES = {v: k for k, v in SCHEDULES.items()}
+
+
+def fmm_autotune(n: int, algos, max_depth: int = 3, min_leaf: int = 64, reps: int = 5, stream=None) -> dict:
+    """The fastest configuration for size n: {"algo", "depth", "tile_n", "schedule", "ms", "depth0_ms",
+    "candidates"} ("algo" is one of ``algos``; depth 0 is the classic product)."""
     structs = [a.c_struct() for a in algos]
     ptrs = (ctypes.POINTER(fmm_algo_t) * len(algos))(*[ctypes.pointer(x) for x in structs])
     res = fmm_tune_result_t()
-    _check(lib().fmm_autotune(int(n), ptrs, len(algos), int(max_depth), int(min_leaf),
+    _check(lib().fmm_autotune(int(n), ptrs, len(algos), int(max_depth), int(min_leaf), int(reps),
                               ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(res)), f"fmm_autotune(n={n})")
-    return algos[res.algo_index], res.depth, res.ms
+    return {"algo": algos[res.algo_index], "depth": res.depth, "tile_n": res.tile_n,
+            "schedule": _SCHEDULE_NAMES[res.schedule], "ms": res.ms, "depth0_ms": res.depth0_ms,
+            "candidates": res.candidates}
 
 
 def fmm_sync_status(plan: Plan, stream=None) -> int:

@@ -97,8 +97,8 @@ __device__ void setup_task(Smem<BNT> &S, const F64Problem &pr, const F64Geom &g,
     if (local < g.tasks_core) {
         const int tiles = g.tiles_m * g.tiles_n;
         const long long per_sub = (long long)tiles * g.R_src;
-        const int sub = (int)(local / per_sub);
-        const long long rem = local - (long long)sub * per_sub;
+        const int sub = g.sub_begin + (int)(local / per_sub);
+        const long long rem = local - (long long)(sub - g.sub_begin) * per_sub;
         const int t = (int)(rem / g.R_src);
         const int r = (int)(rem - (long long)t * g.R_src);
         const int ti = t / g.tiles_n, tj = t - ti * g.tiles_n;

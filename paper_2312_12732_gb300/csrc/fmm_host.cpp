@@ -145,6 +145,20 @@ extern "C" const char *fmm_status_string(fmm_status_t s) {
     return "unknown status";
 }
 
+extern "C" fmm_status_t fmm_shard_range(int64_t units, int shard_count, int shard_index, int64_t *begin,
+                                        int64_t *end) {
+    if (units < 0 || shard_count < 1 || shard_index < 0 || shard_index >= shard_count || !begin || !end)
+        return FMM_ERR_INVALID;
+    // floor(k units / count) without overflow for any units below 2^62 and count below 2^31
+    const auto start = [&](int k) {
+        const int64_t q = units / shard_count, r = units % shard_count;
+        return q * k + (r * k) / shard_count;
+    };
+    *begin = start(shard_index);
+    *end = start(shard_index + 1);
+    return FMM_OK;
+}
+
 extern "C" fmm_status_t fmm_algo_builtin(const char *name, fmm_algo_t *out) {
     if (!name || !out) return FMM_ERR_INVALID;
     const std::string s(name);
@@ -315,6 +329,9 @@ struct fmm_plan {
     double timeout_s = 5.0;
     int poison = 0;
     double wscale = 1.0;  // (den_u den_v den_w)^-depth of a rational algorithm, applied with W
+    // product sharding: this plan computes sub-problems [sub_begin, sub_end) of nsub
+    int shard_count = 1;
+    long long sub_begin = 0, sub_end = 0;
     // double complex (FMM_C128, FMM_C128_3M): the FP64 plan the real parts run on, and its planes
     fmm_plan *inner = nullptr;
     double *d_planes = nullptr;
@@ -337,6 +354,7 @@ struct fmm_plan {
         const int *uptr = nullptr, *vptr = nullptr;
         const int4 *uent = nullptr, *vent = nullptr;
         bool with_next = false;  // formed in one pass with the next step (both 2 x 2, at most 8 products)
+        bool unit_u = false, unit_v = false;  // every coefficient of the step's U (V) is +-1
     };
     std::vector<MatStep> mat_steps;
     // emulated leaf (FMM_F64_OZAKI)
@@ -351,8 +369,12 @@ struct fmm_plan {
     const int *d_wl_ptr = nullptr;                      // per C block: products (r, coefficient) in ascending r
     const int2 *d_wl_ent = nullptr;
     double flops_lowp = 0;
-    // host-buffer path
+    // host-buffer path: device copies of the operands, a stream for B's copy and its events
     double *d_hostA = nullptr, *d_hostB = nullptr, *d_hostC = nullptr;
+    cudaStream_t host_copy_stream = nullptr;
+    cudaEvent_t host_ev[2] = {nullptr, nullptr};
+    // set only inside fmm_gemm_host: the event B's copy records; the pre-additions of B wait for it
+    cudaEvent_t b_ready = nullptr;
     // optional timing events: [0] call start, [1] leaf start, [2] leaf end,
     // [3] after counter reset + materialization, [4] call end, [5] after the
     // separate post-additions of the emulated leaf
@@ -480,6 +502,10 @@ void free_plan_memory(fmm_plan *pl) {
     dev_free(pl->d_hostA);
     dev_free(pl->d_hostB);
     dev_free(pl->d_hostC);
+    for (auto &e : pl->host_ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+    if (pl->host_copy_stream) cudaStreamDestroy(pl->host_copy_stream);
+    pl->host_copy_stream = nullptr;
     pl->d_tables = pl->d_ws = nullptr;
     pl->d_hostA = pl->d_hostB = pl->d_hostC = nullptr;
 }
@@ -605,6 +631,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     *out = nullptr;
     if (n < 1 || depth < 0 || depth > 8 || !algo_shape_ok(algo) || den < 1) return FMM_ERR_INVALID;
     if (n > (1LL << 31) / 2) return FMM_ERR_UNSUPPORTED;
+    if (opts && opts->shard_count > 1 && dtype != FMM_F64) return FMM_ERR_UNSUPPORTED;
     if (dtype == FMM_F32) {
         // an emulated-FP64 plan with fewer slices (6 by default: 30 bits for 24-bit operands) and
         // three binary64 planes for A, B and C
@@ -671,6 +698,9 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     }
     if (dtype != FMM_F64 && dtype != FMM_F64_OZAKI) return FMM_ERR_UNSUPPORTED;
     if (den == 1 && fmm_algo_brent_mismatches(algo) != 0) return FMM_ERR_BRENT;
+    const int shards = opts && opts->shard_count > 1 ? opts->shard_count : 1;
+    if (opts && (opts->shard_count < 0 || opts->shard_index < 0 || opts->shard_index >= shards))
+        return FMM_ERR_INVALID;
     // the scale (den^depth)^-1, rounded once; den^depth must be an exact double
     double den_d = 1.0;
     for (int l = 0; l < depth; ++l) {
@@ -712,6 +742,20 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     pl->R_src = ipow(R, depth - mat);
     pl->nsub = ipow(R, mat);
     pl->b_src = pl->P_src * pl->m;
+    // the shard's range of sub-problems (all of them unless sharded)
+    pl->shard_count = shards;
+    if (shards > (long long)pl->nsub) {
+        host_delete(pl);
+        return FMM_ERR_UNSUPPORTED;
+    }
+    {
+        int64_t b = 0, e = 0;
+        fmm_shard_range((int64_t)pl->nsub, shards, shards > 1 ? opts->shard_index : 0, &b, &e);
+        pl->sub_begin = b;
+        pl->sub_end = e;
+    }
+    const long long prod_lo = pl->sub_begin * pl->R_src, prod_hi = pl->sub_end * pl->R_src;
+    const bool with_peel = pl->sub_begin == 0;
     pl->tiles_m = (int)((pl->m + fmm::kBM - 1) / fmm::kBM);
     if (dtype == FMM_F64_OZAKI) {
         pl->bn = fmm::kBN;  // the slice GEMM and its counters use 128 x 128 tiles
@@ -770,20 +814,25 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         csc2(flatten(f.p, f.R, f.V.data(), 1), st_vptr[k], tmp);
         for (const int2 &e : tmp) st_vent[k].push_back(make_int4(e.x / f.p, e.x % f.p, e.y, 0));
     }
+    // W entries of every product; the ordering positions (and each C block's count of contributions)
+    // cover only the shard's products, the others are never read
     w_ptr.assign(wcols.size() + 1, 0);
     for (size_t c = 0; c < wcols.size(); ++c) {
         w_ptr[c + 1] = w_ptr[c] + (int)wcols[c].size();
-        for (const Entry &e : wcols[c]) w_ent.push_back(make_int4(e.blk, e.coef, w_row[e.blk]++, 0));
+        const bool mine = (long long)c >= prod_lo && (long long)c < prod_hi;
+        for (const Entry &e : wcols[c]) w_ent.push_back(make_int4(e.blk, e.coef, mine ? w_row[e.blk]++ : 0, 0));
     }
     // the same nonzeros by C block, products in ascending order (separate post-additions)
     std::vector<int> wl_ptr((size_t)P * P + 1, 0);
     std::vector<int2> wl_ent(w_ent.size());
     for (size_t l = 0; l < (size_t)P * P; ++l) wl_ptr[l + 1] = wl_ptr[l] + w_row[l];
-    for (size_t c = 0; c < wcols.size(); ++c)
+    for (size_t c = 0; c < wcols.size(); ++c) {
+        if ((long long)c < prod_lo || (long long)c >= prod_hi) continue;
         for (int k = w_ptr[c]; k < w_ptr[c + 1]; ++k) {
             const int4 &e = w_ent[k];
             wl_ent[wl_ptr[e.x] + e.z] = make_int2((int)c, e.y);
         }
+    }
 
     // Task counts.
     const long long tiles = (long long)pl->tiles_m * pl->tiles_n;
@@ -797,8 +846,9 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     g.ld_src_b = g.ld_src_a;
     g.sub_stride_a = mat > 0 ? pl->b_src * pl->b_src : 0;
     g.sub_stride_b = g.sub_stride_a;
-    g.tasks_core = tiles * Rt;
-    if (q > 0) {
+    g.sub_begin = (int)pl->sub_begin;
+    g.tasks_core = tiles * (prod_hi - prod_lo);
+    if (q > 0 && with_peel) {
         g.rb_tm = (int)((pl->n_core + fmm::kBM - 1) / fmm::kBM);
         g.rb_tn = (int)((q + pl->bn - 1) / pl->bn);
         g.bb_tm = (int)((q + fmm::kBM - 1) / fmm::kBM);
@@ -811,7 +861,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
 
     // Flop accounting (executed, as scheduled; multiply-add = 2 flops).
     const double md = (double)pl->m;
-    pl->flops_leaf = 2.0 * (double)Rt * md * md * md;
+    pl->flops_leaf = 2.0 * (double)(prod_hi - prod_lo) * md * md * md;
     double adds = 0;
     {
         long long nnz_u = (long long)u_ent.size(), nnz_v = (long long)v_ent.size();
@@ -823,9 +873,14 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             const double bl = (double)(pl->n_core / ipow(p, lev - 1));  // input side of the level
             adds += (double)ipow(R, lev - 1) * steps_cost(steps) * bl * bl;
         }
-        adds += (double)((long long)w_ent.size() - (long long)P * P) * md * md;
+        long long w_nnz = 0, blocks_hit = 0;  // the shard's post-additions: all but each block's first term
+        for (int c : w_row) {
+            w_nnz += c;
+            blocks_hit += c > 0;
+        }
+        adds += (double)(w_nnz - blocks_hit) * md * md;
     }
-    const double qd = (double)q, ncd = (double)pl->n_core, nd = (double)n;
+    const double qd = with_peel ? (double)q : 0.0, ncd = (double)pl->n_core, nd = (double)n;
     const double peel = 2.0 * (ncd * qd * nd + qd * nd * nd + ncd * ncd * qd);
     pl->flops_exec = (dtype == FMM_F64_OZAKI ? 0.0 : pl->flops_leaf) + adds + peel;
 
@@ -891,6 +946,8 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             ms.uent = (const int4 *)(base + o_st[4 * k + 1]);
             ms.vptr = (const int *)(base + o_st[4 * k + 2]);
             ms.vent = (const int4 *)(base + o_st[4 * k + 3]);
+            ms.unit_u = std::all_of(st_uent[k].begin(), st_uent[k].end(), [](const int4 &e) { return e.z == 1 || e.z == -1; });
+            ms.unit_v = std::all_of(st_vent[k].begin(), st_vent[k].end(), [](const int4 &e) { return e.z == 1 || e.z == -1; });
             pl->mat_steps.push_back(ms);
         }
     for (size_t k = 0; k + 1 < pl->mat_steps.size(); ++k) {
@@ -1084,6 +1141,8 @@ fmm_status_t prepare(const fmm_plan *pl, const double *A, const double *B, cudaS
     int G = 0;
     for (int k = 0; k < K; ++k) G += pl->mat_steps[k].with_next ? 0 : 1;
     for (int side = 0; side < 2; ++side) {
+        // the host-buffer path copies B on its own stream while A's passes run
+        if (side == 1 && pl->b_ready && cudaStreamWaitEvent(st, pl->b_ready, 0) != cudaSuccess) return FMM_ERR_CUDA;
         const double *src = side == 0 ? A : B;
         double *fin = side == 0 ? pl->d_SA : pl->d_SB;
         double *tmp = side == 0 ? pl->d_TA : pl->d_TB;
@@ -1100,15 +1159,17 @@ fmm_status_t prepare(const fmm_plan *pl, const double *A, const double *B, cudaS
                 e = fmm::launch_materialize_two_steps(src, ld_in, in_stride, (int)n_in, b_out, ms.R,
                                                       side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent,
                                                       m2.R, side == 0 ? m2.uptr : m2.vptr,
-                                                      side == 0 ? m2.uent : m2.vent, dst, st);
+                                                      side == 0 ? m2.uent : m2.vent,
+                                                      side == 0 ? (ms.unit_u && m2.unit_u) : (ms.unit_v && m2.unit_v),
+                                                      dst, st);
                 n_in *= (long long)ms.R * m2.R;
                 b_in = b_out;
                 ++k;
             } else {
                 const long long b_out = b_in / ms.p;
                 e = fmm::launch_materialize_level(src, ld_in, in_stride, (int)n_in, b_out, ms.p, ms.R,
-                                                  side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent, dst,
-                                                  st);
+                                                  side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent,
+                                                  side == 0 ? ms.unit_u : ms.unit_v, dst, st);
                 n_in *= ms.R;
                 b_in = b_out;
             }
@@ -1283,9 +1344,13 @@ extern "C" fmm_status_t fmm_gemm_ex(const fmm_plan_t *pl, double alpha, const do
     cudaStream_t st = (cudaStream_t)stream;
     const long long doubles = pl->n * pl->n * (pl->inner ? 2 : 1);
     if (pl->inner && ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15) != 0) return FMM_ERR_INVALID;
+    if (pl->shard_count > 1 && beta != 0.0) return FMM_ERR_UNSUPPORTED;
     if (alpha == 0.0) return cuda_status(fmm::launch_scale_c(C, doubles, beta, st));  // A, B unread
     if (pl->inner) return gemm_complex(pl, alpha, A, B, beta, C, st);
     if (pl->ev[0] && cudaEventRecord(pl->ev[0], st) != cudaSuccess) return FMM_ERR_CUDA;
+    // a shard writes only the C blocks its products reach: the rest of its partial C is zero
+    if (pl->shard_count > 1 && cudaMemsetAsync(C, 0, (size_t)doubles * sizeof(double), st) != cudaSuccess)
+        return FMM_ERR_CUDA;
     fmm_status_t s = prepare(pl, A, B, st);
     if (s != FMM_OK) return s;
     if (pl->ev[3] && cudaEventRecord(pl->ev[3], st) != cudaSuccess) return FMM_ERR_CUDA;
@@ -1369,25 +1434,55 @@ extern "C" fmm_status_t fmm_gemm_host(fmm_plan_t *pl, const double *hA, const do
     const size_t elem = pl->dtype == FMM_F32 ? sizeof(float) : sizeof(double) * (pl->inner ? 2 : 1);
     const size_t bytes = (size_t)pl->n * (size_t)pl->n * elem;
     if (!pl->d_hostA) {
-        if (cudaMalloc(&pl->d_hostA, bytes) != cudaSuccess || cudaMalloc(&pl->d_hostB, bytes) != cudaSuccess ||
-            cudaMalloc(&pl->d_hostC, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            if (pl->d_hostA) cudaFree(pl->d_hostA);
-            if (pl->d_hostB) cudaFree(pl->d_hostB);
-            if (pl->d_hostC) cudaFree(pl->d_hostC);
+        if (dev_alloc(&pl->d_hostA, bytes) != cudaSuccess || dev_alloc(&pl->d_hostB, bytes) != cudaSuccess ||
+            dev_alloc(&pl->d_hostC, bytes) != cudaSuccess) {
+            dev_free(pl->d_hostA);
+            dev_free(pl->d_hostB);
+            dev_free(pl->d_hostC);
             pl->d_hostA = pl->d_hostB = pl->d_hostC = nullptr;
             return FMM_ERR_OOM;
         }
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(pl->d_hostA, hA, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FMM_ERR_CUDA;
-    if (cudaMemcpyAsync(pl->d_hostB, hB, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FMM_ERR_CUDA;
-    fmm_status_t s = pl->dtype == FMM_F32
-                         ? fmm_gemm_f32_ex(pl, 1.0f, reinterpret_cast<const float *>(pl->d_hostA),
-                                           reinterpret_cast<const float *>(pl->d_hostB),
-                                           0.0f, reinterpret_cast<float *>(pl->d_hostC), stream)
-                         : fmm_gemm(pl, pl->d_hostA, pl->d_hostB, pl->d_hostC, stream);
-    if (s != FMM_OK) return s;
+    const bool overlap = pl->dtype == FMM_F64 || pl->dtype == FMM_F64_OZAKI;
+    if (overlap && !pl->host_copy_stream) {
+        if (cudaStreamCreateWithFlags(&pl->host_copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->host_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->host_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return FMM_ERR_CUDA;
+        }
+    }
+    fmm_status_t s = FMM_OK;
+    if (overlap) {
+        // A on the call's stream; B on the plan's copy stream once the work already queued on `stream`
+        // is done, so that (for page-locked sources, whose copies return at once) A's pre-addition
+        // passes run while B is still in flight; B's own passes wait for its copy
+        cudaStream_t cs = pl->host_copy_stream;
+        if (cudaEventRecord(pl->host_ev[0], st) != cudaSuccess || cudaStreamWaitEvent(cs, pl->host_ev[0], 0) != cudaSuccess ||
+            cudaMemcpyAsync(pl->d_hostA, hA, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(pl->d_hostB, hB, bytes, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+            cudaEventRecord(pl->host_ev[1], cs) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        pl->b_ready = pl->host_ev[1];
+        s = fmm_gemm(pl, pl->d_hostA, pl->d_hostB, pl->d_hostC, stream);
+        pl->b_ready = nullptr;
+        // a launch that failed before B's passes leaves the copy unwaited: order it before C's copy
+        if (s != FMM_OK) {
+            cudaStreamWaitEvent(st, pl->host_ev[1], 0);
+            cudaStreamSynchronize(st);
+            return s;
+        }
+    } else {
+        if (cudaMemcpyAsync(pl->d_hostA, hA, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FMM_ERR_CUDA;
+        if (cudaMemcpyAsync(pl->d_hostB, hB, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return FMM_ERR_CUDA;
+        s = pl->dtype == FMM_F32
+                ? fmm_gemm_f32_ex(pl, 1.0f, reinterpret_cast<const float *>(pl->d_hostA),
+                                  reinterpret_cast<const float *>(pl->d_hostB), 0.0f,
+                                  reinterpret_cast<float *>(pl->d_hostC), stream)
+                : fmm_gemm(pl, pl->d_hostA, pl->d_hostB, pl->d_hostC, stream);
+        if (s != FMM_OK) return s;
+    }
     if (cudaMemcpyAsync(hC, pl->d_hostC, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return FMM_ERR_CUDA;
     return cuda_status(cudaStreamSynchronize(st));
 }
@@ -1403,7 +1498,8 @@ extern "C" fmm_status_t fmm_gemm_batched_ex(fmm_plan_t *const *plans, const doub
     if (count < 0 || (count > 0 && (!plans || !A || !B || !C))) return FMM_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     for (int i = 0; i < count; ++i) {
-        if (!plans[i] || !A[i] || !B[i] || !C[i] || plans[i]->dtype != FMM_F64) return FMM_ERR_INVALID;
+        if (!plans[i] || !A[i] || !B[i] || !C[i] || plans[i]->dtype != FMM_F64 || plans[i]->shard_count > 1)
+            return FMM_ERR_INVALID;
         if ((alpha && !std::isfinite(alpha[i])) || (beta && !std::isfinite(beta[i]))) return FMM_ERR_INVALID;
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return FMM_ERR_INVALID;  // a plan's counters serve one product
@@ -1540,8 +1636,10 @@ __global__ void fill_kernel(double *x, long long count, unsigned long long seed)
 }  // namespace
 
 extern "C" fmm_status_t fmm_autotune(int64_t n, const fmm_algo_t *const *algos, int nalgos, int max_depth,
-                                     int64_t min_leaf, void *stream, fmm_tune_result_t *best) {
+                                     int64_t min_leaf, int reps, void *stream, fmm_tune_result_t *best) {
     if (n < 1 || !algos || nalgos < 1 || max_depth < 0 || !best || min_leaf < 1) return FMM_ERR_INVALID;
+    if (reps < 1) reps = 5;
+    if (reps > 64) reps = 64;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
     double *A = nullptr, *B = nullptr, *C = nullptr;
@@ -1557,34 +1655,71 @@ extern "C" fmm_status_t fmm_autotune(int64_t n, const fmm_algo_t *const *algos, 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    fmm_status_t result = FMM_ERR_INVALID;
-    best->ms = 1e30;
+    // the candidate list: (algorithm, depth, tile width, schedule); depth 0 once
+    struct Cand { int ai, depth, tile; fmm_schedule_t sched; };
+    std::vector<Cand> cands;
+    const fmm_algo_t *first = nullptr;
+    for (int ai = 0; ai < nalgos && !first; ++ai)
+        if (algos[ai]) first = algos[ai];
+    for (int tile : {64, 128}) cands.push_back({0, 0, tile, FMM_SCHED_AUTO});
     for (int ai = 0; ai < nalgos; ++ai) {
-        if (!algos[ai]) continue;
-        for (int d = (ai == 0 ? 0 : 1); d <= max_depth; ++d) {
+        if (!algo_shape_ok(algos[ai])) continue;
+        for (int d = 1; d <= max_depth; ++d) {
             long long P = 1;
             for (int k = 0; k < d; ++k) P *= algos[ai]->p;
-            if (d > 0 && n / P < min_leaf) break;
-            fmm_plan_t *pl = nullptr;
-            if (fmm_plan_create(&pl, n, algos[ai], d, FMM_F64) != FMM_OK) continue;
-            float ms = 0.f, best_run = 1e30f;
-            bool ok = fmm_gemm(pl, A, B, C, st) == FMM_OK;  // warm-up
-            for (int rep = 0; rep < 2 && ok; ++rep) {
-                cudaEventRecord(e0, st);
-                ok = fmm_gemm(pl, A, B, C, st) == FMM_OK;
-                cudaEventRecord(e1, st);
-                if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
-                    best_run = ms < best_run ? ms : best_run;
-                else
-                    ok = false;
+            if (n / P < min_leaf) break;
+            const bool both = d == 1 && default_materialized_levels(algos[ai]->p, algos[ai]->R, algos[ai], 1) > 0;
+            for (int tile : {64, 128}) {
+                cands.push_back({ai, d, tile, FMM_SCHED_AUTO});
+                if (both) cands.push_back({ai, d, tile, FMM_SCHED_FUSED});
             }
-            if (ok && fmm_sync_status(pl, stream) == FMM_OK && best_run < best->ms) {
-                best->ms = best_run;
-                best->algo_index = ai;
-                best->depth = d;
-                result = FMM_OK;
+        }
+    }
+    fmm_status_t result = FMM_ERR_INVALID;
+    best->ms = 1e30;
+    best->depth0_ms = 1e30;
+    best->candidates = 0;
+    for (const Cand &c : cands) {
+        const fmm_algo_t *al = c.depth == 0 ? first : algos[c.ai];
+        if (!al) continue;
+        fmm_plan_options_t o{};
+        o.schedule = c.sched;
+        o.tile_n = c.tile;
+        fmm_plan_t *pl = nullptr;
+        const fmm_status_t cs = fmm_plan_create_ex(&pl, n, al, c.depth, FMM_F64, &o);
+        if (cs == FMM_ERR_OOM) {
+            result = FMM_ERR_OOM;
+            break;
+        }
+        if (cs != FMM_OK) continue;
+        std::vector<float> runs;
+        bool ok = fmm_gemm(pl, A, B, C, st) == FMM_OK;  // warm-up
+        for (int rep = 0; rep < reps && ok; ++rep) {
+            float ms = 0.f;
+            cudaEventRecord(e0, st);
+            ok = fmm_gemm(pl, A, B, C, st) == FMM_OK;
+            cudaEventRecord(e1, st);
+            if (!(ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)) {
+                ok = false;
+                break;
             }
-            fmm_plan_destroy(pl);
+            runs.push_back(ms);
+            if (rep == 0 && best->ms < 1e29 && ms > 1.5 * best->ms) break;  // clearly slower: pruned
+        }
+        ok = ok && fmm_sync_status(pl, stream) == FMM_OK;
+        fmm_plan_destroy(pl);
+        if (!ok || runs.empty()) continue;
+        std::sort(runs.begin(), runs.end());
+        const double med = runs[runs.size() / 2];
+        ++best->candidates;
+        if (c.depth == 0 && med < best->depth0_ms) best->depth0_ms = med;
+        if (med < best->ms) {
+            best->ms = med;
+            best->algo_index = c.ai;
+            best->depth = c.depth;
+            best->tile_n = c.tile;
+            best->schedule = c.sched;
+            result = FMM_OK;
         }
     }
     cudaEventDestroy(e0);
@@ -1646,6 +1781,8 @@ extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t 
     info->tile_n = pl->bn;
     info->flops_lowp = pl->flops_lowp;
     info->coef_scale = pl->wscale;
+    info->product_begin = pl->sub_begin * pl->R_src;
+    info->product_end = pl->sub_end * pl->R_src;
     info->materialize_passes = 0;
     for (const fmm_plan::MatStep &ms : pl->mat_steps) info->materialize_passes += ms.with_next ? 0 : 1;
     return FMM_OK;

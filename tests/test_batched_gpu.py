@@ -72,13 +72,56 @@ def test_batched_rejects_repeated_plan(fmm):
         fmm.fmm_gemm_batched([p, p], [A, A], [A, A], [A.clone(), A.clone()])
 
 
-def test_autotuner_picks_a_valid_choice(fmm):
+def median_ms(fmm, plan, n, reps=5):
+    A = torch.rand(n, n, dtype=torch.float64, device="cuda")
+    B = torch.rand(n, n, dtype=torch.float64, device="cuda")
+    C = torch.empty_like(A)
+    fmm.fmm_gemm(plan, A, B, C)
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fmm.fmm_gemm(plan, A, B, C)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    assert fmm.fmm_sync_status(plan) == 0
+    return sorted(times)[reps // 2]
+
+
+@pytest.mark.parametrize("n", [1024, 2896])
+def test_autotuner_pick_is_no_slower_than_the_classic_product(fmm, n):
+    """The tuner searches algorithm, depth, tile width and schedule; re-timed independently (median of 5),
+    its pick is no slower than the best depth-0 configuration at the same size."""
+    algos = [fmm.fmm_algo_builtin("strassen"), fmm.fmm_algo_builtin("winograd")]
+    r = fmm.fmm_autotune(n, algos, max_depth=3, min_leaf=128)
+    assert r["algo"].name in ("strassen", "winograd") and 0 <= r["depth"] <= 3
+    assert r["tile_n"] in (64, 128) and r["schedule"] in ("auto", "fused")
+    assert r["candidates"] >= 2 + 2 * 4  # depth 0 at both tiles, and both algorithms at depth 1 (x2 x2)
+    assert r["ms"] <= r["depth0_ms"]
+    pick = fmm.fmm_plan_create(n, r["algo"], r["depth"], schedule=r["schedule"], tile_n=r["tile_n"])
+    t_pick = median_ms(fmm, pick, n)
+    t_classic = min(median_ms(fmm, fmm.fmm_plan_create(n, algos[0], 0, tile_n=t), n) for t in (64, 128))
+    assert t_pick <= 1.05 * t_classic, (r, t_pick, t_classic)
+
+
+def test_autotune_choice_is_cached_in_memory_and_on_disk(fmm, monkeypatch, tmp_path):
     from paper_2312_12732_gb300 import autotune
 
-    algos = [fmm.fmm_algo_builtin("strassen"), fmm.fmm_algo_builtin("winograd")]
-    algo, depth, ms = fmm.fmm_autotune(1024, algos, max_depth=3, min_leaf=128)
-    assert algo.name in ("strassen", "winograd") and 0 <= depth <= 3 and ms > 0
-    name, d, ms2 = autotune.choose(300)
-    assert name in ("strassen", "winograd") and 0 <= d <= 1
-    plans, picks = autotune.plan_batch([150, 300, 2000])
-    assert len(plans) == 3 and all(p.depth == k[1] for p, k in zip(plans, picks))
+    autotune._memo.clear()
+    path = str(tmp_path / "tune.json")
+    first = autotune.choose(300, cache_path=path)
+    assert first["algo"] in ("strassen", "winograd") and 0 <= first["depth"] <= 1
+    count = autotune.tuned_count
+    again = autotune.choose(310, cache_path=path)  # same half-octave bucket: from memory
+    assert autotune.tuned_count == count and again == first
+
+    def must_not_tune(*a, **k):
+        raise AssertionError("a cached choice was tuned again")
+
+    autotune._memo.clear()
+    monkeypatch.setattr(autotune.B, "fmm_autotune", must_not_tune)
+    from_disk = autotune.choose(300, cache_path=path)  # a fresh memo reads the file
+    assert from_disk == first
+    plans, picks = autotune.plan_batch([300, 305], cache_path=path)
+    assert all(p.info()["tile_n"] == first["tile_n"] and p.depth == first["depth"] for p in plans)
