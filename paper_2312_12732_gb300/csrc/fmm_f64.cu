@@ -424,15 +424,21 @@ __global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __gri
             const bool first = dst.pos == 0;
             const int cf = dst.coef;
             const double alpha = S.alpha, beta = S.beta;
-            // With alpha = 1 the coefficient stays an integer test (+-1: add or
-            // subtract); otherwise every term is fma(alpha * cf, v, o).  The
-            // first contribution reads C only for beta != 0 and scales it by beta.
-            const int unit = alpha == 1.0 ? cf : 0;
-            const double cfd = alpha * (double)cf;  // used only when unit is not +-1
+            // Every read-modify-write term is one fma(w, v, o) with w = alpha * cf:
+            // for w = +-1 it rounds exactly like o + v or o - v, so a single
+            // FP64 operation per element replaces a per-mode choice (a mode
+            // tested per element would let the compiler issue the add, the
+            // subtract and the fma alike, on the FP64 pipe the leaf products
+            // need).  The first contribution with beta = 0 stores w * v, a
+            // sign flip (integer XOR) for w = +-1; it reads C only for
+            // beta != 0 and scales it by beta.
+            const double w = alpha * (double)cf;
+            const bool unit = w == 1.0 || w == -1.0;
+            const unsigned long long wsign = w < 0.0 ? 0x8000000000000000ull : 0ull;
             const bool load = !first || beta != 0.0;
             const bool scale_old = first && beta != 1.0;
-            // mode: 0 store v, 1 store -v, 2 store cfd*v, 3 add, 4 subtract, 5 fma
-            const int mode = load ? (unit == 1 ? 3 : (unit == -1 ? 4 : 5)) : (unit == 1 ? 0 : (unit == -1 ? 1 : 2));
+            // mode: 0 store v with w's sign, 2 store w * v, 5 fma(w, v, o)
+            const int mode = load ? 5 : (unit ? 0 : 2);
             // Column pairs (2 t4, 2 t4 + 1) are 16 bytes apart-aligned when the tile
             // start and ldc are even.  Read-modify-writes load a whole subtile row
             // (16 values) before the first store, so the loads overlap instead of
@@ -441,7 +447,7 @@ __global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __gri
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 double o[4][2][2];
-                if (mode >= 3) {
+                if (load) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -482,14 +488,12 @@ __global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __gri
 #pragma unroll
                         for (int c2 = 0; c2 < 2; ++c2) {
                             const double v = acc[i][j][2 * h + c2];
-                            switch (mode) {
-                                case 0: out[c2] = v; break;
-                                case 1: out[c2] = neg(v); break;
-                                case 2: out[c2] = cfd * v; break;
-                                case 3: out[c2] = o[j][h][c2] + v; break;
-                                case 4: out[c2] = o[j][h][c2] - v; break;
-                                default: out[c2] = fma(cfd, v, o[j][h][c2]); break;
-                            }
+                            if (mode == 5)
+                                out[c2] = fma(w, v, o[j][h][c2]);
+                            else if (mode == 0)
+                                out[c2] = __longlong_as_double(__double_as_longlong(v) ^ (long long)wsign);
+                            else
+                                out[c2] = w * v;
                         }
                         if (pair_ok && col + 1 < cols) {
                             *reinterpret_cast<double2 *>(p) = make_double2(out[0], out[1]);

@@ -354,7 +354,6 @@ struct fmm_plan {
         const int *uptr = nullptr, *vptr = nullptr;
         const int4 *uent = nullptr, *vent = nullptr;
         bool with_next = false;  // formed in one pass with the next step (both 2 x 2, at most 8 products)
-        bool unit_u = false, unit_v = false;  // every coefficient of the step's U (V) is +-1
     };
     std::vector<MatStep> mat_steps;
     // emulated leaf (FMM_F64_OZAKI)
@@ -946,8 +945,6 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             ms.uent = (const int4 *)(base + o_st[4 * k + 1]);
             ms.vptr = (const int *)(base + o_st[4 * k + 2]);
             ms.vent = (const int4 *)(base + o_st[4 * k + 3]);
-            ms.unit_u = std::all_of(st_uent[k].begin(), st_uent[k].end(), [](const int4 &e) { return e.z == 1 || e.z == -1; });
-            ms.unit_v = std::all_of(st_vent[k].begin(), st_vent[k].end(), [](const int4 &e) { return e.z == 1 || e.z == -1; });
             pl->mat_steps.push_back(ms);
         }
     for (size_t k = 0; k + 1 < pl->mat_steps.size(); ++k) {
@@ -1159,17 +1156,15 @@ fmm_status_t prepare(const fmm_plan *pl, const double *A, const double *B, cudaS
                 e = fmm::launch_materialize_two_steps(src, ld_in, in_stride, (int)n_in, b_out, ms.R,
                                                       side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent,
                                                       m2.R, side == 0 ? m2.uptr : m2.vptr,
-                                                      side == 0 ? m2.uent : m2.vent,
-                                                      side == 0 ? (ms.unit_u && m2.unit_u) : (ms.unit_v && m2.unit_v),
-                                                      dst, st);
+                                                      side == 0 ? m2.uent : m2.vent, dst, st);
                 n_in *= (long long)ms.R * m2.R;
                 b_in = b_out;
                 ++k;
             } else {
                 const long long b_out = b_in / ms.p;
                 e = fmm::launch_materialize_level(src, ld_in, in_stride, (int)n_in, b_out, ms.p, ms.R,
-                                                  side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent,
-                                                  side == 0 ? ms.unit_u : ms.unit_v, dst, st);
+                                                  side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent, dst,
+                                                  st);
                 n_in *= ms.R;
                 b_in = b_out;
             }

@@ -14,15 +14,8 @@ namespace {
 
 using dev::neg;
 
-// s (+)= c * v.  UNIT (every coefficient of the table is +-1): the first
-// term is v or its sign flip (an integer XOR) and every later one a single
-// fma(+-1, v, s), which rounds exactly like s + v or s - v; a coefficient
-// tested per term would make the compiler issue the add, the subtract and
-// the fma of each term, three FP64 operations where one suffices.
-// Otherwise the general form (a multiply or fma for |c| > 1).
-template <bool UNIT>
+// s (+)= c * v with the fewest FP64 operations: +-1 coefficients are adds.
 __device__ __forceinline__ double combine(double s, double v, int c, bool first) {
-    if (UNIT) return first ? (c < 0 ? neg(v) : v) : fma((double)c, v, s);
     if (first) return c == 1 ? v : (c == -1 ? neg(v) : (double)c * v);
     return c == 1 ? s + v : (c == -1 ? s - v : fma((double)c, v, s));
 }
@@ -31,7 +24,6 @@ __device__ __forceinline__ double combine(double s, double v, int c, bool first)
 // CTAs stride over rows y of the b x b output blocks and threads over
 // columns x, so every load and store is coalesced and no index needs a
 // division.  All R outputs of a position are formed from the p^2 inputs.
-template <bool UNIT>
 __global__ void materialize_level_kernel(const double *__restrict__ in, long long ld_in, long long in_stride,
                                          long long b, int p, int R, const int *__restrict__ ptr,
                                          const int4 *__restrict__ ent, double *__restrict__ out) {
@@ -48,7 +40,7 @@ __global__ void materialize_level_kernel(const double *__restrict__ in, long lon
                 for (int k = e0; k < e1; ++k) {
                     const int4 en = ent[k];  // {block row, block col, coefficient, 0}
                     const double v = __ldg(pos + (long long)en.x * b * ld_in + (long long)en.y * b);
-                    acc = combine<UNIT>(acc, v, en.z, k == e0);
+                    acc = combine(acc, v, en.z, k == e0);
                 }
                 dst[(long long)s * total + y * b + x] = acc;
             }
@@ -64,7 +56,6 @@ __global__ void materialize_level_kernel(const double *__restrict__ in, long lon
 // two separate steps, so the results are identical; the first step's output
 // never reaches HBM.  Entries: {block row, block col, coefficient, 0}.
 constexpr int kPairStepMaxR = 8;
-template <bool UNIT>
 __global__ void materialize_two_steps_kernel(const double *__restrict__ in, long long ld_in, long long in_stride,
                                              long long b2, int R1, const int *__restrict__ ptr1,
                                              const int4 *__restrict__ ent1, int R2, const int *__restrict__ ptr2,
@@ -97,7 +88,7 @@ __global__ void materialize_two_steps_kernel(const double *__restrict__ in, long
                         // selects, not a pointer, keep v in registers
                         const double w = en.x == 0 ? (en.y == 0 ? v[0][0][q] : v[0][1][q])
                                                    : (en.y == 0 ? v[1][0][q] : v[1][1][q]);
-                        t[q] = combine<UNIT>(t[q], w, en.z, k == e0);
+                        t[q] = combine(t[q], w, en.z, k == e0);
                     }
                 }
                 double *o = dst + (long long)r1 * R2 * total + y * b2 + x;
@@ -108,7 +99,7 @@ __global__ void materialize_two_steps_kernel(const double *__restrict__ in, long
                         const int4 en = ent2[k];
                         const int q = 2 * en.x + en.y;
                         const double w = q == 0 ? t[0] : (q == 1 ? t[1] : (q == 2 ? t[2] : t[3]));
-                        acc = combine<UNIT>(acc, w, en.z, k == f0);
+                        acc = combine(acc, w, en.z, k == f0);
                     }
                     o[(long long)r2 * total] = acc;
                 }
@@ -120,8 +111,8 @@ __global__ void materialize_two_steps_kernel(const double *__restrict__ in, long
 }  // namespace
 
 cudaError_t launch_materialize_level(const double *in, long long ld_in, long long in_stride, int n_in,
-                                     long long b_out, int p, int R, const int *ptr, const int4 *ent, bool unit,
-                                     double *out, cudaStream_t s) {
+                                     long long b_out, int p, int R, const int *ptr, const int4 *ent, double *out,
+                                     cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -132,13 +123,8 @@ cudaError_t launch_materialize_level(const double *in, long long ld_in, long lon
     for (int c0 = 0; c0 < n_in; c0 += 65535) {
         const int cnt = n_in - c0 < 65535 ? n_in - c0 : 65535;
         dim3 grid((unsigned)bx, (unsigned)cnt);
-        double *o = out + (long long)c0 * R * b_out * b_out;
-        if (unit)
-            materialize_level_kernel<true><<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride,
-                                                                    b_out, p, R, ptr, ent, o);
-        else
-            materialize_level_kernel<false><<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride,
-                                                                     b_out, p, R, ptr, ent, o);
+        materialize_level_kernel<<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride, b_out, p,
+                                                          R, ptr, ent, out + (long long)c0 * R * b_out * b_out);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -147,7 +133,7 @@ cudaError_t launch_materialize_level(const double *in, long long ld_in, long lon
 
 cudaError_t launch_materialize_two_steps(const double *in, long long ld_in, long long in_stride, int n_in,
                                          long long b2, int R1, const int *ptr1, const int4 *ent1, int R2,
-                                         const int *ptr2, const int4 *ent2, bool unit, double *out, cudaStream_t s) {
+                                         const int *ptr2, const int4 *ent2, double *out, cudaStream_t s) {
     if (R1 > kPairStepMaxR || R2 > kPairStepMaxR) return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -159,13 +145,9 @@ cudaError_t launch_materialize_two_steps(const double *in, long long ld_in, long
     for (int c0 = 0; c0 < n_in; c0 += 65535) {
         const int cnt = n_in - c0 < 65535 ? n_in - c0 : 65535;
         dim3 grid((unsigned)bx, (unsigned)cnt);
-        double *o = out + (long long)c0 * R1 * R2 * b2 * b2;
-        if (unit)
-            materialize_two_steps_kernel<true><<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride,
-                                                                        b2, R1, ptr1, ent1, R2, ptr2, ent2, o);
-        else
-            materialize_two_steps_kernel<false><<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in,
-                                                                         in_stride, b2, R1, ptr1, ent1, R2, ptr2, ent2, o);
+        materialize_two_steps_kernel<<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride, b2, R1,
+                                                              ptr1, ent1, R2, ptr2, ent2,
+                                                              out + (long long)c0 * R1 * R2 * b2 * b2);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
