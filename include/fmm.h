@@ -56,7 +56,9 @@ typedef enum {
 typedef enum {
     FMM_F64 = 0,       /* binary64 operands, FP64 tensor-core (DMMA) leaf products */
     FMM_F64_OZAKI = 1, /* binary64 operands; S_r/T_r formed in FP64, leaf products emulated from
-                          e4m3 slices (Ozaki scheme) on the tensor cores, post-additions in FP64 */
+                          e4m3 slices (Ozaki scheme) on the tensor cores, post-additions in FP64.
+                          Read at plan creation: FMM_OZAKI_ENGINE=tc1 or mma_sync selects the
+                          one-CTA tcgen05 or the mma.sync slice GEMM instead of CTA pairs */
     /* Double complex (Section 1 lists double complex among the types the
      * algorithms deploy to): A, B, C are n x n row-major arrays of interleaved
      * (re, im) binary64 pairs, 16-byte aligned, so each pointer addresses 2 n^2
