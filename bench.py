@@ -415,7 +415,7 @@ def run_sweep(a):
         for d in (1, 2, 3):
             configs += [(algo, d, "fused", 0), (algo, d, "auto", 0)]
     configs += [("strassen^2", 1, "fused", 0), ("strassen^2", 1, "auto", 0), ("strassen^2", 2, "auto", 0),
-                ("strassen", 4, "auto", 0)]
+                ("strassen", 4, "auto", 0), ("strassen", 5, "auto", 0)]
     configs = [c + ("f64",) for c in configs]
     configs += [("strassen", d, "auto", 0, "f64_ozaki") for d in (0, 1, 2, 3)]
     if a.n >= 16384:
