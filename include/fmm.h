@@ -30,6 +30,17 @@
  *   - the library never takes ownership of caller memory;
  *   - every function returns an fmm_status_t; on error no GPU work was
  *     enqueued unless the error is FMM_ERR_CUDA from a launch.
+ *
+ * Environment variables (none is needed; each is read when it applies):
+ *   FMM_LOG          1: one line on stderr per plan created or rejected (size,
+ *                    algorithm shape, depth, dtype, leaf size, product range,
+ *                    materialized levels, tile, tasks, workspace, or the
+ *                    reason of the rejection); 2: also one line per
+ *                    multiplication enqueued.  Read at every call.
+ *   FMM_TILE_N       64 or 128: the FP64 leaf tile width when a plan does not
+ *                    set one (read at plan creation).
+ *   FMM_OZAKI_ENGINE see FMM_F64_OZAKI (read at plan creation).
+ *   FMM_FORCE_DEPTH  d: fmm_autotune times only depth-d candidates.
  */
 #ifndef FMM_H_
 #define FMM_H_
@@ -389,6 +400,8 @@ void fmm_batch_graph_destroy(fmm_batch_graph_t *g);
  *   - for each of those, both leaf tile widths (tile_n 64 and 128) and, at
  *     depth 1 when the planner would materialize it, both the default
  *     (materialized) and the fused schedule.
+ * With FMM_FORCE_DEPTH=d set, only the depth-d candidates are timed
+ * (depth0_ms is then 1e30 unless d = 0); FMM_ERR_INVALID if none qualifies.
  * Each candidate runs once untimed, then up to `reps` timed runs (CUDA events
  * on `stream`; reps < 1 means 5); its time is the median.  A candidate whose
  * first timed run is more than 1.5 times the best median so far stops there.

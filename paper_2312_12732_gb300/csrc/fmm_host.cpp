@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -1097,9 +1098,52 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
 
 }  // namespace
 
+namespace {
+
+// FMM_LOG: 0 (default) silent; 1 one line per plan created or rejected; 2 also one line per multiplication
+// enqueued.  Read on every use, so a process can change it between calls.
+int log_level() {
+    const char *e = std::getenv("FMM_LOG");
+    return e ? std::atoi(e) : 0;
+}
+
+const char *dtype_name(fmm_dtype_t d) {
+    switch (d) {
+        case FMM_F64: return "f64";
+        case FMM_F64_OZAKI: return "f64_ozaki";
+        case FMM_C128: return "c128";
+        case FMM_C128_3M: return "c128_3m";
+        case FMM_F32: return "f32";
+    }
+    return "?";
+}
+
+fmm_status_t log_plan(const char *what, fmm_status_t st, const fmm_plan_t *pl, int64_t n, const fmm_algo_t *algo,
+                      int depth, fmm_dtype_t dtype) {
+    if (log_level() < 1) return st;
+    if (st != FMM_OK) {
+        std::fprintf(stderr, "fmm: %s rejected n=%lld p=%d R=%d depth=%d dtype=%s: %s\n", what, (long long)n,
+                     algo ? algo->p : 0, algo ? algo->R : 0, depth, dtype_name(dtype), fmm_status_string(st));
+        return st;
+    }
+    fmm_plan_info_t in{};
+    fmm_plan_get_info(pl, &in);
+    std::fprintf(stderr,
+                 "fmm: %s n=%lld p=%d R=%d depth=%d dtype=%s leaf=%lld products=%lld..%lld materialized=%d "
+                 "passes=%d tile_n=%d tasks=%lld slices=%d workspace=%.1f MB\n",
+                 what, (long long)n, in.p, algo->R, depth, dtype_name(dtype), (long long)in.m,
+                 (long long)in.product_begin, (long long)in.product_end, in.materialized_levels,
+                 in.materialize_passes, in.tile_n, (long long)in.tasks, in.ozaki_slices,
+                 (double)in.workspace_bytes / 1048576.0);
+    return st;
+}
+
+}  // namespace
+
 extern "C" fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
                                            fmm_dtype_t dtype, const fmm_plan_options_t *opts) {
-    return plan_create(out, n, algo, depth, dtype, opts, 1);
+    const fmm_status_t st = plan_create(out, n, algo, depth, dtype, opts, 1);
+    return log_plan("fmm_plan_create", st, st == FMM_OK ? *out : nullptr, n, algo, depth, dtype);
 }
 
 extern "C" fmm_status_t fmm_plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, int depth,
@@ -1112,10 +1156,15 @@ extern "C" fmm_status_t fmm_plan_create_rational(fmm_plan_t **out, int64_t n, co
     if (!out) return FMM_ERR_INVALID;
     *out = nullptr;
     const int64_t bad = fmm_algo_rational_brent_mismatches(algo);
-    if (bad < 0) return FMM_ERR_INVALID;
-    if (bad > 0) return FMM_ERR_BRENT;
+    if (bad != 0) {
+        const fmm_algo_t shape{algo ? algo->p : 0, algo ? algo->R : 0, nullptr, nullptr, nullptr};
+        return log_plan("fmm_plan_create_rational", bad < 0 ? FMM_ERR_INVALID : FMM_ERR_BRENT, nullptr, n, &shape,
+                        depth, dtype);
+    }
     const fmm_algo_t num{algo->p, algo->R, algo->U, algo->V, algo->W};
-    return plan_create(out, n, &num, depth, dtype, opts, (int64_t)algo->den_u * algo->den_v * algo->den_w);
+    const fmm_status_t st =
+        plan_create(out, n, &num, depth, dtype, opts, (int64_t)algo->den_u * algo->den_v * algo->den_w);
+    return log_plan("fmm_plan_create_rational", st, st == FMM_OK ? *out : nullptr, n, &num, depth, dtype);
 }
 
 namespace {
@@ -1340,6 +1389,9 @@ extern "C" fmm_status_t fmm_gemm_ex(const fmm_plan_t *pl, double alpha, const do
     const long long doubles = pl->n * pl->n * (pl->inner ? 2 : 1);
     if (pl->inner && ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15) != 0) return FMM_ERR_INVALID;
     if (pl->shard_count > 1 && beta != 0.0) return FMM_ERR_UNSUPPORTED;
+    if (log_level() >= 2)
+        std::fprintf(stderr, "fmm: gemm n=%lld depth=%d dtype=%s alpha=%g beta=%g stream=%p\n", (long long)pl->n,
+                     pl->depth, dtype_name(pl->dtype), alpha, beta, stream);
     if (alpha == 0.0) return cuda_status(fmm::launch_scale_c(C, doubles, beta, st));  // A, B unread
     if (pl->inner) return gemm_complex(pl, alpha, A, B, beta, C, st);
     if (pl->ev[0] && cudaEventRecord(pl->ev[0], st) != cudaSuccess) return FMM_ERR_CUDA;
@@ -1656,10 +1708,14 @@ extern "C" fmm_status_t fmm_autotune(int64_t n, const fmm_algo_t *const *algos, 
     const fmm_algo_t *first = nullptr;
     for (int ai = 0; ai < nalgos && !first; ++ai)
         if (algos[ai]) first = algos[ai];
-    for (int tile : {64, 128}) cands.push_back({0, 0, tile, FMM_SCHED_AUTO});
-    for (int ai = 0; ai < nalgos; ++ai) {
+    // FMM_FORCE_DEPTH=d keeps only the candidates of depth d (still searching algorithm, tile and schedule)
+    const char *fd = std::getenv("FMM_FORCE_DEPTH");
+    const int force = fd && *fd ? std::atoi(fd) : -1;
+    if (force <= 0)
+        for (int tile : {64, 128}) cands.push_back({0, 0, tile, FMM_SCHED_AUTO});
+    for (int ai = 0; ai < nalgos && force != 0; ++ai) {
         if (!algo_shape_ok(algos[ai])) continue;
-        for (int d = 1; d <= max_depth; ++d) {
+        for (int d = force > 0 ? force : 1; d <= (force > 0 ? force : max_depth); ++d) {
             long long P = 1;
             for (int k = 0; k < d; ++k) P *= algos[ai]->p;
             if (n / P < min_leaf) break;

@@ -316,3 +316,30 @@ def test_injected_allocation_failure_returns_oom_and_leaks_nothing(fmm, dtype):
             assert fmm.fmm_debug_live_allocations() == base, k
     finally:
         fmm.fmm_debug_fail_allocation(-1)
+
+
+def test_fmm_log_reports_rejected_plans_on_stderr():
+    """FMM_LOG=1: a plan rejected before any CUDA call (Brent failure, bad size) leaves one line on stderr
+    naming the reason; without FMM_LOG nothing is printed."""
+    import subprocess
+    import sys
+
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import paper_2312_12732_gb300 as f\n"
+            "s = f.fmm_algo_builtin('strassen')\n"
+            "bad = f.Algo(2, s.U, s.V, s.W[[0, 2, 1, 3]])\n"
+            "for args in ((64, bad, 1), (0, s, 1)):\n"
+            "    try:\n"
+            "        f.fmm_plan_create(*args)\n"
+            "    except f.FmmError:\n"
+            "        pass\n") % ROOT
+    env = dict(os.environ, FMM_LOG="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stderr.splitlines() if ln.startswith("fmm: ")]
+    assert len(lines) == 2, r.stderr
+    assert "rejected" in lines[0] and "Brent" in lines[0] and "p=2 R=7 depth=1" in lines[0]
+    assert "rejected" in lines[1] and "invalid argument" in lines[1]
+    env.pop("FMM_LOG")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+    assert r.returncode == 0 and "fmm: " not in r.stderr

@@ -125,3 +125,23 @@ def test_autotune_choice_is_cached_in_memory_and_on_disk(fmm, monkeypatch, tmp_p
     assert from_disk == first
     plans, picks = autotune.plan_batch([300, 305], cache_path=path)
     assert all(p.info()["tile_n"] == first["tile_n"] and p.depth == first["depth"] for p in plans)
+
+
+def test_force_depth_and_plan_log(fmm, monkeypatch, capfd):
+    """FMM_FORCE_DEPTH restricts the tuner to one depth; FMM_LOG=2 logs each plan and each multiplication."""
+    algos = [fmm.fmm_algo_builtin("strassen"), fmm.fmm_algo_builtin("winograd")]
+    monkeypatch.setenv("FMM_FORCE_DEPTH", "2")
+    r = fmm.fmm_autotune(1024, algos, max_depth=3, min_leaf=128)
+    assert r["depth"] == 2 and r["depth0_ms"] > 1e29 and r["candidates"] >= 4
+    monkeypatch.delenv("FMM_FORCE_DEPTH")
+    monkeypatch.setenv("FMM_LOG", "2")
+    capfd.readouterr()
+    plan = fmm.fmm_plan_create(512, algos[0], 1)
+    A = torch.ones(512, 512, dtype=torch.float64, device="cuda")
+    C = torch.empty_like(A)
+    fmm.fmm_gemm(plan, A, A, C)
+    assert fmm.fmm_sync_status(plan) == 0
+    err = capfd.readouterr().err
+    assert "fmm: fmm_plan_create n=512 p=2 R=7 depth=1 dtype=f64 leaf=256 products=0..7" in err, err
+    assert "fmm: gemm n=512 depth=1 dtype=f64" in err, err
+    assert bool(torch.all(C == 512.0))
