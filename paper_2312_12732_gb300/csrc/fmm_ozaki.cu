@@ -24,6 +24,7 @@
 //    ascending r, ordered by the same per-tile counters as the FP64 kernel.
 // Slicing, folding and scaling use integer arithmetic; FP64 work is one
 // conversion and one multiply per element of P_r plus the post-additions.
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
@@ -83,31 +84,41 @@ __device__ __forceinline__ long long to_fixed(double x, int E, int bs) {
     return (b >> 63) ? -Y : Y;
 }
 
-__device__ __forceinline__ unsigned char e4m3(int v) {
-    return (unsigned char)__nv_cvt_float_to_fp8((float)v, __NV_SATFINITE, __NV_E4M3);
-}
-
 // Digits by bit fields: with O = 16 (32^s - 1) / 31, Z = Y + O has plain
 // base-32 digits z_t in [0, 31] (the top one in [0, 32]) and Y's balanced
-// digits are z_t - 16, so each digit is a shift and a mask; the e4m3 byte of
-// z - 16 comes from a 33-entry table.  Writes byte t of the element into
-// bits [8q, 8q + 8) of packed[t].
+// digits are z_t - 16, so each digit is a shift and a mask.
 __device__ __forceinline__ long long digit_offset(int s) { return ((1LL << (OB * s)) - 1) / 31 * 16; }
 
+// Field t of Z (most significant first), a value in [0, 32].
 template <int S>
-__device__ __forceinline__ void pack_digits(long long Z, const unsigned char *lut, unsigned (&packed)[kOzMaxSlices],
-                                            int q) {
-    // S is a compile-time constant, so every field is a constant shift of Z
-#pragma unroll
-    for (int t = 0; t < S; ++t) {
-        const int sh = OB * (S - 1 - t);
-        const int z = t == 0 ? (int)(Z >> sh) : (int)((Z >> sh) & 31);
-        packed[t] |= (unsigned)lut[z] << (8 * q);
-    }
+__device__ __forceinline__ unsigned digit_field(long long Z, int t) {
+    const int sh = OB * (S - 1 - t);
+    return t == 0 ? (unsigned)(Z >> sh) : (unsigned)((Z >> sh) & 31);
 }
 
-__device__ __forceinline__ void fill_lut(unsigned char *lut) {
-    for (int i = threadIdx.x; i < 33; i += blockDim.x) lut[i] = e4m3(i - 16);
+// The e4m3 bytes of two balanced digits f0 - 16, f1 - 16 (f in [0, 32]), f0's
+// in the low byte: the binary16 pattern 0x6400 | f is 1024 + f, subtracting
+// 1040 leaves f - 16 exactly, and the hardware conversion of a binary16 pair
+// to an e4m3 pair is exact for these integers.  Two digits per conversion and
+// no table lookup.
+__device__ __forceinline__ unsigned e4m3x2_of_fields(unsigned f0, unsigned f1) {
+    __half2_raw h;
+    h.x = (unsigned short)(0x6400u | f0);
+    h.y = (unsigned short)(0x6400u | f1);
+    const __half2 d = __hsub2(__half2(h), __float2half2_rn(1040.0f));
+    return (unsigned)__nv_cvt_halfraw2_to_fp8x2(__half2_raw(d), __NV_SATFINITE, __NV_E4M3);
+}
+
+// Digit t of four elements (Z[q] = the element's fixed-point value plus the
+// digit offset; an element outside the matrix has Z = offset, all digits 0)
+// as byte q of packed[t].  S is a compile-time constant, so every field is a
+// constant shift.
+template <int S>
+__device__ __forceinline__ void pack_digits4(const long long (&Z)[4], unsigned (&packed)[kOzMaxSlices]) {
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+        packed[t] = e4m3x2_of_fields(digit_field<S>(Z[0], t), digit_field<S>(Z[1], t)) |
+                    (e4m3x2_of_fields(digit_field<S>(Z[2], t), digit_field<S>(Z[3], t)) << 16);
 }
 
 // ---------------------------------------------------------------------------
@@ -127,9 +138,6 @@ __global__ void slice_rows_kernel(const double *__restrict__ X, long long ld, lo
                                   int cols, int *__restrict__ mx, int pitch, int Mp, int Kp,
                                   unsigned char *__restrict__ out) {
     constexpr int s = S;
-    __shared__ unsigned char lut[33];
-    fill_lut(lut);
-    __syncthreads();
     const int mat = blockIdx.y;
     const double *Xm = X + (long long)mat * mat_stride;
     const int lane = threadIdx.x & 31;
@@ -149,13 +157,13 @@ __global__ void slice_rows_kernel(const double *__restrict__ X, long long ld, lo
         const long long slice_stride = (long long)Mp * Kp;
         for (int c4 = lane; c4 * 4 < cols; c4 += 32) {
             unsigned packed[kOzMaxSlices];
-#pragma unroll
-            for (int t = 0; t < kOzMaxSlices; ++t) packed[t] = 0u;
+            long long Z[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = c4 * 4 + q;
-                if (c < cols) pack_digits<S>(to_fixed(__ldg(row + c), E, bs) + O, lut, packed, q);
+                Z[q] = (c < cols ? to_fixed(__ldg(row + c), E, bs) : 0) + O;
             }
+            pack_digits4<S>(Z, packed);
 #pragma unroll
             for (int t = 0; t < kOzMaxSlices; ++t)
                 if (t < s) *reinterpret_cast<unsigned *>(orow + t * slice_stride + c4 * 4) = packed[t];
@@ -176,8 +184,6 @@ __global__ void slice_cols_kernel(const double *__restrict__ X, long long ld, lo
     constexpr int s = S;
     __shared__ unsigned tile[S][32][9];  // [slice][column][K word], padded: conflict-free both ways
     __shared__ int colmax[8][32];
-    __shared__ unsigned char lut[33];
-    fill_lut(lut);
     const long long O = digit_offset(s);
     const int mat = blockIdx.y;
     const double *Xm = X + (long long)mat * mat_stride;
@@ -203,13 +209,13 @@ __global__ void slice_cols_kernel(const double *__restrict__ X, long long ld, lo
     unsigned char *obase = out + ((long long)mat * s * Mp + c0 + cc) * Kp;
     for (int k0 = 0; k0 < rows; k0 += 32) {
         unsigned packed[kOzMaxSlices];
-#pragma unroll
-        for (int t = 0; t < kOzMaxSlices; ++t) packed[t] = 0u;
+        long long Z[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k = k0 + 4 * ty + q;
-            if (c < cols && k < rows) pack_digits<S>(to_fixed(__ldg(Xm + (long long)k * ld + c), E, bs) + O, lut, packed, q);
+            Z[q] = (c < cols && k < rows ? to_fixed(__ldg(Xm + (long long)k * ld + c), E, bs) : 0) + O;
         }
+        pack_digits4<S>(Z, packed);
 #pragma unroll
         for (int t = 0; t < S; ++t) tile[t][tx][ty] = packed[t];
         __syncthreads();
