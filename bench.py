@@ -13,9 +13,10 @@ flush is needed between steps.
     python bench.py --impl reference ...                      # CPU oracle arm
     python bench.py --sweep                                   # per-algorithm table
 
-With N > 1 (launched by torchrun) every rank runs an independent replica of
-the workload on its own GPU (the product does not shard across GPUs): the
-value is the multiplications of all ranks / the slowest rank's time.
+With N > 1 (launched by torchrun) the ranks shard one multiplication by its
+leaf products (Section 2: the products are independent) and sum their partial
+C with one all-reduce; the value is that one multiplication's flops / the
+slowest rank's time (strong scaling).
 """
 from __future__ import annotations
 
@@ -689,13 +690,14 @@ def run_ours(a):
     if not a.no_e2e:
         k_e2e = max(2, a.steps // 2)
         dev_ms, call_ms = [], []
-        # The clock sampler starts (forks nvidia-smi) before the host buffers are pinned: copies from a
-        # buffer pinned before a fork of the process drop from about 210 to 25 GB/s on this system.
+        # the clock sampler covers the whole end-to-end section, host buffer set-up included
         sampler_e2e = ClockSampler(gpu_uuid(torch, dev))
         with sampler_e2e:
-            hA = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
-            hB = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
-            hC = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+            # the library's page-locked buffers (huge-page backed where the host has transparent huge
+            # pages): the host link keeps its rate from them after other processes have churned memory
+            hA = fmm.host_empty((n, n), torch.float64)
+            hB = fmm.host_empty((n, n), torch.float64)
+            hC = fmm.host_empty((n, n), torch.float64)
             hA.copy_(torch.from_numpy(A))
             hB.copy_(torch.from_numpy(B))
 
@@ -743,6 +745,18 @@ def run_ours(a):
         torch.cuda.synchronize()
         gbs = [n * n * 8 / (ev[i].elapsed_time(ev[i + 1]) * 1e-3) / 1e9 for i in range(3)]
         h2d_gbs, d2h_gbs = min(gbs[0], gbs[1]), gbs[2]
+        # context: the same copies from a plain cudaHostAlloc buffer (torch's pinned memory)
+        hP = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        evp = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        evp[0].record()
+        dA.copy_(hP, non_blocking=True)
+        evp[1].record()
+        hP.copy_(dC, non_blocking=True)
+        evp[2].record()
+        torch.cuda.synchronize()
+        gbs_pinned = [n * n * 8 / (evp[i].elapsed_time(evp[i + 1]) * 1e-3) / 1e9 for i in range(2)]
+        del hP
+        dA.copy_(hA)  # restore the operand the copy above overwrote
         e2e = {"value": (flops_eff / te if sharded else job_throughput(flops_eff, ws, te)) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": ws * 2 * n * n * 8, "d2h_bytes_per_step": (1 if sharded else ws) * n * n * 8,
                "ms_per_step": te * 1e3, "steps": k_e2e,
@@ -750,8 +764,10 @@ def run_ours(a):
                "device_ms": [round(x, 2) for x in dev_ms], "copies_alone_ms": round(copy_ms, 2),
                "h2d_gbs": round(h2d_gbs, 1), "d2h_gbs": round(d2h_gbs, 1),
                "copy_gbs_A_B_C": [round(x, 1) for x in gbs],
+               "host_buffers": "fmm_host_alloc (huge pages: %d bytes)" % fmm.fmm_host_huge_page_bytes(),
+               "context_cudahostalloc_gbs_h2d_d2h": [round(x, 1) for x in gbs_pinned],
                "clocks": sampler_e2e.summary(),
-               "path": "fmm_gemm_host (pinned host buffers, copies inside the timed region)" if not sharded else
+               "path": "fmm_gemm_host (fmm_host_alloc buffers, copies inside the timed region)" if not sharded else
                "per rank: copies of A and B in, its shard (fmm_gemm), all-reduce of C, rank 0 copies C out"}
 
     nc = info["n_core"]

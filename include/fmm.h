@@ -352,12 +352,38 @@ fmm_status_t fmm_gemm_f32_ex(const fmm_plan_t *plan, float alpha, const float *A
  * overlap; a pageable source's copy returns only once it is done.  For an
  * FMM_C128 plan the buffers hold interleaved complex pairs and for an
  * FMM_F32 plan binary32 values (pass their addresses cast to these types);
- * both copy A, then B, on `stream`.  On GB300 (Grace host) page-locked
- * buffers copy at about 210 GB/s host to device and 190 GB/s back, pageable
- * ones at 180-200 GB/s.  FMM_ERR_OOM if the device buffers cannot be
- * allocated, FMM_ERR_CUDA if a copy or launch fails. */
+ * both copy A, then B, on `stream`.  On GB300 (Grace host) buffers from
+ * fmm_host_alloc copy at about 210 GB/s host to device and 193 GB/s back;
+ * other page-locked and pageable buffers reach 180-210 GB/s on a fresh host
+ * but can fall far below that later (see fmm_host_alloc).  FMM_ERR_OOM if
+ * the device buffers cannot be allocated, FMM_ERR_CUDA if a copy or launch
+ * fails. */
 fmm_status_t fmm_gemm_host(fmm_plan_t *plan, const double *A_host, const double *B_host,
                            double *C_host, void *stream);
+
+/* Page-locked host memory for the buffers of fmm_gemm_host (usable for any
+ * copy to or from the GPU).  No counterpart in the paper, whose timings
+ * exclude host transfers.  On Linux with transparent huge pages, a request of
+ * at least one huge page (hpage_pmd_size: 2 MiB with 4 KiB base pages,
+ * 512 MiB with 64 KiB pages) is mapped at a huge-page boundary, rounded up to
+ * whole huge pages, advised to use them and registered with the CUDA driver
+ * (portable to every context); smaller requests, and systems where that
+ * fails, get cudaHostAlloc memory.  Why: on GB300 (Grace host, 64 KiB base
+ * pages), once other processes had used and freed much memory, host-to-device
+ * copies from cudaHostAlloc buffers fell to 12-16 GB/s while huge-page buffers
+ * kept 210 GB/s (193 GB/s back).  On success *out holds the address (aligned
+ * to at least the base page); the caller owns it until fmm_host_free.
+ * FMM_ERR_INVALID for out == NULL, FMM_ERR_OOM if no page-locked memory could
+ * be had (also without a CUDA driver). */
+fmm_status_t fmm_host_alloc(void **out, size_t bytes);
+
+/* Releases memory from fmm_host_alloc; NULL is a no-op.  FMM_ERR_INVALID for
+ * an address that fmm_host_alloc did not return or that was freed already. */
+fmm_status_t fmm_host_free(void *p);
+
+/* The transparent huge-page size fmm_host_alloc uses, in bytes (0 if the
+ * system has none). */
+int64_t fmm_host_huge_page_bytes(void);
 
 /* Batched: count independent products C[i] = A[i] * B[i], each with its own
  * plan (sizes and algorithms may differ), as one persistent grouped launch

@@ -46,6 +46,10 @@ from ._binding import (  # noqa: F401
     fmm_gemm_ex,
     fmm_gemm_f32_ex,
     fmm_gemm_host,
+    fmm_host_alloc,
+    fmm_host_free,
+    fmm_host_huge_page_bytes,
+    host_empty,
     fmm_debug_fail_allocation,
     fmm_debug_live_allocations,
     fmm_gemm_noalloc,

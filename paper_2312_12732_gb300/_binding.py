@@ -121,6 +121,9 @@ SIGNATURES = [
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fmm_measure_e4m3_peak", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("fmm_noalloc_sync_status", ctypes.c_int, [ctypes.c_void_p]),
+    ("fmm_host_alloc", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t]),
+    ("fmm_host_free", ctypes.c_int, [ctypes.c_void_p]),
+    ("fmm_host_huge_page_bytes", ctypes.c_int64, []),
     ("fmm_debug_fail_allocation", None, [ctypes.c_int64]),
     ("fmm_debug_live_allocations", ctypes.c_int64, []),
     ("fmm_noalloc_set_debug", ctypes.c_int, [ctypes.c_double, ctypes.c_int]),
@@ -509,6 +512,55 @@ def fmm_gemm_host(plan: Plan, A, B, C, stream=None):
                                ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
            "fmm_gemm_host")
     return C
+
+
+def fmm_host_alloc(nbytes: int) -> int:
+    """Page-locked host memory (huge-page backed and registered where the system allows); returns the
+    address, to be released with fmm_host_free."""
+    p = ctypes.c_void_p()
+    _check(lib().fmm_host_alloc(ctypes.byref(p), ctypes.c_size_t(int(nbytes))), "fmm_host_alloc")
+    return int(p.value)
+
+
+def fmm_host_free(addr: int):
+    _check(lib().fmm_host_free(ctypes.c_void_p(int(addr) if addr else None)), "fmm_host_free")
+
+
+def fmm_host_huge_page_bytes() -> int:
+    return int(lib().fmm_host_huge_page_bytes())
+
+
+class _HostBlock:
+    """Owns one fmm_host_alloc block; released when the last tensor viewing it is gone."""
+
+    def __init__(self, nbytes: int):
+        self.addr = fmm_host_alloc(nbytes)
+        self.nbytes = nbytes
+
+    def __del__(self):
+        if getattr(self, "addr", 0):
+            try:
+                fmm_host_free(self.addr)
+            except Exception:
+                pass
+            self.addr = 0
+
+
+def host_empty(shape, dtype=None):
+    """An uninitialised CPU tensor in fmm_host_alloc memory (the buffers fmm_gemm_host copies fastest
+    from and to); the memory is released with the tensor and its views."""
+    import torch
+
+    dtype = torch.float64 if dtype is None else dtype
+    shape = tuple(int(x) for x in (shape if isinstance(shape, (tuple, list)) else (shape,)))
+    count = 1
+    for x in shape:
+        count *= x
+    nbytes = max(count * torch.empty((), dtype=dtype).element_size(), 1)
+    block = _HostBlock(nbytes)
+    arr = (ctypes.c_byte * nbytes).from_address(block.addr)
+    arr._fmm_block = block  # torch.frombuffer keeps arr, and so the block, alive
+    return torch.frombuffer(arr, dtype=dtype, count=count).view(shape)
 
 
 def fmm_gemm_noalloc(algo: Algo, depth: int, A, B, C, stream=None):

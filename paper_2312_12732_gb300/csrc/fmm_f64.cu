@@ -94,7 +94,12 @@ __device__ void setup_task(Smem<BNT> &S, const F64Problem &pr, const F64Geom &g,
     const int tid = threadIdx.x;
     const long long n = g.n, m = g.m, nc = g.n_core;
     const long long q = n - nc;
-    if (local < g.tasks_core) {
+    // Task order: the border products first (K = n, the longest tasks, and independent of all others),
+    // then the core products, then the rank-q updates, which wait for the core contributions to their
+    // C block.  Started last, the border products left a tail of a few long tasks on few SMs.
+    const long long border = g.tasks_right + g.tasks_bottom;
+    if (local >= border && local - border < g.tasks_core) {
+        local -= border;
         const int tiles = g.tiles_m * g.tiles_n;
         const long long per_sub = (long long)tiles * g.R_src;
         const int sub = g.sub_begin + (int)(local / per_sub);
@@ -139,7 +144,7 @@ __device__ void setup_task(Smem<BNT> &S, const F64Problem &pr, const F64Geom &g,
         }
         return;
     }
-    local -= g.tasks_core;
+    if (local >= border) local -= g.tasks_core;
     if (tid != 0) return;
     S.alpha = pr.alpha_peel; S.beta = pr.beta;
     S.nA = S.nB = S.nD = 1;

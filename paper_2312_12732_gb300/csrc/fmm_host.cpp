@@ -12,9 +12,14 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
+
+#include <sys/mman.h>
+#include <unistd.h>
 
 #include "fmm_internal.h"
 
@@ -354,6 +359,7 @@ struct fmm_plan {
         int p = 0, R = 0;
         const int *uptr = nullptr, *vptr = nullptr;
         const int4 *uent = nullptr, *vent = nullptr;
+        bool unit_u = false, unit_v = false;  // every coefficient of the step's U (V) is +-1
         bool with_next = false;  // formed in one pass with the next step (both 2 x 2, at most 8 products)
     };
     std::vector<MatStep> mat_steps;
@@ -426,18 +432,92 @@ void dev_free(void *p) {
     cudaFree(p);
     --g_live_allocs;
 }
+// Page-locked host memory (fmm_host_alloc).  A request of at least one
+// transparent huge page is mapped at a huge-page boundary, rounded up to whole
+// huge pages, advised to use them and registered with the driver; anything
+// else, or a registration the driver refuses, comes from cudaHostAlloc.  The
+// registry maps each returned address to how it was obtained.
+struct HostBlock {
+    size_t len;       // bytes mapped and registered (0: cudaHostAlloc memory)
+};
+std::mutex g_host_mu;
+std::unordered_map<void *, HostBlock> g_host_blocks;
+
+size_t huge_page_bytes() {
+    static const size_t hp = [] {
+        unsigned long long v = 0;
+        if (FILE *f = std::fopen("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size", "r")) {
+            if (std::fscanf(f, "%llu", &v) != 1) v = 0;
+            std::fclose(f);
+        }
+        const long page = sysconf(_SC_PAGESIZE);
+        // a usable size is a power of two above the base page
+        if (page <= 0 || v <= (unsigned long long)page || (v & (v - 1)) != 0) v = 0;
+        return (size_t)v;
+    }();
+    return hp;
+}
+
+void *huge_page_registered(size_t bytes, size_t *len_out) {
+    const size_t hp = huge_page_bytes();
+    if (hp == 0 || bytes < hp || bytes > SIZE_MAX / 2 - hp) return nullptr;
+    const size_t len = (bytes + hp - 1) / hp * hp;
+    void *raw = mmap(nullptr, len + hp, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (raw == MAP_FAILED) return nullptr;
+    const uintptr_t r = (uintptr_t)raw, a = (r + hp - 1) / hp * hp;
+    const size_t head = a - r, tail = hp - head;
+    if (head) munmap(raw, head);
+    if (tail) munmap(reinterpret_cast<void *>(a + len), tail);
+    void *q = reinterpret_cast<void *>(a);
+    madvise(q, len, MADV_HUGEPAGE);  // advice only: without huge pages the buffer still works
+    if (cudaHostRegister(q, len, cudaHostRegisterPortable) != cudaSuccess) {
+        cudaGetLastError();
+        munmap(q, len);
+        return nullptr;
+    }
+    *len_out = len;
+    return q;
+}
+
 cudaError_t pinned_alloc(void **p, size_t bytes) {
     *p = nullptr;
     if (inject_failure()) return cudaErrorMemoryAllocation;
-    const cudaError_t e = cudaHostAlloc(p, bytes, cudaHostAllocDefault);
-    if (e == cudaSuccess) ++g_live_allocs;
-    else cudaGetLastError();
-    return e;
+    size_t len = 0;
+    void *q = huge_page_registered(bytes, &len);
+    if (!q) {
+        const cudaError_t e = cudaHostAlloc(&q, bytes ? bytes : 1, cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        len = 0;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        g_host_blocks[q] = HostBlock{len};
+    }
+    ++g_live_allocs;
+    *p = q;
+    return cudaSuccess;
 }
-void pinned_free(void *p) {
-    if (!p) return;
-    cudaFreeHost(p);
+bool pinned_free(void *p) {
+    HostBlock b{};
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        auto it = g_host_blocks.find(p);
+        if (it == g_host_blocks.end()) return false;
+        b = it->second;
+        g_host_blocks.erase(it);
+    }
+    if (b.len) {
+        cudaHostUnregister(p);
+        munmap(p, b.len);
+    } else {
+        cudaFreeHost(p);
+    }
+    cudaGetLastError();
     --g_live_allocs;
+    return true;
 }
 // Host objects of the library (plans, batch graphs, launch descriptors).
 template <class T>
@@ -802,17 +882,31 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     std::vector<int4> w_ent;
     csc2(ucols, u_ptr, u_ent);
     csc2(vcols, v_ptr, v_ent);
-    // per materialization step: CSC over its products of {block row, block col, coef}
+    // per materialization step: CSC over its products of {block row, block col, coefficient as the two
+    // words of a double}, and whether every coefficient of the step is +-1
     std::vector<std::vector<int>> st_uptr(steps.size()), st_vptr(steps.size());
     std::vector<std::vector<int4>> st_uent(steps.size()), st_vent(steps.size());
+    std::vector<char> st_unit_u(steps.size(), 1), st_unit_v(steps.size(), 1);
+    auto mat_entry = [](int blk, int p, int c) {
+        const double d = (double)c;
+        unsigned long long bits = 0;
+        std::memcpy(&bits, &d, sizeof bits);
+        return make_int4(blk / p, blk % p, (int)(unsigned)(bits & 0xffffffffULL), (int)(unsigned)(bits >> 32));
+    };
     for (size_t k = 0; k < steps.size(); ++k) {
         const LevelFactor &f = steps[k];
         std::vector<int2> tmp;
         csc2(flatten(f.p, f.R, f.U.data(), 1), st_uptr[k], tmp);
-        for (const int2 &e : tmp) st_uent[k].push_back(make_int4(e.x / f.p, e.x % f.p, e.y, 0));
+        for (const int2 &e : tmp) {
+            st_uent[k].push_back(mat_entry(e.x, f.p, e.y));
+            if (e.y != 1 && e.y != -1) st_unit_u[k] = 0;
+        }
         tmp.clear();
         csc2(flatten(f.p, f.R, f.V.data(), 1), st_vptr[k], tmp);
-        for (const int2 &e : tmp) st_vent[k].push_back(make_int4(e.x / f.p, e.x % f.p, e.y, 0));
+        for (const int2 &e : tmp) {
+            st_vent[k].push_back(mat_entry(e.x, f.p, e.y));
+            if (e.y != 1 && e.y != -1) st_unit_v[k] = 0;
+        }
     }
     // W entries of every product; the ordering positions (and each C block's count of contributions)
     // cover only the shard's products, the others are never read
@@ -946,6 +1040,8 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             ms.uent = (const int4 *)(base + o_st[4 * k + 1]);
             ms.vptr = (const int *)(base + o_st[4 * k + 2]);
             ms.vent = (const int4 *)(base + o_st[4 * k + 3]);
+            ms.unit_u = st_unit_u[k] != 0;
+            ms.unit_v = st_unit_v[k] != 0;
             pl->mat_steps.push_back(ms);
         }
     for (size_t k = 0; k + 1 < pl->mat_steps.size(); ++k) {
@@ -1202,18 +1298,19 @@ fmm_status_t prepare(const fmm_plan *pl, const double *A, const double *B, cudaS
             if (ms.with_next) {
                 const fmm_plan::MatStep &m2 = pl->mat_steps[k + 1];
                 const long long b_out = b_in / 4;
+                const bool unit = side == 0 ? ms.unit_u && m2.unit_u : ms.unit_v && m2.unit_v;
                 e = fmm::launch_materialize_two_steps(src, ld_in, in_stride, (int)n_in, b_out, ms.R,
                                                       side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent,
                                                       m2.R, side == 0 ? m2.uptr : m2.vptr,
-                                                      side == 0 ? m2.uent : m2.vent, dst, st);
+                                                      side == 0 ? m2.uent : m2.vent, unit, dst, st);
                 n_in *= (long long)ms.R * m2.R;
                 b_in = b_out;
                 ++k;
             } else {
                 const long long b_out = b_in / ms.p;
                 e = fmm::launch_materialize_level(src, ld_in, in_stride, (int)n_in, b_out, ms.p, ms.R,
-                                                  side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent, dst,
-                                                  st);
+                                                  side == 0 ? ms.uptr : ms.vptr, side == 0 ? ms.uent : ms.vent,
+                                                  side == 0 ? ms.unit_u : ms.unit_v, dst, st);
                 n_in *= ms.R;
                 b_in = b_out;
             }
@@ -1860,3 +1957,16 @@ extern "C" void fmm_plan_destroy(fmm_plan_t *pl) {
 extern "C" void fmm_debug_fail_allocation(int64_t k) { g_fail_countdown.store(k < 0 ? -1 : (long long)k); }
 
 extern "C" int64_t fmm_debug_live_allocations(void) { return (int64_t)g_live_allocs.load(); }
+
+extern "C" fmm_status_t fmm_host_alloc(void **out, size_t bytes) {
+    if (!out) return FMM_ERR_INVALID;
+    *out = nullptr;
+    return pinned_alloc(out, bytes) == cudaSuccess ? FMM_OK : FMM_ERR_OOM;
+}
+
+extern "C" fmm_status_t fmm_host_free(void *p) {
+    if (!p) return FMM_OK;
+    return pinned_free(p) ? FMM_OK : FMM_ERR_INVALID;
+}
+
+extern "C" int64_t fmm_host_huge_page_bytes(void) { return (int64_t)huge_page_bytes(); }

@@ -184,16 +184,18 @@ size_t f64_kernel_smem_bytes(int bn = kBN);
 // dimension ld_in and is split into p x p blocks of size b_out; output
 // c * R + s is the b_out x b_out matrix sum_e coef_e * block(row_e, col_e)
 // over the CSC column s (s < R) of the one-level coefficient matrix, entries
-// {block row, block col, coefficient, 0}, stored densely at
-// out + (c * R + s) * b_out^2.
+// {block row, block col, low word, high word of coef_e as a double}, stored
+// densely at out + (c * R + s) * b_out^2.  unit: every coefficient is +-1.
 cudaError_t launch_materialize_level(const double *in, long long ld_in, long long in_stride, int n_in,
-                                     long long b_out, int p, int R, const int *ptr, const int4 *ent, double *out,
-                                     cudaStream_t s);
+                                     long long b_out, int p, int R, const int *ptr, const int4 *ent, bool unit,
+                                     double *out, cudaStream_t s);
 // Two consecutive steps with 2 x 2 block grids (at most 8 products each) in
 // one pass; out receives n_in * R1 * R2 matrices of side b2 (= input side / 4).
+// unit: every coefficient of both steps is +-1.
 cudaError_t launch_materialize_two_steps(const double *in, long long ld_in, long long in_stride, int n_in,
                                          long long b2, int R1, const int *ptr1, const int4 *ent1, int R2,
-                                         const int *ptr2, const int4 *ent2, double *out, cudaStream_t s);
+                                         const int *ptr2, const int4 *ent2, bool unit, double *out,
+                                         cudaStream_t s);
 
 // Calibration (fmm_calib.cu): FP64 throughput of DMMA (mma.sync m16n8k4) and
 // DFMA on the current device, in TFLOP/s, timed with CUDA events on `s`.

@@ -318,6 +318,27 @@ def test_injected_allocation_failure_returns_oom_and_leaks_nothing(fmm, dtype):
         fmm.fmm_debug_fail_allocation(-1)
 
 
+def test_host_alloc_rejects_what_it_did_not_hand_out(fmm):
+    """fmm_host_free: NULL is a no-op, an unknown address is FMM_ERR_INVALID.  Without a CUDA driver
+    fmm_host_alloc cannot lock pages: FMM_ERR_OOM, nothing left allocated."""
+    fmm.fmm_host_free(0)
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_host_free(4096)
+    assert e.value.status == 1
+    hp = fmm.fmm_host_huge_page_bytes()
+    assert hp == 0 or (hp & (hp - 1)) == 0
+    import torch
+
+    if torch.cuda.is_available():
+        return
+    base = fmm.fmm_debug_live_allocations()
+    for nbytes in (64, max(hp, 1 << 21)):
+        with pytest.raises(fmm.FmmError) as e:
+            fmm.fmm_host_alloc(nbytes)
+        assert e.value.status == 4
+    assert fmm.fmm_debug_live_allocations() == base
+
+
 def test_fmm_log_reports_rejected_plans_on_stderr():
     """FMM_LOG=1: a plan rejected before any CUDA call (Brent failure, bad size) leaves one line on stderr
     naming the reason; without FMM_LOG nothing is printed."""
