@@ -32,21 +32,45 @@ __device__ __forceinline__ double first_term(double v, const int4 &en) {
     return coef_of(en) * v;
 }
 
-// One materialized recursion level.  blockIdx.y selects the input matrix;
-// CTAs stride over rows y of the b x b output blocks and threads over
-// columns x, so every load and store is coalesced and no index needs a
-// division.  All R outputs of a position are formed from the p^2 inputs.
+// The output positions (c, y, x) of n_in input matrices with b x b output
+// blocks, walked in the linear order c b^2 + y b + x: each thread starts at its
+// global index and advances by the grid's thread count, whose split into
+// (dc, dy, dx) is taken once, so the loop needs no division.  Every thread
+// gets the same number of positions (to within one), and a warp's positions
+// are consecutive in x, so loads and stores stay coalesced.
+struct PosWalk {
+    long long c, y, x, dc, dy, dx, b;
+    __device__ PosWalk(long long b_, long long bb) : b(b_) {
+        const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const long long G = (long long)gridDim.x * blockDim.x;
+        c = i / bb;
+        y = (i - c * bb) / b;
+        x = i - c * bb - y * b;
+        dc = G / bb;
+        dy = (G - dc * bb) / b;
+        dx = G - dc * bb - dy * b;
+    }
+    __device__ __forceinline__ void next() {
+        x += dx;
+        if (x >= b) { x -= b; ++y; }
+        y += dy;
+        if (y >= b) { y -= b; ++c; }
+        c += dc;
+    }
+};
+
+// One materialized recursion level: all R outputs of a position are formed
+// from the p^2 inputs.
 template <bool UNIT>
-__global__ void materialize_level_kernel(const double *__restrict__ in, long long ld_in, long long in_stride,
-                                         long long b, int p, int R, const int *__restrict__ ptr,
+__global__ void __launch_bounds__(256) materialize_level_kernel(const double *__restrict__ in, long long ld_in, long long in_stride,
+                                         int n_in, long long b, int p, int R, const int *__restrict__ ptr,
                                          const int4 *__restrict__ ent, double *__restrict__ out) {
     const long long total = b * b;
-    const int c = blockIdx.y;
-    const double *src = in + (long long)c * in_stride;
-    double *dst = out + (long long)c * R * total;
-    for (long long y = blockIdx.x; y < b; y += gridDim.x) {
-        for (long long x = threadIdx.x; x < b; x += blockDim.x) {
-            const double *pos = src + y * ld_in + x;
+    for (PosWalk w(b, total); w.c < n_in; w.next()) {
+        {
+            const long long c = w.c, y = w.y, x = w.x;
+            const double *pos = in + c * in_stride + y * ld_in + x;
+            double *dst = out + c * R * total;
             for (int s = 0; s < R; ++s) {
                 const int e0 = ptr[s], e1 = ptr[s + 1];
                 double acc = 0.0;  // an all-zero column (a product that uses no block) stays zero
@@ -72,66 +96,66 @@ __global__ void materialize_level_kernel(const double *__restrict__ in, long lon
 // two separate steps, so the results are identical; the first step's output
 // never reaches HBM.
 constexpr int kPairStepMaxR = 8;
+constexpr int kWalkThreads = 256;
 template <bool UNIT>
-__global__ void materialize_two_steps_kernel(const double *__restrict__ in, long long ld_in, long long in_stride,
-                                             long long b2, int R1, const int *__restrict__ ptr1,
+__global__ void __launch_bounds__(kWalkThreads) materialize_two_steps_kernel(const double *__restrict__ in, long long ld_in, long long in_stride,
+                                             int n_in, long long b2, int R1, const int *__restrict__ ptr1,
                                              const int4 *__restrict__ ent1, int R2, const int *__restrict__ ptr2,
                                              const int4 *__restrict__ ent2, double *__restrict__ out) {
     const long long total = b2 * b2;
     const long long b1 = 2 * b2;
-    const int c = blockIdx.y;
-    const double *src = in + (long long)c * in_stride;
-    double *dst = out + (long long)c * R1 * R2 * total;
-    for (long long y = blockIdx.x; y < b2; y += gridDim.x) {
-        for (long long x = threadIdx.x; x < b2; x += blockDim.x) {
-            // v[i1][j1][q]: input at outer block (i1, j1), inner block q = 2 i2 + j2
-            double v[2][2][4];
+    for (PosWalk wk(b2, total); wk.c < n_in; wk.next()) {
+        const long long y = wk.y, x = wk.x;
+        const double *src = in + wk.c * in_stride;
+        double *dst = out + wk.c * R1 * R2 * total;
+        // v[i1][j1][q]: input at outer block (i1, j1), inner block q = 2 i2 + j2
+        double v[2][2][4];
 #pragma unroll
-            for (int i1 = 0; i1 < 2; ++i1)
+        for (int i1 = 0; i1 < 2; ++i1)
 #pragma unroll
-                for (int j1 = 0; j1 < 2; ++j1)
+            for (int j1 = 0; j1 < 2; ++j1)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        v[i1][j1][q] = __ldg(src + (i1 * b1 + (q >> 1) * b2 + y) * ld_in + j1 * b1 + (q & 1) * b2 + x);
-            for (int r1 = 0; r1 < R1; ++r1) {
-                double t[4] = {0.0, 0.0, 0.0, 0.0};
-                const int e0 = ptr1[r1], e1 = ptr1[r1 + 1];
-                if (e0 < e1) {
-                    const int4 f = ent1[e0];
+                for (int q = 0; q < 4; ++q)
+                    v[i1][j1][q] = __ldg(src + (i1 * b1 + (q >> 1) * b2 + y) * ld_in + j1 * b1 + (q & 1) * b2 + x);
+        for (int r1 = 0; r1 < R1; ++r1) {
+            double t[4] = {0.0, 0.0, 0.0, 0.0};
+            const int e0 = ptr1[r1], e1 = ptr1[r1 + 1];
+            if (e0 < e1) {
+                const int4 f = ent1[e0];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        // selects, not a pointer, keep v in registers
-                        const double w = f.x == 0 ? (f.y == 0 ? v[0][0][q] : v[0][1][q])
-                                                  : (f.y == 0 ? v[1][0][q] : v[1][1][q]);
-                        t[q] = first_term<UNIT>(w, f);
-                    }
+                for (int q = 0; q < 4; ++q) {
+                    // selects, not a pointer, keep v in registers (a per-thread column of shared memory
+                    // addressed by the table measured no faster)
+                    const double w = f.x == 0 ? (f.y == 0 ? v[0][0][q] : v[0][1][q])
+                                              : (f.y == 0 ? v[1][0][q] : v[1][1][q]);
+                    t[q] = first_term<UNIT>(w, f);
                 }
-                for (int k = e0 + 1; k < e1; ++k) {
-                    const int4 en = ent1[k];
-                    const double cf = coef_of(en);
+            }
+            for (int k = e0 + 1; k < e1; ++k) {
+                const int4 en = ent1[k];
+                const double cf = coef_of(en);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const double w = en.x == 0 ? (en.y == 0 ? v[0][0][q] : v[0][1][q])
-                                                   : (en.y == 0 ? v[1][0][q] : v[1][1][q]);
-                        t[q] = fma(cf, w, t[q]);
-                    }
+                for (int q = 0; q < 4; ++q) {
+                    const double w = en.x == 0 ? (en.y == 0 ? v[0][0][q] : v[0][1][q])
+                                               : (en.y == 0 ? v[1][0][q] : v[1][1][q]);
+                    t[q] = fma(cf, w, t[q]);
                 }
-                double *o = dst + (long long)r1 * R2 * total + y * b2 + x;
-                for (int r2 = 0; r2 < R2; ++r2) {
-                    const int f0 = ptr2[r2], f1 = ptr2[r2 + 1];
-                    double acc = 0.0;
-                    if (f0 < f1) {
-                        const int4 f = ent2[f0];
-                        const int qf = 2 * f.x + f.y;
-                        acc = first_term<UNIT>(qf == 0 ? t[0] : (qf == 1 ? t[1] : (qf == 2 ? t[2] : t[3])), f);
-                    }
-                    for (int k = f0 + 1; k < f1; ++k) {
-                        const int4 en = ent2[k];
-                        const int q = 2 * en.x + en.y;
-                        acc = fma(coef_of(en), q == 0 ? t[0] : (q == 1 ? t[1] : (q == 2 ? t[2] : t[3])), acc);
-                    }
-                    o[(long long)r2 * total] = acc;
+            }
+            double *o = dst + (long long)r1 * R2 * total + y * b2 + x;
+            for (int r2 = 0; r2 < R2; ++r2) {
+                const int f0 = ptr2[r2], f1 = ptr2[r2 + 1];
+                double acc = 0.0;
+                if (f0 < f1) {
+                    const int4 f = ent2[f0];
+                    const int qf = 2 * f.x + f.y;
+                    acc = first_term<UNIT>(qf == 0 ? t[0] : (qf == 1 ? t[1] : (qf == 2 ? t[2] : t[3])), f);
                 }
+                for (int k = f0 + 1; k < f1; ++k) {
+                    const int4 en = ent2[k];
+                    const int q = 2 * en.x + en.y;
+                    acc = fma(coef_of(en), q == 0 ? t[0] : (q == 1 ? t[1] : (q == 2 ? t[2] : t[3])), acc);
+                }
+                o[(long long)r2 * total] = acc;
             }
         }
     }
@@ -139,30 +163,39 @@ __global__ void materialize_two_steps_kernel(const double *__restrict__ in, long
 
 }  // namespace
 
+namespace {
+
+// One CTA of 256 threads per resident slot (the kernel's occupancy times the
+// SM count), or fewer for small inputs: the linear walk then gives every
+// thread the same share of positions and the grid runs as one wave.
+template <class Kernel>
+unsigned walk_grid(Kernel kernel, long long positions) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kWalkThreads, 0) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    const long long slots = (long long)(sms > 0 ? sms : 1) * occ;
+    const long long need = (positions + kWalkThreads - 1) / kWalkThreads;
+    return (unsigned)(need < slots ? need : slots);
+}
+
+}  // namespace
+
 cudaError_t launch_materialize_level(const double *in, long long ld_in, long long in_stride, int n_in,
                                      long long b_out, int p, int R, const int *ptr, const int4 *ent, bool unit,
                                      double *out, cudaStream_t s) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long bx = (long long)sms * 8 / (n_in > 0 ? n_in : 1);
-    if (bx > b_out) bx = b_out;
-    if (bx < 1) bx = 1;
-    const int threads = b_out >= 256 ? 256 : (int)((b_out + 31) / 32 * 32);
-    for (int c0 = 0; c0 < n_in; c0 += 65535) {
-        const int cnt = n_in - c0 < 65535 ? n_in - c0 : 65535;
-        dim3 grid((unsigned)bx, (unsigned)cnt);
-        double *o = out + (long long)c0 * R * b_out * b_out;
-        if (unit)
-            materialize_level_kernel<true><<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride,
-                                                                    b_out, p, R, ptr, ent, o);
-        else
-            materialize_level_kernel<false><<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in, in_stride,
-                                                                     b_out, p, R, ptr, ent, o);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    const long long positions = (long long)n_in * b_out * b_out;
+    if (positions <= 0) return cudaSuccess;
+    if (unit)
+        materialize_level_kernel<true><<<walk_grid(materialize_level_kernel<true>, positions), kWalkThreads, 0, s>>>(
+            in, ld_in, in_stride, n_in, b_out, p, R, ptr, ent, out);
+    else
+        materialize_level_kernel<false><<<walk_grid(materialize_level_kernel<false>, positions), kWalkThreads, 0, s>>>(
+            in, ld_in, in_stride, n_in, b_out, p, R, ptr, ent, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_materialize_two_steps(const double *in, long long ld_in, long long in_stride, int n_in,
@@ -170,29 +203,17 @@ cudaError_t launch_materialize_two_steps(const double *in, long long ld_in, long
                                          const int *ptr2, const int4 *ent2, bool unit, double *out,
                                          cudaStream_t s) {
     if (R1 > kPairStepMaxR || R2 > kPairStepMaxR) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long bx = (long long)sms * 8 / (n_in > 0 ? n_in : 1);
-    if (bx > b2) bx = b2;
-    if (bx < 1) bx = 1;
-    const int threads = b2 >= 256 ? 256 : (int)((b2 + 31) / 32 * 32);
-    for (int c0 = 0; c0 < n_in; c0 += 65535) {
-        const int cnt = n_in - c0 < 65535 ? n_in - c0 : 65535;
-        dim3 grid((unsigned)bx, (unsigned)cnt);
-        double *o = out + (long long)c0 * R1 * R2 * b2 * b2;
-        if (unit)
-            materialize_two_steps_kernel<true><<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in,
-                                                                        in_stride, b2, R1, ptr1, ent1, R2, ptr2,
-                                                                        ent2, o);
-        else
-            materialize_two_steps_kernel<false><<<grid, threads, 0, s>>>(in + (long long)c0 * in_stride, ld_in,
-                                                                         in_stride, b2, R1, ptr1, ent1, R2, ptr2,
-                                                                         ent2, o);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    const long long positions = (long long)n_in * b2 * b2;
+    if (positions <= 0) return cudaSuccess;
+    if (unit)
+        materialize_two_steps_kernel<true>
+            <<<walk_grid(materialize_two_steps_kernel<true>, positions), kWalkThreads, 0, s>>>(
+                in, ld_in, in_stride, n_in, b2, R1, ptr1, ent1, R2, ptr2, ent2, out);
+    else
+        materialize_two_steps_kernel<false>
+            <<<walk_grid(materialize_two_steps_kernel<false>, positions), kWalkThreads, 0, s>>>(
+                in, ld_in, in_stride, n_in, b2, R1, ptr1, ent1, R2, ptr2, ent2, out);
+    return cudaGetLastError();
 }
 
 // C = beta C (the whole update when alpha = 0: A and B are not read).  With
