@@ -40,6 +40,11 @@
  *   FMM_TILE_N       64 or 128: the FP64 leaf tile width when a plan does not
  *                    set one (read at plan creation).
  *   FMM_OZAKI_ENGINE see FMM_F64_OZAKI (read at plan creation).
+ *   FMM_OZAKI_POSTADD flat: an FMM_F64_OZAKI plan of two levels of a 2 x 2
+ *                    algorithm applies its post-additions in the flattened
+ *                    form (every C block summed over all leaf products in
+ *                    ascending order) instead of level by level (read at
+ *                    plan creation).
  *   FMM_FORCE_DEPTH  d: fmm_autotune times only depth-d candidates.
  */
 #ifndef FMM_H_
@@ -122,7 +127,10 @@ typedef struct fmm_plan fmm_plan_t;
  *                       the remaining levels are fused into staging.
  * The post-additions C_l = sum_r W[l][r] P_r are fused into the FP64 leaf
  * kernel's epilogue; the emulated leaf (FMM_F64_OZAKI, FMM_F32) stores its
- * leaf products and applies them in a separate kernel, in the same order. */
+ * leaf products and applies them in a separate kernel: in the same order, or,
+ * for two levels of a 2 x 2 algorithm, level by level as the recursion forms
+ * them (each product's blocks first, then the sums over the outer products;
+ * FMM_OZAKI_POSTADD=flat selects the first form). */
 typedef enum { FMM_SCHED_AUTO = 0, FMM_SCHED_FUSED = 1, FMM_SCHED_HYBRID = 2 } fmm_schedule_t;
 
 /* Optional knobs for fmm_plan_create_ex.  Zero-initialise, then set fields;

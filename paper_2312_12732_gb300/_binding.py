@@ -552,6 +552,10 @@ def host_empty(shape, dtype=None):
     import torch
 
     dtype = torch.float64 if dtype is None else dtype
+    if torch.cuda.is_available():
+        # torch reports a buffer as page-locked (and copies from it asynchronously) only once its own
+        # CUDA state is initialised
+        torch.cuda.init()
     shape = tuple(int(x) for x in (shape if isinstance(shape, (tuple, list)) else (shape,)))
     count = 1
     for x in shape:

@@ -1,5 +1,6 @@
 // Device helpers shared by the library's kernels (bounded waits on the
-// post-addition ordering counters, integer-pipe sign flips).
+// post-addition ordering counters, integer-pipe sign flips, the balanced walk
+// over matrix positions).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,6 +46,33 @@ __device__ __forceinline__ bool chain_wait(const unsigned *ctr, unsigned target,
 __device__ __forceinline__ double neg(double v) {
     return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL);
 }
+
+// The positions (c, y, x) of matrices of side b, walked in the linear order
+// c b^2 + y b + x: each thread starts at its global index and advances by the
+// grid's thread count, whose split into
+// (dc, dy, dx) is taken once, so the loop needs no division.  Every thread
+// gets the same number of positions (to within one), and a warp's positions
+// are consecutive in x, so loads and stores stay coalesced.
+struct PosWalk {
+    long long c, y, x, dc, dy, dx, b;
+    __device__ PosWalk(long long b_, long long bb) : b(b_) {
+        const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const long long G = (long long)gridDim.x * blockDim.x;
+        c = i / bb;
+        y = (i - c * bb) / b;
+        x = i - c * bb - y * b;
+        dc = G / bb;
+        dy = (G - dc * bb) / b;
+        dx = G - dc * bb - dy * b;
+    }
+    __device__ __forceinline__ void next() {
+        x += dx;
+        if (x >= b) { x -= b; ++y; }
+        y += dy;
+        if (y >= b) { y -= b; ++c; }
+        c += dc;
+    }
+};
 
 }  // namespace dev
 }  // namespace fmm

@@ -31,7 +31,8 @@ namespace fmm {
 namespace {
 
 // Tile configurations (template parameter BNT): BM = 128 rows by BNT = 128
-// or 64 columns, NT = 2 * BNT threads (2 x BNT/32 warps, warp tile 64 x 32).
+// or 64 columns, NT = 2 * BNT threads (2 x BNT/32 warps, 4 x 4 m16 x n8
+// sub-tiles each, interleaved over the tile).
 // The 128-column tile runs one CTA per SM; the 64-column tile fits two, so
 // one CTA's prologue and epilogue overlap the other's MMAs.
 constexpr int BM = kBM, BK = kBK;
@@ -289,6 +290,17 @@ __device__ __forceinline__ void store_slab(Smem<BNT> &S, int buf, const double (
     }
 }
 
+// Warp tiling: the 128 x BNT tile is split into m16 x n8 sub-tiles, and warp
+// (wm, wn) of the 2 x BNT/32 warps takes sub-tile rows i = 0..3 at 16 (2 i + wm)
+// and columns j = 0..3 at 8 (BNT/32 j + wn), interleaved rather than as one
+// 64 x 32 block, so that the valid part of a ragged tile (a leaf side that is
+// not a multiple of the tile) is spread over all warps: the task takes as long
+// as its busiest warp.
+template <int BNT>
+__device__ __forceinline__ int sub_row(int wm, int i) { return 16 * (2 * i + wm); }
+template <int BNT>
+__device__ __forceinline__ int sub_col(int wn, int j) { return 8 * ((BNT / 32) * j + wn); }
+
 // One K slab of MMAs.  m16 x n8 sub-tiles that lie entirely outside the
 // valid rows / columns of a ragged tile are skipped (row_ok / col_ok are
 // uniform across the warp): the FP64 pipe is shared by the SM's warps, so the
@@ -299,7 +311,7 @@ __device__ __forceinline__ void mma_slab(const Smem<BNT> &S, int buf, double (&a
     constexpr int B_LD = BNT + 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int wm = warp & 1, wn = warp >> 1;  // 2 x BNT/32 warps, warp tile 64 x 32
+    const int wm = warp & 1, wn = warp >> 1;  // 2 x BNT/32 warps, 4 x 4 interleaved sub-tiles each
     const double *As = S.a[buf];
     const double *Bs = S.b[buf];
 #pragma unroll
@@ -307,12 +319,12 @@ __device__ __forceinline__ void mma_slab(const Smem<BNT> &S, int buf, double (&a
         double af[4][2], bf[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int row = wm * 64 + i * 16 + g;
+            const int row = sub_row<BNT>(wm, i) + g;
             af[i][0] = As[row * A_LD + kq * 4 + t];
             af[i][1] = As[(row + 8) * A_LD + kq * 4 + t];
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bf[j] = Bs[(kq * 4 + t) * B_LD + wn * 32 + j * 8 + g];
+        for (int j = 0; j < 4; ++j) bf[j] = Bs[(kq * 4 + t) * B_LD + sub_col<BNT>(wn, j) + g];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -400,8 +412,8 @@ __global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __gri
         unsigned row_ok = 0, col_ok = 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            row_ok |= (unsigned)(wm * 64 + i * 16 < S.rows) << i;
-            col_ok |= (unsigned)(wn * 32 + i * 8 < S.cols) << i;
+            row_ok |= (unsigned)(sub_row<BNT>(wm, i) < S.rows) << i;
+            col_ok |= (unsigned)(sub_col<BNT>(wn, i) < S.cols) << i;
         }
         double ra[1024 / BNT], rb[8];
         if (nk > 0) {
@@ -457,8 +469,8 @@ __global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __gri
                     for (int j = 0; j < 4; ++j)
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            const int row = wm * 64 + i * 16 + g + 8 * h;
-                            const int col = wn * 32 + j * 8 + 2 * t4;
+                            const int row = sub_row<BNT>(wm, i) + g + 8 * h;
+                            const int col = sub_col<BNT>(wn, j) + 2 * t4;
                             const double *p = dst.ptr + row * ldc + col;
                             o[j][h][0] = o[j][h][1] = 0.0;
                             if (row >= rows || col >= cols) continue;
@@ -485,8 +497,8 @@ __global__ void __launch_bounds__(2 * BNT, 128 / BNT) fmm_f64_kernel(const __gri
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const int row = wm * 64 + i * 16 + g + 8 * h;
-                        const int col = wn * 32 + j * 8 + 2 * t4;
+                        const int row = sub_row<BNT>(wm, i) + g + 8 * h;
+                        const int col = sub_col<BNT>(wn, j) + 2 * t4;
                         if (row >= rows || col >= cols) continue;
                         double *p = dst.ptr + row * ldc + col;
                         double out[2];

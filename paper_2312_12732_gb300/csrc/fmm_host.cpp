@@ -374,6 +374,10 @@ struct fmm_plan {
     double *d_pout = nullptr;                           // [R][m][m] leaf products of the tcgen05 engines
     const int *d_wl_ptr = nullptr;                      // per C block: products (r, coefficient) in ascending r
     const int2 *d_wl_ent = nullptr;
+    // post-additions level by level (two levels of a 2 x 2 algorithm): inner W rows, outer W columns
+    bool post_two_steps = false, post_unit_inner = false;
+    const int *d_wi_ptr = nullptr, *d_wo_ptr = nullptr;
+    const int4 *d_wi_ent = nullptr, *d_wo_ent = nullptr;
     double flops_lowp = 0;
     // host-buffer path: device copies of the operands, a stream for B's copy and its events
     double *d_hostA = nullptr, *d_hostB = nullptr, *d_hostC = nullptr;
@@ -928,6 +932,43 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         }
     }
 
+    // The emulated leaf's post-additions level by level when the plan is two levels of a 2 x 2 algorithm
+    // with at most 8 products: rows q of W as {r2, coefficient as a double's low and high word} (inner
+    // level) and columns r1 of W as {l1, coefficient, first term of row l1} (outer level), both ascending.
+    std::vector<int> wi_ptr, wo_ptr;
+    std::vector<int4> wi_ent, wo_ent;
+    const char *post_env = std::getenv("FMM_OZAKI_POSTADD");
+    bool two_step_post = dtype == FMM_F64_OZAKI && depth == 2 && algo->p == 2 && algo->R <= 8 && shards == 1 &&
+                         !(post_env && std::string(post_env) == "flat");
+    bool unit_inner = true;
+    if (two_step_post) {
+        const int R = algo->R;
+        wi_ptr.assign(5, 0);
+        int first_r[4] = {-1, -1, -1, -1};
+        for (int q = 0; q < 4; ++q) {
+            for (int r = 0; r < R; ++r) {
+                const int c = algo->W[q * R + r];
+                if (c == 0) continue;
+                const double d = (double)c;
+                unsigned long long bits = 0;
+                std::memcpy(&bits, &d, sizeof bits);
+                wi_ent.push_back(make_int4(r, (int)(unsigned)(bits & 0xffffffffULL), (int)(unsigned)(bits >> 32), 0));
+                if (c != 1 && c != -1) unit_inner = false;
+                if (first_r[q] < 0) first_r[q] = r;
+            }
+            wi_ptr[q + 1] = (int)wi_ent.size();
+            if (first_r[q] < 0) two_step_post = false;  // an all-zero row of W: use the flattened form
+        }
+        wo_ptr.assign((size_t)R + 1, 0);
+        for (int r = 0; r < R; ++r) {
+            for (int l1 = 0; l1 < 4; ++l1) {
+                const int c = algo->W[l1 * R + r];
+                if (c != 0) wo_ent.push_back(make_int4(l1, c, first_r[l1] == r ? 1 : 0, 0));
+            }
+            wo_ptr[r + 1] = (int)wo_ent.size();
+        }
+    }
+
     // Task counts.
     const long long tiles = (long long)pl->tiles_m * pl->tiles_n;
     const long long q = n - pl->n_core;
@@ -992,6 +1033,10 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     const size_t o_wrow = reserve(w_row.size() * sizeof(int));
     const size_t o_wlptr = reserve(wl_ptr.size() * sizeof(int));
     const size_t o_wlent = reserve(std::max<size_t>(1, wl_ent.size()) * sizeof(int2));
+    const size_t o_wiptr = reserve(std::max<size_t>(1, wi_ptr.size()) * sizeof(int));
+    const size_t o_wient = reserve(std::max<size_t>(1, wi_ent.size()) * sizeof(int4));
+    const size_t o_woptr = reserve(std::max<size_t>(1, wo_ptr.size()) * sizeof(int));
+    const size_t o_woent = reserve(std::max<size_t>(1, wo_ent.size()) * sizeof(int4));
     std::vector<size_t> o_st(4 * steps.size());
     for (size_t k = 0; k < steps.size(); ++k) {
         o_st[4 * k] = reserve(st_uptr[k].size() * sizeof(int));
@@ -1014,6 +1059,12 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     g.w_row_nnz = (const int *)(base + o_wrow);
     pl->d_wl_ptr = (const int *)(base + o_wlptr);
     pl->d_wl_ent = (const int2 *)(base + o_wlent);
+    pl->post_two_steps = two_step_post;
+    pl->post_unit_inner = unit_inner;
+    pl->d_wi_ptr = (const int *)(base + o_wiptr);
+    pl->d_wi_ent = (const int4 *)(base + o_wient);
+    pl->d_wo_ptr = (const int *)(base + o_woptr);
+    pl->d_wo_ent = (const int4 *)(base + o_woent);
     std::vector<char> host(pl->tables_bytes, 0);
     auto put = [&](size_t o2, const void *src, size_t bytes) { if (bytes) std::memcpy(host.data() + o2, src, bytes); };
     put(o_uptr, u_ptr.data(), u_ptr.size() * sizeof(int));
@@ -1025,6 +1076,10 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     put(o_wrow, w_row.data(), w_row.size() * sizeof(int));
     put(o_wlptr, wl_ptr.data(), wl_ptr.size() * sizeof(int));
     put(o_wlent, wl_ent.data(), wl_ent.size() * sizeof(int2));
+    put(o_wiptr, wi_ptr.data(), wi_ptr.size() * sizeof(int));
+    put(o_wient, wi_ent.data(), wi_ent.size() * sizeof(int4));
+    put(o_woptr, wo_ptr.data(), wo_ptr.size() * sizeof(int));
+    put(o_woent, wo_ent.data(), wo_ent.size() * sizeof(int4));
     for (size_t k = 0; k < steps.size(); ++k) {
         put(o_st[4 * k], st_uptr[k].data(), st_uptr[k].size() * sizeof(int));
         put(o_st[4 * k + 1], st_uent[k].data(), st_uent[k].size() * sizeof(int4));
@@ -1401,11 +1456,18 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
         if (fmm::launch_ozaki_gemm(P, grid < 1 ? 1 : grid, st) != cudaSuccess) return FMM_ERR_CUDA;
     }
     if (pl->ev[2] && cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
-    if (pl->oz_engine >= 1 &&
-        fmm::launch_ozaki_postadd(pl->d_pout, m, (int)pl->P, pl->d_wl_ptr, pl->d_wl_ent, C, pl->n, pl->d_chain,
-                                  pl->geom.w_row_nnz, pl->tiles_m * pl->tiles_n, alpha * pl->wscale, beta,
-                                  st) != cudaSuccess)
-        return FMM_ERR_CUDA;
+    if (pl->oz_engine >= 1) {
+        const cudaError_t e =
+            pl->post_two_steps
+                ? fmm::launch_ozaki_postadd_two_steps(pl->d_pout, m, pl->R, pl->R, pl->d_wi_ptr, pl->d_wi_ent,
+                                                      pl->d_wo_ptr, pl->d_wo_ent, C, pl->n, pl->d_chain,
+                                                      pl->geom.w_row_nnz, pl->tiles_m * pl->tiles_n,
+                                                      alpha * pl->wscale, beta, pl->post_unit_inner, st)
+                : fmm::launch_ozaki_postadd(pl->d_pout, m, (int)pl->P, pl->d_wl_ptr, pl->d_wl_ent, C, pl->n,
+                                            pl->d_chain, pl->geom.w_row_nnz, pl->tiles_m * pl->tiles_n,
+                                            alpha * pl->wscale, beta, st);
+        if (e != cudaSuccess) return FMM_ERR_CUDA;
+    }
     if (pl->ev[5] && cudaEventRecord(pl->ev[5], st) != cudaSuccess) return FMM_ERR_CUDA;
     const long long peel = pl->geom.tasks_right + pl->geom.tasks_bottom + pl->geom.tasks_rankq;
     if (peel > 0) {

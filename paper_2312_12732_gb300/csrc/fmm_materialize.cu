@@ -20,6 +20,8 @@
 namespace fmm {
 namespace {
 
+using dev::PosWalk;
+
 // entry {block row, block col, low word, high word of the coefficient as a double}
 __device__ __forceinline__ double coef_of(const int4 &en) { return __hiloint2double(en.w, en.z); }
 
@@ -31,33 +33,6 @@ __device__ __forceinline__ double first_term(double v, const int4 &en) {
     }
     return coef_of(en) * v;
 }
-
-// The output positions (c, y, x) of n_in input matrices with b x b output
-// blocks, walked in the linear order c b^2 + y b + x: each thread starts at its
-// global index and advances by the grid's thread count, whose split into
-// (dc, dy, dx) is taken once, so the loop needs no division.  Every thread
-// gets the same number of positions (to within one), and a warp's positions
-// are consecutive in x, so loads and stores stay coalesced.
-struct PosWalk {
-    long long c, y, x, dc, dy, dx, b;
-    __device__ PosWalk(long long b_, long long bb) : b(b_) {
-        const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        const long long G = (long long)gridDim.x * blockDim.x;
-        c = i / bb;
-        y = (i - c * bb) / b;
-        x = i - c * bb - y * b;
-        dc = G / bb;
-        dy = (G - dc * bb) / b;
-        dx = G - dc * bb - dy * b;
-    }
-    __device__ __forceinline__ void next() {
-        x += dx;
-        if (x >= b) { x -= b; ++y; }
-        y += dy;
-        if (y >= b) { y -= b; ++c; }
-        c += dc;
-    }
-};
 
 // One materialized recursion level: all R outputs of a position are formed
 // from the p^2 inputs.

@@ -125,3 +125,34 @@ def test_every_slice_gemm_engine(fmm, oracle_mod, monkeypatch, engine, name, dep
     A, B = inputs.operands(n, "uniform", seed=n)
     rows, cols, ref = ref_entries(oracle_mod, A, B)
     assert nerr(run(fmm, plan, A, B)[rows, cols], ref, A, B) <= 1e-13
+
+
+@pytest.mark.parametrize("name,n", [("strassen", 1030), ("winograd", 1024)])
+def test_post_additions_level_by_level_and_flattened(fmm, oracle_mod, monkeypatch, name, n):
+    """Two levels of a 2 x 2 algorithm: the post-additions run level by level (each leaf product read
+    once, the inner sums forming the outer products' blocks, as the recursion of Section 2 defines them)
+    unless FMM_OZAKI_POSTADD=flat asks for the flattened sums.  Both are bit-exact on integers, with and
+    without alpha and beta, at a peeled size (1030 = 4 * 257 + 2), and within the depth-2 tolerance of the
+    oracle's Dot2 entries on real inputs; they differ only by the rounding of the sums' association."""
+    algo = fmm.fmm_algo_builtin(name)
+    monkeypatch.delenv("FMM_OZAKI_POSTADD", raising=False)
+    level = fmm.fmm_plan_create(n, algo, 2, dtype="f64_ozaki")
+    monkeypatch.setenv("FMM_OZAKI_POSTADD", "flat")
+    flat = fmm.fmm_plan_create(n, algo, 2, dtype="f64_ozaki")
+    monkeypatch.delenv("FMM_OZAKI_POSTADD")
+    A, B = inputs.operands(n, "integer", seed=n)
+    C0 = inputs.matrix(n, "integer", seed=n + 1)
+    AB = oracle_mod.classic(A, B)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    for alpha, beta in [(1.0, 0.0), (-2.0, 3.0), (0.5, 1.0)]:
+        for plan in (level, flat):
+            dC = torch.from_numpy(C0.copy()).cuda()
+            fmm.fmm_gemm_ex(plan, alpha, dA, dB, beta, dC)
+            assert fmm.fmm_sync_status(plan) == 0
+            assert np.array_equal(dC.cpu().numpy(), oracle_mod.axpby(alpha, AB, beta, C0)), (alpha, beta)
+    A, B = inputs.operands(n, "uniform", seed=n + 2)
+    rows, cols, ref = ref_entries(oracle_mod, A, B)
+    C_level, C_flat = run(fmm, level, A, B), run(fmm, flat, A, B)
+    assert nerr(C_level[rows, cols], ref, A, B) <= 1e-13
+    assert nerr(C_flat[rows, cols], ref, A, B) <= 1e-13
+    assert nerr(C_level, C_flat, A, B) <= 1e-15
