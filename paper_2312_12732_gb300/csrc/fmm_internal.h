@@ -110,6 +110,7 @@ struct OzParams {
     int Mp, Kp;               // padded to multiples of 128
     int s;                    // slices per operand
     int L;                    // right shift keeping the int64 recombination in range
+    int kparts;               // CTA-pair engine: K pieces per slice pair, each a diagonal group of its own
     int tiles_m, tiles_n;
     int R;                    // leaf products
     int P;                    // C blocks per side

@@ -190,7 +190,7 @@ __device__ __forceinline__ double ldexp_i64_rn(long long v, int e) {
 // its groups are still drained.  Returns false when the CTA must stop.
 template <int EW0, class Release>
 __device__ __forceinline__ bool epilogue_tile(const OzParams &P, unsigned long long *accfull, volatile int *abort,
-                                              uint32_t tmem, int r, int ti, int tj, bool emit, int G0,
+                                              uint32_t tmem, int r, int ti, int tj, bool emit, int G0, int H,
                                               Release release) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int e = warp - EW0;            // 0..7
@@ -202,9 +202,11 @@ __device__ __forceinline__ bool epilogue_tile(const OzParams &P, unsigned long l
     long long acc[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) acc[j] = 0;
-    for (int g = 2; g <= s + 1; ++g) {
-        // global group index G0 + g - 2 selects the accumulator and its use parity
-        const int G = G0 + g - 2;
+    for (int V = 0; V < H * s; ++V) {
+        // group V of the task is diagonal g over K piece V / s; the global group index G0 + V selects
+        // the accumulator and its use parity
+        const int g = 2 + V % s;
+        const int G = G0 + V;
         const uint32_t buf = (uint32_t)(G % NBUF), bphase = (uint32_t)((G / NBUF) & 1);
         if (!mbar_wait(&accfull[buf], bphase, abort, P.error, P.timeout_ns)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int r = (int)(task / tiles);
             const int t = (int)(task - (long long)r * tiles);
             const int ti = t / P.tiles_n, tj = t - ti * P.tiles_n;
-            if (!epilogue_tile<EPI_WARP0>(P, B.accfull, abort, tmem, r, ti, tj, true, tseq * s,
+            if (!epilogue_tile<EPI_WARP0>(P, B.accfull, abort, tmem, r, ti, tj, true, tseq * s, 1,
                                           [&](uint32_t b) { mbar_arrive(&B.accempty[b]); }))
                 break;
             ++tseq;
@@ -647,6 +649,9 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
     const int nbox = P.Kp / BOX;
     const int nkb = (nbox + P_KBOX - 1) / P_KBOX;
     const int s = P.s;
+    // K pieces per slice pair: each piece of each diagonal is a group of its own, so a task streams
+    // 1/H of its slice panels at a time (a smaller working set in L2); the host keeps H <= nkb
+    const int H = P.kparts < 1 ? 1 : (P.kparts > nkb ? nkb : P.kparts);
 
     if (tid == 0) {
         for (int q = 0; q < NRING; ++q)
@@ -735,10 +740,12 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                 const int tj = 2 * (t2 - tp * tn2) + (int)(item & 1);
                 const int ti = 2 * tp + rp;
                 bool ok = true;
-                for (int g = 2; g <= s + 1 && ok; ++g) {
-                    if (ring_of_group(tseq * s + g - 2) != q) continue;
+                for (int V = 0; V < H * s && ok; ++V) {
+                    if (ring_of_group(tseq * H * s + V) != q) continue;
+                    const int g = 2 + V % s, kh = V / s;
+                    const int kb0 = kh * nkb / H, kb1 = (kh + 1) * nkb / H;
                     for (int ta = max(1, g - s); ta <= min(s, g - 1) && ok; ++ta)
-                        for (int kb = 0; kb < nkb; ++kb) {
+                        for (int kb = kb0; kb < kb1; ++kb) {
                             if (!mbar_wait(&B.empty[q][stage], sphase ^ 1u, abort, P.error, P.timeout_ns)) {
                                 ok = false;
                                 break;
@@ -793,9 +800,11 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                 }
                 if (task >= P.tasks) break;
                 bool ok = true;
-                for (int g = 2; g <= s + 1 && ok; ++g) {
-                    const int G = tseq * s + g - 2;
+                for (int V = 0; V < H * s && ok; ++V) {
+                    const int G = tseq * H * s + V;
                     if (ring_of_group(G) != q) continue;
+                    const int g = 2 + V % s, kh = V / s;
+                    const int kb0 = kh * nkb / H, kb1 = (kh + 1) * nkb / H;
                     const uint32_t buf = (uint32_t)(G % NBUF), bphase = (uint32_t)((G / NBUF) & 1);
                     if (!mbar_wait(&B.accempty[buf], bphase ^ 1u, abort, P.error, P.timeout_ns)) {
                         ok = false;
@@ -805,7 +814,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
                     const uint32_t dtm = tmem + buf * TN;
                     bool first = true;
                     for (int ta = max(1, g - s); ta <= min(s, g - 1) && ok; ++ta)
-                        for (int kb = 0; kb < nkb; ++kb) {
+                        for (int kb = kb0; kb < kb1; ++kb) {
                             if (!mbar_wait(&B.full[q][stage], sphase, abort, P.error, P.timeout_ns)) {
                                 ok = false;
                                 break;
@@ -869,7 +878,7 @@ __global__ void __launch_bounds__(P_NTHREADS, 1)
             const int tj = 2 * (t2 - tp * tn2) + (int)(item & 1);
             const int ti = 2 * tp + rp;
             if (!epilogue_tile<P_EPI_WARP0>(P, B.accfull, abort, tmem, r, ti, tj, ti < P.tiles_m && tj < P.tiles_n,
-                                            tseq * s, [&](uint32_t b) {
+                                            tseq * H * s, H, [&](uint32_t b) {
                                                 if (lead) mbar_arrive(&B.accempty[b]);
                                                 else arrive_remote_relaxed(mapa(su32(&B.accempty[b]), pair_lead));
                                             }))
