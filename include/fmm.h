@@ -47,8 +47,8 @@
  *                    plan creation).
  *   FMM_OZAKI_KPARTS k (1..8): the CTA-pair slice GEMM of FMM_F64_OZAKI plans
  *                    splits each slice pair's K range into k pieces, each
- *                    accumulated on its own (default 2 from K = 1024 up, else
- *                    1; read at plan creation).
+ *                    accumulated on its own (default K / 1024 pieces, at least
+ *                    1 and at most 4; read at plan creation).
  *   FMM_FORCE_DEPTH  d: fmm_autotune times only depth-d candidates.
  */
 #ifndef FMM_H_

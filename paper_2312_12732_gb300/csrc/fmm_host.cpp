@@ -1198,9 +1198,11 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         const char *eng = std::getenv("FMM_OZAKI_ENGINE");
         const std::string es = eng ? eng : "";
         pl->oz_engine = es == "mma_sync" ? 0 : (es == "tc1" ? 1 : 2);
-        // K pieces of the CTA-pair slice GEMM: two from K = 1024 up (at n = 8192, Strassen depth 2 the
-        // kernel's DRAM reads fell by 57 % and its time by 2 %; four pieces read no less and ran slower)
-        pl->oz_kparts = pl->oz_Mp >= 1024 ? 2 : 1;
+        // K pieces of the CTA-pair slice GEMM, about 1024 of K each, at most four.  Measured leaf times
+        // for one / two / four pieces: K = 1024 2.51 / 2.66 / 3.10 ms (n = 4096, Strassen depth 2),
+        // K = 2048 19.08 / 18.81 / 19.62 ms (n = 8192, depth 2; DRAM reads 57 % lower with two),
+        // K = 4096 24.13 / 23.34 / 23.07 ms (n = 8192, depth 1)
+        pl->oz_kparts = (int)std::max<int64_t>(1, std::min<int64_t>(4, pl->oz_Mp / 1024));
         if (const char *kp = std::getenv("FMM_OZAKI_KPARTS")) pl->oz_kparts = std::max(1, std::min(8, std::atoi(kp)));
         if (pl->oz_engine == 2 && fmm::ozaki_tc_max_pairs() < 1) pl->oz_engine = 1;
         const unsigned long long srows = (unsigned long long)Rt * oz_s * pl->oz_Mp;
