@@ -156,3 +156,25 @@ def test_post_additions_level_by_level_and_flattened(fmm, oracle_mod, monkeypatc
     assert nerr(C_level[rows, cols], ref, A, B) <= 1e-13
     assert nerr(C_flat[rows, cols], ref, A, B) <= 1e-13
     assert nerr(C_level, C_flat, A, B) <= 1e-15
+
+
+@pytest.mark.parametrize("kparts", [1, 2, 3, 4])
+def test_slice_gemm_k_pieces(fmm, oracle_mod, monkeypatch, kparts):
+    """The CTA-pair slice GEMM may take each slice pair's K range in pieces, each accumulated in TMEM and
+    folded into the int64 sums on its own (FMM_OZAKI_KPARTS, read at plan creation; the default is about
+    one piece per 1024 of K).  At n = 2051 (Strassen depth 1, leaf 1025 after peeling, K padded to 9
+    stages of 128) two and four pieces are uneven; every piece count gives the exact product on integers
+    and stays within the depth-1 tolerance of the oracle and within 2x of the FP64 path's error on real
+    inputs."""
+    monkeypatch.setenv("FMM_OZAKI_KPARTS", str(kparts))
+    algo = fmm.fmm_algo_builtin("strassen")
+    n = 2 * 1024 + 3
+    plan = fmm.fmm_plan_create(n, algo, 1, dtype="f64_ozaki")
+    monkeypatch.delenv("FMM_OZAKI_KPARTS")
+    A, B = inputs.operands(n, "integer", seed=kparts)
+    assert np.array_equal(run(fmm, plan, A, B), oracle_mod.classic(A, B))
+    A, B = inputs.operands(n, "uniform", seed=10 + kparts)
+    rows, cols, ref = ref_entries(oracle_mod, A, B)
+    e_oz = nerr(run(fmm, plan, A, B)[rows, cols], ref, A, B)
+    e_64 = nerr(run(fmm, fmm.fmm_plan_create(n, algo, 1), A, B)[rows, cols], ref, A, B)
+    assert e_oz <= 1e-13 and e_oz <= 2.0 * e_64, (e_oz, e_64)
