@@ -354,6 +354,13 @@ def ozaki_launches(passes: int, peeled: bool) -> int:
     return 2 * passes + 4 + (1 if peeled else 0)
 
 
+def f64_launches(info: dict, peeled: bool) -> int:
+    """Kernels of one FP64 call: each materialization pass for both operands, the leaf kernel and, when
+    the plan stores its leaf products, the post-addition passes and (for peeled sizes) the rank-q launch."""
+    passes = info.get("post_passes", 0)
+    return 1 + 2 * info["materialize_passes"] + passes + (1 if peeled and passes else 0)
+
+
 def materialized_bytes(n_core: int, p: int, R_total: int, depth: int, levels: int) -> float:
     """Algorithmic HBM bytes of the materialized pre-additions of both operands: level l reads the
     R^(l-1) blocks of side n_core/p^(l-1) once and writes R^l blocks of side n_core/p^l."""
@@ -899,7 +906,7 @@ def run_ours(a):
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": a.steps * ozaki_launches(info["materialize_passes"], q > 0) if a.dtype == "f64_ozaki"
-        else a.steps * (1 + 2 * info["materialize_passes"]),
+        else a.steps * f64_launches(info, q > 0),
         "roofline": roofline,
         "emulated_fp64": emulated,
         "batched": batched,

@@ -49,6 +49,9 @@
  *                    splits each slice pair's K range into k pieces, each
  *                    accumulated on its own (default K / 1024 pieces, at least
  *                    1 and at most 4; read at plan creation).
+ *   FMM_F64_POSTADD  fused or levels: the post-additions of an FMM_F64 plan
+ *                    whose options leave them to the planner (see
+ *                    fmm_plan_options_t.post_additions; read at plan creation).
  *   FMM_FORCE_DEPTH  d: fmm_autotune times only depth-d candidates.
  */
 #ifndef FMM_H_
@@ -170,6 +173,27 @@ typedef struct {
      * shard_index outside [0, shard_count). */
     int shard_count;
     int shard_index;
+    /* FMM_F64 post-additions (Section 2: C_l = sum_r W[l][r] P_r, or level by
+     * level as the recursion forms the blocks):
+     *   0 -- the planner's choice (FMM_F64_POSTADD=fused or levels overrides it):
+     *        stored when the fused form's adds, (nnz(W flattened) - p^(2 depth)) m^2,
+     *        reach 0.4 % of the leaf flops 2 R^depth m^3 and the buffers take at
+     *        most a quarter of the free device memory, fused otherwise;
+     *   1 -- fused into the leaf kernel's epilogue: each leaf tile is added into
+     *        every C block of its W column, in ascending product order;
+     *   2 -- stored: each leaf product P_r is written once to plan workspace
+     *        (R^depth m^2 doubles, plus an intermediate buffer), then separate
+     *        passes sum W's Kronecker factors level by level, innermost first
+     *        (two 2 x 2 factors per pass where both have at most 8 products),
+     *        the last pass writing C = alpha sum + beta C; a non-divisible n's
+     *        rank-q fix-ups run after it.  Fewer FP64 operations than the fused
+     *        sums (for Strassen at depth d, 12^d - 4^d adds per position of a
+     *        leaf block become 8 (7^d - 4^d) / 3: 20480 and 5720 at depth 4),
+     *        and no ordering waits.  FMM_ERR_UNSUPPORTED with
+     *        shard_count > 1, debug_poison_chain, or a factor of W wider than
+     *        8 x 8 blocks; ignored at depth 0 and for other dtypes.
+     * Batched launches always use the fused epilogue. */
+    int post_additions;
 } fmm_plan_options_t;
 
 /* Read-only description of a plan (all sizes in elements). */
@@ -193,6 +217,7 @@ typedef struct {
     double coef_scale;      /* (den_u den_v den_w)^-depth for a rational plan, 1 otherwise */
     int64_t product_begin;  /* leaf products [product_begin, product_end) of this plan's shard */
     int64_t product_end;    /* (0 and R_total for an unsharded plan) */
+    int post_passes;        /* FMM_F64 with stored leaf products: post-addition passes (0: fused) */
 } fmm_plan_info_t;
 
 /* The contiguous range [*begin, *end) of `units` work units that shard

@@ -25,6 +25,7 @@ FMM_SCHED_AUTO, FMM_SCHED_FUSED, FMM_SCHED_HYBRID = 0, 1, 2
 DTYPES = {"f64": FMM_F64, "f64_ozaki": FMM_F64_OZAKI, "c128": FMM_C128, "c128_3m": FMM_C128_3M, "f32": FMM_F32}
 COMPLEX_DTYPES = ("c128", "c128_3m")
 SCHEDULES = {"auto": FMM_SCHED_AUTO, "fused": FMM_SCHED_FUSED, "hybrid": FMM_SCHED_HYBRID}
+POST_ADDITIONS = {"auto": 0, "fused": 1, "levels": 2}
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 
@@ -47,7 +48,7 @@ class fmm_plan_options_t(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int), ("materialize_levels", ctypes.c_int), ("ozaki_slices", ctypes.c_int),
                 ("wait_timeout_s", ctypes.c_double), ("debug_poison_chain", ctypes.c_int),
                 ("record_kernel_time", ctypes.c_int), ("tile_n", ctypes.c_int), ("shard_count", ctypes.c_int),
-                ("shard_index", ctypes.c_int)]
+                ("shard_index", ctypes.c_int), ("post_additions", ctypes.c_int)]
 
 
 class fmm_plan_info_t(ctypes.Structure):
@@ -57,7 +58,7 @@ class fmm_plan_info_t(ctypes.Structure):
                 ("flops_leaf", ctypes.c_double), ("flops_executed", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_size_t), ("ozaki_slices", ctypes.c_int), ("flops_lowp", ctypes.c_double),
                 ("tile_n", ctypes.c_int), ("materialize_passes", ctypes.c_int), ("coef_scale", ctypes.c_double),
-                ("product_begin", ctypes.c_int64), ("product_end", ctypes.c_int64)]
+                ("product_begin", ctypes.c_int64), ("product_end", ctypes.c_int64), ("post_passes", ctypes.c_int)]
 
 
 # (name, restype, argtypes) for every symbol declared in include/fmm.h.
@@ -382,15 +383,16 @@ class Plan:
 def fmm_plan_create(n: int, algo: Algo, depth: int, dtype: str = "f64", schedule: str = "auto",
                     materialize_levels: int = 0, ozaki_slices: int = 0, wait_timeout_s: float = 0.0,
                     debug_poison_chain: int = 0, record_kernel_time: bool = False, tile_n: int = 0,
-                    shard_count: int = 0, shard_index: int = 0) -> Plan:
+                    shard_count: int = 0, shard_index: int = 0, post_additions: str = "auto") -> Plan:
     """A plan for ``algo`` (an :class:`Algo`, or a :class:`RationalAlgo` through
     fmm_plan_create_rational) with the given options; ``shard_count`` > 1 makes it compute shard
-    ``shard_index`` of the leaf products only (see fmm_plan_options_t)."""
+    ``shard_index`` of the leaf products only; ``post_additions`` is "auto", "fused" or "levels"
+    (see fmm_plan_options_t)."""
     h = ctypes.c_void_p()
     a = algo.c_struct()
     opts = fmm_plan_options_t(SCHEDULES[schedule], int(materialize_levels), int(ozaki_slices),
                               float(wait_timeout_s), int(debug_poison_chain), int(bool(record_kernel_time)),
-                              int(tile_n), int(shard_count), int(shard_index))
+                              int(tile_n), int(shard_count), int(shard_index), POST_ADDITIONS[post_additions])
     create = lib().fmm_plan_create_rational if isinstance(algo, RationalAlgo) else lib().fmm_plan_create_ex
     _check(create(ctypes.byref(h), int(n), ctypes.byref(a), int(depth), DTYPES[dtype], ctypes.byref(opts)),
            f"fmm_plan_create(n={n}, {algo}, depth={depth})")

@@ -113,7 +113,9 @@ __device__ void setup_task(Smem<BNT> &S, const F64Problem &pr, const F64Geom &g,
         const double *SB = pr.SB + (long long)sub * g.sub_stride_b;
         const int ua = g.u_ptr[r], nA = g.u_ptr[r + 1] - ua;
         const int vb = g.v_ptr[r], nB = g.v_ptr[r + 1] - vb;
-        const int wc = g.w_ptr[rglob], nD = g.w_ptr[rglob + 1] - wc;
+        const int wc = g.w_ptr[rglob];
+        // stored products: one destination, P_r itself (coefficient 1, alpha 1, beta 0)
+        const int nD = g.pout != nullptr ? 1 : g.w_ptr[rglob + 1] - wc;
         for (int e = tid; e < nA; e += NT) {
             const int2 en = g.u_ent[ua + e];
             const long long br = en.x / g.P_src, bc = en.x % g.P_src;
@@ -125,6 +127,22 @@ __device__ void setup_task(Smem<BNT> &S, const F64Problem &pr, const F64Geom &g,
             const long long br = en.x / g.P_src, bc = en.x % g.P_src;
             S.srcB[e].ptr = SB + (br * m) * g.ld_src_b + bc * m + (long long)tj * BN;
             S.srcB[e].coef = en.y;
+        }
+        if (g.pout != nullptr) {
+            if (tid == 0) {
+                S.dst[0].ptr = g.pout + (long long)rglob * (m * m) + (long long)ti * BM * m + (long long)tj * BN;
+                S.dst[0].chain = nullptr;
+                S.dst[0].coef = 1;
+                S.dst[0].pos = 0;
+                S.done[0] = 0;
+                S.nA = nA; S.nB = nB; S.nD = 1;
+                S.lda = g.ld_src_a; S.ldb = g.ld_src_b; S.ldc = m;
+                S.rows = (int)lmin(BM, m - (long long)ti * BM);
+                S.cols = (int)lmin(BN, m - (long long)tj * BN);
+                S.K = (int)m;
+                S.alpha = 1.0; S.beta = 0.0;
+            }
+            return;
         }
         for (int e = tid; e < nD; e += NT) {
             const int4 en = g.w_ent[wc + e];
@@ -186,8 +204,8 @@ __device__ void setup_task(Smem<BNT> &S, const F64Problem &pr, const F64Geom &g,
         S.srcA[0].ptr = pr.A + row0 * n + nc;
         S.srcB[0].ptr = pr.B + nc * n + col0;
         S.dst[0].ptr = pr.C + row0 * n + col0;
-        S.dst[0].chain = pr.chain + (long long)l * tiles + t;
-        S.dst[0].pos = g.w_row_nnz[l];
+        S.dst[0].chain = g.rankq_free ? nullptr : pr.chain + (long long)l * tiles + t;
+        S.dst[0].pos = g.w_row_nnz[l];  // > 0: added into C, after the core contributions
         S.rows = (int)lmin(BM, m - (long long)ti * BM);
         S.cols = (int)lmin(BN, m - (long long)tj * BN);
         S.K = (int)q;

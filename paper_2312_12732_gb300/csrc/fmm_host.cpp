@@ -379,6 +379,15 @@ struct fmm_plan {
     const int *d_wi_ptr = nullptr, *d_wo_ptr = nullptr;
     const int4 *d_wi_ent = nullptr, *d_wo_ent = nullptr;
     double flops_lowp = 0;
+    // FMM_F64 plans whose leaf products are stored and summed level by level in separate passes:
+    // the passes (tables set at creation; buffers, C, alpha and beta per call), the product and
+    // intermediate buffers, the leaf launch's geometry (border and core tasks, products stored)
+    // and the rank-q launch's (after the passes)
+    bool post_levels = false;
+    std::vector<fmm::LevelPass> level_passes;
+    double *d_pbuf = nullptr, *d_xbuf = nullptr;
+    const F64Geom *d_geom_leaf = nullptr, *d_geom_rq = nullptr;
+    long long leaf_tasks = 0, rq_tasks = 0;
     // host-buffer path: device copies of the operands, a stream for B's copy and its events
     double *d_hostA = nullptr, *d_hostB = nullptr, *d_hostC = nullptr;
     cudaStream_t host_copy_stream = nullptr;
@@ -679,6 +688,49 @@ std::vector<LevelFactor> decompose_level(const LevelFactor &f) {
     return best;
 }
 
+// W of one recursion level, or a Kronecker factor of it (the post-additions).
+struct WFactor {
+    int p = 0, R = 0;
+    std::vector<int32_t> W;
+};
+
+// FP64 operations of summing one level's products into its blocks by the
+// factors `seq`, innermost first, per position of a leaf block: factor k
+// runs once per (product of the outer factors, block of the inner ones).
+double w_steps_cost(const std::vector<WFactor> &seq) {
+    double cost = 0;
+    for (size_t k = 0; k < seq.size(); ++k) {
+        double groups = 1;
+        for (size_t j = 0; j < k; ++j) groups *= seq[j].R;
+        for (size_t j = k + 1; j < seq.size(); ++j) groups *= (double)seq[j].p * seq[j].p;
+        long long nnz = 0;
+        for (int32_t x : seq[k].W) nnz += x != 0;
+        cost += groups * (double)nnz;
+    }
+    return cost;
+}
+
+// Cheapest sequence of Kronecker factors of one level's W (the level itself
+// when it has none), outermost first.
+std::vector<WFactor> decompose_w(const WFactor &f) {
+    std::vector<WFactor> best{f};
+    double best_cost = w_steps_cost(best);
+    for (int p1 = 2; p1 < f.p; ++p1) {
+        if (f.p % p1) continue;
+        for (int R1 = 2; R1 < f.R; ++R1) {
+            if (f.R % R1) continue;
+            WFactor a, b;
+            a.p = p1; a.R = R1; b.p = f.p / p1; b.R = f.R / R1;
+            if (!kron_split(f.W, f.p, f.R, p1, R1, a.W, b.W)) continue;
+            std::vector<WFactor> seq = decompose_w(a);
+            for (const WFactor &x : decompose_w(b)) seq.push_back(x);
+            const double c = w_steps_cost(seq);
+            if (c < best_cost) { best_cost = c; best = seq; }
+        }
+    }
+    return best;
+}
+
 int default_materialized_levels(int p, int R, const fmm_algo_t *a, int depth) {
     if (depth < 1) return 0;
     long long nnz_u = 0, nnz_v = 0;
@@ -969,6 +1021,149 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         }
     }
 
+    // Stored leaf products, summed level by level (FMM_F64): W's Kronecker factors over all levels,
+    // outermost first; passes from the innermost factor up, two 2 x 2 factors of at most 8 products
+    // at a time, else one.  Option, then FMM_F64_POSTADD (fused / levels), then the planner's choice.
+    int post_mode = o.post_additions;
+    if (post_mode < 0 || post_mode > 2) { host_delete(pl); return FMM_ERR_INVALID; }
+    if (post_mode == 0)
+        if (const char *pe = std::getenv("FMM_F64_POSTADD")) {
+            if (std::string(pe) == "fused") post_mode = 1;
+            if (std::string(pe) == "levels") post_mode = 2;
+        }
+    std::vector<WFactor> wseq;
+    if (dtype == FMM_F64 && depth >= 1) {
+        WFactor lvl;
+        lvl.p = p; lvl.R = R;
+        lvl.W.assign(algo->W, algo->W + (size_t)p * p * R);
+        const std::vector<WFactor> wf = decompose_w(lvl);
+        for (int lev = 0; lev < depth; ++lev)
+            for (const WFactor &f : wf) wseq.push_back(f);
+    }
+    bool levels_ok = !wseq.empty() && shards == 1 && !o.debug_poison_chain;
+    for (const WFactor &f : wseq) {
+        if (f.p * f.p > fmm::kLevelMaxQ) levels_ok = false;
+        for (int q = 0; q < f.p * f.p; ++q) {
+            bool any = false;
+            for (int r = 0; r < f.R; ++r) any = any || f.W[(size_t)q * f.R + r] != 0;
+            if (!any) levels_ok = false;
+        }
+    }
+    if (post_mode == 2 && !levels_ok && depth >= 1) { host_delete(pl); return FMM_ERR_UNSUPPORTED; }
+    if (post_mode == 0 && levels_ok) {
+        // The planner stores the products when the fused epilogue's adds, (nnz(W flattened) - P^2) m^2,
+        // reach 0.4 % of the leaf's 2 R^depth m^3 flops, and the product buffers take at most a quarter
+        // of the free device memory.  Measured at n = 1024 .. 8192 (Strassen depth 1-7, <4,4,4;49>,
+        // Winograd, Laderman): above that ratio the stored form was faster, by 1.1 % (n = 4096, depth 3,
+        // ratio 0.0095) up to 3.8x (n = 8192, depth 7); below it the two were within 0.7 % of each
+        // other, except Laderman at n = 1024 (ratio 0.0054), 4.5 % slower stored.
+        long long nnz_flat = 0;
+        for (const auto &c : wcols) nnz_flat += (long long)c.size();
+        const double ratio = (double)(nnz_flat - P * P) / ((double)Rt * (double)pl->m);
+        const double extra = 1.5 * (double)Rt * (double)pl->m * (double)pl->m * sizeof(double);
+        size_t free_b = 0, total_b = 0;
+        const bool room = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && extra <= 0.25 * (double)free_b;
+        if (!room) cudaGetLastError();
+        post_mode = ratio >= 0.008 && room ? 2 : 1;
+    }
+    const bool post_levels = levels_ok && post_mode == 2;
+    struct PassTables {
+        std::vector<int> bptr, aptr;
+        std::vector<int4> bent, aent;
+    };
+    std::vector<fmm::LevelPass> lpasses;
+    std::vector<PassTables> ltables;
+    std::vector<int2> c_blk;
+    double post_fma = 0;  // FP64 operations of the passes, per position of a leaf block
+    if (post_levels) {
+        auto words = [](int c, int &lo, int &hi) {
+            const double d = (double)c;
+            unsigned long long bits = 0;
+            std::memcpy(&bits, &d, sizeof bits);
+            lo = (int)(unsigned)(bits & 0xffffffffULL);
+            hi = (int)(unsigned)(bits >> 32);
+        };
+        // columns r of f's W: {q, coefficient, flags: 1 first term of row q, 2 coefficient +-1}
+        auto by_columns = [&](const WFactor &f, std::vector<int> &ptr, std::vector<int4> &ent) {
+            const int Q = f.p * f.p;
+            std::vector<int> first(Q, -1);
+            for (int q = 0; q < Q; ++q)
+                for (int r = 0; r < f.R && first[q] < 0; ++r)
+                    if (f.W[(size_t)q * f.R + r]) first[q] = r;
+            ptr.assign((size_t)f.R + 1, 0);
+            for (int r = 0; r < f.R; ++r) {
+                for (int q = 0; q < Q; ++q) {
+                    const int c = f.W[(size_t)q * f.R + r];
+                    if (!c) continue;
+                    int lo = 0, hi = 0;
+                    words(c, lo, hi);
+                    ent.push_back(make_int4(q, lo, hi, (first[q] == r ? 1 : 0) | (c == 1 || c == -1 ? 2 : 0)));
+                }
+                ptr[r + 1] = (int)ent.size();
+            }
+        };
+        long long np = 1, ns = 1;
+        for (const WFactor &f : wseq) np *= f.R;
+        for (int k = (int)wseq.size() - 1; k >= 0;) {
+            fmm::LevelPass a{};
+            PassTables t;
+            const WFactor &fb = wseq[k];
+            long long nnz_b = 0;
+            for (int32_t x : fb.W) nnz_b += x != 0;
+            if (k >= 1 && fb.p == 2 && wseq[k - 1].p == 2 && fb.R <= 8 && wseq[k - 1].R <= 8) {
+                const WFactor &fa = wseq[k - 1];
+                long long nnz_a = 0;
+                for (int32_t x : fa.W) nnz_a += x != 0;
+                np /= (long long)fa.R * fb.R;
+                a.ra = fa.R; a.qa = 4; a.rb = fb.R; a.qb = 4;
+                a.unit_b = 1;
+                t.bptr.assign(5, 0);
+                for (int q = 0; q < 4; ++q) {
+                    for (int r = 0; r < fb.R; ++r) {
+                        const int c = fb.W[(size_t)q * fb.R + r];
+                        if (!c) continue;
+                        int lo = 0, hi = 0;
+                        words(c, lo, hi);
+                        t.bent.push_back(make_int4(r, lo, hi, 0));
+                        if (c != 1 && c != -1) a.unit_b = 0;
+                    }
+                    t.bptr[q + 1] = (int)t.bent.size();
+                }
+                by_columns(fa, t.aptr, t.aent);
+                post_fma += (double)np * ns * (double)(fa.R * (nnz_b - 4) + 4 * (nnz_a - 4));
+                k -= 2;
+            } else {
+                np /= fb.R;
+                a.ra = 1; a.qa = 1; a.rb = fb.R; a.qb = fb.p * fb.p;
+                by_columns(fb, t.bptr, t.bent);
+                post_fma += (double)np * ns * (double)(nnz_b - a.qb);
+                k -= 1;
+            }
+            a.np = (int)np;
+            a.ns = (int)ns;
+            ns *= (long long)a.qa * a.qb;
+            a.m = pl->m;
+            a.mm = pl->m * pl->m;
+            a.last = k < 0;
+            lpasses.push_back(a);
+            ltables.push_back(std::move(t));
+        }
+        // C block (row, column) of output o of the last pass: digits q_k = i_k p_k + j_k, innermost last
+        c_blk.resize((size_t)P * P);
+        for (long long o2 = 0; o2 < P * P; ++o2) {
+            long long rem = o2, row = 0, col = 0, mult = 1;
+            for (int k = (int)wseq.size() - 1; k >= 0; --k) {
+                const int pk = wseq[k].p;
+                const long long q = rem % (pk * pk);
+                rem /= pk * pk;
+                row += (q / pk) * mult;
+                col += (q % pk) * mult;
+                mult *= pk;
+            }
+            c_blk[(size_t)o2] = make_int2((int)row, (int)col);
+        }
+    }
+
     // Task counts.
     const long long tiles = (long long)pl->tiles_m * pl->tiles_n;
     const long long q = n - pl->n_core;
@@ -1013,7 +1208,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             w_nnz += c;
             blocks_hit += c > 0;
         }
-        adds += (double)(w_nnz - blocks_hit) * md * md;
+        adds += post_levels ? post_fma * md * md : (double)(w_nnz - blocks_hit) * md * md;
     }
     const double qd = with_peel ? (double)q : 0.0, ncd = (double)pl->n_core, nd = (double)n;
     const double peel = 2.0 * (ncd * qd * nd + qd * nd * nd + ncd * ncd * qd);
@@ -1037,6 +1232,17 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     const size_t o_wient = reserve(std::max<size_t>(1, wi_ent.size()) * sizeof(int4));
     const size_t o_woptr = reserve(std::max<size_t>(1, wo_ptr.size()) * sizeof(int));
     const size_t o_woent = reserve(std::max<size_t>(1, wo_ent.size()) * sizeof(int4));
+    const size_t o_geom_leaf = reserve(sizeof(F64Geom));
+    const size_t o_geom_rq = reserve(sizeof(F64Geom));
+    const size_t o_cblk = reserve(std::max<size_t>(1, c_blk.size()) * sizeof(int2));
+    std::vector<size_t> o_lp(4 * lpasses.size());
+    for (size_t k = 0; k < lpasses.size(); ++k) {
+        const PassTables &t = ltables[k];
+        o_lp[4 * k] = reserve(t.bptr.size() * sizeof(int));
+        o_lp[4 * k + 1] = reserve(std::max<size_t>(1, t.bent.size()) * sizeof(int4));
+        o_lp[4 * k + 2] = reserve(std::max<size_t>(1, t.aptr.size()) * sizeof(int));
+        o_lp[4 * k + 3] = reserve(std::max<size_t>(1, t.aent.size()) * sizeof(int4));
+    }
     std::vector<size_t> o_st(4 * steps.size());
     for (size_t k = 0; k < steps.size(); ++k) {
         o_st[4 * k] = reserve(st_uptr[k].size() * sizeof(int));
@@ -1103,6 +1309,24 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         fmm_plan::MatStep &a = pl->mat_steps[k], &b = pl->mat_steps[k + 1];
         if (a.p == 2 && b.p == 2 && a.R <= 8 && b.R <= 8 && !(k > 0 && pl->mat_steps[k - 1].with_next)) a.with_next = true;
     }
+    put(o_cblk, c_blk.data(), c_blk.size() * sizeof(int2));
+    for (size_t k = 0; k < lpasses.size(); ++k) {
+        const PassTables &t = ltables[k];
+        put(o_lp[4 * k], t.bptr.data(), t.bptr.size() * sizeof(int));
+        put(o_lp[4 * k + 1], t.bent.data(), t.bent.size() * sizeof(int4));
+        put(o_lp[4 * k + 2], t.aptr.data(), t.aptr.size() * sizeof(int));
+        put(o_lp[4 * k + 3], t.aent.data(), t.aent.size() * sizeof(int4));
+        fmm::LevelPass &a = lpasses[k];
+        a.b_ptr = (const int *)(base + o_lp[4 * k]);
+        a.b_ent = (const int4 *)(base + o_lp[4 * k + 1]);
+        a.a_ptr = t.aptr.empty() ? nullptr : (const int *)(base + o_lp[4 * k + 2]);
+        a.a_ent = t.aent.empty() ? nullptr : (const int4 *)(base + o_lp[4 * k + 3]);
+        a.c_blk = (const int2 *)(base + o_cblk);
+    }
+    pl->post_levels = post_levels;
+    pl->level_passes = lpasses;
+    pl->d_geom_leaf = (const F64Geom *)(base + o_geom_leaf);
+    pl->d_geom_rq = (const F64Geom *)(base + o_geom_rq);
     put(o_geom, &g, sizeof(F64Geom));
     {
         F64Geom gp = g;  // the peel tasks alone, run after the emulated leaf products
@@ -1168,6 +1392,19 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         o_slb = ws; ws = align_up(ws + slice_bytes, 256);
         o_pout = ws; ws = align_up(ws + (size_t)Rt * (size_t)pl->m * (size_t)pl->m * sizeof(double), 256);
     }
+    size_t o_pbuf = 0, o_xbuf = 0;
+    if (post_levels) {
+        // pass k reads pass k-1's output (pass 0: the products) and writes the intermediate
+        // buffer (even k) or the product buffer (odd k); the last pass writes C
+        const size_t blk = (size_t)pl->m * (size_t)pl->m * sizeof(double);
+        size_t xblocks = 0;
+        for (size_t k = 0; k + 1 < lpasses.size(); k += 2) {
+            const fmm::LevelPass &a = lpasses[k];
+            xblocks = std::max(xblocks, (size_t)a.np * a.qa * a.qb * a.ns);
+        }
+        o_pbuf = ws; ws = align_up(ws + (size_t)Rt * blk, 256);
+        if (xblocks) { o_xbuf = ws; ws = align_up(ws + xblocks * blk, 256); }
+    }
     pl->ws_bytes = ws;
     if (dev_alloc(&pl->d_ws, ws) != cudaSuccess) {
         free_plan_memory(pl);
@@ -1185,6 +1422,25 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         if (o_ta) {
             pl->d_TA = (double *)(wsb + o_ta);
             pl->d_TB = (double *)(wsb + o_tb);
+        }
+    }
+    if (post_levels) {
+        pl->d_pbuf = (double *)(wsb + o_pbuf);
+        pl->d_xbuf = o_xbuf ? (double *)(wsb + o_xbuf) : nullptr;
+        F64Geom gl = g;  // border and core tasks, products stored
+        gl.pout = pl->d_pbuf;
+        gl.tasks_rankq = 0;
+        F64Geom gq = g;  // the rank-q tasks alone, after the passes
+        gq.tasks_core = gq.tasks_right = gq.tasks_bottom = 0;
+        gq.rankq_free = 1;
+        pl->leaf_tasks = gl.tasks_core + gl.tasks_right + gl.tasks_bottom;
+        pl->rq_tasks = gq.tasks_rankq;
+        if (cudaMemcpy((void *)pl->d_geom_leaf, &gl, sizeof gl, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy((void *)pl->d_geom_rq, &gq, sizeof gq, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            free_plan_memory(pl);
+            host_delete(pl);
+            return FMM_ERR_CUDA;
         }
     }
     if (dtype == FMM_F64_OZAKI) {
@@ -1501,6 +1757,51 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     return FMM_OK;
 }
 
+// Stored leaf products: the leaf launch (border tasks, then every core task
+// storing its P_r tile), the level-by-level post-addition passes into C, then
+// the rank-q fix-ups of a non-divisible n, which add into C's core blocks.
+fmm_status_t gemm_levels(const fmm_plan *pl, const double *A, const double *B, double *C, double alpha, double beta,
+                         cudaStream_t st) {
+    F64Launch<1> L{};
+    L.nprobs = 1;
+    L.total_tasks = pl->leaf_tasks;
+    L.task_counter = pl->d_task_counter;
+    L.error = pl->d_error;
+    L.timeout_ns = (long long)(pl->timeout_s * 1e9);
+    L.probs[0] = problem_of(pl, A, B, C, 0, alpha, beta);
+    L.probs[0].g = pl->d_geom_leaf;
+    const int per_sm = fmm::f64_kernel_ctas_per_sm(pl->bn);
+    const int grid = (int)std::max<long long>(1, std::min<long long>(pl->leaf_tasks, (long long)pl->sms * per_sm));
+    if (pl->leaf_tasks > 0 && fmm::launch_f64_single(L, grid, st, pl->bn) != cudaSuccess) return FMM_ERR_CUDA;
+    if (pl->ev[2] && cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
+    const size_t npass = pl->level_passes.size();
+    for (size_t k = 0; k < npass; ++k) {
+        fmm::LevelPass a = pl->level_passes[k];
+        a.in = k == 0 ? pl->d_pbuf : (k % 2 == 1 ? pl->d_xbuf : pl->d_pbuf);
+        a.out = a.last ? C : (k % 2 == 0 ? pl->d_xbuf : pl->d_pbuf);
+        a.ldc = pl->n;
+        a.alpha = a.last ? alpha * pl->wscale : 1.0;
+        a.beta = a.last ? beta : 0.0;
+        if (fmm::launch_level_pass(a, st) != cudaSuccess) return FMM_ERR_CUDA;
+    }
+    if (pl->ev[5] && cudaEventRecord(pl->ev[5], st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (pl->rq_tasks > 0) {
+        F64Launch<1> Q{};
+        Q.nprobs = 1;
+        Q.total_tasks = pl->rq_tasks;
+        Q.task_counter = pl->d_task_counter2;
+        Q.error = pl->d_error;
+        Q.timeout_ns = L.timeout_ns;
+        Q.probs[0] = L.probs[0];
+        Q.probs[0].g = pl->d_geom_rq;
+        const int g2 = (int)std::max<long long>(1, std::min<long long>(pl->rq_tasks, (long long)pl->sms * per_sm));
+        if (fmm::launch_f64_single(Q, g2, st, pl->bn) != cudaSuccess) return FMM_ERR_CUDA;
+    }
+    if (pl->ev[4] && cudaEventRecord(pl->ev[4], st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (pl->ev[2]) const_cast<fmm_plan *>(pl)->timed_once = true;
+    return FMM_OK;
+}
+
 // Double complex through real fast products on split planes (FMM_C128: four,
 // FMM_C128_3M: three; see fmm_dtype_t).  The 4M form accumulates its second
 // product of each part with beta = 1, so every part is one ordered sum.
@@ -1574,6 +1875,7 @@ extern "C" fmm_status_t fmm_gemm_ex(const fmm_plan_t *pl, double alpha, const do
         return s;
     }
     if (pl->ev[1] && cudaEventRecord(pl->ev[1], st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (pl->post_levels) return gemm_levels(pl, A, B, C, alpha, beta, st);
     F64Launch<1> L{};
     L.nprobs = 1;
     L.total_tasks = pl->total_tasks;
@@ -2000,6 +2302,7 @@ extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t 
     info->coef_scale = pl->wscale;
     info->product_begin = pl->sub_begin * pl->R_src;
     info->product_end = pl->sub_end * pl->R_src;
+    info->post_passes = pl->post_levels ? (int)pl->level_passes.size() : 0;
     info->materialize_passes = 0;
     for (const fmm_plan::MatStep &ms : pl->mat_steps) info->materialize_passes += ms.with_next ? 0 : 1;
     return FMM_OK;

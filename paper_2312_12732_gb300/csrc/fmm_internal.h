@@ -51,6 +51,14 @@ struct F64Geom {
     long long tasks_core, tasks_right, tasks_bottom, tasks_rankq;
     int rb_tm, rb_tn;  // right-border tiling (n_core x q)
     int bb_tm, bb_tn;  // bottom-border tiling (q x n)
+    // Stored leaf products (post-additions in separate passes): when pout is
+    // set, core task r stores P_r = S_r T_r unscaled at pout + r m^2 (leading
+    // dimension m) instead of adding it into C.
+    double *pout;
+    // 1: rank-q tasks add into C without waiting on ordering counters (C's
+    // core blocks are complete before the launch that runs them).
+    int rankq_free;
+    int pad_;
 };
 
 struct F64Problem {
@@ -162,6 +170,38 @@ cudaError_t launch_ozaki_postadd_two_steps(const double *pout, long long m, int 
                                            const int4 *wi_ent, const int *wo_ptr, const int4 *wo_ent, double *C,
                                            long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
                                            double alpha, double beta, bool unit_inner, cudaStream_t s);
+// One pass of level-by-level post-additions of an FP64 plan whose leaf
+// products are stored (fmm_postadd.cu).  The products are indexed by the
+// digits (r_1, ..., r_K) of the Kronecker factors of W over all recursion
+// levels, outermost first, and C blocks by (q_1, ..., q_K), q_k = i_k p_k +
+// j_k.  A pass sums the innermost factor not yet summed (or the two innermost
+// when both are 2 x 2 with at most 8 products): input block
+// ((x R_a + r_a) R_b + r_b) ns + s, output block ((x Q_a + q_a) Q_b + q_b) ns + s
+// for prefix x < np and suffix s < ns, each block m x m contiguous.  A
+// single-factor pass has R_a = Q_a = 1.  The last pass (np = 1) writes C block
+// c_blk[o] = (block row, block column) of output o as alpha sum + beta C.
+struct LevelPass {
+    const double *in;
+    double *out;          // intermediate blocks, or C (leading dimension ldc) in the last pass
+    long long m, mm, ldc;
+    int np, ns;
+    int ra, qa, rb, qb;
+    // single pass: columns r of W_b, entries {q, coefficient low word, high word, flags}
+    // (bit 0: first term of row q, bit 1: coefficient +-1); pair pass: rows q of W_b,
+    // entries {r, low word, high word, 0} ascending r
+    const int *b_ptr;
+    const int4 *b_ent;
+    // pair pass: columns r of W_a, entries {q, low word, high word, flags}
+    const int *a_ptr;
+    const int4 *a_ent;
+    const int2 *c_blk;
+    double alpha, beta;
+    int last;
+    int unit_b;           // pair pass: every coefficient of W_b is +-1
+};
+cudaError_t launch_level_pass(const LevelPass &a, cudaStream_t s);
+constexpr int kLevelMaxQ = 64;  // blocks of one single-factor pass (p <= 8)
+
 // C = beta C over `count` contiguous doubles; beta = 0 stores zeros without
 // reading C (fmm_materialize.cu).
 cudaError_t launch_scale_c(double *C, long long count, double beta, cudaStream_t s);

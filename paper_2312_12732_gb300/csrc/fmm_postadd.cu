@@ -219,6 +219,148 @@ __global__ void __launch_bounds__(kTwoStepThreads)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Level-by-level post-additions of an FP64 plan with stored leaf products
+// (Section 2, equation `eq:recursion` read from the leaf upwards: the blocks of
+// every product of one level are sums of the products of the level below).
+// One pass sums one Kronecker factor of W (or two 2 x 2 factors) for every
+// (prefix, suffix) group: each thread takes one position of the m x m blocks
+// and keeps its running sums in its own column of shared memory.  Work units
+// of kLevelChunk positions of one group are spread over a persistent grid.
+// Every term of a sum is one fma(c, v, s) with the integer coefficient c;
+// the first term of each sum is c v (a sign flip for c = +-1), so a pass
+// costs nnz(W_f) - (blocks) fma per group and position.  Bound by those FP64
+// operations (about 0.5 T/s) or by the block reads and writes.
+constexpr int kLevelThreads = 128;
+constexpr int kLevelChunk = 8 * kLevelThreads;
+constexpr int kLevelLoads = 8;  // products whose loads are in flight together (single-factor pass)
+
+__device__ __forceinline__ double coef_of(int lo, int hi) { return __hiloint2double(hi, lo); }
+
+// Walks the positions [p0, p1) of a unit, kLevelThreads apart, keeping the
+// (row, column) of the position inside its m x m block for the stores into C.
+struct LevelPos {
+    long long pos, y, x;
+    __device__ LevelPos(long long p, long long m) : pos(p), y(p / m), x(p - (p / m) * m) {}
+    __device__ void next(long long m) {
+        pos += kLevelThreads;
+        x += kLevelThreads;
+        while (x >= m) {
+            x -= m;
+            ++y;
+        }
+    }
+};
+
+// The result of output o (ordinal among the pass's outputs) at this position:
+// stored as is in an intermediate block, or as alpha v + beta C into C.
+__device__ __forceinline__ void level_store(const LevelPass &a, long long o, const LevelPos &w, double v) {
+    if (!a.last) {
+        a.out[o * a.mm + w.pos] = v;
+        return;
+    }
+    const int2 blk = a.c_blk[o];
+    double *c = a.out + ((long long)blk.x * a.m + w.y) * a.ldc + (long long)blk.y * a.m + w.x;
+    if (a.beta != 0.0) {
+        const double old = __ldcg(c);
+        *c = fma(a.alpha, v, a.beta == 1.0 ? old : a.beta * old);
+    } else {
+        *c = a.alpha == 1.0 ? v : a.alpha * v;
+    }
+}
+
+__global__ void __launch_bounds__(kLevelThreads) level_single_kernel(const __grid_constant__ LevelPass a) {
+    extern __shared__ double cs[];  // [qb][kLevelThreads]
+    const int tid = threadIdx.x;
+    const long long chunks = (a.mm + kLevelChunk - 1) / kLevelChunk;
+    const long long units = (long long)a.np * a.ns * chunks;
+    const long long istride = (long long)a.ns * a.mm;  // between consecutive products of a group
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const long long grp = u / chunks, p0 = (u - grp * chunks) * kLevelChunk;
+        const long long p1 = p0 + kLevelChunk < a.mm ? p0 + kLevelChunk : a.mm;
+        const long long x = grp / a.ns, sfx = grp - x * a.ns;
+        const double *in = a.in + (x * a.rb * a.ns + sfx) * a.mm;
+        const long long obase = x * a.qb * a.ns + sfx;
+        for (LevelPos w(p0 + tid, a.m); w.pos < p1; w.next(a.m)) {
+            for (int r0 = 0; r0 < a.rb; r0 += kLevelLoads) {
+                double v[kLevelLoads];
+#pragma unroll
+                for (int k = 0; k < kLevelLoads; ++k)
+                    if (r0 + k < a.rb) v[k] = __ldcs(in + (long long)(r0 + k) * istride + w.pos);
+#pragma unroll
+                for (int k = 0; k < kLevelLoads; ++k) {
+                    if (r0 + k >= a.rb) break;
+                    for (int e = a.b_ptr[r0 + k]; e < a.b_ptr[r0 + k + 1]; ++e) {
+                        const int4 en = a.b_ent[e];  // uniform across the CTA
+                        double *acc = &cs[en.x * kLevelThreads + tid];
+                        if (en.w & 1)
+                            *acc = (en.w & 2) ? times_unit(v[k], en.z) : coef_of(en.y, en.z) * v[k];
+                        else
+                            *acc = fma(coef_of(en.y, en.z), v[k], *acc);
+                    }
+                }
+            }
+            for (int q = 0; q < a.qb; ++q) level_store(a, obase + (long long)q * a.ns, w, cs[q * kLevelThreads + tid]);
+        }
+    }
+}
+
+template <bool UNIT>
+__global__ void __launch_bounds__(kLevelThreads) level_pair_kernel(const __grid_constant__ LevelPass a) {
+    __shared__ double ps[kTwoStepMaxR][kLevelThreads];
+    __shared__ double cs[16][kLevelThreads];
+    const int tid = threadIdx.x;
+    const long long chunks = (a.mm + kLevelChunk - 1) / kLevelChunk;
+    const long long units = (long long)a.np * a.ns * chunks;
+    const long long istride = (long long)a.ns * a.mm;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const long long grp = u / chunks, p0 = (u - grp * chunks) * kLevelChunk;
+        const long long p1 = p0 + kLevelChunk < a.mm ? p0 + kLevelChunk : a.mm;
+        const long long x = grp / a.ns, sfx = grp - x * a.ns;
+        const double *in = a.in + (x * a.ra * a.rb * a.ns + sfx) * a.mm;
+        const long long obase = x * 16 * a.ns + sfx;
+        for (LevelPos w(p0 + tid, a.m); w.pos < p1; w.next(a.m)) {
+            for (int ra = 0; ra < a.ra; ++ra) {
+                const double *pr = in + (long long)ra * a.rb * istride + w.pos;
+#pragma unroll
+                for (int rb = 0; rb < kTwoStepMaxR; ++rb)
+                    if (rb < a.rb) ps[rb][tid] = __ldcs(pr + (long long)rb * istride);
+                double ub[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e0 = a.b_ptr[q], e1 = a.b_ptr[q + 1];
+                    const int4 f = a.b_ent[e0];  // every row of W_b has a term (checked on the host)
+                    ub[q] = UNIT ? times_unit(ps[f.x][tid], f.z) : coef_of(f.y, f.z) * ps[f.x][tid];
+                    for (int k = e0 + 1; k < e1; ++k) {
+                        const int4 en = a.b_ent[k];
+                        ub[q] = fma(coef_of(en.y, en.z), ps[en.x][tid], ub[q]);
+                    }
+                }
+                for (int k = a.a_ptr[ra]; k < a.a_ptr[ra + 1]; ++k) {
+                    const int4 en = a.a_ent[k];
+                    const int qa = en.x;
+                    if (en.w & 1) {  // the first term of row qa (uniform: the table decides)
+                        if (en.w & 2) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) cs[4 * qa + q][tid] = times_unit(ub[q], en.z);
+                        } else {
+                            const double c = coef_of(en.y, en.z);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) cs[4 * qa + q][tid] = c * ub[q];
+                        }
+                    } else {
+                        const double c = coef_of(en.y, en.z);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) cs[4 * qa + q][tid] = fma(c, ub[q], cs[4 * qa + q][tid]);
+                    }
+                }
+            }
+#pragma unroll 4
+            for (int l = 0; l < 16; ++l) level_store(a, obase + (long long)l * a.ns, w, cs[l][tid]);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
@@ -266,6 +408,44 @@ cudaError_t launch_ozaki_postadd_two_steps(const double *pout, long long m, int 
     else
         ozaki_postadd_two_steps_kernel<false><<<grid, kTwoStepThreads, 0, s>>>(
             pout, m, R1, R2, wi_ptr, wi_ent, wo_ptr, wo_ent, C, ldc, chain, w_row_nnz, tiles, alpha, beta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_pass(const LevelPass &a, cudaStream_t s) {
+    if (a.mm <= 0 || a.np <= 0 || a.ns <= 0) return cudaSuccess;
+    const bool pair = a.ra > 1;
+    if (pair ? (a.qa != 4 || a.qb != 4 || a.ra > kTwoStepMaxR || a.rb > kTwoStepMaxR || a.rb < 1)
+             : (a.qb < 1 || a.qb > kLevelMaxQ || a.rb < 1))
+        return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = pair ? 0 : (size_t)a.qb * kLevelThreads * sizeof(double);
+    cudaError_t e = pair ? (a.unit_b ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_pair_kernel<true>,
+                                                                                    kLevelThreads, 0)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_pair_kernel<false>,
+                                                                                    kLevelThreads, 0))
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_single_kernel, kLevelThreads,
+                                                                         smem);
+    if (e != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    const long long units = (long long)a.np * a.ns * ((a.mm + kLevelChunk - 1) / kLevelChunk);
+    const long long slots = (long long)(sms > 0 ? sms : 1) * occ;
+    const unsigned grid = (unsigned)(units < slots ? units : slots);
+    if (pair) {
+        if (a.unit_b)
+            level_pair_kernel<true><<<grid, kLevelThreads, 0, s>>>(a);
+        else
+            level_pair_kernel<false><<<grid, kLevelThreads, 0, s>>>(a);
+    } else {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(level_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        level_single_kernel<<<grid, kLevelThreads, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
