@@ -423,13 +423,17 @@ def run_sweep(a):
         for d in (1, 2, 3):
             configs += [(algo, d, "fused", 0), (algo, d, "auto", 0)]
     configs += [("strassen^2", 1, "fused", 0), ("strassen^2", 1, "auto", 0), ("strassen^2", 2, "auto", 0),
-                ("strassen", 4, "auto", 0), ("strassen", 5, "auto", 0)]
+                ("strassen", 4, "auto", 0), ("strassen", 5, "auto", 0), ("strassen", 6, "auto", 0)]
     configs = [c + ("f64",) for c in configs]
+    # both post-addition forms where the planner's choice is close or the depth is large
+    configs += [(al, d, "auto", 0, "f64", post) for al, d in (("strassen", 3), ("strassen^2", 2), ("strassen", 5),
+                                                              ("strassen", 6)) for post in ("fused", "levels")]
     configs += [("strassen", d, "auto", 0, "f64_ozaki") for d in (0, 1, 2, 3)]
     if a.n >= 16384:
         # large sizes: the materialized schedules only (a fused row takes seconds per call)
         configs = [c for c in configs if c[2] == "auto" and c[0] in ("strassen", "strassen^2", "winograd")
-                   and (c[0] != "winograd" or c[1] == 3)]
+                   and (c[0] != "winograd" or c[1] == 3) and not (len(c) > 5 and c[5] == "fused" and c[1] >= 5)
+                   and c[1] <= 5]
     else:
         configs += [("strassen_dyadic", d, "auto", 0, "f64") for d in (1, 2, 3)]
         configs += [("strassen_thirds", 2, "auto", 0, "f64"), ("strassen_dyadic", 2, "auto", 0, "f64_ozaki")]
@@ -449,7 +453,9 @@ def run_sweep(a):
     if a.only:
         rows = [r for r in rows if r[1][0] in set(a.only.split(","))]
     cache = {n: (dA, dB, dC)}
-    for nn, (algo_name, depth, sched, ml, dt) in rows:
+    for nn, cfg in rows:
+        algo_name, depth, sched, ml, dt = cfg[:5]
+        post = cfg[5] if len(cfg) > 5 else "auto"
         if nn not in cache:
             A2, B2 = inputs.operands(nn, a.kind, seed=1)
             xA2 = torch.from_numpy(A2).to(dev)
@@ -457,11 +463,12 @@ def run_sweep(a):
         xA, xB, xC = cache[nn]
         algo = make_algo(fmm, algo_name)
         plan = fmm.fmm_plan_create(nn, algo, depth, dtype=dt, schedule=sched, materialize_levels=ml,
-                                   record_kernel_time=True)
+                                   record_kernel_time=True, post_additions=post if dt == "f64" else "auto")
         ms, leaf = time_plan(torch, fmm, plan, xA, xB, xC, 1, 2)
         info = plan.info()
         lowp = info["flops_lowp"] / leaf / 1e9 if dt == "f64_ozaki" else None
         print(json.dumps({"n": nn, "algo": algo_name, "depth": depth, "schedule": sched, "dtype": dt,
+                          "post": ("levels" if info["post_passes"] else "fused") if dt == "f64" else "separate",
                           "lowp_tflops_leaf_kernel": round(lowp, 1) if lowp else None,
                           "materialized": info["materialized_levels"], "ms": round(ms, 3),
                           "leaf_ms": round(leaf, 3), "eff_tflops": round(2.0 * nn ** 3 / ms / 1e9, 4),
