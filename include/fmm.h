@@ -192,7 +192,9 @@ typedef struct {
      *        and no ordering waits.  FMM_ERR_UNSUPPORTED with
      *        shard_count > 1, debug_poison_chain, or a factor of W wider than
      *        8 x 8 blocks; ignored at depth 0 and for other dtypes.
-     * Batched launches always use the fused epilogue. */
+     * In a batched launch each plan keeps its form: stored plans write their
+     * products in the grouped leaf launch, then run their passes, then their
+     * rank-q fix-ups in one more grouped launch per tile width. */
     int post_additions;
 } fmm_plan_options_t;
 
@@ -424,7 +426,10 @@ int64_t fmm_host_huge_page_bytes(void);
 
 /* Batched: count independent products C[i] = A[i] * B[i], each with its own
  * plan (sizes and algorithms may differ), as one persistent grouped launch
- * over the union of their tile tasks.  plans/A/B/C are HOST arrays of
+ * over the union of their tile tasks (one per leaf tile width present).
+ * Plans with stored leaf products (fmm_plan_options_t.post_additions) then
+ * run their post-addition passes and one more grouped launch of their rank-q
+ * fix-ups.  plans/A/B/C are HOST arrays of
  * `count` entries; A[i], B[i], C[i] are device pointers.  All plans must be
  * FMM_F64 and not in use by another call at the same time.  Asynchronous. */
 fmm_status_t fmm_gemm_batched(fmm_plan_t *const *plans, const double *const *A,
@@ -439,8 +444,8 @@ fmm_status_t fmm_gemm_batched_ex(fmm_plan_t *const *plans, const double *alpha, 
                                  void *stream);
 
 /* A batched multiplication captured once into a CUDA graph (the counter
- * resets, materialization passes and the one grouped leaf launch of
- * fmm_gemm_batched), replayed with fmm_batch_graph_launch.  The plans and the
+ * resets, materialization passes, grouped leaf launches and post-addition
+ * passes of fmm_gemm_batched), replayed with fmm_batch_graph_launch.  The plans and the
  * A/B/C pointers are baked into the graph: they must stay valid and unchanged
  * until fmm_batch_graph_destroy.  Creation captures on a private stream and
  * does not run the work. */

@@ -71,10 +71,9 @@ def choose(n: int, candidates=("strassen", "winograd"), max_depth: int = 3, min_
 
 
 def plan_for(n: int, pick: dict):
-    """A plan of size n with a tuned configuration, for a batched launch: its post-additions fused
-    into the leaf epilogue (what grouped launches run), so no product buffers are allocated."""
+    """A plan of size n with a tuned configuration (post-additions in the planner's form, as tuned)."""
     return B.fmm_plan_create(n, B.fmm_algo_builtin(pick["algo"]), pick["depth"], schedule=pick["schedule"],
-                             tile_n=pick["tile_n"], post_additions="fused")
+                             tile_n=pick["tile_n"])
 
 
 def plan_batch(sizes, candidates=("strassen", "winograd"), max_depth: int = 3, min_leaf: int = 128,

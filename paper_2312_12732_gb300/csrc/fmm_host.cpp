@@ -1757,6 +1757,25 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     return FMM_OK;
 }
 
+// The post-addition passes of a plan with stored leaf products, from its
+// product buffer into C (C = alpha sum + beta C in the last pass).
+fmm_status_t run_level_passes(const fmm_plan *pl, double *C, double alpha, double beta, cudaStream_t st) {
+    const size_t npass = pl->level_passes.size();
+    for (size_t k = 0; k < npass; ++k) {
+        fmm::LevelPass a = pl->level_passes[k];
+        a.in = k == 0 ? pl->d_pbuf : (k % 2 == 1 ? pl->d_xbuf : pl->d_pbuf);
+        a.out = a.last ? C : (k % 2 == 0 ? pl->d_xbuf : pl->d_pbuf);
+        a.ldc = pl->n;
+        a.alpha = a.last ? alpha * pl->wscale : 1.0;
+        a.beta = a.last ? beta : 0.0;
+        if (fmm::launch_level_pass(a, st) != cudaSuccess) return FMM_ERR_CUDA;
+    }
+    return FMM_OK;
+}
+
+// Tasks of a plan in the (first) leaf launch of a call.
+long long launch_tasks(const fmm_plan *pl) { return pl->post_levels ? pl->leaf_tasks : pl->total_tasks; }
+
 // Stored leaf products: the leaf launch (border tasks, then every core task
 // storing its P_r tile), the level-by-level post-addition passes into C, then
 // the rank-q fix-ups of a non-divisible n, which add into C's core blocks.
@@ -1774,16 +1793,7 @@ fmm_status_t gemm_levels(const fmm_plan *pl, const double *A, const double *B, d
     const int grid = (int)std::max<long long>(1, std::min<long long>(pl->leaf_tasks, (long long)pl->sms * per_sm));
     if (pl->leaf_tasks > 0 && fmm::launch_f64_single(L, grid, st, pl->bn) != cudaSuccess) return FMM_ERR_CUDA;
     if (pl->ev[2] && cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
-    const size_t npass = pl->level_passes.size();
-    for (size_t k = 0; k < npass; ++k) {
-        fmm::LevelPass a = pl->level_passes[k];
-        a.in = k == 0 ? pl->d_pbuf : (k % 2 == 1 ? pl->d_xbuf : pl->d_pbuf);
-        a.out = a.last ? C : (k % 2 == 0 ? pl->d_xbuf : pl->d_pbuf);
-        a.ldc = pl->n;
-        a.alpha = a.last ? alpha * pl->wscale : 1.0;
-        a.beta = a.last ? beta : 0.0;
-        if (fmm::launch_level_pass(a, st) != cudaSuccess) return FMM_ERR_CUDA;
-    }
+    if (run_level_passes(pl, C, alpha, beta, st) != FMM_OK) return FMM_ERR_CUDA;
     if (pl->ev[5] && cudaEventRecord(pl->ev[5], st) != cudaSuccess) return FMM_ERR_CUDA;
     if (pl->rq_tasks > 0) {
         F64Launch<1> Q{};
@@ -2041,7 +2051,8 @@ extern "C" fmm_status_t fmm_gemm_batched_ex(fmm_plan_t *const *plans, const doub
                 fmm_status_t s = prepare(pl, A[i], B[i], st);
                 if (s != FMM_OK) { host_delete(L); return s; }
                 L->probs[k] = problem_of(pl, A[i], B[i], C[i], begin, al(i), be(i));
-                begin += pl->total_tasks;
+                if (pl->post_levels) L->probs[k].g = pl->d_geom_leaf;  // border and core tasks, P_r stored
+                begin += launch_tasks(pl);
             }
             const fmm_plan *lead = plans[sel[c0]];
             L->nprobs = cnt;
@@ -2054,11 +2065,11 @@ extern "C" fmm_status_t fmm_gemm_batched_ex(fmm_plan_t *const *plans, const doub
                 std::vector<int> idx(cnt);
                 for (int k = 0; k < cnt; ++k) idx[k] = k;
                 std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
-                    return plans[sel[c0 + x]]->total_tasks > plans[sel[c0 + y]]->total_tasks;
+                    return launch_tasks(plans[sel[c0 + x]]) > launch_tasks(plans[sel[c0 + y]]);
                 });
                 std::vector<long long> c(cnt + 1, 0);
                 for (int j = 0; j < cnt; ++j) {
-                    c[j] = plans[sel[c0 + idx[j]]]->total_tasks;
+                    c[j] = launch_tasks(plans[sel[c0 + idx[j]]]);
                     L->order[j] = (short)idx[j];
                 }
                 long long G = 0;
@@ -2073,6 +2084,42 @@ extern "C" fmm_status_t fmm_gemm_batched_ex(fmm_plan_t *const *plans, const doub
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lead->device);
             int grid = (int)std::min<long long>(begin, (long long)sms * fmm::f64_kernel_ctas_per_sm(bn));
             if (grid < 1) grid = 1;
+            cudaError_t e = fmm::launch_f64_batch(*L, grid, st, bn);
+            host_delete(L);
+            if (e != cudaSuccess) return FMM_ERR_CUDA;
+        }
+    }
+    // plans with stored leaf products: their post-addition passes, then one grouped launch per tile
+    // width of their rank-q fix-ups
+    for (int i = 0; i < count; ++i)
+        if (plans[i]->post_levels && al(i) != 0.0 && run_level_passes(plans[i], C[i], al(i), be(i), st) != FMM_OK)
+            return FMM_ERR_CUDA;
+    for (int bn : {128, 64}) {
+        std::vector<int> sel;
+        for (int i = 0; i < count; ++i)
+            if (plans[i]->bn == bn && al(i) != 0.0 && plans[i]->post_levels && plans[i]->rq_tasks > 0)
+                sel.push_back(i);
+        for (size_t c0 = 0; c0 < sel.size(); c0 += fmm::kMaxBatchPerLaunch) {
+            const int cnt = (int)std::min<size_t>(sel.size() - c0, fmm::kMaxBatchPerLaunch);
+            F64Launch<fmm::kMaxBatchPerLaunch> *L = host_new<F64Launch<fmm::kMaxBatchPerLaunch>>();
+            if (!L) return FMM_ERR_OOM;
+            long long begin = 0;
+            for (int k = 0; k < cnt; ++k) {
+                const int i = sel[c0 + k];
+                L->probs[k] = problem_of(plans[i], A[i], B[i], C[i], begin, al(i), be(i));
+                L->probs[k].g = plans[i]->d_geom_rq;
+                begin += plans[i]->rq_tasks;
+            }
+            const fmm_plan *lead = plans[sel[c0]];
+            L->nprobs = cnt;
+            L->total_tasks = begin;
+            L->task_counter = lead->d_task_counter2;
+            L->error = lead->d_error;
+            L->timeout_ns = (long long)(lead->timeout_s * 1e9);
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lead->device);
+            const int grid = (int)std::max<long long>(
+                1, std::min<long long>(begin, (long long)sms * fmm::f64_kernel_ctas_per_sm(bn)));
             cudaError_t e = fmm::launch_f64_batch(*L, grid, st, bn);
             host_delete(L);
             if (e != cudaSuccess) return FMM_ERR_CUDA;

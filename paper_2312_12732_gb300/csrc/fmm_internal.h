@@ -198,6 +198,8 @@ struct LevelPass {
     double alpha, beta;
     int last;
     int unit_b;           // pair pass: every coefficient of W_b is +-1
+    int chunk;            // positions per work unit (a multiple of 128; set by the launcher)
+    int store;            // last pass, set by the launcher: 1 C = s, 2 alpha s, 3 fma(alpha, s, C), 4 fma(alpha, s, beta C)
 };
 cudaError_t launch_level_pass(const LevelPass &a, cudaStream_t s);
 constexpr int kLevelMaxQ = 64;  // blocks of one single-factor pass (p <= 8)

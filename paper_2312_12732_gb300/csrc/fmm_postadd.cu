@@ -226,13 +226,13 @@ __global__ void __launch_bounds__(kTwoStepThreads)
 // One pass sums one Kronecker factor of W (or two 2 x 2 factors) for every
 // (prefix, suffix) group: each thread takes one position of the m x m blocks
 // and keeps its running sums in its own column of shared memory.  Work units
-// of kLevelChunk positions of one group are spread over a persistent grid.
+// of a.chunk positions of one group are spread over a persistent grid.
 // Every term of a sum is one fma(c, v, s) with the integer coefficient c;
 // the first term of each sum is c v (a sign flip for c = +-1), so a pass
 // costs nnz(W_f) - (blocks) fma per group and position.  Bound by those FP64
 // operations (about 0.5 T/s) or by the block reads and writes.
 constexpr int kLevelThreads = 128;
-constexpr int kLevelChunk = 8 * kLevelThreads;
+constexpr int kLevelMaxChunk = 8 * kLevelThreads;
 constexpr int kLevelLoads = 8;  // products whose loads are in flight together (single-factor pass)
 
 __device__ __forceinline__ double coef_of(int lo, int hi) { return __hiloint2double(hi, lo); }
@@ -261,23 +261,23 @@ __device__ __forceinline__ void level_store(const LevelPass &a, long long o, con
     }
     const int2 blk = a.c_blk[o];
     double *c = a.out + ((long long)blk.x * a.m + w.y) * a.ldc + (long long)blk.y * a.m + w.x;
-    if (a.beta != 0.0) {
-        const double old = __ldcg(c);
-        *c = fma(a.alpha, v, a.beta == 1.0 ? old : a.beta * old);
-    } else {
-        *c = a.alpha == 1.0 ? v : a.alpha * v;
+    switch (a.store) {  // uniform, decided on the host (no FP64 compare per element)
+        case 1: *c = v; break;
+        case 2: *c = a.alpha * v; break;
+        case 3: *c = fma(a.alpha, v, __ldcg(c)); break;
+        default: *c = fma(a.alpha, v, a.beta * __ldcg(c)); break;
     }
 }
 
 __global__ void __launch_bounds__(kLevelThreads) level_single_kernel(const __grid_constant__ LevelPass a) {
     extern __shared__ double cs[];  // [qb][kLevelThreads]
     const int tid = threadIdx.x;
-    const long long chunks = (a.mm + kLevelChunk - 1) / kLevelChunk;
+    const long long chunks = (a.mm + a.chunk - 1) / a.chunk;
     const long long units = (long long)a.np * a.ns * chunks;
     const long long istride = (long long)a.ns * a.mm;  // between consecutive products of a group
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-        const long long grp = u / chunks, p0 = (u - grp * chunks) * kLevelChunk;
-        const long long p1 = p0 + kLevelChunk < a.mm ? p0 + kLevelChunk : a.mm;
+        const long long grp = u / chunks, p0 = (u - grp * chunks) * a.chunk;
+        const long long p1 = p0 + a.chunk < a.mm ? p0 + a.chunk : a.mm;
         const long long x = grp / a.ns, sfx = grp - x * a.ns;
         const double *in = a.in + (x * a.rb * a.ns + sfx) * a.mm;
         const long long obase = x * a.qb * a.ns + sfx;
@@ -310,12 +310,12 @@ __global__ void __launch_bounds__(kLevelThreads) level_pair_kernel(const __grid_
     __shared__ double ps[kTwoStepMaxR][kLevelThreads];
     __shared__ double cs[16][kLevelThreads];
     const int tid = threadIdx.x;
-    const long long chunks = (a.mm + kLevelChunk - 1) / kLevelChunk;
+    const long long chunks = (a.mm + a.chunk - 1) / a.chunk;
     const long long units = (long long)a.np * a.ns * chunks;
     const long long istride = (long long)a.ns * a.mm;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-        const long long grp = u / chunks, p0 = (u - grp * chunks) * kLevelChunk;
-        const long long p1 = p0 + kLevelChunk < a.mm ? p0 + kLevelChunk : a.mm;
+        const long long grp = u / chunks, p0 = (u - grp * chunks) * a.chunk;
+        const long long p1 = p0 + a.chunk < a.mm ? p0 + a.chunk : a.mm;
         const long long x = grp / a.ns, sfx = grp - x * a.ns;
         const double *in = a.in + (x * a.ra * a.rb * a.ns + sfx) * a.mm;
         const long long obase = x * 16 * a.ns + sfx;
@@ -411,8 +411,10 @@ cudaError_t launch_ozaki_postadd_two_steps(const double *pout, long long m, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_level_pass(const LevelPass &a, cudaStream_t s) {
-    if (a.mm <= 0 || a.np <= 0 || a.ns <= 0) return cudaSuccess;
+cudaError_t launch_level_pass(const LevelPass &a0, cudaStream_t s) {
+    if (a0.mm <= 0 || a0.np <= 0 || a0.ns <= 0) return cudaSuccess;
+    LevelPass a = a0;
+    a.store = a.beta != 0.0 ? (a.beta == 1.0 ? 3 : 4) : (a.alpha == 1.0 ? 1 : 2);
     const bool pair = a.ra > 1;
     if (pair ? (a.qa != 4 || a.qb != 4 || a.ra > kTwoStepMaxR || a.rb > kTwoStepMaxR || a.rb < 1)
              : (a.qb < 1 || a.qb > kLevelMaxQ || a.rb < 1))
@@ -431,8 +433,13 @@ cudaError_t launch_level_pass(const LevelPass &a, cudaStream_t s) {
         cudaGetLastError();
         occ = 1;
     }
-    const long long units = (long long)a.np * a.ns * ((a.mm + kLevelChunk - 1) / kLevelChunk);
     const long long slots = (long long)(sms > 0 ? sms : 1) * occ;
+    // units of up to 1024 positions, smaller while there would be fewer than 8 per resident CTA (the
+    // last wave of a pass with few groups left most of the GPU idle)
+    a.chunk = kLevelMaxChunk;
+    while (a.chunk > kLevelThreads && (long long)a.np * a.ns * ((a.mm + a.chunk - 1) / a.chunk) < 8 * slots)
+        a.chunk /= 2;
+    const long long units = (long long)a.np * a.ns * ((a.mm + a.chunk - 1) / a.chunk);
     const unsigned grid = (unsigned)(units < slots ? units : slots);
     if (pair) {
         if (a.unit_b)

@@ -192,17 +192,28 @@ def test_planner_choice_and_override(fmm, monkeypatch):
 
 
 def test_stored_plans_in_a_batched_launch(fmm, oracle_mod):
-    """A grouped launch runs every plan's fused epilogue, whatever its own post-addition form."""
-    specs = [(1024, 4), (515, 2), (300, 1)]
-    plans, As, Bs, Cs, host = [], [], [], [], []
-    for i, (n, depth) in enumerate(specs):
-        plans.append(fmm.fmm_plan_create(n, fmm.fmm_algo_builtin("strassen"), depth, post_additions="levels"))
+    """Stored and fused plans in one grouped launch: the stored ones write their products there, then
+    run their passes and one grouped launch of their rank-q fix-ups (peeled sizes 1031 and 515)."""
+    specs = [(1024, 4, "levels"), (515, 2, "levels"), (300, 1, "fused"), (1031, 3, "levels"), (777, 2, "fused"),
+             (64, 0, "auto")]
+    plans, As, Bs, Cs, C0s, host = [], [], [], [], [], []
+    for i, (n, depth, post) in enumerate(specs):
+        plans.append(fmm.fmm_plan_create(n, fmm.fmm_algo_builtin("strassen"), depth, post_additions=post))
         A, B = inputs.operands(n, "integer", seed=60 + i)
-        host.append((A, B))
+        C0 = inputs.matrix(n, "integer", seed=70 + i)
+        host.append((A, B, C0))
         As.append(torch.from_numpy(A).cuda())
         Bs.append(torch.from_numpy(B).cuda())
         Cs.append(torch.full_like(As[-1], float("nan")))
+        C0s.append(torch.from_numpy(C0).cuda())
+    assert [p.info()["post_passes"] > 0 for p in plans] == [True, True, False, True, False, False]
     fmm.fmm_gemm_batched(plans, As, Bs, Cs)
     assert fmm.fmm_sync_status(plans[0]) == 0
-    for (A, B), C in zip(host, Cs):
+    for (A, B, _), C in zip(host, Cs):
         assert np.array_equal(C.cpu().numpy(), oracle_mod.classic(A, B))
+    alphas = [2.0, -1.0, 1.0, 3.0, 1.0, 2.0]
+    betas = [-3.0, 1.0, 0.0, 2.0, 1.0, 0.0]
+    fmm.fmm_gemm_batched(plans, As, Bs, C0s, alphas=alphas, betas=betas)
+    assert fmm.fmm_sync_status(plans[0]) == 0
+    for (A, B, C0), C, al, be in zip(host, C0s, alphas, betas):
+        assert np.array_equal(C.cpu().numpy(), oracle_mod.axpby(al, oracle_mod.classic(A, B), be, C0))
