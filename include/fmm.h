@@ -40,11 +40,10 @@
  *   FMM_TILE_N       64 or 128: the FP64 leaf tile width when a plan does not
  *                    set one (read at plan creation).
  *   FMM_OZAKI_ENGINE see FMM_F64_OZAKI (read at plan creation).
- *   FMM_OZAKI_POSTADD flat: an FMM_F64_OZAKI plan of two levels of a 2 x 2
- *                    algorithm applies its post-additions in the flattened
- *                    form (every C block summed over all leaf products in
- *                    ascending order) instead of level by level (read at
- *                    plan creation).
+ *   FMM_OZAKI_POSTADD flat: an FMM_F64_OZAKI plan of depth 2 or more applies
+ *                    its post-additions in the flattened form (every C block
+ *                    summed over all leaf products in ascending order)
+ *                    instead of level by level (read at plan creation).
  *   FMM_OZAKI_KPARTS k (1..8): the CTA-pair slice GEMM of FMM_F64_OZAKI plans
  *                    splits each slice pair's K range into k pieces, each
  *                    accumulated on its own (default K / 1024 pieces, at least
@@ -132,12 +131,13 @@ typedef struct fmm_plan fmm_plan_t;
  *   FMM_SCHED_HYBRID -- the top `materialize_levels` levels are formed level
  *                       by level in plan workspace by an elementwise pass,
  *                       the remaining levels are fused into staging.
- * The post-additions C_l = sum_r W[l][r] P_r are fused into the FP64 leaf
- * kernel's epilogue; the emulated leaf (FMM_F64_OZAKI, FMM_F32) stores its
- * leaf products and applies them in a separate kernel: in the same order, or,
- * for two levels of a 2 x 2 algorithm, level by level as the recursion forms
- * them (each product's blocks first, then the sums over the outer products;
- * FMM_OZAKI_POSTADD=flat selects the first form). */
+ * The post-additions C_l = sum_r W[l][r] P_r of an FMM_F64 plan are fused into
+ * the leaf kernel's epilogue or run from stored leaf products
+ * (fmm_plan_options_t.post_additions); the emulated leaf (FMM_F64_OZAKI,
+ * FMM_F32) always stores its leaf products and sums them in separate kernels:
+ * at depth 1 in ascending product order per C block, from depth 2 level by
+ * level as the recursion forms the blocks (the passes of the stored FMM_F64
+ * form; FMM_OZAKI_POSTADD=flat selects the flattened order instead). */
 typedef enum { FMM_SCHED_AUTO = 0, FMM_SCHED_FUSED = 1, FMM_SCHED_HYBRID = 2 } fmm_schedule_t;
 
 /* Optional knobs for fmm_plan_create_ex.  Zero-initialise, then set fields;
@@ -191,7 +191,8 @@ typedef struct {
      *        leaf block become 8 (7^d - 4^d) / 3: 20480 and 5720 at depth 4),
      *        and no ordering waits.  FMM_ERR_UNSUPPORTED with
      *        shard_count > 1, debug_poison_chain, or a factor of W wider than
-     *        8 x 8 blocks; ignored at depth 0 and for other dtypes.
+     *        8 x 8 blocks; ignored at depth 0 and for other dtypes (the
+     *        emulated leaf always stores its products).
      * In a batched launch each plan keeps its form: stored plans write their
      * products in the grouped leaf launch, then run their passes, then their
      * rank-q fix-ups in one more grouped launch per tile width. */
@@ -219,7 +220,8 @@ typedef struct {
     double coef_scale;      /* (den_u den_v den_w)^-depth for a rational plan, 1 otherwise */
     int64_t product_begin;  /* leaf products [product_begin, product_end) of this plan's shard */
     int64_t product_end;    /* (0 and R_total for an unsharded plan) */
-    int post_passes;        /* FMM_F64 with stored leaf products: post-addition passes (0: fused) */
+    int post_passes;        /* level-by-level post-addition passes of stored leaf products (FMM_F64
+                               stored form, FMM_F64_OZAKI from depth 2); 0: fused or flattened */
 } fmm_plan_info_t;
 
 /* The contiguous range [*begin, *end) of `units` work units that shard

@@ -374,16 +374,13 @@ struct fmm_plan {
     double *d_pout = nullptr;                           // [R][m][m] leaf products of the tcgen05 engines
     const int *d_wl_ptr = nullptr;                      // per C block: products (r, coefficient) in ascending r
     const int2 *d_wl_ent = nullptr;
-    // post-additions level by level (two levels of a 2 x 2 algorithm): inner W rows, outer W columns
-    bool post_two_steps = false, post_unit_inner = false;
-    const int *d_wi_ptr = nullptr, *d_wo_ptr = nullptr;
-    const int4 *d_wi_ent = nullptr, *d_wo_ent = nullptr;
     double flops_lowp = 0;
     // FMM_F64 plans whose leaf products are stored and summed level by level in separate passes:
     // the passes (tables set at creation; buffers, C, alpha and beta per call), the product and
     // intermediate buffers, the leaf launch's geometry (border and core tasks, products stored)
     // and the rank-q launch's (after the passes)
     bool post_levels = false;
+    bool oz_levels = false;  // FMM_F64_OZAKI: its stored products summed by the same passes
     std::vector<fmm::LevelPass> level_passes;
     double *d_pbuf = nullptr, *d_xbuf = nullptr;
     const F64Geom *d_geom_leaf = nullptr, *d_geom_rq = nullptr;
@@ -984,46 +981,13 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         }
     }
 
-    // The emulated leaf's post-additions level by level when the plan is two levels of a 2 x 2 algorithm
-    // with at most 8 products: rows q of W as {r2, coefficient as a double's low and high word} (inner
-    // level) and columns r1 of W as {l1, coefficient, first term of row l1} (outer level), both ascending.
-    std::vector<int> wi_ptr, wo_ptr;
-    std::vector<int4> wi_ent, wo_ent;
     const char *post_env = std::getenv("FMM_OZAKI_POSTADD");
-    bool two_step_post = dtype == FMM_F64_OZAKI && depth == 2 && algo->p == 2 && algo->R <= 8 && shards == 1 &&
-                         !(post_env && std::string(post_env) == "flat");
-    bool unit_inner = true;
-    if (two_step_post) {
-        const int R = algo->R;
-        wi_ptr.assign(5, 0);
-        int first_r[4] = {-1, -1, -1, -1};
-        for (int q = 0; q < 4; ++q) {
-            for (int r = 0; r < R; ++r) {
-                const int c = algo->W[q * R + r];
-                if (c == 0) continue;
-                const double d = (double)c;
-                unsigned long long bits = 0;
-                std::memcpy(&bits, &d, sizeof bits);
-                wi_ent.push_back(make_int4(r, (int)(unsigned)(bits & 0xffffffffULL), (int)(unsigned)(bits >> 32), 0));
-                if (c != 1 && c != -1) unit_inner = false;
-                if (first_r[q] < 0) first_r[q] = r;
-            }
-            wi_ptr[q + 1] = (int)wi_ent.size();
-            if (first_r[q] < 0) two_step_post = false;  // an all-zero row of W: use the flattened form
-        }
-        wo_ptr.assign((size_t)R + 1, 0);
-        for (int r = 0; r < R; ++r) {
-            for (int l1 = 0; l1 < 4; ++l1) {
-                const int c = algo->W[l1 * R + r];
-                if (c != 0) wo_ent.push_back(make_int4(l1, c, first_r[l1] == r ? 1 : 0, 0));
-            }
-            wo_ptr[r + 1] = (int)wo_ent.size();
-        }
-    }
+    const bool oz_flat = post_env && std::string(post_env) == "flat";
 
-    // Stored leaf products, summed level by level (FMM_F64): W's Kronecker factors over all levels,
-    // outermost first; passes from the innermost factor up, two 2 x 2 factors of at most 8 products
-    // at a time, else one.  Option, then FMM_F64_POSTADD (fused / levels), then the planner's choice.
+    // Stored leaf products, summed level by level (FMM_F64, and FMM_F64_OZAKI from depth 2): W's
+    // Kronecker factors over all levels, outermost first; passes from the innermost factor up, two 2 x 2
+    // factors of at most 8 products at a time, else one.  FMM_F64: option, then FMM_F64_POSTADD (fused /
+    // levels), then the planner's choice; FMM_F64_OZAKI: always, unless FMM_OZAKI_POSTADD=flat.
     int post_mode = o.post_additions;
     if (post_mode < 0 || post_mode > 2) { host_delete(pl); return FMM_ERR_INVALID; }
     if (post_mode == 0)
@@ -1032,7 +996,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             if (std::string(pe) == "levels") post_mode = 2;
         }
     std::vector<WFactor> wseq;
-    if (dtype == FMM_F64 && depth >= 1) {
+    if ((dtype == FMM_F64 && depth >= 1) || (dtype == FMM_F64_OZAKI && depth >= 2 && !oz_flat)) {
         WFactor lvl;
         lvl.p = p; lvl.R = R;
         lvl.W.assign(algo->W, algo->W + (size_t)p * p * R);
@@ -1049,8 +1013,11 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             if (!any) levels_ok = false;
         }
     }
-    if (post_mode == 2 && !levels_ok && depth >= 1) { host_delete(pl); return FMM_ERR_UNSUPPORTED; }
-    if (post_mode == 0 && levels_ok) {
+    if (dtype == FMM_F64 && post_mode == 2 && !levels_ok && depth >= 1) {
+        host_delete(pl);
+        return FMM_ERR_UNSUPPORTED;
+    }
+    if (dtype == FMM_F64 && post_mode == 0 && levels_ok) {
         // The planner stores the products when the fused epilogue's adds, (nnz(W flattened) - P^2) m^2,
         // reach 0.4 % of the leaf's 2 R^depth m^3 flops, and the product buffers take at most a quarter
         // of the free device memory.  Measured at n = 1024 .. 8192 (Strassen depth 1-7, <4,4,4;49>,
@@ -1066,7 +1033,9 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         if (!room) cudaGetLastError();
         post_mode = ratio >= 0.008 && room ? 2 : 1;
     }
-    const bool post_levels = levels_ok && post_mode == 2;
+    const bool post_levels = dtype == FMM_F64 && levels_ok && post_mode == 2;
+    const bool oz_levels = dtype == FMM_F64_OZAKI && levels_ok;
+    const bool build_levels = post_levels || oz_levels;
     struct PassTables {
         std::vector<int> bptr, aptr;
         std::vector<int4> bent, aent;
@@ -1075,7 +1044,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     std::vector<PassTables> ltables;
     std::vector<int2> c_blk;
     double post_fma = 0;  // FP64 operations of the passes, per position of a leaf block
-    if (post_levels) {
+    if (build_levels) {
         auto words = [](int c, int &lo, int &hi) {
             const double d = (double)c;
             unsigned long long bits = 0;
@@ -1208,7 +1177,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             w_nnz += c;
             blocks_hit += c > 0;
         }
-        adds += post_levels ? post_fma * md * md : (double)(w_nnz - blocks_hit) * md * md;
+        adds += build_levels ? post_fma * md * md : (double)(w_nnz - blocks_hit) * md * md;
     }
     const double qd = with_peel ? (double)q : 0.0, ncd = (double)pl->n_core, nd = (double)n;
     const double peel = 2.0 * (ncd * qd * nd + qd * nd * nd + ncd * ncd * qd);
@@ -1228,10 +1197,6 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     const size_t o_wrow = reserve(w_row.size() * sizeof(int));
     const size_t o_wlptr = reserve(wl_ptr.size() * sizeof(int));
     const size_t o_wlent = reserve(std::max<size_t>(1, wl_ent.size()) * sizeof(int2));
-    const size_t o_wiptr = reserve(std::max<size_t>(1, wi_ptr.size()) * sizeof(int));
-    const size_t o_wient = reserve(std::max<size_t>(1, wi_ent.size()) * sizeof(int4));
-    const size_t o_woptr = reserve(std::max<size_t>(1, wo_ptr.size()) * sizeof(int));
-    const size_t o_woent = reserve(std::max<size_t>(1, wo_ent.size()) * sizeof(int4));
     const size_t o_geom_leaf = reserve(sizeof(F64Geom));
     const size_t o_geom_rq = reserve(sizeof(F64Geom));
     const size_t o_cblk = reserve(std::max<size_t>(1, c_blk.size()) * sizeof(int2));
@@ -1265,12 +1230,6 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     g.w_row_nnz = (const int *)(base + o_wrow);
     pl->d_wl_ptr = (const int *)(base + o_wlptr);
     pl->d_wl_ent = (const int2 *)(base + o_wlent);
-    pl->post_two_steps = two_step_post;
-    pl->post_unit_inner = unit_inner;
-    pl->d_wi_ptr = (const int *)(base + o_wiptr);
-    pl->d_wi_ent = (const int4 *)(base + o_wient);
-    pl->d_wo_ptr = (const int *)(base + o_woptr);
-    pl->d_wo_ent = (const int4 *)(base + o_woent);
     std::vector<char> host(pl->tables_bytes, 0);
     auto put = [&](size_t o2, const void *src, size_t bytes) { if (bytes) std::memcpy(host.data() + o2, src, bytes); };
     put(o_uptr, u_ptr.data(), u_ptr.size() * sizeof(int));
@@ -1282,10 +1241,6 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
     put(o_wrow, w_row.data(), w_row.size() * sizeof(int));
     put(o_wlptr, wl_ptr.data(), wl_ptr.size() * sizeof(int));
     put(o_wlent, wl_ent.data(), wl_ent.size() * sizeof(int2));
-    put(o_wiptr, wi_ptr.data(), wi_ptr.size() * sizeof(int));
-    put(o_wient, wi_ent.data(), wi_ent.size() * sizeof(int4));
-    put(o_woptr, wo_ptr.data(), wo_ptr.size() * sizeof(int));
-    put(o_woent, wo_ent.data(), wo_ent.size() * sizeof(int4));
     for (size_t k = 0; k < steps.size(); ++k) {
         put(o_st[4 * k], st_uptr[k].data(), st_uptr[k].size() * sizeof(int));
         put(o_st[4 * k + 1], st_uent[k].data(), st_uent[k].size() * sizeof(int4));
@@ -1324,13 +1279,15 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         a.c_blk = (const int2 *)(base + o_cblk);
     }
     pl->post_levels = post_levels;
+    pl->oz_levels = oz_levels;
     pl->level_passes = lpasses;
     pl->d_geom_leaf = (const F64Geom *)(base + o_geom_leaf);
     pl->d_geom_rq = (const F64Geom *)(base + o_geom_rq);
     put(o_geom, &g, sizeof(F64Geom));
     {
-        F64Geom gp = g;  // the peel tasks alone, run after the emulated leaf products
+        F64Geom gp = g;  // the peel tasks alone, run after the emulated leaf products and their post-additions
         gp.tasks_core = 0;
+        gp.rankq_free = 1;
         put(o_geom_peel, &gp, sizeof(F64Geom));
         pl->d_geom_peel = (const F64Geom *)(base + o_geom_peel);
     }
@@ -1393,7 +1350,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         o_pout = ws; ws = align_up(ws + (size_t)Rt * (size_t)pl->m * (size_t)pl->m * sizeof(double), 256);
     }
     size_t o_pbuf = 0, o_xbuf = 0;
-    if (post_levels) {
+    if (build_levels) {
         // pass k reads pass k-1's output (pass 0: the products) and writes the intermediate
         // buffer (even k) or the product buffer (odd k); the last pass writes C
         const size_t blk = (size_t)pl->m * (size_t)pl->m * sizeof(double);
@@ -1402,7 +1359,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             const fmm::LevelPass &a = lpasses[k];
             xblocks = std::max(xblocks, (size_t)a.np * a.qa * a.qb * a.ns);
         }
-        o_pbuf = ws; ws = align_up(ws + (size_t)Rt * blk, 256);
+        if (post_levels) { o_pbuf = ws; ws = align_up(ws + (size_t)Rt * blk, 256); }  // the emulated leaf's: d_pout
         if (xblocks) { o_xbuf = ws; ws = align_up(ws + xblocks * blk, 256); }
     }
     pl->ws_bytes = ws;
@@ -1424,9 +1381,9 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
             pl->d_TB = (double *)(wsb + o_tb);
         }
     }
+    pl->d_xbuf = o_xbuf ? (double *)(wsb + o_xbuf) : nullptr;
     if (post_levels) {
         pl->d_pbuf = (double *)(wsb + o_pbuf);
-        pl->d_xbuf = o_xbuf ? (double *)(wsb + o_xbuf) : nullptr;
         F64Geom gl = g;  // border and core tasks, products stored
         gl.pout = pl->d_pbuf;
         gl.tasks_rankq = 0;
@@ -1449,6 +1406,7 @@ fmm_status_t plan_create(fmm_plan_t **out, int64_t n, const fmm_algo_t *algo, in
         pl->d_sla = (unsigned char *)(wsb + o_sla);
         pl->d_slb = (unsigned char *)(wsb + o_slb);
         pl->d_pout = (double *)(wsb + o_pout);
+        pl->d_pbuf = pl->d_pout;  // the passes read the products from here
         // engine: CTA pairs (one pair per cluster) by default; FMM_OZAKI_ENGINE=tc1 (one CTA per
         // tile) or mma_sync
         const char *eng = std::getenv("FMM_OZAKI_ENGINE");
@@ -1658,6 +1616,22 @@ F64Problem problem_of(const fmm_plan *pl, const double *A, const double *B, doub
 
 namespace {
 
+// The post-addition passes of a plan with stored leaf products, from its
+// product buffer into C (C = alpha sum + beta C in the last pass).
+fmm_status_t run_level_passes(const fmm_plan *pl, double *C, double alpha, double beta, cudaStream_t st) {
+    const size_t npass = pl->level_passes.size();
+    for (size_t k = 0; k < npass; ++k) {
+        fmm::LevelPass a = pl->level_passes[k];
+        a.in = k == 0 ? pl->d_pbuf : (k % 2 == 1 ? pl->d_xbuf : pl->d_pbuf);
+        a.out = a.last ? C : (k % 2 == 0 ? pl->d_xbuf : pl->d_pbuf);
+        a.ldc = pl->n;
+        a.alpha = a.last ? alpha * pl->wscale : 1.0;
+        a.beta = a.last ? beta : 0.0;
+        if (fmm::launch_level_pass(a, st) != cudaSuccess) return FMM_ERR_CUDA;
+    }
+    return FMM_OK;
+}
+
 // Emulated leaf: FP64 pre-additions, exponents and slices of every S_r / T_r,
 // the slice GEMM with fused post-additions, then the FP64 peel tasks.
 fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, double *C, double alpha, double beta,
@@ -1720,16 +1694,13 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
     }
     if (pl->ev[2] && cudaEventRecord(pl->ev[2], st) != cudaSuccess) return FMM_ERR_CUDA;
     if (pl->oz_engine >= 1) {
-        const cudaError_t e =
-            pl->post_two_steps
-                ? fmm::launch_ozaki_postadd_two_steps(pl->d_pout, m, pl->R, pl->R, pl->d_wi_ptr, pl->d_wi_ent,
-                                                      pl->d_wo_ptr, pl->d_wo_ent, C, pl->n, pl->d_chain,
-                                                      pl->geom.w_row_nnz, pl->tiles_m * pl->tiles_n,
-                                                      alpha * pl->wscale, beta, pl->post_unit_inner, st)
-                : fmm::launch_ozaki_postadd(pl->d_pout, m, (int)pl->P, pl->d_wl_ptr, pl->d_wl_ent, C, pl->n,
-                                            pl->d_chain, pl->geom.w_row_nnz, pl->tiles_m * pl->tiles_n,
-                                            alpha * pl->wscale, beta, st);
-        if (e != cudaSuccess) return FMM_ERR_CUDA;
+        if (pl->oz_levels) {
+            if (run_level_passes(pl, C, alpha, beta, st) != FMM_OK) return FMM_ERR_CUDA;
+        } else if (fmm::launch_ozaki_postadd(pl->d_pout, m, (int)pl->P, pl->d_wl_ptr, pl->d_wl_ent, C, pl->n,
+                                             pl->d_chain, pl->geom.w_row_nnz, pl->tiles_m * pl->tiles_n,
+                                             alpha * pl->wscale, beta, st) != cudaSuccess) {
+            return FMM_ERR_CUDA;
+        }
     }
     if (pl->ev[5] && cudaEventRecord(pl->ev[5], st) != cudaSuccess) return FMM_ERR_CUDA;
     const long long peel = pl->geom.tasks_right + pl->geom.tasks_bottom + pl->geom.tasks_rankq;
@@ -1753,22 +1724,6 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
         L.probs[0].beta = beta;
         const int g2 = (int)std::min<long long>(peel, (long long)pl->sms * fmm::f64_kernel_ctas_per_sm(pl->bn));
         if (fmm::launch_f64_single(L, g2 < 1 ? 1 : g2, st, pl->bn) != cudaSuccess) return FMM_ERR_CUDA;
-    }
-    return FMM_OK;
-}
-
-// The post-addition passes of a plan with stored leaf products, from its
-// product buffer into C (C = alpha sum + beta C in the last pass).
-fmm_status_t run_level_passes(const fmm_plan *pl, double *C, double alpha, double beta, cudaStream_t st) {
-    const size_t npass = pl->level_passes.size();
-    for (size_t k = 0; k < npass; ++k) {
-        fmm::LevelPass a = pl->level_passes[k];
-        a.in = k == 0 ? pl->d_pbuf : (k % 2 == 1 ? pl->d_xbuf : pl->d_pbuf);
-        a.out = a.last ? C : (k % 2 == 0 ? pl->d_xbuf : pl->d_pbuf);
-        a.ldc = pl->n;
-        a.alpha = a.last ? alpha * pl->wscale : 1.0;
-        a.beta = a.last ? beta : 0.0;
-        if (fmm::launch_level_pass(a, st) != cudaSuccess) return FMM_ERR_CUDA;
     }
     return FMM_OK;
 }
@@ -2349,7 +2304,7 @@ extern "C" fmm_status_t fmm_plan_get_info(const fmm_plan_t *pl, fmm_plan_info_t 
     info->coef_scale = pl->wscale;
     info->product_begin = pl->sub_begin * pl->R_src;
     info->product_end = pl->sub_end * pl->R_src;
-    info->post_passes = pl->post_levels ? (int)pl->level_passes.size() : 0;
+    info->post_passes = pl->post_levels || pl->oz_levels ? (int)pl->level_passes.size() : 0;
     info->materialize_passes = 0;
     for (const fmm_plan::MatStep &ms : pl->mat_steps) info->materialize_passes += ms.with_next ? 0 : 1;
     return FMM_OK;

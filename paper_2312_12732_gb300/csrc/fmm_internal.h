@@ -161,17 +161,8 @@ int ozaki_tc_max_pairs();
 cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
                                  double *C, long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
                                  double alpha, double beta, cudaStream_t s);
-// The same for a two-level plan of a 2 x 2 algorithm (P = 4), level by level:
-// inner W rows (wi_ptr[0..4], entries {r2, coefficient as a double's low and
-// high word, 0}), outer W columns (wo_ptr[0..R1], entries {l1, coefficient,
-// first term of row l1, 0}); R1, R2 <= 8 and every row of both nonempty.
-// unit_inner: every inner coefficient is +-1.
-cudaError_t launch_ozaki_postadd_two_steps(const double *pout, long long m, int R1, int R2, const int *wi_ptr,
-                                           const int4 *wi_ent, const int *wo_ptr, const int4 *wo_ent, double *C,
-                                           long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
-                                           double alpha, double beta, bool unit_inner, cudaStream_t s);
-// One pass of level-by-level post-additions of an FP64 plan whose leaf
-// products are stored (fmm_postadd.cu).  The products are indexed by the
+// One pass of level-by-level post-additions of a plan whose leaf products
+// are stored (fmm_postadd.cu).  The products are indexed by the
 // digits (r_1, ..., r_K) of the Kronecker factors of W over all recursion
 // levels, outermost first, and C blocks by (q_1, ..., q_K), q_k = i_k p_k +
 // j_k.  A pass sums the innermost factor not yet summed (or the two innermost

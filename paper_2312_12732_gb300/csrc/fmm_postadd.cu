@@ -1,14 +1,15 @@
-// Post-additions of the emulated leaf (Section 2, equation `strassen`):
-// C_l = alpha sum_r W[l][r] P_r + beta C_l for every C block l, from the leaf
-// products P_r that the tcgen05 slice GEMM stores in full.  Two forms: the
-// flattened sums below, and the level-by-level sums further down for two
-// levels of a 2 x 2 algorithm.  In the flattened form the terms of a
-// block are taken in ascending r with the operation sequence of ordered
-// read-modify-writes (first term w P, or beta C and then every term; then
-// o + P, o - P or fma(w, P, o)), so the result is the one a fused epilogue
-// gives.  blockIdx.y is the block, CTAs stride over its rows, threads over
-// column pairs.  Bound by the FP64 adds (nnz(W) - P^2 per element of a block)
-// and the P_r reads.
+// Post-additions from stored leaf products (Section 2, equation `strassen`):
+// C_l = alpha sum_r W[l][r] P_r + beta C_l for every C block l.  Two forms:
+//   * the flattened sums of the emulated leaf (depth 1, or on request): the
+//     terms of a block are taken in ascending r with the operation sequence of
+//     ordered read-modify-writes (first term w P, or beta C and then every
+//     term; then o + P, o - P or fma(w, P, o)), so the result is the one a
+//     fused epilogue gives.  blockIdx.y is the block, CTAs stride over its
+//     rows, threads over column pairs.  Bound by the FP64 adds (nnz(W) - P^2
+//     per element of a block) and the P_r reads;
+//   * the level-by-level passes further down, which sum W's Kronecker factors
+//     from the leaf upwards (FP64 plans that store their products, and the
+//     emulated leaf from depth 2).
 #include <cuda_runtime.h>
 
 #include "fmm_device.cuh"
@@ -127,96 +128,11 @@ __global__ void __launch_bounds__(256) ozaki_postadd_kernel(const double *__rest
     }
 }
 
-// Post-additions of a two-level plan of a 2 x 2 algorithm, taken level by
-// level as the recursion defines them (Section 2, equation `eq:recursion`):
-// for each outer product r1 its inner products P_{r1 R2 + r2} form the four
-// blocks of that product, U_q = sum_{r2} Wi[q][r2] P_{r1 R2 + r2} (ascending
-// r2), which are then added into the C blocks, C_(l1, q) = alpha sum_{r1}
-// Wo[l1][r1] U_q + beta C (ascending r1).  Each P_r entry is read once (the
-// flattened form reads it once per C block that uses it) and the sums take
-// (nnz(Wi) - 4) R1 + 4 (nnz(Wo) - 4) fma per position instead of
-// 16 (nnz(Wi) nnz(Wo) / 16 - 1).  C block (l1, q) is block row 2 i1 + i2,
-// column 2 j1 + j2 of the 4 x 4 grid (l1 = 2 i1 + j1, q = 2 i2 + j2).
-// Each thread keeps its products and its 16 running sums in its own column of
-// shared memory, indexed by the tables.  Tables: rows q of Wi as {r2, low
-// word, high word of the coefficient as a double, 0}; columns r1 of Wo as
-// {l1, coefficient, 1 if this is the first term of row l1, 0}.
-// UNIT: every coefficient of Wi is +-1, so the first term of an inner sum is
-// a sign flip (integer pipe) instead of a multiply.
-constexpr int kTwoStepThreads = 128;
-constexpr int kTwoStepMaxR = 8;
+// Sign of a coefficient applied to v on the integer pipe (hi_word: the high
+// word of the coefficient as a double; used where the coefficient is +-1).
 __device__ __forceinline__ double times_unit(double v, int hi_word) {
     const unsigned long long sign = (unsigned long long)((unsigned)hi_word & 0x80000000u) << 32;
     return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(v) ^ sign));
-}
-template <bool UNIT>
-__global__ void __launch_bounds__(kTwoStepThreads)
-    ozaki_postadd_two_steps_kernel(const double *__restrict__ pout, long long m, int R1, int R2,
-                                   const int *__restrict__ wi_ptr, const int4 *__restrict__ wi_ent,
-                                   const int *__restrict__ wo_ptr, const int4 *__restrict__ wo_ent,
-                                   double *__restrict__ C, long long ldc, unsigned *chain,
-                                   const int *__restrict__ w_row_nnz, int tiles, double alpha, double beta) {
-    __shared__ double ps[kTwoStepMaxR][kTwoStepThreads];
-    __shared__ double cs[16][kTwoStepThreads];
-    __shared__ double sw[4 * kTwoStepMaxR];  // alpha * Wo coefficients, in wo_ent order
-    const int tid = threadIdx.x;
-    if (chain != nullptr && blockIdx.x == 0)
-        for (int t = tid; t < 16 * tiles; t += blockDim.x) chain[t] = (unsigned)w_row_nnz[t / tiles];
-    for (int k = tid; k < wo_ptr[R1]; k += blockDim.x) sw[k] = alpha * (double)wo_ent[k].y;
-    __syncthreads();
-    const long long mm = m * m;
-    const bool from_c = beta != 0.0;
-    for (dev::PosWalk w(m, mm); w.c < 1; w.next()) {
-        const long long y = w.y, x = w.x, pos = y * m + x;
-        auto cptr = [&](int l1, int q) {
-            return C + ((long long)(2 * (l1 >> 1) + (q >> 1)) * m + y) * ldc +
-                   (long long)(2 * (l1 & 1) + (q & 1)) * m + x;
-        };
-        if (from_c) {
-#pragma unroll
-            for (int l = 0; l < 16; ++l) {
-                const double c = __ldcg(cptr(l >> 2, l & 3));
-                cs[l][tid] = beta == 1.0 ? c : beta * c;
-            }
-        }
-        for (int r1 = 0; r1 < R1; ++r1) {
-            const double *pr = pout + (long long)r1 * R2 * mm + pos;
-#pragma unroll
-            for (int r2 = 0; r2 < kTwoStepMaxR; ++r2)
-                if (r2 < R2) ps[r2][tid] = __ldg(pr + (long long)r2 * mm);
-            double u[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int e0 = wi_ptr[q], e1 = wi_ptr[q + 1];
-                const int4 f = wi_ent[e0];  // every row of Wi has a term (checked on the host)
-                u[q] = UNIT ? times_unit(ps[f.x][tid], f.z) : __hiloint2double(f.z, f.y) * ps[f.x][tid];
-                for (int k = e0 + 1; k < e1; ++k) {
-                    const int4 en = wi_ent[k];
-                    u[q] = fma(__hiloint2double(en.z, en.y), ps[en.x][tid], u[q]);
-                }
-            }
-            for (int k = wo_ptr[r1]; k < wo_ptr[r1 + 1]; ++k) {
-                const int4 en = wo_ent[k];
-                const double wk = sw[k];
-                const int l1 = en.x;
-                if (en.z && !from_c) {  // the first term of row l1 (a uniform branch: the table decides)
-                    if (wk == 1.0 || wk == -1.0) {
-                        const int hi = __double2hiint(wk);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) cs[4 * l1 + q][tid] = times_unit(u[q], hi);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) cs[4 * l1 + q][tid] = wk * u[q];
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) cs[4 * l1 + q][tid] = fma(wk, u[q], cs[4 * l1 + q][tid]);
-                }
-            }
-        }
-#pragma unroll
-        for (int l = 0; l < 16; ++l) *cptr(l >> 2, l & 3) = cs[l][tid];
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -233,6 +149,7 @@ __global__ void __launch_bounds__(kTwoStepThreads)
 // operations (about 0.5 T/s) or by the block reads and writes.
 constexpr int kLevelThreads = 128;
 constexpr int kLevelMaxChunk = 8 * kLevelThreads;
+constexpr int kLevelMaxR = 8;  // products of each factor of a pair pass
 constexpr int kLevelLoads = 8;  // products whose loads are in flight together (single-factor pass)
 
 __device__ __forceinline__ double coef_of(int lo, int hi) { return __hiloint2double(hi, lo); }
@@ -307,7 +224,7 @@ __global__ void __launch_bounds__(kLevelThreads) level_single_kernel(const __gri
 
 template <bool UNIT>
 __global__ void __launch_bounds__(kLevelThreads) level_pair_kernel(const __grid_constant__ LevelPass a) {
-    __shared__ double ps[kTwoStepMaxR][kLevelThreads];
+    __shared__ double ps[kLevelMaxR][kLevelThreads];
     __shared__ double cs[16][kLevelThreads];
     const int tid = threadIdx.x;
     const long long chunks = (a.mm + a.chunk - 1) / a.chunk;
@@ -323,7 +240,7 @@ __global__ void __launch_bounds__(kLevelThreads) level_pair_kernel(const __grid_
             for (int ra = 0; ra < a.ra; ++ra) {
                 const double *pr = in + (long long)ra * a.rb * istride + w.pos;
 #pragma unroll
-                for (int rb = 0; rb < kTwoStepMaxR; ++rb)
+                for (int rb = 0; rb < kLevelMaxR; ++rb)
                     if (rb < a.rb) ps[rb][tid] = __ldcs(pr + (long long)rb * istride);
                 double ub[4];
 #pragma unroll
@@ -384,39 +301,12 @@ cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const i
     return cudaSuccess;
 }
 
-cudaError_t launch_ozaki_postadd_two_steps(const double *pout, long long m, int R1, int R2, const int *wi_ptr,
-                                           const int4 *wi_ent, const int *wo_ptr, const int4 *wo_ent, double *C,
-                                           long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
-                                           double alpha, double beta, bool unit_inner, cudaStream_t s) {
-    if (m <= 0) return cudaSuccess;
-    if (R1 < 1 || R1 > kTwoStepMaxR || R2 < 1 || R2 > kTwoStepMaxR) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ozaki_postadd_two_steps_kernel<true>, kTwoStepThreads,
-                                                      0) != cudaSuccess ||
-        occ < 1) {
-        cudaGetLastError();
-        occ = 1;
-    }
-    const long long need = (m * m + kTwoStepThreads - 1) / kTwoStepThreads;
-    const long long slots = (long long)(sms > 0 ? sms : 1) * occ;
-    const unsigned grid = (unsigned)(need < slots ? need : slots);
-    if (unit_inner)
-        ozaki_postadd_two_steps_kernel<true><<<grid, kTwoStepThreads, 0, s>>>(
-            pout, m, R1, R2, wi_ptr, wi_ent, wo_ptr, wo_ent, C, ldc, chain, w_row_nnz, tiles, alpha, beta);
-    else
-        ozaki_postadd_two_steps_kernel<false><<<grid, kTwoStepThreads, 0, s>>>(
-            pout, m, R1, R2, wi_ptr, wi_ent, wo_ptr, wo_ent, C, ldc, chain, w_row_nnz, tiles, alpha, beta);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_level_pass(const LevelPass &a0, cudaStream_t s) {
     if (a0.mm <= 0 || a0.np <= 0 || a0.ns <= 0) return cudaSuccess;
     LevelPass a = a0;
     a.store = a.beta != 0.0 ? (a.beta == 1.0 ? 3 : 4) : (a.alpha == 1.0 ? 1 : 2);
     const bool pair = a.ra > 1;
-    if (pair ? (a.qa != 4 || a.qb != 4 || a.ra > kTwoStepMaxR || a.rb > kTwoStepMaxR || a.rb < 1)
+    if (pair ? (a.qa != 4 || a.qb != 4 || a.ra > kLevelMaxR || a.rb > kLevelMaxR || a.rb < 1)
              : (a.qb < 1 || a.qb > kLevelMaxQ || a.rb < 1))
         return cudaErrorInvalidValue;
     int dev = 0, sms = 0, occ = 0;

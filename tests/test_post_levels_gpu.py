@@ -217,3 +217,27 @@ def test_stored_plans_in_a_batched_launch(fmm, oracle_mod):
     assert fmm.fmm_sync_status(plans[0]) == 0
     for (A, B, C0), C, al, be in zip(host, C0s, alphas, betas):
         assert np.array_equal(C.cpu().numpy(), oracle_mod.axpby(al, oracle_mod.classic(A, B), be, C0))
+
+
+@pytest.mark.parametrize("n,depth,passes", [(1030, 2, 1), (1027, 3, 2), (2048, 3, 2)])
+def test_emulated_leaf_sums_by_the_same_passes(fmm, oracle_mod, monkeypatch, n, depth, passes):
+    """The emulated leaf stores its products and, from depth 2, sums them by the level passes (the
+    flattened order with FMM_OZAKI_POSTADD=flat): bit-exact on integers with and without alpha and beta,
+    also at peeled sizes, whose rank-q fix-ups run after the passes."""
+    algo = fmm.fmm_algo_builtin("strassen")
+    monkeypatch.delenv("FMM_OZAKI_POSTADD", raising=False)
+    level = fmm.fmm_plan_create(n, algo, depth, dtype="f64_ozaki")
+    monkeypatch.setenv("FMM_OZAKI_POSTADD", "flat")
+    flat = fmm.fmm_plan_create(n, algo, depth, dtype="f64_ozaki")
+    monkeypatch.delenv("FMM_OZAKI_POSTADD")
+    assert level.info()["post_passes"] == passes and flat.info()["post_passes"] == 0
+    A, B = inputs.operands(n, "integer", seed=n + depth)
+    C0 = inputs.matrix(n, "integer", seed=n + 3)
+    AB = oracle_mod.classic(A, B)
+    for alpha, beta in [(1.0, 0.0), (-2.0, 3.0), (0.5, 1.0)]:
+        for plan in (level, flat):
+            assert np.array_equal(run(fmm, plan, A, B, alpha, beta, C0), oracle_mod.axpby(alpha, AB, beta, C0))
+    A, B = inputs.operands(n, "uniform", seed=n + 5)
+    ref = oracle_mod.bilinear(A, B, algo.p, algo.U, algo.V, algo.W, depth)
+    assert nerr(run(fmm, level, A, B), ref, A, B) <= tol(depth)
+    assert nerr(run(fmm, flat, A, B), ref, A, B) <= tol(depth)
