@@ -65,6 +65,7 @@ def parse_args(argv=None):
     ap.add_argument("--batched", action="store_true",
                     help="batched workload: 256 products, n log-uniform in [128, 4096], one captured graph")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-max-depth", type=int, default=4, help="batched workload: deepest depth the tuner tries")
     ap.add_argument("--no-emulated", action="store_true",
                     help="skip the emulated-FP64 (Ozaki, Strassen depth 2) measurement added to the JSON line")
     ap.add_argument("--no-batched", action="store_true",
@@ -534,7 +535,8 @@ def run_sweep(a):
     return 0
 
 
-def batched_measurement(torch, fmm, dev, count: int, steps: int, warmup: int, tune_reps: int = 5):
+def batched_measurement(torch, fmm, dev, count: int, steps: int, warmup: int, tune_reps: int = 5,
+                        max_depth: int = 3):
     """The batched workload: `count` products with n_i log-uniform in [128, 4096] (SplitMix64 seed 3),
     entries uniform[-1, 1] (seeded on the device), each planned with its bucket's autotuned (algorithm,
     depth, leaf tile, schedule), all of them run by one CUDA graph (per-plan counter resets and
@@ -546,8 +548,8 @@ def batched_measurement(torch, fmm, dev, count: int, steps: int, warmup: int, tu
 
     sizes = inputs.batch_sizes(count, 128, 4096, seed=3)
     t0 = time.perf_counter()
-    plans, picks = autotune.plan_batch(sizes, candidates=("strassen", "winograd"), max_depth=3, min_leaf=128,
-                                       reps=tune_reps)
+    plans, picks = autotune.plan_batch(sizes, candidates=("strassen", "winograd"), max_depth=max_depth,
+                                       min_leaf=128, reps=tune_reps)
     tune_s = time.perf_counter() - t0
     gen = torch.Generator(device=dev)
     gen.manual_seed(1000)
@@ -622,7 +624,7 @@ def run_batched(a):
     _build.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    b = batched_measurement(torch, fmm, dev, a.batch_count, a.steps, a.warmup)
+    b = batched_measurement(torch, fmm, dev, a.batch_count, a.steps, a.warmup, max_depth=a.batch_max_depth)
     line = {
         "metric": METRIC, "value": b["value"], "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps,
         "warmup": b["warmup"], "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -843,7 +845,7 @@ def run_ours(a):
     # the batched workload (256 autotuned products of log-uniform size in one CUDA graph), three timed steps
     batched = None
     if a.dtype == "f64" and not a.no_batched and not sharded:
-        batched = batched_measurement(torch, fmm, dev, a.batch_count, 3, 3)
+        batched = batched_measurement(torch, fmm, dev, a.batch_count, 3, 3, max_depth=a.batch_max_depth)
         batched["gpu_launches_note"] = "counted separately from the main step's gpu_launches"
 
     # context only, not on the product path: the vendor FP64 GEMM (cuBLAS DGEMM through torch.matmul)
