@@ -63,24 +63,26 @@ __device__ __forceinline__ int biased_exponent(double x) {
     return (int)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF;
 }
 
-// round(x * 2^(bs - E)) as an integer with |result| < 2^(bs - 1), where every
-// |x| of the row or column is below 2^(E - 1) (integer pipe only).
-__device__ __forceinline__ long long to_fixed(double x, int E, int bs) {
+// With bs = BS: round(x * 2^(bs - E)) as an integer with |result| < 2^(bs - 1), where every
+// |x| of the row or column is below 2^(E - 1) (integer pipe only), halves
+// rounded away from zero.  x = M 2^(ex - 1075) with the 53-bit significand M,
+// so the value is M 2^sh with sh = ex - 1075 + bs - E; since ex <= E + 1021,
+// sh <= bs - 54 = K.  With M pre-shifted by K (M 2^K < 2^59 for bs <= 60) one
+// rounding right shift by d = K - sh >= 0 covers both signs of sh without a
+// branch: for sh >= 0 the added half-unit lies below the shifted-out zeros.
+template <int BS>
+__device__ __forceinline__ long long to_fixed(double x, int E) {
+    constexpr int K = BS > 54 ? BS - 54 : 0;
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    int ex = (int)(b >> 52) & 0x7FF;
-    long long M = (long long)(b & 0xFFFFFFFFFFFFFULL);
-    if (ex == 0)
-        ex = 1;
-    else
-        M |= 1LL << 52;
-    const int sh = ex - 1075 + bs - E;
-    long long Y;
-    if (sh >= 0)
-        Y = M << sh;
-    else if (sh > -63)
-        Y = (M + (1LL << (-sh - 1))) >> (-sh);
-    else
-        Y = 0;
+    const int ex0 = (int)(b >> 52) & 0x7FF;
+    const int ex = ex0 > 0 ? ex0 : 1;
+    const long long M = (long long)(b & 0xFFFFFFFFFFFFFULL) | (ex0 > 0 ? 1LL << 52 : 0LL);
+    int d = K - (ex - 1075 + BS - E);
+    d = d < 63 ? d : 63;
+    // unsigned: the half-unit 2^(d - 1) reaches 2^62 (d = 63 for elements 57 binades or more below the
+    // line's largest), and the sum stays below 2^63
+    const unsigned long long half = (1ULL << d) >> 1;
+    const long long Y = (long long)((((unsigned long long)M << K) + half) >> d);
     return (b >> 63) ? -Y : Y;
 }
 
@@ -89,24 +91,43 @@ __device__ __forceinline__ long long to_fixed(double x, int E, int bs) {
 // digits are z_t - 16, so each digit is a shift and a mask.
 __device__ __forceinline__ long long digit_offset(int s) { return ((1LL << (OB * s)) - 1) / 31 * 16; }
 
-// Field t of Z (most significant first), a value in [0, 32].
-template <int S>
-__device__ __forceinline__ unsigned digit_field(long long Z, int t) {
-    const int sh = OB * (S - 1 - t);
-    return t == 0 ? (unsigned)(Z >> sh) : (unsigned)((Z >> sh) & 31);
+// Field t of Z (most significant first) is (Z >> 5 (S - 1 - t)) & 31, a
+// value in [0, 32] (the top field may be 32).
+// The binary16 pair (0x6400 | f0, 0x6400 | f1) of field t of z0 and z1 as
+// one 32-bit word, built in place: z0's field shifted down to bit 0, z1's to
+// bit 16, both masked and the constant halves set with bitwise operations
+// only (no per-field assembly of the pair).  The top field (t = 0) takes six
+// bits: its value is at most 32.
+template <int S, int T>
+__device__ __forceinline__ unsigned half2_fields(long long z0, long long z1) {
+    constexpr int sh = OB * (S - 1 - T);
+    constexpr unsigned mask = T == 0 ? 0x3Fu : 0x1Fu;
+    const unsigned a = (unsigned)(z0 >> sh);
+    const unsigned b = sh >= 16 ? (unsigned)(z1 >> (sh >= 16 ? sh - 16 : 0))
+                                : (unsigned)((unsigned long long)z1 << (sh >= 16 ? 0 : 16 - sh));
+    return (a & mask) | (b & (mask << 16)) | 0x64006400u;
 }
 
 // The e4m3 bytes of two balanced digits f0 - 16, f1 - 16 (f in [0, 32]), f0's
-// in the low byte: the binary16 pattern 0x6400 | f is 1024 + f, subtracting
-// 1040 leaves f - 16 exactly, and the hardware conversion of a binary16 pair
-// to an e4m3 pair is exact for these integers.  Two digits per conversion and
-// no table lookup.
-__device__ __forceinline__ unsigned e4m3x2_of_fields(unsigned f0, unsigned f1) {
+// in the low byte, from their binary16 pair w = (0x6400 | f0, 0x6400 | f1):
+// the pattern 0x6400 | f is 1024 + f, subtracting 1040 leaves f - 16 exactly,
+// and the hardware conversion of a binary16 pair to an e4m3 pair is exact for
+// these integers.  Two digits per conversion and no table lookup.
+__device__ __forceinline__ unsigned e4m3x2_of_half2(unsigned w) {
     __half2_raw h;
-    h.x = (unsigned short)(0x6400u | f0);
-    h.y = (unsigned short)(0x6400u | f1);
+    h.x = (unsigned short)(w & 0xFFFFu);
+    h.y = (unsigned short)(w >> 16);
     const __half2 d = __hsub2(__half2(h), __float2half2_rn(1040.0f));
     return (unsigned)__nv_cvt_halfraw2_to_fp8x2(__half2_raw(d), __NV_SATFINITE, __NV_E4M3);
+}
+
+template <int S, int T>
+__device__ __forceinline__ void pack_digit4(const long long (&Z)[4], unsigned (&packed)[kOzMaxSlices]) {
+    if constexpr (T < S) {
+        packed[T] = e4m3x2_of_half2(half2_fields<S, T>(Z[0], Z[1])) |
+                    (e4m3x2_of_half2(half2_fields<S, T>(Z[2], Z[3])) << 16);
+        pack_digit4<S, T + 1>(Z, packed);
+    }
 }
 
 // Digit t of four elements (Z[q] = the element's fixed-point value plus the
@@ -115,10 +136,7 @@ __device__ __forceinline__ unsigned e4m3x2_of_fields(unsigned f0, unsigned f1) {
 // constant shift.
 template <int S>
 __device__ __forceinline__ void pack_digits4(const long long (&Z)[4], unsigned (&packed)[kOzMaxSlices]) {
-#pragma unroll
-    for (int t = 0; t < S; ++t)
-        packed[t] = e4m3x2_of_fields(digit_field<S>(Z[0], t), digit_field<S>(Z[1], t)) |
-                    (e4m3x2_of_fields(digit_field<S>(Z[2], t), digit_field<S>(Z[3], t)) << 16);
+    pack_digit4<S, 0>(Z, packed);
 }
 
 // ---------------------------------------------------------------------------
@@ -143,7 +161,6 @@ __global__ void slice_rows_kernel(const double *__restrict__ X, long long ld, lo
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int bs = OB * s;
     const long long O = digit_offset(s);
     for (int r = warp; r < rows; r += nwarps) {
         const double *row = Xm + (long long)r * ld;
@@ -161,7 +178,7 @@ __global__ void slice_rows_kernel(const double *__restrict__ X, long long ld, lo
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = c4 * 4 + q;
-                Z[q] = (c < cols ? to_fixed(__ldg(row + c), E, bs) : 0) + O;
+                Z[q] = (c < cols ? to_fixed<OB * S>(__ldg(row + c), E) : 0) + O;
             }
             pack_digits4<S>(Z, packed);
 #pragma unroll
@@ -190,7 +207,6 @@ __global__ void slice_cols_kernel(const double *__restrict__ X, long long ld, lo
     const int c0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int c = c0 + tx;
-    const int bs = OB * s;
     int m = 0;
     if (c < cols)
         for (int k = ty; k < rows; k += 8) m = max(m, biased_exponent(__ldg(Xm + (long long)k * ld + c)));
@@ -213,7 +229,7 @@ __global__ void slice_cols_kernel(const double *__restrict__ X, long long ld, lo
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k = k0 + 4 * ty + q;
-            Z[q] = (c < cols && k < rows ? to_fixed(__ldg(Xm + (long long)k * ld + c), E, bs) : 0) + O;
+            Z[q] = (c < cols && k < rows ? to_fixed<OB * S>(__ldg(Xm + (long long)k * ld + c), E) : 0) + O;
         }
         pack_digits4<S>(Z, packed);
 #pragma unroll
