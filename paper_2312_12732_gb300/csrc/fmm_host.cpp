@@ -1697,7 +1697,6 @@ fmm_status_t gemm_ozaki(const fmm_plan *pl, const double *A, const double *B, do
         if (pl->oz_levels) {
             if (run_level_passes(pl, C, alpha, beta, st) != FMM_OK) return FMM_ERR_CUDA;
         } else if (fmm::launch_ozaki_postadd(pl->d_pout, m, (int)pl->P, pl->d_wl_ptr, pl->d_wl_ent, C, pl->n,
-                                             pl->d_chain, pl->geom.w_row_nnz, pl->tiles_m * pl->tiles_n,
                                              alpha * pl->wscale, beta, st) != cudaSuccess) {
             return FMM_ERR_CUDA;
         }

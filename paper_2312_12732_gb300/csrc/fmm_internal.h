@@ -156,11 +156,9 @@ int ozaki_tc_max_pairs();
 // C_l = alpha sum_r W[l][r] P_r + beta C_l for the P x P blocks of side m of
 // C (leading dimension ldc), in ascending r: wl_ptr / wl_ent list, per block
 // l, the products (r, coefficient) in ascending r.  beta = 0 writes C without
-// reading it.  Also sets the ordering counters of the peel tasks:
-// chain[l * tiles + t] = w_row_nnz[l].
+// reading it.  The peel tasks that follow add into C without ordering waits.
 cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
-                                 double *C, long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
-                                 double alpha, double beta, cudaStream_t s);
+                                 double *C, long long ldc, double alpha, double beta, cudaStream_t s);
 // One pass of level-by-level post-additions of a plan whose leaf products
 // are stored (fmm_postadd.cu).  The products are indexed by the
 // digits (r_1, ..., r_K) of the Kronecker factors of W over all recursion

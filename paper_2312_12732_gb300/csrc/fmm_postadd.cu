@@ -28,17 +28,13 @@ constexpr int kMaxScaledTerms = 1024;  // coefficients of a block kept in shared
 __global__ void __launch_bounds__(256) ozaki_postadd_kernel(const double *__restrict__ pout, long long m, int Pb,
                                                             const int *__restrict__ wl_ptr,
                                                             const int2 *__restrict__ wl_ent, double *__restrict__ C,
-                                                            long long ldc, unsigned *chain,
-                                                            const int *__restrict__ w_row_nnz, int tiles, int l0,
-                                                            double alpha, double beta) {
+                                                            long long ldc, int l0, double alpha, double beta) {
     __shared__ double sw[kMaxScaledTerms];
     __shared__ long long soff[kMaxScaledTerms];
     const int l = l0 + (int)blockIdx.y;
     const long long br = l / Pb, bc = l % Pb;
     const int e0 = wl_ptr[l], e1 = wl_ptr[l + 1];
     const long long mm = m * m;
-    if (chain != nullptr && blockIdx.x == 0)
-        for (int t = threadIdx.x; t < tiles; t += blockDim.x) chain[(long long)l * tiles + t] = (unsigned)w_row_nnz[l];
     for (int t = threadIdx.x; t < e1 - e0 && t < kMaxScaledTerms; t += blockDim.x) {
         const int2 en = wl_ent[e0 + t];  // {product r, coefficient}
         sw[t] = alpha * (double)en.y;
@@ -136,8 +132,8 @@ __device__ __forceinline__ double times_unit(double v, int hi_word) {
 }
 
 // ---------------------------------------------------------------------------
-// Level-by-level post-additions of an FP64 plan with stored leaf products
-// (Section 2, equation `eq:recursion` read from the leaf upwards: the blocks of
+// Level-by-level post-additions of a plan with stored leaf products (FP64
+// leaf or emulated leaf; Section 2, equation `eq:recursion` read from the leaf upwards: the blocks of
 // every product of one level are sums of the products of the level below).
 // One pass sums one Kronecker factor of W (or two 2 x 2 factors) for every
 // (prefix, suffix) group: each thread takes one position of the m x m blocks
@@ -281,8 +277,7 @@ __global__ void __launch_bounds__(kLevelThreads) level_pair_kernel(const __grid_
 }  // namespace
 
 cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const int *wl_ptr, const int2 *wl_ent,
-                                 double *C, long long ldc, unsigned *chain, const int *w_row_nnz, int tiles,
-                                 double alpha, double beta, cudaStream_t s) {
+                                 double *C, long long ldc, double alpha, double beta, cudaStream_t s) {
     if (m <= 0 || P <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -293,8 +288,7 @@ cudaError_t launch_ozaki_postadd(const double *pout, long long m, int P, const i
     for (int l0 = 0; l0 < P * P; l0 += 65535) {
         const int cnt = P * P - l0 < 65535 ? P * P - l0 : 65535;
         dim3 grid((unsigned)bx, (unsigned)cnt);
-        ozaki_postadd_kernel<<<grid, 256, 0, s>>>(pout, m, P, wl_ptr, wl_ent, C, ldc, chain, w_row_nnz, tiles, l0,
-                                                   alpha, beta);
+        ozaki_postadd_kernel<<<grid, 256, 0, s>>>(pout, m, P, wl_ptr, wl_ent, C, ldc, l0, alpha, beta);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
