@@ -96,3 +96,21 @@ def test_materialized_bytes_counts_each_level_once():
     two = 2 * 8 * (n * n + 7 * (n // 2) ** 2 + 7 * (n // 2) ** 2 + 49 * (n // 4) ** 2)
     assert bench.materialized_bytes(n, 2, 49, 2, 2) == two
     assert bench.materialized_bytes(n, 2, 49, 2, 0) == 0.0
+
+
+def test_launch_counts_follow_the_plan_info():
+    """The bench's claimed kernel launches per FP64 call: the leaf kernel, each materialization pass for
+    both operands and, for plans with stored leaf products, their post-addition passes plus one rank-q
+    launch when the size is peeled; the emulated leaf adds slicing, the slice GEMM, its post-additions and
+    the peel launch."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert bench.f64_launches({"materialize_passes": 2, "post_passes": 0}, False) == 5
+    assert bench.f64_launches({"materialize_passes": 2, "post_passes": 0}, True) == 5
+    assert bench.f64_launches({"materialize_passes": 2, "post_passes": 2}, False) == 7
+    assert bench.f64_launches({"materialize_passes": 2, "post_passes": 2}, True) == 8
+    assert bench.f64_launches({"materialize_passes": 0}, False) == 1
+    assert bench.ozaki_launches(1, False) == 6 and bench.ozaki_launches(1, True) == 7
