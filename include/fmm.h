@@ -345,7 +345,8 @@ fmm_status_t fmm_plan_create_ex(fmm_plan_t **out, int64_t n, const fmm_algo_t *a
  * fmm_algo_rational_brent_mismatches rejects), then plans the integer
  * numerator tables as fmm_plan_create_ex does and applies the product of the
  * denominators, (den_u den_v den_w)^-depth, once per leaf product in the
- * post-additions (folded into alpha: w -> alpha * scale * w); the peel fix-ups
+ * post-additions (folded into alpha: w -> alpha * scale * w; with stored leaf
+ * products, alpha * scale once per element of C in the last pass); the peel fix-ups
  * of non-divisible sizes are plain products and are not scaled.  With
  * power-of-two denominators the scale is exact, so integer-valued inputs still
  * give exact results while every intermediate stays below 2^53.  Every call
